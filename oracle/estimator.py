@@ -1,0 +1,146 @@
+"""Multilevel Monte-Carlo estimator of tr(A^{-1}) (Secs. 2 and 4).
+
+Oracle (test infrastructure only): imported by tests, ``__graft_entry__.smoke``
+and the CPU-baseline leg of ``bench.py``; never by the product path.
+
+Per-level difference samples:
+  simplified form (Remark 4.3, needs R_l P_l = I): x in F^{n_l},
+      s = x^* A_l^{-1} x - (R_l x)^* A_{l+1}^{-1} (R_l x)
+  hat form (Eq. tr_ml_dec and the estimator after it): x in F^{n_1},
+      s = (R^_l x)^* A_l^{-1} (R^_l x) - (R^_{l+1} x)^* A_{l+1}^{-1} (R^_{l+1} x)
+      using x^* P^_l = (R^_l x)^* since R = P^*.
+The coarsest term is exact (Remark 4.2): tr(A_L^{-1} R^_L P^_L), which is
+tr(A_L^{-1}) in the simplified form.
+
+Estimate (Sec. 2): sum over levels of the sample means plus the exact term;
+variance sum_l V_l / N_l with V_l the unbiased sample variance of |s - mean|^2
+(complex variance convention of Sec. 3).
+
+Stopping rule (Sec. 5): five full estimates t_1..t_5 (one sample per level
+difference plus the exact term, drawn from the warm-up noise stream) give
+tau = mean(t) - rms(t - mean(t)) (real parts); rho_l = sqrt(w_l) eps |tau| with
+sum w_l = 1 (default w_l = 1/(L-1)); level l draws blocks of `block` samples
+until N_l >= 5 and the standard error sqrt(V_l / N_l) <= rho_l.
+"""
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from .hierarchy import accumulated_prolongation
+from .philox import noise, PURPOSE_NOISE, PURPOSE_WARMUP
+from .solver import exact_solver, dense_inverse
+
+
+class LevelSolvers:
+    """Exact solves y = A_l^{-1} x for every level (sparse LU; dense inverse on the coarsest)."""
+
+    def __init__(self, levels):
+        self.levels = levels
+        self.coarse_inv = dense_inverse(levels[-1].A)
+        self.solvers = [exact_solver(L.A) for L in levels[:-1]]
+
+    def solve(self, l, b):           # l is 0-based
+        if l == len(self.levels) - 1:
+            return self.coarse_inv @ b
+        return self.solvers[l](b)
+
+
+def exact_coarse_trace(levels, form="simplified"):
+    """Remark 4.2: tr(P^_L A_L^{-1} R^_L) = tr(A_L^{-1} R^_L P^_L)."""
+    Ainv = dense_inverse(levels[-1].A)
+    if form == "simplified":
+        return np.trace(Ainv)
+    L = len(levels)
+    Ph = accumulated_prolongation(levels, L)
+    RP = (Ph.conj().T @ Ph).toarray()
+    return np.trace(Ainv @ RP)
+
+
+def sample(levels, solvers, l, x, form="simplified", hats=None):
+    """One difference sample at level l (1-based, l < L) for the noise vector x."""
+    i = l - 1
+    if form == "simplified":
+        y = solvers.solve(i, x)
+        z = levels[i].P.conj().T @ x
+        w = solvers.solve(i + 1, z)
+        return np.vdot(x, y) - np.vdot(z, w)
+    zl = hats[i].conj().T @ x
+    zl1 = hats[i + 1].conj().T @ x
+    return np.vdot(zl, solvers.solve(i, zl)) - np.vdot(zl1, solvers.solve(i + 1, zl1))
+
+
+def noise_length(levels, l, form):
+    return levels[l - 1].n if form == "simplified" else levels[0].n
+
+
+def level_samples(levels, solvers, l, kind, seed, first, count, form="simplified",
+                  purpose=PURPOSE_NOISE, hats=None):
+    """Samples first..first+count-1 of level l (1-based)."""
+    n = noise_length(levels, l, form)
+    out = np.zeros(count, dtype=np.complex128)
+    for j in range(count):
+        x = noise(n, kind, seed, l, first + j, purpose)
+        out[j] = sample(levels, solvers, l, x, form, hats)
+    return out
+
+
+@dataclass
+class Accumulator:
+    n: int = 0
+    values: List[complex] = field(default_factory=list)
+
+    def add(self, s):
+        self.values.extend(list(s))
+        self.n = len(self.values)
+
+    def mean(self):
+        return np.mean(self.values) if self.n else 0.0
+
+    def var(self):
+        if self.n < 2:
+            return np.inf
+        v = np.asarray(self.values)
+        return float(np.sum(np.abs(v - v.mean()) ** 2) / (self.n - 1))
+
+
+@dataclass
+class EstimateResult:
+    trace: complex
+    std_err: float
+    tau: float
+    coarse_term: complex
+    n_samples: List[int]
+    means: List[complex]
+    variances: List[float]
+    warmup: List[complex]
+
+
+def trace_estimate(levels, kind, seed=0, eps=1e-3, weights=None, block=64, min_samples=5,
+                   max_samples=1 << 20, form="simplified", solvers=None):
+    """Sec. 5 procedure; returns an EstimateResult."""
+    L = len(levels)
+    solvers = solvers or LevelSolvers(levels)
+    hats = None
+    if form == "hat":
+        hats = [accumulated_prolongation(levels, l) for l in range(1, L + 1)]
+    TL = exact_coarse_trace(levels, form)
+    # warm-up: five full estimates from the warm-up stream
+    warm = np.zeros(5, dtype=np.complex128) + TL
+    for l in range(1, L):
+        warm += level_samples(levels, solvers, l, kind, seed, 0, 5, form, PURPOSE_WARMUP, hats)
+    tr = warm.real
+    tau = tr.mean() - np.sqrt(np.mean((tr - tr.mean()) ** 2))
+    w = np.full(L - 1, 1.0 / (L - 1)) if weights is None else np.asarray(weights, dtype=float)
+    rho = np.sqrt(w) * eps * abs(tau)
+    acc = [Accumulator() for _ in range(L - 1)]
+    for l in range(1, L):
+        a = acc[l - 1]
+        while a.n < max_samples:
+            a.add(level_samples(levels, solvers, l, kind, seed, a.n, block, form, PURPOSE_NOISE, hats))
+            if a.n >= min_samples and np.sqrt(a.var() / a.n) <= rho[l - 1]:
+                break
+    est = TL + sum(a.mean() for a in acc)
+    se = np.sqrt(sum(a.var() / a.n for a in acc))
+    return EstimateResult(est, se, tau, TL, [a.n for a in acc], [a.mean() for a in acc],
+                          [a.var() for a in acc], list(warm))

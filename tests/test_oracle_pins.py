@@ -1,0 +1,269 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test names the passage it checks.  None of these compares the oracle
+with itself: values come from closed forms, an independent generator
+(numpy.random.Philox), exhaustive enumeration, dense linear algebra or the
+table sizes printed in the paper.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import estimator as E
+from oracle.hierarchy import SetupParams, build_hierarchy, accumulated_prolongation
+from oracle.operators import laplace2d, wilson2d, spin_parity
+from oracle.philox import philox4x64_10, rademacher, z4, noise_key, PURPOSE_NOISE
+from oracle.solver import Cycle, fgmres, exact_solver, dense_inverse
+from paper_2108_11281_gb300.workloads import gauge_links, pure_gauge_links
+
+
+# ---------------------------------------------------------------- Philox / noise
+def test_philox_matches_numpy_generator():
+    """Philox4x64-10 (Salmon et al. 2011) vs numpy's independent implementation.
+    numpy pre-increments its counter, so its first block is counter c+1."""
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        key = rng.integers(0, 2**63, size=2, dtype=np.uint64)
+        c0 = int(rng.integers(0, 2**40))
+        ref = np.random.Philox(key=key, counter=np.array([c0, 7, 0, 0], dtype=np.uint64)).random_raw(4)
+        ours = philox4x64_10(np.array([[c0 + 1], [7], [0], [0]], dtype=np.uint64), (key[0], key[1]))
+        assert np.array_equal(ours[:, 0], ref)
+
+
+def test_noise_bit_mapping_against_numpy_words():
+    """Rademacher row 256b + 64q + bit uses bit `bit` of word q; Z4 uses 2 bits per row."""
+    seed, level, sample = 11, 3, 42
+    k0, k1 = noise_key(seed, level, PURPOSE_NOISE)
+    x = rademacher(600, seed, level, sample)
+    zc = z4(300, seed, level, sample)
+    for blk in range(3):
+        words = np.random.Philox(key=np.array([k0, k1], dtype=np.uint64),
+                                 counter=np.array([blk - 1, sample, 0, 0] if blk else
+                                                  [2**64 - 1, sample - 1, 0, 0],   # carry into word 1
+                                                  dtype=np.uint64)).random_raw(4)
+        for row in range(256 * blk, min(256 * (blk + 1), 600)):
+            q, b = divmod(row - 256 * blk, 64)
+            bit = (int(words[q]) >> b) & 1
+            assert x[row] == (1.0 if bit == 0 else -1.0)
+        for row in range(128 * blk, min(128 * (blk + 1), 300)):
+            q, b = divmod(row - 128 * blk, 32)
+            v = (int(words[q]) >> (2 * b)) & 3
+            assert zc[row] == [1, 1j, -1, -1j][v]
+
+
+def test_noise_moments():
+    """Eq. P_assumptions: E[x_i] = 0, E[conj(x_i) x_j] = delta_ij (statistical, 4 sigma)."""
+    X = np.stack([rademacher(64, 1, 1, j) for j in range(4000)])
+    assert abs(X.mean()) < 4 / np.sqrt(X.size)
+    C = X.T @ X / len(X)
+    assert np.allclose(np.diag(C), 1.0)
+    assert np.abs(C - np.eye(64)).max() < 5 / np.sqrt(len(X))
+    Z = np.stack([z4(64, 1, 1, j) for j in range(4000)])
+    assert np.allclose(np.abs(Z), 1.0)
+    assert abs(Z.mean()) < 4 / np.sqrt(Z.size)
+    assert abs((Z ** 2).mean()) < 4 / np.sqrt(Z.size)          # E[x^2] = 0 for Z4 (Cor. 3.2)
+
+
+# ---------------------------------------------------------------- operators
+def laplace_trace_inverse_closed_form(N, shift=0.0):
+    """Example 5.1: eigenvalues 4 - 2cos(i pi/(N+1)) - 2cos(j pi/(N+1)) (+ shift)."""
+    c = 2 * np.cos(np.arange(1, N + 1) * np.pi / (N + 1))
+    return float(np.sum(1.0 / (4.0 + shift - c[:, None] - c[None, :])))
+
+
+@pytest.mark.parametrize("N,shift", [(7, 0.0), (16, 0.0), (12, 0.05)])
+def test_laplace_closed_form_trace(N, shift):
+    A = laplace2d(N, N, shift)
+    assert np.isclose(np.trace(np.linalg.inv(A.toarray())), laplace_trace_inverse_closed_form(N, shift),
+                      rtol=1e-12)
+    assert A.nnz == 5 * N * N - 4 * N                 # Table 1 nnz rule (1.96e4 for N = 63)
+
+
+def test_laplace_table1_nnz():
+    assert laplace2d(63, 63).nnz == 19593            # printed 1.96e4
+    assert laplace2d(127, 127).nnz == 80137          # printed 8.01e4
+
+
+def free_wilson_trace(N, m):
+    """Eq. schwinger_coupling with U = 1 in momentum space: M(k) = a I + 2i(sin kx s1 + sin ky s2),
+    a = 4 + m - 2cos kx - 2cos ky; s1, s2 anticommute and square to I, so
+    tr M(k)^{-1} = 2a / (a^2 + 4 sin^2 kx + 4 sin^2 ky)."""
+    k = 2 * np.pi * np.arange(N) / N
+    kx, ky = k[None, :], k[:, None]
+    a = 4 + m - 2 * np.cos(kx) - 2 * np.cos(ky)
+    return float(np.sum(2 * a / (a ** 2 + 4 * np.sin(kx) ** 2 + 4 * np.sin(ky) ** 2)))
+
+
+def test_wilson_free_field_closed_form():
+    N, m = 8, 0.3
+    S = wilson2d(N, N, m, np.ones((2, N, N), dtype=complex)).toarray()
+    assert np.isclose(np.trace(np.linalg.inv(S)), free_wilson_trace(N, m), rtol=1e-12)
+
+
+def test_wilson_gauge_covariance():
+    """Pure-gauge links U_mu(x) = g(x) conj(g(x+mu)) give S' = G S_free G^*."""
+    N, m = 6, 0.2
+    U, g = pure_gauge_links(N, N, 3)
+    S = wilson2d(N, N, m, U).toarray()
+    S0 = wilson2d(N, N, m, np.ones((2, N, N), dtype=complex)).toarray()
+    G = np.diag(np.repeat(g.reshape(-1), 2))
+    assert np.allclose(S, G @ S0 @ G.conj().T, atol=1e-14)
+    assert np.isclose(np.trace(np.linalg.inv(S)), free_wilson_trace(N, m), rtol=1e-11)
+
+
+def test_wilson_table3_nnz_and_symmetry():
+    """Table 3: nnz(S_1) = 2.94e5 at N = 128; Sec. 5: J S = S^* J."""
+    N = 128
+    S = wilson2d(N, N, -0.1, gauge_links(N, N, 0.3, 0))
+    assert S.shape == (2 * N * N, 2 * N * N)
+    assert S.nnz == 9 * 2 * N * N == 294912
+    small = wilson2d(8, 8, -0.1, gauge_links(8, 8, 0.3, 0)).toarray()
+    J = spin_parity(64, 2)
+    assert np.allclose(J[:, None] * small, small.conj().T * J[None, :], atol=1e-15)
+
+
+# ---------------------------------------------------------------- hierarchy
+def wilson_hierarchy(N=16, levels=3, n_tv=(2, 4), agg=4):
+    U = gauge_links(N, N, 0.3, 7)
+    S = wilson2d(N, N, -0.05, U)
+    prm = SetupParams(levels=levels, agg_x=agg, agg_y=agg, n_tv=list(n_tv), spin_split=True,
+                      kind="inverse", sweeps=6,
+                      coarse_sweeps=4, omega=1.0, noise_kind="z4", bootstrap=1)
+    return S, build_hierarchy(S, N, N, 2, prm)
+
+
+def test_hierarchy_orthonormal_galerkin_and_spin_structure():
+    """Sec. 4.1 (A_{l+1} = R A P, R = P^*), Remark 4.3 (R P = I), Example 5.3 (J-symmetry kept)."""
+    S, h = wilson_hierarchy()
+    rng = np.random.default_rng(0)
+    for lv, nxt in zip(h[:-1], h[1:]):
+        P = lv.P
+        assert np.abs((P.conj().T @ P).toarray() - np.eye(P.shape[1])).max() < 1e-13
+        v = rng.normal(size=P.shape[1]) + 1j * rng.normal(size=P.shape[1])
+        assert np.allclose(nxt.A @ v, P.conj().T @ (lv.A @ (P @ v)), atol=1e-12)
+    for lv in h:
+        J = spin_parity(lv.nx * lv.ny, lv.d)
+        Ad = lv.A.toarray()
+        assert np.abs(J[:, None] * Ad - Ad.conj().T * J[None, :]).max() < 1e-12
+    # the exact coarse trace is real because of the J-symmetry
+    assert abs(E.exact_coarse_trace(h).imag) < 1e-10 * abs(E.exact_coarse_trace(h))
+
+
+def test_table3_level_sizes():
+    """Table 3: n_l = 2*128^2, 4*32^2, 8*8^2, 8*2^2 with 4x4 aggregates, 2 then 4 test vectors,
+    doubled by the spin split."""
+    N = 128
+    U = gauge_links(N, N, 0.3, 0)
+    S = wilson2d(N, N, -0.1, U)
+    prm = SetupParams(levels=4, n_tv=[2, 4, 4], spin_split=True, kind="inverse", sweeps=1,
+                      coarse_sweeps=1, omega=1.0, noise_kind="z4", bootstrap=0)
+    h = build_hierarchy(S, N, N, 2, prm)
+    assert [lv.n for lv in h] == [2 * 128 ** 2, 4 * 32 ** 2, 8 * 8 ** 2, 8 * 2 ** 2]
+
+
+def test_piecewise_constant_prolongation_entries():
+    A = laplace2d(16, 16)
+    h = build_hierarchy(A, 16, 16, 1, SetupParams(levels=2, n_tv=1, kind="constant"))
+    assert np.allclose(np.abs(h[0].P.data), 0.25) and h[0].P.nnz == 256
+    # Galerkin operator of the constant aggregation is exact in binary: (1/16) * integer sums
+    assert np.array_equal(h[1].A.toarray() * 16, np.round(h[1].A.toarray() * 16))
+
+
+# ---------------------------------------------------------------- telescoping and Hutchinson
+def dense_level_traces(h):
+    """tr(A_l^{-1}) and tr(P_l A_{l+1}^{-1} R_l) for every level from dense inverses."""
+    inv = [np.linalg.inv(lv.A.toarray()) for lv in h]
+    diffs = [np.trace(inv[i]) - np.trace(h[i].P.toarray() @ inv[i + 1] @ h[i].P.toarray().conj().T)
+             for i in range(len(h) - 1)]
+    return inv, diffs
+
+
+def test_telescoping_identity_simplified_and_hat():
+    """Eq. tr_ml_dec and Remark 4.3: the level differences plus the coarsest term give tr(A^{-1})."""
+    S, h = wilson_hierarchy(N=8, levels=3, n_tv=(2, 2), agg=2)
+    inv, diffs = dense_level_traces(h)
+    total = np.trace(inv[0])
+    assert np.isclose(sum(diffs) + np.trace(inv[-1]), total, rtol=1e-12)
+    L = len(h)
+    hats = [accumulated_prolongation(h, l).toarray() for l in range(1, L + 1)]
+    hat_diffs = [np.trace(hats[i] @ inv[i] @ hats[i].conj().T) -
+                 np.trace(hats[i + 1] @ inv[i + 1] @ hats[i + 1].conj().T) for i in range(L - 1)]
+    assert np.isclose(sum(hat_diffs) + E.exact_coarse_trace(h, "hat"), total, rtol=1e-12)
+    assert np.isclose(E.exact_coarse_trace(h, "hat"), E.exact_coarse_trace(h), rtol=1e-12)
+
+
+def _enumerate_level_samples(h, kind, n):
+    solv = E.LevelSolvers(h)
+    if kind == "rademacher":
+        vecs = itertools.product([1.0, -1.0], repeat=n)
+    else:
+        vecs = itertools.product([1, 1j, -1, -1j], repeat=n)
+    return np.array([E.sample(h, solv, 1, np.array(v, dtype=complex)) for v in vecs])
+
+
+def test_hutchinson_unbiased_and_variance_real_noise():
+    """Thm. 3.1 and Cor. 3.2 by enumerating all 2^n sign vectors: the mean of the
+    level-1 samples is tr(B), B = A_1^{-1} - P A_2^{-1} R, and their variance is
+    (1/2) ||offdiag(B + B^T)||_F^2."""
+    A = laplace2d(4, 2, 0.3)
+    h = build_hierarchy(A, 4, 2, 1, SetupParams(levels=2, agg_x=2, agg_y=2, n_tv=1, kind="constant"))
+    s = _enumerate_level_samples(h, "rademacher", 8)
+    B = np.linalg.inv(A.toarray()) - h[0].P.toarray() @ np.linalg.inv(h[1].A.toarray()) @ h[0].P.toarray().T
+    assert np.isclose(s.mean(), np.trace(B), rtol=1e-12)
+    off = B + B.T
+    np.fill_diagonal(off, 0)
+    assert np.isclose(np.mean(np.abs(s - s.mean()) ** 2), 0.5 * np.sum(off ** 2), rtol=1e-10)
+
+
+def test_hutchinson_unbiased_and_variance_z4_noise():
+    """Same for Z4 noise on a complex Wilson level: variance ||offdiag(B)||_F^2 (Cor. 3.2)."""
+    U = gauge_links(2, 2, 0.5, 4)
+    S = wilson2d(2, 2, 0.4, U)
+    h = build_hierarchy(S, 2, 2, 2, SetupParams(levels=2, agg_x=2, agg_y=2, n_tv=1, spin_split=True,
+                                                kind="inverse", sweeps=2, omega=1.0,
+                                                noise_kind="z4", bootstrap=0))
+    s = _enumerate_level_samples(h, "z4", 8)
+    P = h[0].P.toarray()
+    B = np.linalg.inv(S.toarray()) - P @ np.linalg.inv(h[1].A.toarray()) @ P.conj().T
+    assert np.isclose(s.mean(), np.trace(B), rtol=1e-12)
+    off = B.copy()
+    np.fill_diagonal(off, 0)
+    assert np.isclose(np.mean(np.abs(s - s.mean()) ** 2), np.sum(np.abs(off) ** 2), rtol=1e-10)
+
+
+# ---------------------------------------------------------------- solver and estimator
+@pytest.mark.parametrize("cycle", ["V", "K"])
+def test_fgmres_multigrid_reaches_exact_solve(cycle):
+    A = laplace2d(64, 64)
+    h = build_hierarchy(A, 64, 64, 1, SetupParams(levels=3, n_tv=4, sweeps=20, coarse_sweeps=10))
+    M = Cycle(h, 0, 1, 1, cycle, 2)
+    b = rademacher(A.shape[0], 0, 1, 0)
+    x, its, res = fgmres(A, b, M, tol=1e-11, m=30)
+    assert res <= 1e-11
+    ref = exact_solver(A)(b)
+    assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_wilson_fgmres_multigrid():
+    S, h = wilson_hierarchy(N=16, levels=3, n_tv=(4, 4))
+    M = Cycle(h, 0, 2, 2, "K", 2)
+    b = z4(S.shape[0], 0, 1, 0)
+    x, its, res = fgmres(S, b, M, tol=1e-10, m=30)
+    assert res <= 1e-10
+    assert np.allclose(x, exact_solver(S)(b), rtol=0, atol=1e-7 * np.abs(x).max())
+
+
+def test_small_laplace_estimate_against_closed_form():
+    """64x64 Laplacian, 2 levels, piecewise-constant P: the MLMC estimate is within
+    4 standard errors of the closed-form trace, and the exact coarse term equals the
+    dense tr(A_2^{-1})."""
+    N = 64
+    A = laplace2d(N, N)
+    h = build_hierarchy(A, N, N, 1, SetupParams(levels=2, n_tv=1, kind="constant"))
+    res = E.trace_estimate(h, "rademacher", seed=0, eps=1e-2, block=64)
+    exact = laplace_trace_inverse_closed_form(N)
+    assert abs(res.trace.real - exact) <= 4 * res.std_err
+    assert np.isclose(res.coarse_term, np.trace(np.linalg.inv(h[1].A.toarray())), rtol=1e-12)
+    assert all(n >= 5 for n in res.n_samples)
