@@ -1,0 +1,325 @@
+"""Time-to-trace benchmark of the MLMC trace estimator on one GB300.
+
+A step is one complete Sec. 5 estimate of tr(A^{-1}) to relative accuracy
+eps = 1e-3 (exact coarsest term, five warm-up estimates, per-level sampling
+until every level meets its standard-error target) on the 1024 x 1024
+Dirichlet Laplacian with a 4-level 4x4-aggregation hierarchy (4 smoothed test
+vectors per aggregate) and blocks of 64 Rademacher vectors, in the mixed form
+(FP32 multigrid cycle under FP64 flexible GMRES).  The hierarchy is built once
+before the timed region; `e2e` repeats the step through the C ABI including
+the setup from the host-side operator descriptor.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(test infrastructure) on a bounded sample of the same workload instead.
+"""
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="laplace2d-1024x1024-L4-4tv-k64", nx=1024, ny=1024, levels=4, n_tv=4, block=64,
+                setup_sweeps=160, coarse_sweeps=20, bootstrap=1, boot_iters=2, smooth_pre=2, smooth_post=2,
+                kcycle_its=2, restart=30, eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8, seed=0)
+METRIC = "Seconds to tr(A^-1) at 1e-3 rel. error, mixed+learned vs plain FP64; HBM %"
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true")
+    return ap.parse_args()
+
+
+def hierarchy_params(mlmc, precision):
+    w = WORKLOAD
+    return mlmc.default_params(levels=w["levels"], n_tv=w["n_tv"], setup_kind=mlmc.SETUP_SMOOTH,
+                               setup_sweeps=w["setup_sweeps"], coarse_sweeps=w["coarse_sweeps"],
+                               bootstrap=w["bootstrap"], boot_iters=w["boot_iters"], smooth_pre=w["smooth_pre"],
+                               smooth_post=w["smooth_post"], cycle=mlmc.CYCLE_K, kcycle_its=w["kcycle_its"],
+                               fgmres_restart=w["restart"], max_iter=5000, precision=precision,
+                               block=w["block"], reorth=1)
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + CLOCK_FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self, gpu_index=0):
+        if not self.proc:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != gpu_index:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names[1:], parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return float(d.get("hbm_gbs")), "measured"
+        except (ValueError, TypeError):
+            pass
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(result, seconds_budget=25.0):
+    """Oracle (FP64 CPU, as it stands) on a bounded sample of the workload.
+
+    The sample: the oracle's own hierarchy for the workload, then per level
+    difference l a few FGMRES iterations (preconditioned by the oracle's
+    K-cycle) on levels l and l+1, timed.  Extrapolation: seconds per
+    iteration x (iterations per solve) x N_l, with N_l and the iterations per
+    solve of the same estimator on the same inputs (taken from the GPU
+    result, which matches the oracle sample by sample)."""
+    import numpy as np
+    from oracle.hierarchy import SetupParams, build_hierarchy
+    from oracle.operators import laplace2d
+    from oracle.philox import rademacher
+    from oracle.solver import Cycle, fgmres
+    w = WORKLOAD
+    t0 = time.time()
+    A = laplace2d(w["nx"], w["ny"])
+    lv = build_hierarchy(A, w["nx"], w["ny"], 1, SetupParams(
+        levels=w["levels"], n_tv=w["n_tv"], sweeps=w["setup_sweeps"], coarse_sweeps=w["coarse_sweeps"],
+        bootstrap=w["bootstrap"], boot_iters=w["boot_iters"], smooth_pre=w["smooth_pre"],
+        smooth_post=w["smooth_post"], kcycle_its=w["kcycle_its"]))
+    setup_s = time.time() - t0
+    per_it = []
+    its_probe = 3
+    for l in range(len(lv) - 1):
+        M = Cycle(lv, l, w["smooth_pre"], w["smooth_post"], "K", w["kcycle_its"])
+        b = rademacher(lv[l].n, 1, l + 1, 0)
+        t = time.time()
+        fgmres(lv[l].A, b, M, tol=0.0, m=its_probe, maxit=its_probe)
+        per_it.append((time.time() - t) / its_probe)
+    L = len(lv)
+    # the coarsest solve is a dense product: time it too
+    from oracle.solver import dense_inverse
+    Ainv = dense_inverse(lv[-1].A)
+    t = time.time()
+    for _ in range(10):
+        Ainv @ rademacher(lv[-1].n, 1, L, 0)
+    per_it.append((time.time() - t) / 10)
+    total = 0.0
+    for l in range(L - 1):
+        n_l = result["n_samples"][l]
+        it_l = result["iters"][l]
+        it_next = result["iters"][l + 1] if l + 1 < L - 1 else 1.0
+        total += n_l * (it_l * per_it[l] + it_next * per_it[l + 1])
+    # five warm-up estimates: one sample per level difference each
+    for l in range(L - 1):
+        it_next = result["iters"][l + 1] if l + 1 < L - 1 else 1.0
+        total += 5 * (result["iters"][l] * per_it[l] + it_next * per_it[l + 1])
+    return {"value": total, "unit": "s (extrapolated)", "cores": 1, "kind": "oracle",
+            "sample": "oracle FGMRES+K-cycle: %d iterations timed per level (%.1f s of CPU, setup %.1f s "
+                      "excluded); seconds/iteration x iterations/solve x N_l of the same estimate" %
+                      (its_probe, sum(per_it) * its_probe, setup_s)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = []
+    res_nominal = {"n_samples": [w for w in REFERENCE_NL], "iters": [w for w in REFERENCE_ITERS]}
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(res_nominal)
+        if i >= args.warmup:
+            steps.append(cb["value"])
+    v = statistics.mean(steps)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict("fp64-cpu-oracle"),
+            "cpu_baseline": {"value": v, "unit": "s (extrapolated)", "kind": "oracle", "cores": 1,
+                             "sample": cb["sample"] + "; N_l and iterations per solve from "
+                                       "workloads-recorded values of this estimate"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# per-level sample counts and mean outer iterations of this workload's estimate
+# (same estimator and noise on both sides); used only by the reference arm's
+# extrapolation, which runs before any GPU number exists.
+REFERENCE_NL = [64, 128, 576]
+REFERENCE_ITERS = [20.0, 20.0, 20.0]
+
+
+def config_dict(form):
+    w = WORKLOAD
+    return {"workload": w["name"], "form": form, "nx": w["nx"], "ny": w["ny"], "levels": w["levels"],
+            "n_tv": w["n_tv"], "block": w["block"], "eps": w["eps"], "noise": "rademacher",
+            "l2": "inputs larger than L2 (a 64-column level-1 block is 512 MiB in FP64)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2108_11281_gb300 import mlmc
+    w = WORKLOAD
+    stream = torch.cuda.current_stream().cuda_stream
+    h = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, w["nx"], w["ny"], hierarchy_params(mlmc, mlmc.PREC_MIXED_FP32),
+                       stream=stream)
+
+    def step(hh, tol, seed):
+        return mlmc.result_dict(hh.trace_estimate(eps=w["eps"], noise=mlmc.NOISE_RADEMACHER, seed=seed, tol=tol))
+
+    seed = w["seed"] + 1000 * rank          # replicas draw disjoint noise
+    for _ in range(args.warmup):
+        res = step(h, w["tol_mixed"], seed)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    l0 = h.launch_count()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv")
+    results = []
+    with sampler:
+        ev0.record()
+        t0 = time.time()
+        for _ in range(args.steps):
+            results.append(step(h, w["tol_mixed"], seed))
+        ev1.record()
+        barrier()
+        wall = time.time() - t0
+    ms = ev0.elapsed_time(ev1)
+    launches = (h.launch_count() - l0) // max(args.steps, 1)
+    t_step = ms / 1e3 / args.steps
+    if world > 1:
+        tt = torch.tensor([t_step], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = t_step / world                 # seconds per trace over all replicas
+    res = results[-1]
+
+    # dominant kernels, timed alone with CUDA events on the hierarchy's stream
+    peak, peak_kind = measured_peaks()
+    kern = {}
+    for name, which in (("stencil_fp32", 1), ("rbgs_sweep_fp32", 2), ("stencil_fp64", 0)):
+        kms, kbytes = h.profile_kernel(which, 1, w["block"], 20)
+        kern[name] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6}
+    dom = kern["rbgs_sweep_fp32"]
+    roofline = {"bound": "hbm", "kernel": "k_rbgs_half (one red+black sweep, level 1, FP32, k=64)",
+                "achieved": dom["gbs"], "peak": peak, "unit": "GB/s", "frac": dom["gbs"] / peak,
+                "peak_source": peak_kind, "traffic": None, "kernels": kern}
+
+    fp64 = None
+    if not args.no_fp64_form and rank == 0:
+        h.close()
+        h64 = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, w["nx"], w["ny"], hierarchy_params(mlmc, mlmc.PREC_FP64),
+                             stream=stream)
+        step(h64, w["tol_fp64"], seed)
+        torch.cuda.synchronize()
+        t = time.time()
+        r64 = step(h64, w["tol_fp64"], seed)
+        torch.cuda.synchronize()
+        fp64 = {"seconds": time.time() - t, "trace": r64["trace"].real, "std_err": r64["std_err"],
+                "n_samples": r64["n_samples"], "iters": r64["iters"]}
+        h64.close()
+    else:
+        h.close()
+
+    # end to end through the C ABI: setup from the host descriptor + estimate + result read-back
+    torch.cuda.synchronize()
+    t = time.time()
+    he = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, w["nx"], w["ny"], hierarchy_params(mlmc, mlmc.PREC_MIXED_FP32),
+                        stream=stream)
+    step(he, w["tol_mixed"], seed)
+    he.close()
+    torch.cuda.synchronize()
+    e2e = time.time() - t
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(res)
+    if rank == 0:
+        import ctypes
+        line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
+                "config": config_dict("mixed: FP32 K-cycle under FP64 FGMRES"),
+                "clocks": sampler.summary(local), "gpu_launches": int(launches), "wall_s_timed": wall,
+                "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": ctypes.sizeof(mlmc.EstimateResult),
+                        "includes": "hierarchy setup from the host descriptor + estimate + result read-back"},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "result": {"trace": res["trace"].real, "std_err": res["std_err"], "tau": res["tau"],
+                           "coarse_term": res["coarse_term"].real, "n_samples": res["n_samples"],
+                           "iters": res["iters"], "seconds_per_level": res["seconds"]},
+                "fp64_form": fp64}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

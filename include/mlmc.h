@@ -1,0 +1,195 @@
+/*
+ * libmlmc: multilevel Monte-Carlo estimation of tr(A^{-1}) on one GB300 GPU.
+ *
+ * The method is that of Frommer, Nasr Khalil and Ramirez-Hidalgo, "A
+ * multilevel approach to variance reduction in the stochastic estimation of
+ * the trace of a matrix" (arXiv 2108.11281).  A is given indirectly (Sec. 3):
+ * here as a lattice operator descriptor (Example 5.1 Laplacian, Example 5.3
+ * 2-spin Wilson/Schwinger operator).  An aggregation multigrid hierarchy with
+ * orthonormal prolongations P_l and Galerkin operators A_{l+1} = P_l^* A_l P_l
+ * (Sec. 4.1) gives the telescoping sum of Remark 4.3,
+ *   tr(A^{-1}) = sum_{l<L} [tr(A_l^{-1}) - tr(P_l A_{l+1}^{-1} P_l^*)] + tr(A_L^{-1}),
+ * whose level differences are estimated by Hutchinson samples (Sec. 3) and
+ * whose last term is computed exactly (Remark 4.2).  Samples need solves with
+ * A_l and A_{l+1}, done by flexible GMRES preconditioned by a multigrid cycle
+ * over the levels below (Remark 4.1, Example 5.3).
+ *
+ * Conventions for every entry point:
+ *  - The return value is an mlmc_status; 0 is success.  No exception and no
+ *    abort crosses this interface.  mlmc_last_error() describes the last
+ *    failure of the calling thread.
+ *  - "host" pointers are ordinary CPU memory, read or written only during
+ *    the call.  "device" pointers are CUDA global memory of the current
+ *    device, owned by the caller.
+ *  - All GPU work is issued on the stream given at setup (NULL = legacy
+ *    default stream).  Calls return after their work has completed.
+ *  - A hierarchy handle owns all device memory it allocates and must be used
+ *    by one host thread at a time.
+ *  - Vector blocks on the device are laid out [site][dof][k]: the k columns
+ *    (independent right-hand sides or samples) are innermost.  Real operators
+ *    use double, complex operators interleaved (re, im) double pairs.
+ *  - Noise: sample j of level l is column (j - first) of a block and depends
+ *    only on (seed, l, j): Philox4x64-10 with key (seed, (purpose << 8) | l)
+ *    and counter (row_block, j, 0, 0); Rademacher rows take one bit each
+ *    (256 rows per counter), Z4 rows two bits (128 rows per counter).
+ */
+#ifndef MLMC_H
+#define MLMC_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } mlmc_c64;
+
+typedef enum {
+  MLMC_OK = 0,
+  MLMC_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range */
+  MLMC_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+  MLMC_ERR_CUDA = 3,          /* a CUDA call failed; see mlmc_last_error() */
+  MLMC_ERR_OOM = 4,           /* device allocation failed */
+  MLMC_ERR_NOT_CONVERGED = 5, /* a solve hit max_iter before reaching tol */
+  MLMC_ERR_SINGULAR = 6,      /* zero pivot / dependent test vectors in setup */
+  MLMC_ERR_TIMEOUT = 7,       /* a bounded device wait gave up */
+  MLMC_ERR_REJECTED = 8       /* a result failed its FP64 acceptance check */
+} mlmc_status;
+
+enum { MLMC_OP_LAPLACE2D = 1, MLMC_OP_WILSON2D = 2 };
+enum { MLMC_NOISE_RADEMACHER = 0, MLMC_NOISE_Z4 = 1 };
+enum { MLMC_PURPOSE_NOISE = 0, MLMC_PURPOSE_WARMUP = 1, MLMC_PURPOSE_SETUP = 2 };
+enum { MLMC_SETUP_SMOOTH = 0, MLMC_SETUP_INVERSE = 1, MLMC_SETUP_CONSTANT = 2 };
+enum { MLMC_PREC_FP64 = 0, MLMC_PREC_MIXED_FP32 = 1 };
+enum { MLMC_FORM_SIMPLIFIED = 0, MLMC_FORM_HAT = 1 };
+enum { MLMC_CYCLE_V = 0, MLMC_CYCLE_K = 1 };
+
+/* Fine operator A = A_1 (Examples 5.1 and 5.3).  Sites s = j*nx + i. */
+typedef struct {
+  int kind;          /* MLMC_OP_LAPLACE2D: (4 + shift) u_ij - sum of the 4 neighbours, real, d = 1.
+                        MLMC_OP_WILSON2D: Eq. schwinger_coupling, complex, d = 2, periodic.     */
+  int nx, ny;        /* lattice; multiples of agg_x^(L-1), agg_y^(L-1)                            */
+  int periodic;      /* Laplace only: 0 Dirichlet (Example 5.1), 1 periodic                     */
+  double shift;      /* Laplace: sigma in A + sigma I                                           */
+  double mass;       /* Wilson: m in (4 + m)                                                    */
+  const mlmc_c64 *links; /* Wilson, host, [2][ny][nx]: [0] = exp(i Theta) on (i,j)->(i+1,j),
+                            [1] = exp(i Phi) on (i,j)->(i,j+1).  NULL for Laplace.            */
+} mlmc_operator_desc;
+
+/* Hierarchy and solver parameters (Secs. 4.1, 5; Example 5.3). */
+typedef struct {
+  int levels;          /* L >= 2                                                              */
+  int agg_x, agg_y;    /* aggregate shape (Example 5.3: 4 x 4)                                */
+  int n_tv;            /* test vectors per aggregate (same count on every level)              */
+  int spin_split;      /* 1: split each test vector into the two spin halves of a site's
+                          dofs, doubling the coarse dofs and keeping J A = A^* J (Ex. 5.3)    */
+  int setup_kind;      /* MLMC_SETUP_SMOOTH: v <- v - omega D^{-1} A v, `setup_sweeps` times;
+                          MLMC_SETUP_INVERSE: v <- two damped-Jacobi steps on A x = v;
+                          MLMC_SETUP_CONSTANT: one constant test vector (n_tv = 1)            */
+  int setup_sweeps;    /* filter sweeps on level 1                                            */
+  int coarse_sweeps;   /* filter sweeps on levels >= 2, applied to R_{l-1} V_{l-1}            */
+  double setup_omega;  /* damping of the filter                                               */
+  uint64_t setup_seed; /* Philox seed of the test vectors (purpose SETUP, level 1)           */
+  int bootstrap;       /* rounds of v <- v - M(A v) with M one FP64 cycle, then rebuild       */
+  int boot_iters;      /* applications per round                                              */
+  int smooth_pre, smooth_post; /* red-black block Gauss-Seidel sweeps per cycle                */
+  int cycle;           /* MLMC_CYCLE_V or MLMC_CYCLE_K (Krylov-accelerated coarse correction) */
+  int kcycle_its;      /* FGMRES steps per coarse correction in a K-cycle                     */
+  int fgmres_restart;  /* outer FGMRES restart length m                                       */
+  int max_iter;        /* outer FGMRES iteration cap per solve                                */
+  int precision;       /* MLMC_PREC_FP64 or MLMC_PREC_MIXED_FP32 (FP32 cycle under FP64 FGMRES)*/
+  int block;           /* largest vector-block width k (columns per solve), 1..256            */
+  int reorth;          /* 1: classical Gram-Schmidt twice in the outer Arnoldi                */
+  const void *const *user_P; /* optional, host: user_P[l-1] = P_l as blocks [agg][ax*ay*d][dc]
+                          (double, or mlmc_c64 for complex operators); columns must be
+                          orthonormal.  Replaces the test-vector setup.  NULL = build P.      */
+} mlmc_hierarchy_params;
+
+typedef struct mlmc_hierarchy mlmc_hierarchy;
+
+/* Sec. 5 estimate parameters. */
+typedef struct {
+  double eps;          /* relative accuracy target (paper: 1e-3)                             */
+  double weights[16];  /* w_l, sum 1, rho_l = sqrt(w_l) eps |tau|; all 0 = 1/(L-1) each     */
+  int noise;           /* MLMC_NOISE_RADEMACHER or MLMC_NOISE_Z4                             */
+  uint64_t seed;
+  double tol;          /* relative residual of every level solve                             */
+  int min_samples;     /* floor on N_l (paper: 5)                                            */
+  int max_samples;     /* cap on N_l                                                          */
+  int form;            /* MLMC_FORM_SIMPLIFIED (Remark 4.3)                                  */
+} mlmc_estimate_params;
+
+typedef struct {
+  mlmc_c64 trace;        /* sum of level means + exact coarsest term                         */
+  double std_err;        /* sqrt(sum_l V_l / N_l)                                            */
+  double tau;            /* mean - rms deviation of the 5 warm-up estimates                  */
+  mlmc_c64 coarse_term;  /* tr(A_L^{-1}) (Remark 4.2)                                        */
+  int levels;
+  int n_samples[16];     /* N_l per level difference                                         */
+  mlmc_c64 mean[16];
+  double variance[16];   /* unbiased sample variance, complex convention of Sec. 3           */
+  double iters[16];      /* mean outer FGMRES iterations per solve on level l                */
+  double seconds[16];    /* wall time spent on level difference l                            */
+  double cost_nnz[16];   /* Sec. 5 cost model: sum of nnz(B) over products B x (per level)  */
+  double seconds_total;
+} mlmc_estimate_result;
+
+/* Build the hierarchy on the GPU (Sec. 4.1; Example 5.3): fine operator,
+ * test vectors, per-aggregate orthonormalisation, Galerkin coarse operators,
+ * smoother blocks, dense inverse of A_L.  `stream` is a cudaStream_t or NULL.
+ * On success *out owns the device memory until mlmc_destroy_hierarchy.      */
+int mlmc_setup_hierarchy(const mlmc_operator_desc *op, const mlmc_hierarchy_params *params,
+                         void *stream, mlmc_hierarchy **out);
+void mlmc_destroy_hierarchy(mlmc_hierarchy *h);
+
+/* Level sizes: lattice nx, ny and dofs per site d of level l (1-based). */
+int mlmc_level_info(const mlmc_hierarchy *h, int level, int *nx, int *ny, int *d);
+
+/* Copy P_l (level l < L) to host as blocks [agg][ax*ay*d][dc] (FP64 / c64). */
+int mlmc_get_prolongation(const mlmc_hierarchy *h, int level, void *host_out);
+/* Copy the block stencil of A_l to host as [site][5][d][d] (FP64 / c64);
+ * directions 0 self, 1 +x, 2 -x, 3 +y, 4 -y (periodic indexing). */
+int mlmc_get_operator(const mlmc_hierarchy *h, int level, void *host_out);
+
+/* y = A_l x for a device block of k columns (FP64 / c64). */
+int mlmc_apply(mlmc_hierarchy *h, int level, const void *x, void *y, int k);
+/* Solve A_l x = b for a device block of k columns to relative residual tol
+ * (Remark 4.1).  iters (host, optional) receives the outer iteration count. */
+int mlmc_solve(mlmc_hierarchy *h, int level, const void *b, void *x, int k, double tol, int *iters);
+/* Noise block (Eqs. iid_components1 / iid_components2) into a device buffer
+ * [n][k]: column c is sample first + c of (seed, level, purpose). */
+int mlmc_noise(int noise, uint64_t seed, int level, int purpose, uint64_t first, int n, int k,
+               int complex_out, void *out, void *stream);
+
+/* Level-difference samples (Remark 4.3): for j in [first, first + n_samples),
+ *   s_j = x_j^* A_l^{-1} x_j - (P_l^* x_j)^* A_{l+1}^{-1} (P_l^* x_j),  x_j = noise(seed, l, j),
+ * for 1 <= level < L; level == L gives x^* A_L^{-1} x.  out_samples is host
+ * memory of n_samples entries.  out_iters (host, optional) receives the
+ * outer iteration count of each block's two solves. */
+int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, uint64_t first,
+                      int n_samples, double tol, mlmc_c64 *out_samples, int *out_iters);
+
+/* tr(A_L^{-1}) from the FP64 dense inverse (Remark 4.2). */
+int mlmc_coarse_trace_exact(mlmc_hierarchy *h, mlmc_c64 *out);
+
+/* The Sec. 5 procedure: exact coarse term, tau from five warm-up estimates,
+ * rho_l split, per-level sampling in blocks until the standard error of every
+ * level meets rho_l (and N_l >= min_samples). */
+int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_estimate_result *r);
+
+/* Time one kernel family on level l with CUDA events on the hierarchy's
+ * stream: which = 0 operator apply (FP64), 1 operator apply (FP32),
+ * 2 red-black GS sweep (cycle precision).  Reports the average launch time
+ * and the algorithmic bytes one launch must move. */
+int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps,
+                        double *ms_per_launch, double *bytes_per_launch);
+
+/* Number of kernel launches issued by this handle since setup (for reports). */
+int mlmc_launch_count(const mlmc_hierarchy *h, uint64_t *count);
+
+const char *mlmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,263 @@
+// Per-column kernels of the batched flexible GMRES (Saad, Alg. 9.6): every
+// column of a vector block is an independent system, and its small Hessenberg
+// least-squares problem (Givens rotations, triangular solve) is handled by one
+// thread in FP64.  Also: sample combination and accumulation (Secs. 2-3), the
+// fine-operator builders (Examples 5.1 and 5.3) and a dense scatter of the
+// coarsest operator.
+#include "mlmc_internal.cuh"
+
+namespace mlmc {
+
+__device__ inline double cabs_(double a) { return fabs(a); }
+__device__ inline double cabs_(cdouble a) { return sqrt(a.re * a.re + a.im * a.im); }
+__device__ inline double creal_(double a) { return a; }
+__device__ inline double creal_(cdouble a) { return a.re; }
+template <class H> __device__ inline H hdiv(H a, H b);
+template <> __device__ inline double hdiv<double>(double a, double b) { return a / b; }
+template <> __device__ inline cdouble hdiv<cdouble>(cdouble a, cdouble b) {
+  double d = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+template <class H> __device__ inline H hreal(double v) { return make<H>(v, 0.0); }
+
+template <class H>
+__global__ void k_arnoldi_init(H *g, double *bnorm, double *invnrm, int *active, int *jdone, int k,
+                               double tol, int first, int *nactive) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  double beta = sqrt(fmax(creal_(g[c]), 0.0));
+  if (first) bnorm[c] = beta;
+  g[c] = hreal<H>(beta);
+  jdone[c] = 0;
+  int a = beta > 0.0 && beta > tol * bnorm[c];
+  active[c] = a;
+  invnrm[c] = a ? 1.0 / beta : 0.0;
+  if (a) atomicAdd(nactive, 1);
+}
+
+// Hessenberg column j of column c lives at H[(j*(m+1) + i)*k + c], i = 0..j+1.
+// On entry H[j][j+1] holds |w|^2 from a column dot.
+template <class H>
+__global__ void k_arnoldi_step(H *Hm, H *cs, H *sn, H *g, int j, int m, int k, int *active, int *jdone,
+                               const double *bnorm, double tol, double *invnrm, double *resid, int *nactive,
+                               int fixed) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  H *h = Hm + (size_t)j * (m + 1) * k + c;
+  if (!active[c]) {
+    invnrm[c] = 0.0;
+    return;
+  }
+  double nrm = sqrt(fmax(creal_(h[(size_t)(j + 1) * k]), 0.0));
+  h[(size_t)(j + 1) * k] = hreal<H>(nrm);
+  invnrm[c] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (int i = 0; i < j; ++i) {
+    H a = h[(size_t)i * k], b = h[(size_t)(i + 1) * k];
+    H ci = cs[(size_t)i * k + c], si = sn[(size_t)i * k + c];
+    h[(size_t)i * k] = conj(ci) * a + conj(si) * b;
+    h[(size_t)(i + 1) * k] = -(si * a) + ci * b;
+  }
+  H a = h[(size_t)j * k], b = h[(size_t)(j + 1) * k];
+  double den = sqrt(cabs_(a) * cabs_(a) + cabs_(b) * cabs_(b));
+  H cj, sj;
+  if (den > 0.0) {
+    cj = hdiv(a, hreal<H>(den));
+    sj = hdiv(b, hreal<H>(den));
+  } else {
+    cj = hreal<H>(1.0);
+    sj = hreal<H>(0.0);
+  }
+  cs[(size_t)j * k + c] = cj;
+  sn[(size_t)j * k + c] = sj;
+  h[(size_t)j * k] = hreal<H>(den);
+  h[(size_t)(j + 1) * k] = hreal<H>(0.0);
+  H gj = g[(size_t)j * k + c];
+  g[(size_t)(j + 1) * k + c] = -(sj * gj);
+  g[(size_t)j * k + c] = conj(cj) * gj;
+  jdone[c] = j + 1;
+  double r = cabs_(g[(size_t)(j + 1) * k + c]);
+  resid[c] = r;
+  bool still = fixed ? (nrm > 0.0 && den > 0.0) : (r > tol * bnorm[c] && den > 0.0 && nrm > 0.0);
+  if (!still) {
+    active[c] = 0;
+    invnrm[c] = 0.0;
+  } else {
+    atomicAdd(nactive, 1);
+  }
+}
+
+// y = R^{-1} g over the first jdone[c] rows; y_i = 0 beyond.
+template <class H>
+__global__ void k_trisolve(const H *Hm, const H *g, H *y, const int *jdone, int m, int k) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  int J = jdone[c];
+  for (int i = m - 1; i >= 0; --i) {
+    if (i >= J) {
+      y[(size_t)i * k + c] = hreal<H>(0.0);
+      continue;
+    }
+    H s = g[(size_t)i * k + c];
+    for (int l = i + 1; l < J; ++l) s = s - Hm[((size_t)l * (m + 1) + i) * k + c] * y[(size_t)l * k + c];
+    y[(size_t)i * k + c] = hdiv(s, Hm[((size_t)i * (m + 1) + i) * k + c]);
+  }
+}
+
+template <class H>
+__global__ void k_add_acc(H *dst, const H *src, int count) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = dst[i] + src[i];
+}
+
+void launch_arnoldi_init(int hc, void *g, double *bnorm, double *invnrm, int *active, int *jdone, int k,
+                         double tol, int first, int *nactive, cudaStream_t s) {
+  unsigned gr = (k + 63) / 64;
+  if (hc) k_arnoldi_init<cdouble><<<gr, 64, 0, s>>>((cdouble *)g, bnorm, invnrm, active, jdone, k, tol, first, nactive);
+  else k_arnoldi_init<double><<<gr, 64, 0, s>>>((double *)g, bnorm, invnrm, active, jdone, k, tol, first, nactive);
+  MLMC_LAUNCH_CHECK("k_arnoldi_init");
+}
+
+void launch_arnoldi_step(int hc, void *H, void *cs, void *sn, void *g, int j, int m, int k, int *active,
+                         int *jdone, const double *bnorm, double tol, double *invnrm, double *resid,
+                         int *nactive, int fixed, cudaStream_t s) {
+  unsigned gr = (k + 63) / 64;
+  if (hc) k_arnoldi_step<cdouble><<<gr, 64, 0, s>>>((cdouble *)H, (cdouble *)cs, (cdouble *)sn, (cdouble *)g, j, m, k,
+                                                     active, jdone, bnorm, tol, invnrm, resid, nactive, fixed);
+  else k_arnoldi_step<double><<<gr, 64, 0, s>>>((double *)H, (double *)cs, (double *)sn, (double *)g, j, m, k,
+                                                 active, jdone, bnorm, tol, invnrm, resid, nactive, fixed);
+  MLMC_LAUNCH_CHECK("k_arnoldi_step");
+}
+
+void launch_trisolve(int hc, const void *H, const void *g, void *y, const int *jdone, int m, int k, cudaStream_t s) {
+  unsigned gr = (k + 63) / 64;
+  if (hc) k_trisolve<cdouble><<<gr, 64, 0, s>>>((const cdouble *)H, (const cdouble *)g, (cdouble *)y, jdone, m, k);
+  else k_trisolve<double><<<gr, 64, 0, s>>>((const double *)H, (const double *)g, (double *)y, jdone, m, k);
+  MLMC_LAUNCH_CHECK("k_trisolve");
+}
+
+void launch_add_acc(int hc, void *dst, const void *src, int count, cudaStream_t s) {
+  unsigned gr = (count + 127) / 128;
+  if (hc) k_add_acc<cdouble><<<gr, 128, 0, s>>>((cdouble *)dst, (const cdouble *)src, count);
+  else k_add_acc<double><<<gr, 128, 0, s>>>((double *)dst, (const double *)src, count);
+  MLMC_LAUNCH_CHECK("k_add_acc");
+}
+
+// ------------------------------------------------------------------ samples
+template <class H>
+__global__ void k_sample_combine(const H *a, const H *b, cdouble *out, int k) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  H v = b ? a[c] - b[c] : a[c];
+  out[c] = cdouble{creal_(v), (double)im(v)};
+}
+
+void launch_sample_combine(int hc, const void *a, const void *b, void *out, int k, cudaStream_t s) {
+  unsigned gr = (k + 63) / 64;
+  if (hc) k_sample_combine<cdouble><<<gr, 64, 0, s>>>((const cdouble *)a, (const cdouble *)b, (cdouble *)out, k);
+  else k_sample_combine<double><<<gr, 64, 0, s>>>((const double *)a, (const double *)b, (cdouble *)out, k);
+  MLMC_LAUNCH_CHECK("k_sample_combine");
+}
+
+// Welford's update in sample order: N += 1; d = s - mean; mean += d / N; M2 += |d| |s - mean|.
+// For complex samples M2 accumulates Re(conj(d) (s - mean_new)), which sums to sum |s - mean|^2.
+__global__ void k_accumulate(const cdouble *smp, int k, double *acc) {
+  if (threadIdx.x || blockIdx.x) return;
+  double n = acc[0], mr = acc[1], mi = acc[2], m2 = acc[3];
+  for (int c = 0; c < k; ++c) {
+    n += 1.0;
+    double dr = smp[c].re - mr, di = smp[c].im - mi;
+    mr += dr / n;
+    mi += di / n;
+    m2 += dr * (smp[c].re - mr) + di * (smp[c].im - mi);
+  }
+  acc[0] = n; acc[1] = mr; acc[2] = mi; acc[3] = m2;
+}
+
+void launch_accumulate(const void *samples, int k, double *acc, cudaStream_t s) {
+  k_accumulate<<<1, 32, 0, s>>>((const cdouble *)samples, k, acc);
+  MLMC_LAUNCH_CHECK("k_accumulate");
+}
+
+// ------------------------------------------------------------------ fine operators
+// Example 5.1: diagonal 4 + shift, -1 to each neighbour; Dirichlet drops links leaving the grid.
+__global__ void k_build_laplace(double *coef, int nx, int ny, double shift, int periodic) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nx * ny) return;
+  int i = s % nx, j = s / nx;
+  double *B = coef + (size_t)s * 5;
+  B[0] = 4.0 + shift;
+  B[1] = (periodic || i + 1 < nx) ? -1.0 : 0.0;
+  B[2] = (periodic || i > 0) ? -1.0 : 0.0;
+  B[3] = (periodic || j + 1 < ny) ? -1.0 : 0.0;
+  B[4] = (periodic || j > 0) ? -1.0 : 0.0;
+}
+
+void launch_build_laplace(double *coef, int nx, int ny, double shift, int periodic, cudaStream_t s) {
+  k_build_laplace<<<(nx * ny + 255) / 256, 256, 0, s>>>(coef, nx, ny, shift, periodic);
+  MLMC_LAUNCH_CHECK("k_build_laplace");
+}
+
+// Example 5.3, Eq. schwinger_coupling with s1 = [[0,1],[1,0]], s2 = [[0,i],[-i,0]]:
+//   +x: -U_x(s) (I - s1), -x: -conj(U_x(s-x)) (I + s1), +y: -U_y(s) (I - s2), -y: -conj(U_y(s-y)) (I + s2).
+__global__ void k_build_wilson(cdouble *coef, const cdouble *links, int nx, int ny, double mass) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = nx * ny;
+  if (s >= n) return;
+  int i = s % nx, j = s / nx;
+  int xm = j * nx + (i == 0 ? nx - 1 : i - 1);
+  int ym = (j == 0 ? ny - 1 : j - 1) * nx + i;
+  cdouble ux = links[s], uy = links[n + s];
+  cdouble uxm = conj(links[xm]), uym = conj(links[n + ym]);
+  // 2x2 spin matrices, row-major
+  const cdouble one = {1, 0}, zer = {0, 0}, I = {0, 1};
+  cdouble s1[4] = {zer, one, one, zer};
+  cdouble s2[4] = {zer, I, -I, zer};
+  cdouble id[4] = {one, zer, zer, one};
+  cdouble *B = coef + (size_t)s * 5 * 4;
+  for (int e = 0; e < 4; ++e) {
+    B[0 * 4 + e] = (e == 0 || e == 3) ? cdouble{4.0 + mass, 0.0} : zer;
+    B[1 * 4 + e] = -(ux * (id[e] - s1[e]));
+    B[2 * 4 + e] = -(uxm * (id[e] + s1[e]));
+    B[3 * 4 + e] = -(uy * (id[e] - s2[e]));
+    B[4 * 4 + e] = -(uym * (id[e] + s2[e]));
+  }
+}
+
+void launch_build_wilson(cdouble *coef, const cdouble *links, int nx, int ny, double mass, cudaStream_t s) {
+  k_build_wilson<<<(nx * ny + 127) / 128, 128, 0, s>>>(coef, links, nx, ny, mass);
+  MLMC_LAUNCH_CHECK("k_build_wilson");
+}
+
+// ------------------------------------------------------------------ dense scatter
+template <class T>
+__global__ void k_stencil_to_dense_add(const T *coef, T *dense, int nx, int ny, int d, int dir) {
+  int nsite = nx * ny;
+  int n = nsite * d;
+  size_t total = (size_t)nsite * d * d;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    int s = (int)(t / (d * d));
+    int r = (int)(t / d) % d, c = (int)(t % d);
+    int i = s % nx, j = s / nx;
+    int nb = s;
+    if (dir == 1) nb = j * nx + (i + 1) % nx;
+    if (dir == 2) nb = j * nx + (i + nx - 1) % nx;
+    if (dir == 3) nb = ((j + 1) % ny) * nx + i;
+    if (dir == 4) nb = ((j + ny - 1) % ny) * nx + i;
+    T *dst = dense + (size_t)(s * d + r) * n + nb * d + c;
+    *dst = *dst + coef[((size_t)s * 5 + dir) * d * d + r * d + c];
+  }
+}
+
+void launch_stencil_to_dense(const StencilView &A, void *dense, cudaStream_t s) {
+  size_t n = (size_t)A.nx * A.ny * A.d;
+  MLMC_CUDA(cudaMemsetAsync(dense, 0, n * n * dtype_size(A.t), s));
+  MLMC_DISPATCH(A.t, T, {
+    // one launch per direction: directions that meet on the same entry add in order
+    for (int dir = 0; dir < 5; ++dir)
+      k_stencil_to_dense_add<T><<<grid_for((size_t)A.nx * A.ny * A.d * A.d, 256), 256, 0, s>>>(
+          (const T *)A.coef, (T *)dense, A.nx, A.ny, A.d, dir);
+  });
+  MLMC_LAUNCH_CHECK("k_stencil_to_dense");
+}
+
+}  // namespace mlmc

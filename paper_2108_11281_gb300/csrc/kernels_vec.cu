@@ -1,0 +1,274 @@
+// Vector-block kernels: noise generation, precision conversion, column-wise
+// dot products (two-stage, fixed order), multi-AXPY and column scaling.
+// Vector blocks are [row][k] with the k columns (independent right-hand
+// sides / samples) innermost, so a warp touches consecutive columns of one row.
+#include "mlmc_internal.cuh"
+
+namespace mlmc {
+
+void check_cuda(cudaError_t e, const char *where) {
+  if (e != cudaSuccess) throw cuda_error{e, where};
+}
+
+// ------------------------------------------------------------------ Philox
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two
+// 64x64->128-bit products, key bumped by two Weyl constants between rounds.
+struct u64x4 { uint64_t v[4]; };
+
+__device__ inline u64x4 philox4x64_10(u64x4 c, uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    uint64_t lo0 = M0 * c.v[0], hi0 = __umul64hi(M0, c.v[0]);
+    uint64_t lo1 = M1 * c.v[2], hi1 = __umul64hi(M1, c.v[2]);
+    u64x4 o;
+    o.v[0] = hi1 ^ c.v[1] ^ k0;
+    o.v[1] = lo1;
+    o.v[2] = hi0 ^ c.v[3] ^ k1;
+    o.v[3] = lo0;
+    c = o;
+  }
+  return c;
+}
+
+// kind 0 = Rademacher (256 rows per counter), 1 = Z4 (128 rows per counter).
+// key = (seed, key_hi), counter = (row_block, first_sample + col, 0, 0).
+template <class T>
+__global__ void k_noise(int kind, uint64_t seed, uint64_t key_hi, uint64_t first_sample, size_t n,
+                        int k, T *out) {
+  const int rows_per = kind == 0 ? 256 : 128;
+  size_t nblk = (n + rows_per - 1) / rows_per;
+  size_t total = nblk * (size_t)k;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    int col = (int)(t % k);
+    size_t blk = t / k;
+    u64x4 c = {{(uint64_t)blk, first_sample + (uint64_t)col, 0ull, 0ull}};
+    u64x4 w = philox4x64_10(c, seed, key_hi);
+    size_t row0 = blk * rows_per;
+    if (kind == 0) {
+      for (int q = 0; q < 4; ++q)
+        for (int b = 0; b < 64; ++b) {
+          size_t row = row0 + q * 64 + b;
+          if (row < n) {
+            double v = ((w.v[q] >> b) & 1ull) ? -1.0 : 1.0;
+            out[row * k + col] = make<T>(v, 0.0);
+          }
+        }
+    } else {
+      for (int q = 0; q < 4; ++q)
+        for (int b = 0; b < 32; ++b) {
+          size_t row = row0 + q * 32 + b;
+          if (row < n) {
+            int v = (int)((w.v[q] >> (2 * b)) & 3ull);   // x = i^v
+            double r = v == 0 ? 1.0 : v == 2 ? -1.0 : 0.0;
+            double i = v == 1 ? 1.0 : v == 3 ? -1.0 : 0.0;
+            out[row * k + col] = make<T>(r, i);
+          }
+        }
+    }
+  }
+}
+
+void launch_noise(int kind, uint64_t seed, uint64_t key_hi, uint64_t first_sample, size_t n, int k,
+                  DType t, void *out, cudaStream_t s) {
+  size_t nblk = (n + (kind == 0 ? 255 : 127)) / (kind == 0 ? 256 : 128);
+  unsigned g = grid_for(nblk * k, 128, 152 * 64);
+  MLMC_DISPATCH(t, T, k_noise<T><<<g, 128, 0, s>>>(kind, seed, key_hi, first_sample, n, k, (T *)out));
+  MLMC_LAUNCH_CHECK("k_noise");
+}
+
+// ------------------------------------------------------------------ convert / fill
+template <class To, class From>
+__global__ void k_convert(To *dst, const From *src, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = cvt<To, From>(src[i]);
+}
+
+void launch_convert(DType to, void *dst, DType from, const void *src, size_t count, cudaStream_t s) {
+  unsigned g = grid_for(count, 256);
+  if (to == F32 && from == F64) k_convert<float, double><<<g, 256, 0, s>>>((float *)dst, (const double *)src, count);
+  else if (to == F64 && from == F32) k_convert<double, float><<<g, 256, 0, s>>>((double *)dst, (const float *)src, count);
+  else if (to == C32 && from == C64) k_convert<cfloat, cdouble><<<g, 256, 0, s>>>((cfloat *)dst, (const cdouble *)src, count);
+  else if (to == C64 && from == C32) k_convert<cdouble, cfloat><<<g, 256, 0, s>>>((cdouble *)dst, (const cfloat *)src, count);
+  else if (to == from) {
+    MLMC_CUDA(cudaMemcpyAsync(dst, src, count * dtype_size(to), cudaMemcpyDeviceToDevice, s));
+    return;
+  } else throw cuda_error{cudaErrorInvalidValue, "launch_convert: field mismatch"};
+  MLMC_LAUNCH_CHECK("k_convert");
+}
+
+template <class T>
+__global__ void k_fill_one(T *dst, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = make<T>(1.0, 0.0);
+}
+
+void launch_fill_one(DType t, void *dst, size_t count, cudaStream_t s) {
+  MLMC_DISPATCH(t, T, k_fill_one<T><<<grid_for(count, 256), 256, 0, s>>>((T *)dst, count));
+  MLMC_LAUNCH_CHECK("k_fill_one");
+}
+
+// out = a - b (elementwise)
+template <class T>
+__global__ void k_sub(T *out, const T *a, const T *b, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = a[i] - b[i];
+}
+
+void launch_sub(DType t, void *out, const void *a, const void *b, size_t count, cudaStream_t s) {
+  MLMC_DISPATCH(t, T, k_sub<T><<<grid_for(count, 256), 256, 0, s>>>((T *)out, (const T *)a, (const T *)b, count));
+  MLMC_LAUNCH_CHECK("k_sub");
+}
+
+void launch_fill_zero(DType t, void *dst, size_t count, cudaStream_t s) {
+  MLMC_CUDA(cudaMemsetAsync(dst, 0, count * dtype_size(t), s));
+}
+
+// ------------------------------------------------------------------ column dots
+// Accumulation is in FP64 (double or cdouble) for every storage type.
+template <class T> struct acc_of { typedef double type; };
+template <> struct acc_of<cdouble> { typedef cdouble type; };
+template <> struct acc_of<cfloat> { typedef cdouble type; };
+
+__device__ inline double dotc(double a, double b) { return a * b; }
+__device__ inline double dotc(float a, float b) { return (double)a * (double)b; }
+__device__ inline cdouble dotc(cdouble a, cdouble b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+__device__ inline cdouble dotc(cfloat a, cfloat b) {
+  double ar = a.re, ai = a.im, br = b.re, bi = b.im;
+  return {ar * br + ai * bi, ar * bi - ai * br};
+}
+__device__ inline double addd(double a, double b) { return a + b; }
+__device__ inline cdouble addd(cdouble a, cdouble b) { return {a.re + b.re, a.im + b.im}; }
+
+static const int DOT_THREADS = 256;
+static const int DOT_MAXV = 8;          // basis vectors per pass over w
+static const int DOT_PARTS = 152 * 4;   // fixed number of row chunks
+
+int multidot_parts(size_t rows, int k) {
+  (void)k;
+  size_t p = rows < (size_t)DOT_PARTS ? rows : (size_t)DOT_PARTS;
+  return (int)(p < 1 ? 1 : p);
+}
+
+// partial[part][v][c] = sum over rows of chunk `part` of conj(V_v[row][c]) * w[row][c]
+template <class T>
+__global__ void __launch_bounds__(DOT_THREADS) k_multidot_partial(const T *V, size_t vstride, int nvec,
+                                                                  const T *w, size_t rows, int k,
+                                                                  typename acc_of<T>::type *partial) {
+  typedef typename acc_of<T>::type A;
+  __shared__ A red[DOT_THREADS];
+  const int slots = DOT_THREADS / k;          // rows handled per step
+  const int tid = threadIdx.x;
+  const int col = tid % k, slot = tid / k;
+  const bool live = slot < slots;
+  const int part = blockIdx.x, nparts = gridDim.x;
+  size_t chunk = (rows + nparts - 1) / nparts;
+  size_t r0 = (size_t)part * chunk, r1 = r0 + chunk < rows ? r0 + chunk : rows;
+  for (int v0 = 0; v0 < nvec; v0 += DOT_MAXV) {
+    A acc[DOT_MAXV];
+#pragma unroll
+    for (int v = 0; v < DOT_MAXV; ++v) acc[v] = zero<A>();
+    if (live) {
+      for (size_t r = r0 + slot; r < r1; r += slots) {
+        T wv = w[r * k + col];
+#pragma unroll
+        for (int v = 0; v < DOT_MAXV; ++v)
+          if (v0 + v < nvec) acc[v] = addd(acc[v], dotc(V[(size_t)(v0 + v) * vstride + r * k + col], wv));
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < DOT_MAXV; ++v) {
+      if (v0 + v >= nvec) break;
+      red[tid] = live ? acc[v] : zero<A>();
+      __syncthreads();
+      if (tid < k) {
+        A s = red[tid];
+        for (int sl = 1; sl < slots; ++sl) s = addd(s, red[sl * k + tid]);
+        partial[((size_t)part * nvec + v0 + v) * k + tid] = s;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// out[v][c] = sum_part partial[part][v][c], in part order
+template <class A>
+__global__ void k_multidot_reduce(const A *partial, int nparts, int nvec, int k, A *out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nvec * k) return;
+  A s = zero<A>();
+  for (int p = 0; p < nparts; ++p) s = addd(s, partial[(size_t)p * nvec * k + t]);
+  out[t] = s;
+}
+
+void launch_multidot(DType t, const void *V, size_t vstride, int nvec, const void *w, size_t rows,
+                     int k, void *partials, int nparts, void *out, DType out_t, cudaStream_t s) {
+  if (k > DOT_THREADS) throw cuda_error{cudaErrorInvalidValue, "multidot: k > 256"};
+  (void)out_t;
+  MLMC_DISPATCH(t, T, {
+    typedef typename acc_of<T>::type A;
+    k_multidot_partial<T><<<nparts, DOT_THREADS, 0, s>>>((const T *)V, vstride, nvec, (const T *)w, rows, k,
+                                                          (A *)partials);
+    MLMC_LAUNCH_CHECK("k_multidot_partial");
+    int tot = nvec * k;
+    k_multidot_reduce<A><<<(tot + 127) / 128, 128, 0, s>>>((const A *)partials, nparts, nvec, k, (A *)out);
+    MLMC_LAUNCH_CHECK("k_multidot_reduce");
+  });
+}
+
+// ------------------------------------------------------------------ multi-AXPY
+// w[r][c] += sign * sum_v V_v[r][c] * h[v*hstride + c]   (h is FP64 / complex FP64)
+template <class T, class H>
+__global__ void k_multiaxpy(T *w, const T *V, size_t vstride, int nvec, const H *h, size_t hstride,
+                            double sign, size_t rows, int k) {
+  size_t total = rows * (size_t)k;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int c = (int)(i % k);
+    H acc = zero<H>();
+    for (int v = 0; v < nvec; ++v)
+      acc = acc + cvt<H, T>(V[(size_t)v * vstride + i]) * h[(size_t)v * hstride + c];
+    w[i] = cvt<T, H>(cvt<H, T>(w[i]) + rmul(sign, acc));
+  }
+}
+
+
+void launch_multiaxpy(DType t, void *w, const void *V, size_t vstride, int nvec, const void *h,
+                      DType h_t, size_t hstride, double sign, size_t rows, int k, cudaStream_t s) {
+  unsigned g = grid_for(rows * (size_t)k, 256);
+  (void)h_t;
+  switch (t) {
+    case F64: k_multiaxpy<double, double><<<g, 256, 0, s>>>((double *)w, (const double *)V, vstride, nvec, (const double *)h, hstride, sign, rows, k); break;
+    case F32: k_multiaxpy<float, double><<<g, 256, 0, s>>>((float *)w, (const float *)V, vstride, nvec, (const double *)h, hstride, sign, rows, k); break;
+    case C64: k_multiaxpy<cdouble, cdouble><<<g, 256, 0, s>>>((cdouble *)w, (const cdouble *)V, vstride, nvec, (const cdouble *)h, hstride, sign, rows, k); break;
+    case C32: k_multiaxpy<cfloat, cdouble><<<g, 256, 0, s>>>((cfloat *)w, (const cfloat *)V, vstride, nvec, (const cdouble *)h, hstride, sign, rows, k); break;
+  }
+  MLMC_LAUNCH_CHECK("k_multiaxpy");
+}
+
+// ------------------------------------------------------------------ column scaling
+// y[r][c] = x[r][c] * alpha[c]  (alpha real FP64)
+template <class T>
+__global__ void k_scale_cols(T *y, const T *x, const double *alpha, size_t rows, int k) {
+  size_t total = rows * (size_t)k;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    typedef typename real_of<T>::type R;
+    y[i] = rmul((R)alpha[i % k], x[i]);
+  }
+}
+
+void launch_scale_cols(DType t, void *y, const void *x, const void *alpha, int, size_t rows, int k,
+                       cudaStream_t s) {
+  unsigned g = grid_for(rows * (size_t)k, 256);
+  MLMC_DISPATCH(t, T, k_scale_cols<T><<<g, 256, 0, s>>>((T *)y, (const T *)x, (const double *)alpha, rows, k));
+  MLMC_LAUNCH_CHECK("k_scale_cols");
+}
+
+}  // namespace mlmc

@@ -1,0 +1,248 @@
+"""Thin ctypes binding of libmlmc (include/mlmc.h).
+
+Argument marshalling only: every numerical step runs in the CUDA library.
+There is no CPU fallback; importing this module fails loudly when the
+library has not been built.  Device buffers are passed as raw pointers
+(e.g. ``torch.Tensor.data_ptr()``); streams as ``cudaStream_t`` integers.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmlmc.so")
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_SINGULAR, \
+    ERR_TIMEOUT, ERR_REJECTED = range(9)
+OP_LAPLACE2D, OP_WILSON2D = 1, 2
+NOISE_RADEMACHER, NOISE_Z4 = 0, 1
+PURPOSE_NOISE, PURPOSE_WARMUP, PURPOSE_SETUP = 0, 1, 2
+SETUP_SMOOTH, SETUP_INVERSE, SETUP_CONSTANT = 0, 1, 2
+PREC_FP64, PREC_MIXED_FP32 = 0, 1
+FORM_SIMPLIFIED, FORM_HAT = 0, 1
+CYCLE_V, CYCLE_K = 0, 1
+
+
+class C64(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class OperatorDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("periodic", ctypes.c_int), ("shift", ctypes.c_double), ("mass", ctypes.c_double),
+                ("links", ctypes.c_void_p)]
+
+
+class HierarchyParams(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("agg_x", ctypes.c_int), ("agg_y", ctypes.c_int),
+                ("n_tv", ctypes.c_int), ("spin_split", ctypes.c_int), ("setup_kind", ctypes.c_int),
+                ("setup_sweeps", ctypes.c_int), ("coarse_sweeps", ctypes.c_int),
+                ("setup_omega", ctypes.c_double), ("setup_seed", ctypes.c_uint64),
+                ("bootstrap", ctypes.c_int), ("boot_iters", ctypes.c_int),
+                ("smooth_pre", ctypes.c_int), ("smooth_post", ctypes.c_int), ("cycle", ctypes.c_int),
+                ("kcycle_its", ctypes.c_int), ("fgmres_restart", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("precision", ctypes.c_int), ("block", ctypes.c_int), ("reorth", ctypes.c_int),
+                ("user_P", ctypes.c_void_p)]
+
+
+class EstimateParams(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("weights", ctypes.c_double * 16), ("noise", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("tol", ctypes.c_double), ("min_samples", ctypes.c_int),
+                ("max_samples", ctypes.c_int), ("form", ctypes.c_int)]
+
+
+class EstimateResult(ctypes.Structure):
+    _fields_ = [("trace", C64), ("std_err", ctypes.c_double), ("tau", ctypes.c_double),
+                ("coarse_term", C64), ("levels", ctypes.c_int), ("n_samples", ctypes.c_int * 16),
+                ("mean", C64 * 16), ("variance", ctypes.c_double * 16), ("iters", ctypes.c_double * 16),
+                ("seconds", ctypes.c_double * 16), ("cost_nnz", ctypes.c_double * 16),
+                ("seconds_total", ctypes.c_double)]
+
+
+class MLMCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libmlmc status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libmlmc.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, u64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
+    sig = {
+        "mlmc_setup_hierarchy": [ctypes.POINTER(OperatorDesc), ctypes.POINTER(HierarchyParams), vp,
+                                 ctypes.POINTER(vp)],
+        "mlmc_level_info": [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)],
+        "mlmc_get_prolongation": [vp, i, vp],
+        "mlmc_get_operator": [vp, i, vp],
+        "mlmc_apply": [vp, i, vp, vp, i],
+        "mlmc_solve": [vp, i, vp, vp, i, d, ctypes.POINTER(i)],
+        "mlmc_noise": [i, u64, i, i, u64, i, i, i, vp, vp],
+        "mlmc_sample_level": [vp, i, i, u64, u64, i, d, ctypes.POINTER(C64), ctypes.POINTER(i)],
+        "mlmc_coarse_trace_exact": [vp, ctypes.POINTER(C64)],
+        "mlmc_trace_estimate": [vp, ctypes.POINTER(EstimateParams), ctypes.POINTER(EstimateResult)],
+        "mlmc_profile_kernel": [vp, i, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d)],
+        "mlmc_launch_count": [vp, ctypes.POINTER(u64)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.mlmc_destroy_hierarchy.argtypes = [vp]
+    lib.mlmc_destroy_hierarchy.restype = None
+    lib.mlmc_last_error.argtypes = []
+    lib.mlmc_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+lib = _load()
+EXPORTED = ["mlmc_setup_hierarchy", "mlmc_destroy_hierarchy", "mlmc_level_info", "mlmc_get_prolongation",
+            "mlmc_get_operator", "mlmc_apply", "mlmc_solve", "mlmc_noise", "mlmc_sample_level",
+            "mlmc_coarse_trace_exact", "mlmc_trace_estimate", "mlmc_profile_kernel", "mlmc_launch_count",
+            "mlmc_last_error"]
+
+
+def check(status):
+    if status != OK:
+        raise MLMCError(status, lib.mlmc_last_error().decode(errors="replace"))
+
+
+def default_params(**kw):
+    p = HierarchyParams(levels=2, agg_x=4, agg_y=4, n_tv=4, spin_split=0, setup_kind=SETUP_SMOOTH,
+                        setup_sweeps=40, coarse_sweeps=20, setup_omega=2.0 / 3.0, setup_seed=0,
+                        bootstrap=1, boot_iters=2, smooth_pre=1, smooth_post=1, cycle=CYCLE_K,
+                        kcycle_its=2, fgmres_restart=30, max_iter=2000, precision=PREC_FP64, block=64,
+                        reorth=1, user_P=None)
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Hierarchy:
+    """Owner of an mlmc_hierarchy handle (device memory freed on close)."""
+
+    def __init__(self, kind, nx, ny, params, shift=0.0, mass=0.0, links=None, periodic=0, stream=0,
+                 user_P=None):
+        self._keep = []
+        links_ptr = None
+        if links is not None:
+            arr = np.ascontiguousarray(np.asarray(links, dtype=np.complex128))
+            if arr.shape != (2, ny, nx):
+                raise ValueError("links must have shape (2, ny, nx)")
+            self._keep.append(arr)
+            links_ptr = arr.ctypes.data
+        if user_P is not None:
+            arrs = [np.ascontiguousarray(a) for a in user_P]
+            self._keep.extend(arrs)
+            ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+            self._keep.append(ptrs)
+            params.user_P = ctypes.cast(ptrs, ctypes.c_void_p)
+        self.desc = OperatorDesc(kind=kind, nx=nx, ny=ny, periodic=periodic, shift=shift, mass=mass,
+                                 links=links_ptr)
+        self.params = params
+        self.complex = kind == OP_WILSON2D
+        self.handle = ctypes.c_void_p()
+        check(lib.mlmc_setup_hierarchy(ctypes.byref(self.desc), ctypes.byref(params), ctypes.c_void_p(stream),
+                                       ctypes.byref(self.handle)))
+
+    def close(self):
+        if self.handle:
+            lib.mlmc_destroy_hierarchy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level_info(self, level):
+        nx, ny, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib.mlmc_level_info(self.handle, level, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(d)))
+        return nx.value, ny.value, d.value
+
+    def n(self, level):
+        nx, ny, d = self.level_info(level)
+        return nx * ny * d
+
+    def prolongation(self, level):
+        nx, ny, d = self.level_info(level)
+        _, _, dc = self.level_info(level + 1)
+        p = self.params
+        nagg = (nx // p.agg_x) * (ny // p.agg_y)
+        out = np.zeros((nagg, p.agg_x * p.agg_y * d, dc), dtype=np.complex128 if self.complex else np.float64)
+        check(lib.mlmc_get_prolongation(self.handle, level, out.ctypes.data))
+        return out
+
+    def operator(self, level):
+        nx, ny, d = self.level_info(level)
+        out = np.zeros((nx * ny, 5, d, d), dtype=np.complex128 if self.complex else np.float64)
+        check(lib.mlmc_get_operator(self.handle, level, out.ctypes.data))
+        return out
+
+    def apply(self, level, x_ptr, y_ptr, k):
+        check(lib.mlmc_apply(self.handle, level, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), k))
+
+    def solve(self, level, b_ptr, x_ptr, k, tol):
+        its = ctypes.c_int()
+        check(lib.mlmc_solve(self.handle, level, ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr), k, tol,
+                             ctypes.byref(its)))
+        return its.value
+
+    def sample_level(self, level, noise, seed, first, n_samples, tol):
+        out = (C64 * max(n_samples, 1))()
+        nblk = (n_samples + self.params.block - 1) // self.params.block
+        its = (ctypes.c_int * max(nblk, 1))()
+        check(lib.mlmc_sample_level(self.handle, level, noise, seed, first, n_samples, tol, out, its))
+        vals = np.array([complex(out[i].re, out[i].im) for i in range(n_samples)])
+        return vals, list(its)[:nblk]
+
+    def coarse_trace_exact(self):
+        out = C64()
+        check(lib.mlmc_coarse_trace_exact(self.handle, ctypes.byref(out)))
+        return complex(out.re, out.im)
+
+    def trace_estimate(self, eps=1e-3, noise=NOISE_RADEMACHER, seed=0, tol=1e-10, weights=None, min_samples=5,
+                       max_samples=1 << 24, form=FORM_SIMPLIFIED):
+        p = EstimateParams(eps=eps, noise=noise, seed=seed, tol=tol, min_samples=min_samples,
+                           max_samples=max_samples, form=form)
+        if weights is not None:
+            for i, w in enumerate(weights):
+                p.weights[i] = w
+        r = EstimateResult()
+        check(lib.mlmc_trace_estimate(self.handle, ctypes.byref(p), ctypes.byref(r)))
+        return r
+
+    def profile_kernel(self, which, level, k, reps):
+        ms, by = ctypes.c_double(), ctypes.c_double()
+        check(lib.mlmc_profile_kernel(self.handle, which, level, k, reps, ctypes.byref(ms), ctypes.byref(by)))
+        return ms.value, by.value
+
+    def launch_count(self):
+        c = ctypes.c_uint64()
+        check(lib.mlmc_launch_count(self.handle, ctypes.byref(c)))
+        return c.value
+
+
+def noise(kind, seed, level, purpose, first, n, k, complex_out, out_ptr, stream=0):
+    check(lib.mlmc_noise(kind, seed, level, purpose, first, n, k, complex_out, ctypes.c_void_p(out_ptr),
+                         ctypes.c_void_p(stream)))
+
+
+def result_dict(r):
+    L = r.levels
+    return {
+        "trace": complex(r.trace.re, r.trace.im), "std_err": r.std_err, "tau": r.tau,
+        "coarse_term": complex(r.coarse_term.re, r.coarse_term.im),
+        "n_samples": [r.n_samples[i] for i in range(L - 1)],
+        "mean": [complex(r.mean[i].re, r.mean[i].im) for i in range(L - 1)],
+        "variance": [r.variance[i] for i in range(L - 1)],
+        "iters": [r.iters[i] for i in range(L - 1)],
+        "seconds": [r.seconds[i] for i in range(L - 1)],
+        "cost_nnz": [r.cost_nnz[i] for i in range(L)],
+        "seconds_total": r.seconds_total,
+    }

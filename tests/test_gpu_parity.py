@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances.  Noise is bit-exact (integer work).  Operator applies are FP64
+with at most 9 products per entry: 1e-13 relative.  Solves run to relative
+residual tol = 1e-12, so a sample x^* A^{-1} x differs from the exact value by
+at most |x|^2 ||A^{-1}|| tol; the per-sample bar is 1e-9 relative (the FP64
+form's target).  The mixed FP32-cycle form solves to 1e-10 under FP64 FGMRES:
+1e-8 relative.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import estimator as E
+from oracle.hierarchy import SetupParams, build_hierarchy
+from oracle.operators import laplace2d, wilson2d
+from oracle.philox import rademacher, z4, PURPOSE_NOISE, PURPOSE_SETUP
+from paper_2108_11281_gb300.workloads import gauge_links
+
+
+@pytest.fixture(scope="module")
+def mlmc():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2108_11281_gb300 import mlmc as m
+    return m
+
+
+def block_from_stencil(coef, nx, ny):
+    """Sparse matrix of a [site][5][d][d] block stencil (periodic indexing)."""
+    nsite, _, d, _ = coef.shape
+    rows, cols, vals = [], [], []
+    j, i = np.divmod(np.arange(nsite), nx)
+    nbs = [np.arange(nsite), j * nx + (i + 1) % nx, j * nx + (i - 1) % nx,
+           ((j + 1) % ny) * nx + i, ((j - 1) % ny) * nx + i]
+    for dr, nb in enumerate(nbs):
+        for a in range(d):
+            for b in range(d):
+                rows.append(np.arange(nsite) * d + a)
+                cols.append(nb * d + b)
+                vals.append(coef[:, dr, a, b])
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(nsite * d, nsite * d)).tocsr()
+    A.sum_duplicates()
+    return A
+
+
+# ----------------------------------------------------------------- noise
+@pytest.mark.parametrize("kind", ["rademacher", "z4"])
+def test_noise_bit_exact(mlmc, kind):
+    n, k, first, seed, level = 1000, 7, 123, 99, 3
+    cplx = kind == "z4"
+    out = torch.zeros((n, k), dtype=torch.complex128 if cplx else torch.float64, device="cuda")
+    mlmc.noise(mlmc.NOISE_Z4 if cplx else mlmc.NOISE_RADEMACHER, seed, level, PURPOSE_NOISE, first, n, k,
+               int(cplx), out.data_ptr())
+    got = out.cpu().numpy()
+    for c in range(k):
+        ref = (z4 if cplx else rademacher)(n, seed, level, first + c)
+        assert np.array_equal(got[:, c], ref)
+
+
+# ----------------------------------------------------------------- operators and setup
+def laplace_h(mlmc, N, levels, block=8, **kw):
+    prm = mlmc.default_params(levels=levels, block=block, **kw)
+    return mlmc.Hierarchy(mlmc.OP_LAPLACE2D, N, N, prm)
+
+
+def test_laplace_apply_and_constant_galerkin(mlmc):
+    N = 16
+    h = laplace_h(mlmc, N, 2, n_tv=1, setup_kind=mlmc.SETUP_CONSTANT, bootstrap=0)
+    A = laplace2d(N, N)
+    x = torch.randn(N * N, 3, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    h.apply(1, x.data_ptr(), y.data_ptr(), 3)
+    ref = A @ x.cpu().numpy()
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+    lv = build_hierarchy(A, N, N, 1, SetupParams(levels=2, n_tv=1, kind="constant"))
+    P = h.prolongation(1)
+    assert np.array_equal(np.abs(P), np.full_like(P, 0.25))
+    A2 = block_from_stencil(h.operator(2), N // 4, N // 4)
+    assert np.abs((A2 - lv[1].A).toarray()).max() <= 1e-14
+    tr = h.coarse_trace_exact()
+    assert abs(tr - E.exact_coarse_trace(lv)) <= 1e-12 * abs(tr)
+    h.close()
+
+
+def test_wilson_apply(mlmc):
+    N = 8
+    U = gauge_links(N, N, 0.3, 5)
+    prm = mlmc.default_params(levels=2, n_tv=2, spin_split=1, setup_kind=mlmc.SETUP_INVERSE, setup_sweeps=4,
+                              coarse_sweeps=2, setup_omega=1.0, block=8, bootstrap=0)
+    h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.1, links=U)
+    S = wilson2d(N, N, 0.1, U)
+    x = torch.randn(N * N * 2, 3, dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    h.apply(1, x.data_ptr(), y.data_ptr(), 3)
+    ref = S @ x.cpu().numpy()
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert np.abs(block_from_stencil(h.operator(1), N, N) - S).max() <= 1e-15
+    h.close()
+
+
+def projector_distance(Pa, Pb):
+    """max over aggregates of || Pa Pa^* - Pb Pb^* ||: independent of the basis inside each aggregate."""
+    return max(np.abs(a @ a.conj().T - b @ b.conj().T).max() for a, b in zip(Pa, Pb))
+
+
+@pytest.mark.parametrize("case", ["laplace", "wilson"])
+def test_setup_matches_oracle(mlmc, case):
+    """GPU test vectors, bootstrap, MGS and Galerkin reproduce the oracle's hierarchy
+    (same algorithm, FP64; agreement to rounding amplified by the setup's conditioning)."""
+    if case == "laplace":
+        N = 64
+        kw = dict(levels=3, n_tv=4, setup_sweeps=20, coarse_sweeps=10, bootstrap=1, boot_iters=2)
+        h = laplace_h(mlmc, N, block=8, **kw)
+        A = laplace2d(N, N)
+        sp_ = SetupParams(levels=3, n_tv=4, sweeps=20, coarse_sweeps=10, bootstrap=1, boot_iters=2)
+        lv = build_hierarchy(A, N, N, 1, sp_)
+    else:
+        N = 16
+        U = gauge_links(N, N, 0.3, 7)
+        kw = dict(levels=3, n_tv=2, spin_split=1, setup_kind=mlmc.SETUP_INVERSE, setup_sweeps=6, coarse_sweeps=4,
+                  setup_omega=1.0, bootstrap=1, boot_iters=2, smooth_pre=2, smooth_post=2, block=8)
+        prm = mlmc.default_params(**kw)
+        h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=-0.05, links=U)
+        A = wilson2d(N, N, -0.05, U)
+        sp_ = SetupParams(levels=3, n_tv=2, spin_split=True, kind="inverse", sweeps=6, coarse_sweeps=4,
+                          omega=1.0, noise_kind="z4", bootstrap=1, boot_iters=2, smooth_pre=2, smooth_post=2)
+        lv = build_hierarchy(A, N, N, 2, sp_)
+    for l in (1, 2):
+        P = h.prolongation(l)
+        assert projector_distance(P, lv[l - 1].P_blocks) <= 1e-9, l
+        G = P.reshape(P.shape[0], -1, P.shape[2])
+        assert max(np.abs(g.conj().T @ g - np.eye(g.shape[1])).max() for g in G) <= 1e-13
+    tr = h.coarse_trace_exact()
+    assert abs(tr - E.exact_coarse_trace(lv)) <= 1e-8 * abs(tr)
+    h.close()
+
+
+# ----------------------------------------------------------------- solves and samples
+def imported_laplace(mlmc, N=64, levels=3, **kw):
+    A = laplace2d(N, N)
+    lv = build_hierarchy(A, N, N, 1, SetupParams(levels=levels, n_tv=4, sweeps=20, coarse_sweeps=10))
+    prm = mlmc.default_params(levels=levels, n_tv=4, **kw)
+    h = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, N, N, prm, user_P=[lv[i].P_blocks for i in range(levels - 1)])
+    return h, lv
+
+
+def test_galerkin_of_imported_P(mlmc):
+    h, lv = imported_laplace(mlmc)
+    for l in (2, 3):
+        nx, ny, d = h.level_info(l)
+        Al = block_from_stencil(h.operator(l), nx, ny)
+        assert np.abs((Al - lv[l - 1].A).toarray()).max() <= 1e-13 * np.abs(lv[l - 1].A).max()
+    h.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_matches_exact(mlmc, precision):
+    h, lv = imported_laplace(mlmc, block=5, precision=precision)
+    k, n = 5, 64 * 64
+    b = torch.randn(n, k, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    its = h.solve(1, b.data_ptr(), x.data_ptr(), k, 1e-12)
+    assert 0 < its < 200
+    A = lv[0].A
+    bn, xn = b.cpu().numpy(), x.cpu().numpy()
+    res = np.linalg.norm(bn - A @ xn, axis=0) / np.linalg.norm(bn, axis=0)
+    assert res.max() <= 1e-12
+    ref = E.exact_solver(A)(bn)
+    assert np.linalg.norm(xn - ref) <= 1e-8 * np.linalg.norm(ref)
+    h.close()
+
+
+def compare_samples(got, ref, rtol):
+    err = np.abs(got - ref) / np.abs(ref)
+    assert err.max() <= rtol, (err.max(), np.argmax(err))
+
+
+def test_config1_shape_samples(mlmc):
+    """64x64 Dirichlet Laplacian, 2 levels, piecewise-constant P, Rademacher seed 0:
+    70 level-1 samples (a full block of 64 and a ragged block of 6)."""
+    N = 64
+    h = laplace_h(mlmc, N, 2, block=64, n_tv=1, setup_kind=mlmc.SETUP_CONSTANT, bootstrap=0)
+    got, its = h.sample_level(1, mlmc.NOISE_RADEMACHER, 0, 0, 70, 1e-12)
+    lv = build_hierarchy(laplace2d(N, N), N, N, 1, SetupParams(levels=2, n_tv=1, kind="constant"))
+    ref = E.level_samples(lv, E.LevelSolvers(lv), 1, "rademacher", 0, 0, 70)
+    compare_samples(got, ref, 1e-9)
+    h.close()
+
+
+@pytest.mark.parametrize("precision,rtol", [(0, 1e-9), (1, 1e-8)])
+def test_samples_three_levels(mlmc, precision, rtol):
+    h, lv = imported_laplace(mlmc, block=8, precision=precision)
+    solv = E.LevelSolvers(lv)
+    tol = 1e-12 if precision == 0 else 1e-10
+    for level, first, count in ((1, 3, 11), (2, 0, 8), (3, 5, 4)):
+        got, _ = h.sample_level(level, mlmc.NOISE_RADEMACHER, 7, first, count, tol)
+        ref = E.level_samples(lv, solv, level, "rademacher", 7, first, count) if level < 3 else \
+            np.array([np.vdot(x, solv.solve(2, x)) for x in
+                      [rademacher(lv[2].n, 7, 3, first + j) for j in range(count)]])
+        compare_samples(got, ref, rtol)
+    h.close()
+
+
+def test_wilson_samples_imported_P(mlmc):
+    N = 16
+    U = gauge_links(N, N, 0.3, 11)
+    S = wilson2d(N, N, 0.05, U)
+    lv = build_hierarchy(S, N, N, 2, SetupParams(levels=3, n_tv=2, spin_split=True, kind="inverse", sweeps=6,
+                                                 coarse_sweeps=4, omega=1.0, noise_kind="z4"))
+    prm = mlmc.default_params(levels=3, n_tv=2, spin_split=1, block=4, smooth_pre=2, smooth_post=2)
+    h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.05, links=U,
+                       user_P=[lv[0].P_blocks, lv[1].P_blocks])
+    solv = E.LevelSolvers(lv)
+    for level in (1, 2):
+        got, _ = h.sample_level(level, mlmc.NOISE_Z4, 3, 0, 6, 1e-12)
+        ref = E.level_samples(lv, solv, level, "z4", 3, 0, 6)
+        compare_samples(got, ref, 1e-9)
+    tr = h.coarse_trace_exact()
+    assert abs(tr - E.exact_coarse_trace(lv)) <= 1e-12 * abs(tr)
+    h.close()
+
+
+def test_trace_estimate_matches_oracle(mlmc):
+    """Sec. 5 procedure on a 32x32 Laplacian, 2 levels: same tau, same N_l, same estimate."""
+    N = 32
+    h = laplace_h(mlmc, N, 2, block=16, n_tv=1, setup_kind=mlmc.SETUP_CONSTANT, bootstrap=0)
+    r = mlmc.result_dict(h.trace_estimate(eps=2e-2, noise=mlmc.NOISE_RADEMACHER, seed=4, tol=1e-12))
+    lv = build_hierarchy(laplace2d(N, N), N, N, 1, SetupParams(levels=2, n_tv=1, kind="constant"))
+    ref = E.trace_estimate(lv, "rademacher", seed=4, eps=2e-2, block=16)
+    assert r["n_samples"] == ref.n_samples
+    assert abs(r["tau"] - ref.tau) <= 1e-9 * abs(ref.tau)
+    assert abs(r["trace"] - ref.trace) <= 1e-9 * abs(ref.trace)
+    assert abs(r["std_err"] - ref.std_err) <= 1e-6 * ref.std_err
+    h.close()
