@@ -21,8 +21,9 @@
  *  - "host" pointers are ordinary CPU memory, read or written only during
  *    the call.  "device" pointers are CUDA global memory of the current
  *    device, owned by the caller.
- *  - All GPU work is issued on the stream given at setup (NULL = legacy
- *    default stream).  Calls return after their work has completed.
+ *  - All GPU work is issued on the stream given at setup (NULL: a private
+ *    blocking stream of the handle, ordered with the legacy default stream).
+ *    Calls return after their work has completed.
  *  - A hierarchy handle owns all device memory it allocates and must be used
  *    by one host thread at a time.
  *  - Vector blocks on the device are laid out [site][dof][k]: the k columns
@@ -58,11 +59,12 @@ typedef enum {
 
 enum { MLMC_OP_LAPLACE2D = 1, MLMC_OP_WILSON2D = 2 };
 enum { MLMC_NOISE_RADEMACHER = 0, MLMC_NOISE_Z4 = 1 };
-enum { MLMC_PURPOSE_NOISE = 0, MLMC_PURPOSE_WARMUP = 1, MLMC_PURPOSE_SETUP = 2 };
+enum { MLMC_PURPOSE_NOISE = 0, MLMC_PURPOSE_WARMUP = 1, MLMC_PURPOSE_SETUP = 2, MLMC_PURPOSE_TRAIN = 3 };
 enum { MLMC_SETUP_SMOOTH = 0, MLMC_SETUP_INVERSE = 1, MLMC_SETUP_CONSTANT = 2 };
 enum { MLMC_PREC_FP64 = 0, MLMC_PREC_MIXED_FP32 = 1 };
 enum { MLMC_FORM_SIMPLIFIED = 0, MLMC_FORM_HAT = 1 };
 enum { MLMC_CYCLE_V = 0, MLMC_CYCLE_K = 1 };
+enum { MLMC_ALLOC_RHO = 0, MLMC_ALLOC_OPTIMAL = 1 };
 
 /* Fine operator A = A_1 (Examples 5.1 and 5.3).  Sites s = j*nx + i. */
 typedef struct {
@@ -100,6 +102,10 @@ typedef struct {
   int precision;       /* MLMC_PREC_FP64 or MLMC_PREC_MIXED_FP32 (FP32 cycle under FP64 FGMRES)*/
   int block;           /* largest vector-block width k (columns per solve), 1..256            */
   int reorth;          /* 1: classical Gram-Schmidt twice in the outer Arnoldi                */
+  int inner_its;       /* > 0: the outer FP64 FGMRES is preconditioned by this many FGMRES
+                          steps in the cycle precision (each preconditioned by one cycle);
+                          0: by one cycle                                                      */
+  int graphs;          /* 1: replay each inner solve as a captured CUDA graph                   */
   const void *const *user_P; /* optional, host: user_P[l-1] = P_l as blocks [agg][ax*ay*d][dc]
                           (double, or mlmc_c64 for complex operators); columns must be
                           orthonormal.  Replaces the test-vector setup.  NULL = build P.      */
@@ -117,6 +123,10 @@ typedef struct {
   int min_samples;     /* floor on N_l (paper: 5)                                            */
   int max_samples;     /* cap on N_l                                                          */
   int form;            /* MLMC_FORM_SIMPLIFIED (Remark 4.3)                                  */
+  int allocation;      /* MLMC_ALLOC_RHO: Sec. 5 per-level targets rho_l from `weights`;
+                          MLMC_ALLOC_OPTIMAL: Sec. 2 N_l proportional to sqrt(V_l / C_l) with
+                          V_l, C_l (cost model per sample) estimated as samples arrive, until
+                          sum V_l / N_l <= (eps tau)^2                                         */
 } mlmc_estimate_params;
 
 typedef struct {
@@ -130,7 +140,10 @@ typedef struct {
   double variance[16];   /* unbiased sample variance, complex convention of Sec. 3           */
   double iters[16];      /* mean outer FGMRES iterations per solve on level l                */
   double seconds[16];    /* wall time spent on level difference l                            */
-  double cost_nnz[16];   /* Sec. 5 cost model: sum of nnz(B) over products B x (per level)  */
+  double cost_nnz[16];   /* Sec. 5 cost model: sum of nnz(B) over products B x, per level
+                            difference (both solves, transfers, smoothing sweeps, coarsest
+                            products); entry L-1: n_L^3 for the exact coarsest term          */
+  double weights_used[16]; /* w_l with rho_l^2 = w_l (eps tau)^2 (optimal: sqrt(V_l C_l) share) */
   double seconds_total;
 } mlmc_estimate_result;
 
@@ -179,10 +192,50 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
 
 /* Time one kernel family on level l with CUDA events on the hierarchy's
  * stream: which = 0 operator apply (FP64), 1 operator apply (FP32),
- * 2 red-black GS sweep (cycle precision).  Reports the average launch time
- * and the algorithmic bytes one launch must move. */
+ * 2 red-black GS sweep, 3 column multi-dot of 4 basis blocks against w,
+ * 4 multi-AXPY of 4 basis blocks into w (2-4 in the cycle precision).
+ * Reports the average launch time and the algorithmic bytes one launch must
+ * move. */
 int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps,
                         double *ms_per_launch, double *bytes_per_launch);
+
+/* ---- Learned correction (not in the paper; the project's smoother) --------
+ * A bias-free 3-layer 3x3 convolutional network c0 -> 16 -> 16 -> c0 (ReLU
+ * after layers 1 and 2; c0 = real channels per fine site: 1 Laplace, 4
+ * Wilson) applied in the FP32 cycle on the fine level after the coarse-grid
+ * correction: x += net(b - A x), then the red-black post-smoothing.  Weights
+ * are FP32, concatenated [W1 | W2 | W3], each [c_out][c_in][3][3] with tap
+ * (ty, tx) reading site (i + tx - 1, j + ty - 1).  Needs the mixed form.
+ * Acceptance stays with the FP64 outer FGMRES true residual; a solve that
+ * does not converge with the net is repeated without it.                    */
+typedef struct {
+  int n_pairs;               /* fine-level residuals to capture from plain solves (rounded up to blocks) */
+  int epochs;                /* passes of Adam over the training blocks                                  */
+  double lr;                 /* Adam step size                                                           */
+  double tol;                /* relative tolerance of the plain solves that generate the residuals     */
+  uint64_t seed;             /* right-hand sides of those solves: Philox purpose 3, level 1              */
+  const float *init_weights; /* host, optional: initial weights (else a seeded Rademacher initialisation) */
+  int enable;                /* 1: switch the net on if its validation loss is below 1                  */
+} mlmc_train_params;
+
+typedef struct {
+  int pairs, blocks, epochs, enabled, n_weights;
+  double loss_first, loss_last;   /* mean training loss of the first / last epoch                       */
+  double val_loss;                /* mean ||A net(r) - r||^2 / ||r||^2 on held-out residuals           */
+  double seconds_capture, seconds_train;
+} mlmc_train_report;
+
+/* Capture residual/error pairs from plain multigrid solves (the error enters
+ * through A e = r), train the network on the GPU (forward, backward, Adam),
+ * validate, and install it.  weights_out (host, optional) receives n_weights floats. */
+int mlmc_learned_train(mlmc_hierarchy *h, const mlmc_train_params *p, float *weights_out, mlmc_train_report *rep);
+/* Install weights (host, n_weights floats) and switch the net on (enable = 1) or off. */
+int mlmc_learned_set(mlmc_hierarchy *h, const float *weights, int enable);
+/* e = net(r) for a device block of k columns in the FP32 field of the fine level. */
+int mlmc_learned_apply(mlmc_hierarchy *h, const void *r, void *e, int k);
+/* Loss of a device block r (FP32 field of the fine level, k columns) and its
+ * weight gradient (host, n_weights floats). */
+int mlmc_learned_grad(mlmc_hierarchy *h, const void *r, int k, double *loss, float *grad_out);
 
 /* Number of kernel launches issued by this handle since setup (for reports). */
 int mlmc_launch_count(const mlmc_hierarchy *h, uint64_t *count);

@@ -142,6 +142,21 @@ void launch_add_acc(int hc, void *dst, const void *src, int count, cudaStream_t 
   MLMC_LAUNCH_CHECK("k_add_acc");
 }
 
+template <class H>
+__global__ void k_col_factor(const H *dot, double *alpha, double scale, int k) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  double v = fabs(creal_(dot[c]));
+  alpha[c] = v > 0.0 ? scale / v : 0.0;
+}
+
+void launch_col_factor(int hc, const void *dot, double *alpha, double scale, int k, cudaStream_t s) {
+  unsigned gr = (k + 63) / 64;
+  if (hc) k_col_factor<cdouble><<<gr, 64, 0, s>>>((const cdouble *)dot, alpha, scale, k);
+  else k_col_factor<double><<<gr, 64, 0, s>>>((const double *)dot, alpha, scale, k);
+  MLMC_LAUNCH_CHECK("k_col_factor");
+}
+
 // ------------------------------------------------------------------ samples
 template <class H>
 __global__ void k_sample_combine(const H *a, const H *b, cdouble *out, int k) {

@@ -58,7 +58,7 @@ void launch_block_inverse(DType t, const void *coef, void *dinv, int nsite, int 
   unsigned g = (nsite + 63) / 64;
 #define MLMC_BI_CASE(DD) case DD: MLMC_DISPATCH(t, T, k_block_inverse<T, DD><<<g, 64, 0, s>>>((const T *)coef, (T *)dinv, nsite, err)); break;
   switch (d) {
-    MLMC_BI_CASE(1) MLMC_BI_CASE(2) MLMC_BI_CASE(4) MLMC_BI_CASE(8) MLMC_BI_CASE(16)
+    MLMC_BI_CASE(1) MLMC_BI_CASE(2) MLMC_BI_CASE(4) MLMC_BI_CASE(8)
     default: throw cuda_error{cudaErrorInvalidValue, "block inverse: unsupported d"};
   }
 #undef MLMC_BI_CASE

@@ -7,6 +7,8 @@
 // vector blocks are [site][dof][k] with the k right-hand sides innermost, so
 // the k threads of one site read consecutive addresses and share the
 // coefficient loads through L1.
+#include <type_traits>
+
 #include "mlmc_internal.cuh"
 
 namespace mlmc {
@@ -21,35 +23,62 @@ __device__ inline void neighbours(int s, int nx, int ny, int nb[5]) {
 }
 
 // ------------------------------------------------------------------ apply / residual
-template <class T, int D>
-__global__ void k_stencil(const T *__restrict__ coef, const T *__restrict__ x, const T *__restrict__ b,
-                          T *__restrict__ y, int nx, int ny, int k, int mode) {
-  size_t total = (size_t)nx * ny * k;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    int c = (int)(t % k);
-    int s = (int)(t / k);
+// One thread per (site, VEC consecutive columns): the d x d coefficient blocks
+// are loaded once per VEC columns, the vector entries as 16-byte packs.
+template <class T, int VEC> struct alignas(sizeof(T) * VEC) Pack { T v[VEC]; };
+
+template <class T, int D, int VEC>
+__global__ void __launch_bounds__(256) k_stencil(const T *__restrict__ coef, const T *__restrict__ x,
+                                                 const T *__restrict__ b, T *__restrict__ y, int nx, int ny, int kv,
+                                                 int mode) {
+  typedef Pack<T, VEC> V;
+  const unsigned total = (unsigned)nx * ny * kv;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int s = (int)(t / (unsigned)kv);
+    const int c = (int)(t - (unsigned)s * kv);
     int nb[5];
     neighbours(s, nx, ny, nb);
-    T acc[D];
+    T acc[D][VEC];
 #pragma unroll
-    for (int r = 0; r < D; ++r) acc[r] = zero<T>();
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) acc[r][u] = zero<T>();
 #pragma unroll
     for (int dir = 0; dir < 5; ++dir) {
       const T *B = coef + ((size_t)s * 5 + dir) * D * D;
-      const T *xs = x + (size_t)nb[dir] * D * k + c;
+      const V *xs = (const V *)x + (size_t)nb[dir] * D * kv + c;
 #pragma unroll
       for (int q = 0; q < D; ++q) {
-        T xv = xs[(size_t)q * k];
+        V xv = xs[(size_t)q * kv];
 #pragma unroll
-        for (int r = 0; r < D; ++r) acc[r] = acc[r] + B[r * D + q] * xv;
+        for (int r = 0; r < D; ++r) {
+          T br = B[r * D + q];
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) acc[r][u] = acc[r][u] + br * xv.v[u];
+        }
       }
     }
-    size_t o = (size_t)s * D * k + c;
+    size_t o = (size_t)s * D * kv + c;
 #pragma unroll
-    for (int r = 0; r < D; ++r) y[o + (size_t)r * k] = mode ? b[o + (size_t)r * k] - acc[r] : acc[r];
+    for (int r = 0; r < D; ++r) {
+      V out;
+      if (mode) {
+        V bb = ((const V *)b)[o + (size_t)r * kv];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) out.v[u] = bb.v[u] - acc[r][u];
+      } else {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) out.v[u] = acc[r][u];
+      }
+      ((V *)y)[o + (size_t)r * kv] = out;
+    }
   }
 }
+
+// columns per thread for the generic kernels: 16-byte packs for FP32 data
+template <class T> struct gen_vec { static const int v = 1; };
+template <> struct gen_vec<float> { static const int v = 4; };
+template <> struct gen_vec<cfloat> { static const int v = 2; };
 
 #define MLMC_DDISPATCH(d, DD, ...)                       \
   switch (d) {                                           \
@@ -57,16 +86,152 @@ __global__ void k_stencil(const T *__restrict__ coef, const T *__restrict__ x, c
     case 2: { const int DD = 2; __VA_ARGS__; } break;    \
     case 4: { const int DD = 4; __VA_ARGS__; } break;    \
     case 8: { const int DD = 8; __VA_ARGS__; } break;    \
-    case 16: { const int DD = 16; __VA_ARGS__; } break;  \
     default: throw cuda_error{cudaErrorInvalidValue, "unsupported dofs per site"}; \
   }
 
+template <class T, int D>
+static void stencil_go(const StencilView &A, const void *x, const void *b, void *y, int k, int mode, cudaStream_t s) {
+  constexpr int VW = gen_vec<T>::v;
+  if (VW > 1 && k % VW == 0) {
+    int kv = k / VW;
+    unsigned g = grid_for((size_t)A.nx * A.ny * kv, 256, (size_t)1 << 20);
+    k_stencil<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, mode);
+  } else {
+    unsigned g = grid_for((size_t)A.nx * A.ny * k, 256, (size_t)1 << 20);
+    k_stencil<T, D, 1><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, k, mode);
+  }
+}
+
+// ------------------------------------------------------------------ Example 5.1, constant coefficients
+// y = diag x - (sum of the in-grid neighbours), VEC columns per thread with
+// 16-byte loads; grid.y = lattice row, so the +-y neighbours of a block are
+// the rows just touched by the blocks before it (L2 hits).
+template <class T, int VEC>
+__global__ void __launch_bounds__(256) k_laplace(const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ y,
+                                                 int nx, int ny, int kv, T diag, int periodic, int mode) {
+  typedef Pack<T, VEC> V;
+  const int j = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nx * kv) return;
+  const int i = t / kv, c = t - (t / kv) * kv;
+  const V *X = (const V *)x;
+  const int s = j * nx + i;
+  V xc = X[(size_t)s * kv + c];
+  T acc[VEC];
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) acc[u] = diag * xc.v[u];
+  int nbs[4];
+  int cnt = 0;
+  if (i + 1 < nx) nbs[cnt++] = s + 1; else if (periodic) nbs[cnt++] = j * nx;
+  if (i > 0) nbs[cnt++] = s - 1; else if (periodic) nbs[cnt++] = j * nx + nx - 1;
+  if (j + 1 < ny) nbs[cnt++] = s + nx; else if (periodic) nbs[cnt++] = i;
+  if (j > 0) nbs[cnt++] = s - nx; else if (periodic) nbs[cnt++] = (ny - 1) * nx + i;
+  for (int q = 0; q < cnt; ++q) {
+    V xn = X[(size_t)nbs[q] * kv + c];
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) acc[u] = acc[u] - xn.v[u];
+  }
+  V out;
+  if (mode) {
+    V bb = ((const V *)b)[(size_t)s * kv + c];
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) out.v[u] = bb.v[u] - acc[u];
+  } else {
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) out.v[u] = acc[u];
+  }
+  ((V *)y)[(size_t)s * kv + c] = out;
+}
+
+// Red-black Gauss-Seidel half-sweep for Example 5.1: x_s = (b_s + sum of neighbours) / diag
+// on the sites of `colour`.  other_zero = 1: the other colour holds zeros (not read).
+template <class T, int VEC>
+__global__ void __launch_bounds__(256) k_laplace_rbgs(T *__restrict__ x, const T *__restrict__ b, int nx, int ny,
+                                                      int kv, T dinv, int periodic, int colour, int other_zero) {
+  typedef Pack<T, VEC> V;
+  const int j = blockIdx.y;
+  const int hx = nx >> 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= hx * kv) return;
+  const int m = t / kv, c = t - (t / kv) * kv;
+  const int i = 2 * m + ((j + colour) & 1);
+  const int s = j * nx + i;
+  V *X = (V *)x;
+  V acc = ((const V *)b)[(size_t)s * kv + c];
+  if (!other_zero) {
+    int nbs[4];
+    int cnt = 0;
+    if (i + 1 < nx) nbs[cnt++] = s + 1; else if (periodic) nbs[cnt++] = j * nx;
+    if (i > 0) nbs[cnt++] = s - 1; else if (periodic) nbs[cnt++] = j * nx + nx - 1;
+    if (j + 1 < ny) nbs[cnt++] = s + nx; else if (periodic) nbs[cnt++] = i;
+    if (j > 0) nbs[cnt++] = s - nx; else if (periodic) nbs[cnt++] = (ny - 1) * nx + i;
+    for (int q = 0; q < cnt; ++q) {
+      V xn = X[(size_t)nbs[q] * kv + c];
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) acc.v[u] = acc.v[u] + xn.v[u];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) acc.v[u] = acc.v[u] * dinv;
+  X[(size_t)s * kv + c] = acc;
+}
+
+template <class T>
+static int laplace_vec(int k) {
+  const int v = 16 / (int)sizeof(T);
+  return k % v == 0 ? v : 1;
+}
+
+static void launch_laplace(const StencilView &A, const void *x, const void *b, void *y, int k, int mode,
+                           cudaStream_t s) {
+  auto go = [&](auto tag, auto vtag) {
+    typedef decltype(tag) T;
+    constexpr int VEC = decltype(vtag)::value;
+    int kv = k / VEC;
+    dim3 g((A.nx * kv + 255) / 256, A.ny);
+    k_laplace<T, VEC><<<g, 256, 0, s>>>((const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, (T)A.diag, A.periodic, mode);
+  };
+  if (A.t == F64) {
+    if (laplace_vec<double>(k) == 2) go(double(), std::integral_constant<int, 2>());
+    else go(double(), std::integral_constant<int, 1>());
+  } else if (A.t == F32) {
+    if (laplace_vec<float>(k) == 4) go(float(), std::integral_constant<int, 4>());
+    else go(float(), std::integral_constant<int, 1>());
+  } else {
+    throw cuda_error{cudaErrorInvalidValue, "constant-coefficient Laplacian is real"};
+  }
+  MLMC_LAUNCH_CHECK("k_laplace");
+}
+
+static void launch_laplace_rbgs(const StencilView &A, void *x, const void *b, int k, int colour, int other_zero,
+                                cudaStream_t s) {
+  auto go = [&](auto tag, auto vtag) {
+    typedef decltype(tag) T;
+    constexpr int VEC = decltype(vtag)::value;
+    int kv = k / VEC;
+    dim3 g(((A.nx / 2) * kv + 255) / 256, A.ny);
+    k_laplace_rbgs<T, VEC><<<g, 256, 0, s>>>((T *)x, (const T *)b, A.nx, A.ny, kv, (T)(1.0 / A.diag), A.periodic,
+                                             colour, other_zero);
+  };
+  if (A.t == F64) {
+    if (laplace_vec<double>(k) == 2) go(double(), std::integral_constant<int, 2>());
+    else go(double(), std::integral_constant<int, 1>());
+  } else if (A.t == F32) {
+    if (laplace_vec<float>(k) == 4) go(float(), std::integral_constant<int, 4>());
+    else go(float(), std::integral_constant<int, 1>());
+  } else {
+    throw cuda_error{cudaErrorInvalidValue, "constant-coefficient Laplacian is real"};
+  }
+  MLMC_LAUNCH_CHECK("k_laplace_rbgs");
+}
+
 void launch_stencil(const StencilView &A, const void *x, const void *b, void *y, int k, int mode,
                     cudaStream_t s) {
-  size_t total = (size_t)A.nx * A.ny * k;
-  unsigned g = grid_for(total, 256, (size_t)1 << 20);
-  MLMC_DISPATCH(A.t, T, MLMC_DDISPATCH(A.d, D,
-    k_stencil<T, D><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, k, mode)));
+  if (A.const_laplace) {
+    launch_laplace(A, x, b, y, k, mode, s);
+    return;
+  }
+  MLMC_DISPATCH(A.t, T, MLMC_DDISPATCH(A.d, D, stencil_go<T, D>(A, x, b, y, k, mode, s)));
   MLMC_LAUNCH_CHECK("k_stencil");
 }
 
@@ -74,159 +239,93 @@ void launch_stencil(const StencilView &A, const void *x, const void *b, void *y,
 // For every site s of colour `colour` ((i + j) % 2): x_s += D_s^{-1} (b - A x)_s.
 // Sites of one colour couple only to the other colour, so the half-sweep is
 // an exact block Gauss-Seidel step in red-black order (needs nx, ny even).
-template <class T, int D>
-__global__ void k_rbgs_half(const T *__restrict__ coef, const T *__restrict__ dinv, T *__restrict__ x,
-                            const T *__restrict__ b, int nx, int ny, int k, int colour) {
+template <class T, int D, int VEC>
+__global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, const T *__restrict__ dinv,
+                                                   T *__restrict__ x, const T *__restrict__ b, int nx, int ny, int kv,
+                                                   int colour) {
+  typedef Pack<T, VEC> V;
   int hx = nx / 2;
-  size_t total = (size_t)hx * ny * k;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    int c = (int)(t % k);
-    int idx = (int)(t / k);
+  const unsigned total = (unsigned)hx * ny * kv;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int idx = (int)(t / (unsigned)kv);
+    const int c = (int)(t - (unsigned)idx * kv);
     int j = idx / hx, m = idx % hx;
     int i = 2 * m + ((j + colour) & 1);
     int s = j * nx + i;
     int nb[5];
     neighbours(s, nx, ny, nb);
-    T res[D];
-    size_t o = (size_t)s * D * k + c;
+    T res[D][VEC];
+    size_t o = (size_t)s * D * kv + c;
 #pragma unroll
-    for (int r = 0; r < D; ++r) res[r] = b[o + (size_t)r * k];
+    for (int r = 0; r < D; ++r) {
+      V bb = ((const V *)b)[o + (size_t)r * kv];
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) res[r][u] = bb.v[u];
+    }
 #pragma unroll
     for (int dir = 0; dir < 5; ++dir) {
       const T *B = coef + ((size_t)s * 5 + dir) * D * D;
-      const T *xs = x + (size_t)nb[dir] * D * k + c;
+      const V *xs = (const V *)x + (size_t)nb[dir] * D * kv + c;
 #pragma unroll
       for (int q = 0; q < D; ++q) {
-        T xv = xs[(size_t)q * k];
+        V xv = xs[(size_t)q * kv];
 #pragma unroll
-        for (int r = 0; r < D; ++r) res[r] = res[r] - B[r * D + q] * xv;
+        for (int r = 0; r < D; ++r) {
+          T br = B[r * D + q];
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) res[r][u] = res[r][u] - br * xv.v[u];
+        }
       }
     }
     const T *Di = dinv + (size_t)s * D * D;
+    V *X = (V *)x;
 #pragma unroll
     for (int r = 0; r < D; ++r) {
-      T upd = zero<T>();
+      V cur = X[o + (size_t)r * kv];
 #pragma unroll
-      for (int q = 0; q < D; ++q) upd = upd + Di[r * D + q] * res[q];
-      x[o + (size_t)r * k] = x[o + (size_t)r * k] + upd;
+      for (int q = 0; q < D; ++q) {
+        T dq = Di[r * D + q];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) cur.v[u] = cur.v[u] + dq * res[q][u];
+      }
+      X[o + (size_t)r * kv] = cur;
     }
+  }
+}
+
+template <class T, int D>
+static void rbgs_go(const StencilView &A, void *x, const void *b, int k, int colour, cudaStream_t s) {
+  constexpr int VW = gen_vec<T>::v;
+  if (VW > 1 && k % VW == 0) {
+    int kv = k / VW;
+    unsigned g = grid_for((size_t)(A.nx / 2) * A.ny * kv, 256, (size_t)1 << 20);
+    k_rbgs_half<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny, kv, colour);
+  } else {
+    unsigned g = grid_for((size_t)(A.nx / 2) * A.ny * k, 256, (size_t)1 << 20);
+    k_rbgs_half<T, D, 1><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny, k, colour);
   }
 }
 
 void launch_rbgs_half(const StencilView &A, void *x, const void *b, int k, int colour, cudaStream_t s) {
-  size_t total = (size_t)(A.nx / 2) * A.ny * k;
-  unsigned g = grid_for(total, 256, (size_t)1 << 20);
-  MLMC_DISPATCH(A.t, T, MLMC_DDISPATCH(A.d, D,
-    k_rbgs_half<T, D><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny, k, colour)));
+  if (A.const_laplace) {
+    launch_laplace_rbgs(A, x, b, k, colour, 0, s);
+    return;
+  }
+  MLMC_DISPATCH(A.t, T, MLMC_DDISPATCH(A.d, D, rbgs_go<T, D>(A, x, b, k, colour, s)));
   MLMC_LAUNCH_CHECK("k_rbgs_half");
 }
 
-// ------------------------------------------------------------------ restriction / prolongation
-// rc[I][q][c] = sum_{loc,a} conj(P[I][loc*d + a][q]) r[site(I,loc)][a][c]
-template <class T, int DC>
-__global__ void k_restrict(const T *__restrict__ P, const T *__restrict__ r, T *__restrict__ rc, int nx,
-                           int ny, int d, int ax, int ay, int k) {
-  int ncx = nx / ax, ncy = ny / ay;
-  size_t total = (size_t)ncx * ncy * k;
-  int m = ax * ay * d;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    int c = (int)(t % k);
-    int I = (int)(t / k);
-    int bi = I % ncx, bj = I / ncx;
-    T acc[DC];
-#pragma unroll
-    for (int q = 0; q < DC; ++q) acc[q] = zero<T>();
-    const T *PI = P + (size_t)I * m * DC;
-    for (int jj = 0; jj < ay; ++jj)
-      for (int ii = 0; ii < ax; ++ii) {
-        int s = (bj * ay + jj) * nx + bi * ax + ii;
-        int loc = jj * ax + ii;
-        for (int a = 0; a < d; ++a) {
-          T xv = r[((size_t)s * d + a) * k + c];
-          const T *Pr = PI + (size_t)(loc * d + a) * DC;
-#pragma unroll
-          for (int q = 0; q < DC; ++q) acc[q] = acc[q] + conj(Pr[q]) * xv;
-        }
-      }
-#pragma unroll
-    for (int q = 0; q < DC; ++q) rc[((size_t)I * DC + q) * k + c] = acc[q];
+void launch_rbgs_sweep(const StencilView &A, void *x, const void *b, int k, int order, int x_zero,
+                       cudaStream_t s) {
+  int first = order == 0 ? 0 : 1;
+  if (A.const_laplace) {
+    launch_laplace_rbgs(A, x, b, k, first, x_zero, s);
+    launch_laplace_rbgs(A, x, b, k, 1 - first, 0, s);
+    return;
   }
-}
-
-// x[s][a][c] += sum_q P[I(s)][loc(s)*d + a][q] ec[I][q][c]
-template <class T, int DC>
-__global__ void k_prolong_add(const T *__restrict__ P, const T *__restrict__ ec, T *__restrict__ x, int nx,
-                              int ny, int d, int ax, int ay, int k) {
-  int ncx = nx / ax;
-  size_t total = (size_t)nx * ny * k;
-  int m = ax * ay * d;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    int c = (int)(t % k);
-    int s = (int)(t / k);
-    int i = s % nx, j = s / nx;
-    int I = (j / ay) * ncx + i / ax;
-    int loc = (j % ay) * ax + (i % ax);
-    T e[DC];
-#pragma unroll
-    for (int q = 0; q < DC; ++q) e[q] = ec[((size_t)I * DC + q) * k + c];
-    const T *PI = P + (size_t)I * m * DC;
-    for (int a = 0; a < d; ++a) {
-      const T *Pr = PI + (size_t)(loc * d + a) * DC;
-      T acc = zero<T>();
-#pragma unroll
-      for (int q = 0; q < DC; ++q) acc = acc + Pr[q] * e[q];
-      size_t o = ((size_t)s * d + a) * k + c;
-      x[o] = x[o] + acc;
-    }
-  }
-}
-
-void launch_restrict(const ProlongView &P, const void *r, void *rc, int k, cudaStream_t s) {
-  size_t total = (size_t)(P.nx / P.ax) * (P.ny / P.ay) * k;
-  unsigned g = grid_for(total, 128, (size_t)1 << 20);
-  MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC,
-    k_restrict<T, DC><<<g, 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d, P.ax, P.ay, k)));
-  MLMC_LAUNCH_CHECK("k_restrict");
-}
-
-void launch_prolong_add(const ProlongView &P, const void *ec, void *x, int k, cudaStream_t s) {
-  size_t total = (size_t)P.nx * P.ny * k;
-  unsigned g = grid_for(total, 256, (size_t)1 << 20);
-  MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC,
-    k_prolong_add<T, DC><<<g, 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx, P.ny, P.d, P.ax, P.ay, k)));
-  MLMC_LAUNCH_CHECK("k_prolong_add");
-}
-
-// ------------------------------------------------------------------ damped Jacobi update
-// out = base + omega * D^{-1} (rhs - y); D = diagonal entries of the self block.
-template <class T>
-__global__ void k_jacobi_update(const T *__restrict__ coef, T *out, const T *base, const T *rhs,
-                                const T *__restrict__ y, double omega, int nsite, int d, int k) {
-  size_t total = (size_t)nsite * d * k;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    size_t row = t / k;
-    int s = (int)(row / d), a = (int)(row % d);
-    T diag = coef[((size_t)s * 5) * d * d + a * d + a];
-    T yy = y ? y[t] : zero<T>();
-    T v = rhs ? rhs[t] - yy : -yy;
-    // v / diag = v * conj(diag) / |diag|^2
-    typedef typename real_of<T>::type R;
-    T q = rmul((R)(omega / (double)abs2(diag)), conj(diag) * v);
-    out[t] = base ? base[t] + q : q;
-  }
-}
-
-void launch_jacobi_update(const StencilView &A, void *out, const void *base, const void *rhs,
-                          const void *y, double omega, int k, cudaStream_t s) {
-  int nsite = A.nx * A.ny;
-  unsigned g = grid_for((size_t)nsite * A.d * k, 256, (size_t)1 << 20);
-  MLMC_DISPATCH(A.t, T, k_jacobi_update<T><<<g, 256, 0, s>>>((const T *)A.coef, (T *)out, (const T *)base,
-                                                             (const T *)rhs, (const T *)y, omega, nsite, A.d, k));
-  MLMC_LAUNCH_CHECK("k_jacobi_update");
+  if (x_zero) MLMC_CUDA(cudaMemsetAsync(x, 0, (size_t)A.nx * A.ny * A.d * k * dtype_size(A.t), s));
+  launch_rbgs_half(A, x, b, k, first, s);
+  launch_rbgs_half(A, x, b, k, 1 - first, s);
 }
 
 }  // namespace mlmc

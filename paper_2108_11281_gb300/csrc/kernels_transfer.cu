@@ -1,0 +1,121 @@
+// Aggregation transfers (restriction P^* r and prolongation x += P e, with
+// dense per-aggregate blocks) and the damped-Jacobi update of the setup filter.
+#include "mlmc_internal.cuh"
+
+namespace mlmc {
+
+#define MLMC_DDISPATCH(d, DD, ...)                       \
+  switch (d) {                                           \
+    case 1: { const int DD = 1; __VA_ARGS__; } break;    \
+    case 2: { const int DD = 2; __VA_ARGS__; } break;    \
+    case 4: { const int DD = 4; __VA_ARGS__; } break;    \
+    case 8: { const int DD = 8; __VA_ARGS__; } break;    \
+    default: throw cuda_error{cudaErrorInvalidValue, "unsupported dofs per site"}; \
+  }
+
+// ------------------------------------------------------------------ restriction / prolongation
+// rc[I][q][c] = sum_{loc,a} conj(P[I][loc*d + a][q]) r[site(I,loc)][a][c]
+template <class T, int DC>
+__global__ void k_restrict(const T *__restrict__ P, const T *__restrict__ r, T *__restrict__ rc, int nx,
+                           int ny, int d, int ax, int ay, int k) {
+  int ncx = nx / ax, ncy = ny / ay;
+  const unsigned total = (unsigned)ncx * ncy * k;
+  int m = ax * ay * d;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int I = (int)(t / (unsigned)k);
+    const int c = (int)(t - (unsigned)I * k);
+    int bi = I % ncx, bj = I / ncx;
+    T acc[DC];
+#pragma unroll
+    for (int q = 0; q < DC; ++q) acc[q] = zero<T>();
+    const T *PI = P + (size_t)I * m * DC;
+    for (int jj = 0; jj < ay; ++jj)
+      for (int ii = 0; ii < ax; ++ii) {
+        int s = (bj * ay + jj) * nx + bi * ax + ii;
+        int loc = jj * ax + ii;
+        for (int a = 0; a < d; ++a) {
+          T xv = r[((size_t)s * d + a) * k + c];
+          const T *Pr = PI + (size_t)(loc * d + a) * DC;
+#pragma unroll
+          for (int q = 0; q < DC; ++q) acc[q] = acc[q] + conj(Pr[q]) * xv;
+        }
+      }
+#pragma unroll
+    for (int q = 0; q < DC; ++q) rc[((size_t)I * DC + q) * k + c] = acc[q];
+  }
+}
+
+// x[s][a][c] += sum_q P[I(s)][loc(s)*d + a][q] ec[I][q][c]
+template <class T, int DC>
+__global__ void k_prolong_add(const T *__restrict__ P, const T *__restrict__ ec, T *__restrict__ x, int nx,
+                              int ny, int d, int ax, int ay, int k) {
+  int ncx = nx / ax;
+  const unsigned total = (unsigned)nx * ny * k;
+  int m = ax * ay * d;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int s = (int)(t / (unsigned)k);
+    const int c = (int)(t - (unsigned)s * k);
+    int i = s % nx, j = s / nx;
+    int I = (j / ay) * ncx + i / ax;
+    int loc = (j % ay) * ax + (i % ax);
+    T e[DC];
+#pragma unroll
+    for (int q = 0; q < DC; ++q) e[q] = ec[((size_t)I * DC + q) * k + c];
+    const T *PI = P + (size_t)I * m * DC;
+    for (int a = 0; a < d; ++a) {
+      const T *Pr = PI + (size_t)(loc * d + a) * DC;
+      T acc = zero<T>();
+#pragma unroll
+      for (int q = 0; q < DC; ++q) acc = acc + Pr[q] * e[q];
+      size_t o = ((size_t)s * d + a) * k + c;
+      x[o] = x[o] + acc;
+    }
+  }
+}
+
+void launch_restrict(const ProlongView &P, const void *r, void *rc, int k, cudaStream_t s) {
+  size_t total = (size_t)(P.nx / P.ax) * (P.ny / P.ay) * k;
+  unsigned g = grid_for(total, 128, (size_t)1 << 20);
+  MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC,
+    k_restrict<T, DC><<<g, 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d, P.ax, P.ay, k)));
+  MLMC_LAUNCH_CHECK("k_restrict");
+}
+
+void launch_prolong_add(const ProlongView &P, const void *ec, void *x, int k, cudaStream_t s) {
+  size_t total = (size_t)P.nx * P.ny * k;
+  unsigned g = grid_for(total, 256, (size_t)1 << 20);
+  MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC,
+    k_prolong_add<T, DC><<<g, 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx, P.ny, P.d, P.ax, P.ay, k)));
+  MLMC_LAUNCH_CHECK("k_prolong_add");
+}
+
+// ------------------------------------------------------------------ damped Jacobi update
+// out = base + omega * D^{-1} (rhs - y); D = diagonal entries of the self block.
+template <class T>
+__global__ void k_jacobi_update(const T *__restrict__ coef, T *out, const T *base, const T *rhs,
+                                const T *__restrict__ y, double omega, int nsite, int d, int k) {
+  size_t total = (size_t)nsite * d * k;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    size_t row = t / k;
+    int s = (int)(row / d), a = (int)(row % d);
+    T diag = coef[((size_t)s * 5) * d * d + a * d + a];
+    T yy = y ? y[t] : zero<T>();
+    T v = rhs ? rhs[t] - yy : -yy;
+    // v / diag = v * conj(diag) / |diag|^2
+    typedef typename real_of<T>::type R;
+    T q = rmul((R)(omega / (double)abs2(diag)), conj(diag) * v);
+    out[t] = base ? base[t] + q : q;
+  }
+}
+
+void launch_jacobi_update(const StencilView &A, void *out, const void *base, const void *rhs,
+                          const void *y, double omega, int k, cudaStream_t s) {
+  int nsite = A.nx * A.ny;
+  unsigned g = grid_for((size_t)nsite * A.d * k, 256, (size_t)1 << 20);
+  MLMC_DISPATCH(A.t, T, k_jacobi_update<T><<<g, 256, 0, s>>>((const T *)A.coef, (T *)out, (const T *)base,
+                                                             (const T *)rhs, (const T *)y, omega, nsite, A.d, k));
+  MLMC_LAUNCH_CHECK("k_jacobi_update");
+}
+
+}  // namespace mlmc

@@ -2,6 +2,8 @@
 // dot products (two-stage, fixed order), multi-AXPY and column scaling.
 // Vector blocks are [row][k] with the k columns (independent right-hand
 // sides / samples) innermost, so a warp touches consecutive columns of one row.
+#include <algorithm>
+
 #include "mlmc_internal.cuh"
 
 namespace mlmc {
@@ -130,9 +132,23 @@ void launch_fill_zero(DType t, void *dst, size_t count, cudaStream_t s) {
 
 // ------------------------------------------------------------------ column dots
 // Accumulation is in FP64 (double or cdouble) for every storage type.
+// Per-block partial sums are FP64 (double / cdouble) for every storage type;
+// each thread's own running sum uses the storage precision's ALU (`lane_of`),
+// since GB300's FP64 rate is a small fraction of its FP32 rate.
 template <class T> struct acc_of { typedef double type; };
 template <> struct acc_of<cdouble> { typedef cdouble type; };
 template <> struct acc_of<cfloat> { typedef cdouble type; };
+template <class T> struct lane_of { typedef T type; };
+__device__ inline float dotc_l(float a, float b) { return a * b; }
+__device__ inline double dotc_l(double a, double b) { return a * b; }
+__device__ inline cfloat dotc_l(cfloat a, cfloat b) { return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re}; }
+__device__ inline cdouble dotc_l(cdouble a, cdouble b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+__device__ inline double widen(float a) { return (double)a; }
+__device__ inline double widen(double a) { return a; }
+__device__ inline cdouble widen(cfloat a) { return {(double)a.re, (double)a.im}; }
+__device__ inline cdouble widen(cdouble a) { return a; }
 
 __device__ inline double dotc(double a, double b) { return a * b; }
 __device__ inline double dotc(float a, float b) { return (double)a * (double)b; }
@@ -171,21 +187,22 @@ __global__ void __launch_bounds__(DOT_THREADS) k_multidot_partial(const T *V, si
   size_t chunk = (rows + nparts - 1) / nparts;
   size_t r0 = (size_t)part * chunk, r1 = r0 + chunk < rows ? r0 + chunk : rows;
   for (int v0 = 0; v0 < nvec; v0 += DOT_MAXV) {
-    A acc[DOT_MAXV];
+    T acc[DOT_MAXV];
 #pragma unroll
-    for (int v = 0; v < DOT_MAXV; ++v) acc[v] = zero<A>();
+    for (int v = 0; v < DOT_MAXV; ++v) acc[v] = zero<T>();
     if (live) {
+#pragma unroll 4
       for (size_t r = r0 + slot; r < r1; r += slots) {
         T wv = w[r * k + col];
 #pragma unroll
         for (int v = 0; v < DOT_MAXV; ++v)
-          if (v0 + v < nvec) acc[v] = addd(acc[v], dotc(V[(size_t)(v0 + v) * vstride + r * k + col], wv));
+          if (v0 + v < nvec) acc[v] = acc[v] + dotc_l(V[(size_t)(v0 + v) * vstride + r * k + col], wv);
       }
     }
 #pragma unroll
     for (int v = 0; v < DOT_MAXV; ++v) {
       if (v0 + v >= nvec) break;
-      red[tid] = live ? acc[v] : zero<A>();
+      red[tid] = live ? widen(acc[v]) : zero<A>();
       __syncthreads();
       if (tid < k) {
         A s = red[tid];
@@ -197,14 +214,23 @@ __global__ void __launch_bounds__(DOT_THREADS) k_multidot_partial(const T *V, si
   }
 }
 
-// out[v][c] = sum_part partial[part][v][c], in part order
+// out[v][c] = sum_part partial[part][v][c]: one warp per output, lanes take
+// parts lane, lane+32, ... in order, then a fixed shuffle tree (deterministic).
+__device__ inline double shfl_add(double a, int o) { return a + __shfl_xor_sync(0xffffffffu, a, o); }
+__device__ inline cdouble shfl_add(cdouble a, int o) {
+  return {a.re + __shfl_xor_sync(0xffffffffu, a.re, o), a.im + __shfl_xor_sync(0xffffffffu, a.im, o)};
+}
+
 template <class A>
 __global__ void k_multidot_reduce(const A *partial, int nparts, int nvec, int k, A *out) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nvec * k) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nvec * k) return;
   A s = zero<A>();
-  for (int p = 0; p < nparts; ++p) s = addd(s, partial[(size_t)p * nvec * k + t]);
-  out[t] = s;
+  for (int p = lane; p < nparts; p += 32) s = addd(s, partial[(size_t)p * nvec * k + warp]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = shfl_add(s, o);
+  if (lane == 0) out[warp] = s;
 }
 
 void launch_multidot(DType t, const void *V, size_t vstride, int nvec, const void *w, size_t rows,
@@ -217,37 +243,59 @@ void launch_multidot(DType t, const void *V, size_t vstride, int nvec, const voi
                                                           (A *)partials);
     MLMC_LAUNCH_CHECK("k_multidot_partial");
     int tot = nvec * k;
-    k_multidot_reduce<A><<<(tot + 127) / 128, 128, 0, s>>>((const A *)partials, nparts, nvec, k, (A *)out);
+    k_multidot_reduce<A><<<(tot * 32 + 255) / 256, 256, 0, s>>>((const A *)partials, nparts, nvec, k, (A *)out);
     MLMC_LAUNCH_CHECK("k_multidot_reduce");
   });
 }
 
 // ------------------------------------------------------------------ multi-AXPY
 // w[r][c] += sign * sum_v V_v[r][c] * h[v*hstride + c]   (h is FP64 / complex FP64)
+// The grid is a multiple of k threads wide, so each thread keeps one column c
+// for its whole grid-stride loop (no per-element division).
 template <class T, class H>
-__global__ void k_multiaxpy(T *w, const T *V, size_t vstride, int nvec, const H *h, size_t hstride,
-                            double sign, size_t rows, int k) {
-  size_t total = rows * (size_t)k;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    int c = (int)(i % k);
-    H acc = zero<H>();
-    for (int v = 0; v < nvec; ++v)
-      acc = acc + cvt<H, T>(V[(size_t)v * vstride + i]) * h[(size_t)v * hstride + c];
-    w[i] = cvt<T, H>(cvt<H, T>(w[i]) + rmul(sign, acc));
+__global__ void __launch_bounds__(256) k_multiaxpy(T *__restrict__ w, const T *__restrict__ V, size_t vstride, int nvec,
+                                                   const H *__restrict__ h, size_t hstride, double sign, size_t total, int k) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const int c = (int)(t0 % k);
+  T hv[8];   // coefficients rounded to the storage precision: FP32 lanes for FP32 blocks
+  for (int v0 = 0; v0 < nvec; v0 += 8) {
+    const int nv = nvec - v0 < 8 ? nvec - v0 : 8;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) hv[v] = v < nv ? cvt<T, H>(rmul(sign, h[(size_t)(v0 + v) * hstride + c])) : zero<T>();
+    for (size_t i = t0; i < total; i += stride) {
+      T acc = w[i];
+#pragma unroll
+      for (int v = 0; v < 8; ++v)
+        if (v < nv) acc = acc + V[(size_t)(v0 + v) * vstride + i] * hv[v];
+      w[i] = acc;
+    }
   }
 }
 
+static unsigned column_grid(size_t total, int k) {
+  // threads = a multiple of k, about 4 waves of 152 SMs x 2048 threads at most
+  size_t want = (total + 255) / 256;
+  size_t cap = 152 * 8;
+  size_t g = want < cap ? want : cap;
+  if (g < 1) g = 1;
+  // round up so that g * 256 is a multiple of k
+  size_t per = (size_t)k / std::__gcd((size_t)k, (size_t)256);
+  g = ((g + per - 1) / per) * per;
+  return (unsigned)g;
+}
 
 void launch_multiaxpy(DType t, void *w, const void *V, size_t vstride, int nvec, const void *h,
                       DType h_t, size_t hstride, double sign, size_t rows, int k, cudaStream_t s) {
-  unsigned g = grid_for(rows * (size_t)k, 256);
+  size_t total = rows * (size_t)k;
+  unsigned g = column_grid(total, k);
   (void)h_t;
+  if (nvec <= 0) return;
   switch (t) {
-    case F64: k_multiaxpy<double, double><<<g, 256, 0, s>>>((double *)w, (const double *)V, vstride, nvec, (const double *)h, hstride, sign, rows, k); break;
-    case F32: k_multiaxpy<float, double><<<g, 256, 0, s>>>((float *)w, (const float *)V, vstride, nvec, (const double *)h, hstride, sign, rows, k); break;
-    case C64: k_multiaxpy<cdouble, cdouble><<<g, 256, 0, s>>>((cdouble *)w, (const cdouble *)V, vstride, nvec, (const cdouble *)h, hstride, sign, rows, k); break;
-    case C32: k_multiaxpy<cfloat, cdouble><<<g, 256, 0, s>>>((cfloat *)w, (const cfloat *)V, vstride, nvec, (const cdouble *)h, hstride, sign, rows, k); break;
+    case F64: k_multiaxpy<double, double><<<g, 256, 0, s>>>((double *)w, (const double *)V, vstride, nvec, (const double *)h, hstride, sign, total, k); break;
+    case F32: k_multiaxpy<float, double><<<g, 256, 0, s>>>((float *)w, (const float *)V, vstride, nvec, (const double *)h, hstride, sign, total, k); break;
+    case C64: k_multiaxpy<cdouble, cdouble><<<g, 256, 0, s>>>((cdouble *)w, (const cdouble *)V, vstride, nvec, (const cdouble *)h, hstride, sign, total, k); break;
+    case C32: k_multiaxpy<cfloat, cdouble><<<g, 256, 0, s>>>((cfloat *)w, (const cfloat *)V, vstride, nvec, (const cdouble *)h, hstride, sign, total, k); break;
   }
   MLMC_LAUNCH_CHECK("k_multiaxpy");
 }
@@ -255,19 +303,19 @@ void launch_multiaxpy(DType t, void *w, const void *V, size_t vstride, int nvec,
 // ------------------------------------------------------------------ column scaling
 // y[r][c] = x[r][c] * alpha[c]  (alpha real FP64)
 template <class T>
-__global__ void k_scale_cols(T *y, const T *x, const double *alpha, size_t rows, int k) {
-  size_t total = rows * (size_t)k;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    typedef typename real_of<T>::type R;
-    y[i] = rmul((R)alpha[i % k], x[i]);
-  }
+__global__ void __launch_bounds__(256) k_scale_cols(T *y, const T *x, const double *alpha, size_t total, int k) {
+  typedef typename real_of<T>::type R;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const R a = (R)alpha[t0 % k];
+  for (size_t i = t0; i < total; i += stride) y[i] = rmul(a, x[i]);
 }
 
 void launch_scale_cols(DType t, void *y, const void *x, const void *alpha, int, size_t rows, int k,
                        cudaStream_t s) {
-  unsigned g = grid_for(rows * (size_t)k, 256);
-  MLMC_DISPATCH(t, T, k_scale_cols<T><<<g, 256, 0, s>>>((T *)y, (const T *)x, (const double *)alpha, rows, k));
+  size_t total = rows * (size_t)k;
+  unsigned g = column_grid(total, k);
+  MLMC_DISPATCH(t, T, k_scale_cols<T><<<g, 256, 0, s>>>((T *)y, (const T *)x, (const double *)alpha, total, k));
   MLMC_LAUNCH_CHECK("k_scale_cols");
 }
 

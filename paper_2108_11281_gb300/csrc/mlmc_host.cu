@@ -89,6 +89,15 @@ struct CycleBufs {
   std::unique_ptr<Krylov> kcyc;   // K-cycle FGMRES on this level
 };
 
+// An instantiated CUDA graph of one fixed-length inner solve (level, width k,
+// network state), with the cost-model and launch counts it represents.
+struct GraphEntry {
+  int level = -1, k = 0, net = 0;
+  cudaGraphExec_t exec = nullptr;
+  double cost = 0.0;
+  uint64_t launches = 0;
+};
+
 }  // namespace
 
 struct mlmc_hierarchy {
@@ -100,10 +109,28 @@ struct mlmc_hierarchy {
   std::vector<Level> lv;
   std::vector<CycleBufs> cyc[2];                  // [0] FP64 cycle, [1] FP32 cycle
   std::vector<std::unique_ptr<Krylov>> outer;     // FP64 outer FGMRES per level
+  std::vector<std::unique_ptr<Krylov>> inner[2];  // fixed-length inner FGMRES per level, [0] FP64 [1] FP32
+  int const_laplace = 0, periodic = 0;
+  double laplace_diag = 4.0;
+  // learned correction on the fine level (FP32 cycle only)
+  int net_on = 0, net_c0 = 0, net_nw = 0, net_alloc_k = 0, net_step = 0, net_fallbacks = 0;
+  DevBuf netW, netG, netM, netV, netPart, act0, act1, act2, act3, g1, g2, lcol, lalpha;
+  DevBuf capture;
+  size_t capture_blocks = 0, capture_n = 0;
+  int capturing = 0;
+  // CUDA graphs of the inner solves; a private stream when the caller passes the legacy stream
+  std::vector<GraphEntry> graphs;
+  cudaStream_t own_stream = nullptr;
+  ~mlmc_hierarchy() {
+    for (auto &g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (own_stream) cudaStreamDestroy(own_stream);
+  }
   std::vector<DevBuf> xs, ys;                     // sample blocks per level (FP64)
   DevBuf dots, samples, acc, err, trace;
   uint64_t launches = 0;
-  double iters_accum[16] = {0}, solves_accum[16] = {0}, applies_accum[16] = {0};
+  double iters_accum[16] = {0}, solves_accum[16] = {0};
+  double cost = 0.0;   // Sec. 5 cost model: running sum of nnz(B) over products B x (per column)
 };
 
 namespace {
@@ -121,6 +148,9 @@ StencilView view(const H_t &h, int l, int lo) {
   v.t = lo ? h.t32 : h.t64;
   v.coef = lo ? L.coef32.p : L.coef64.p;
   v.dinv = lo ? L.dinv32.p : L.dinv64.p;
+  v.const_laplace = (l == 0 && h.const_laplace) ? 1 : 0;
+  v.diag = h.laplace_diag;
+  v.periodic = h.periodic;
   return v;
 }
 
@@ -170,22 +200,32 @@ int read_nactive(H_t &h, Krylov &K) {
   return *K.h_nactive;
 }
 
+// nnz of A_l: Example 5.1 (5n - 2nx - 2ny with Dirichlet), Example 5.3 (9 per row),
+// dense d x d blocks in 5 directions on coarse levels
+double nnz_of(const H_t &h, int l) {
+  const Level &L = h.lv[l];
+  if (l == 0 && h.const_laplace) return 5.0 * L.n - (h.periodic ? 0.0 : 2.0 * (L.nx + L.ny));
+  if (l == 0 && h.complex_op) return 9.0 * L.n;
+  return 5.0 * L.nsite * L.d * L.d;
+}
+
 void apply_op(H_t &h, int l, int lo, const void *x, void *y, int k) {
   launch_stencil(view(h, l, lo), x, nullptr, y, k, 0, h.stream);
   h.launches++;
-  if (!lo && l < 16) h.applies_accum[l] += k;
+  h.cost += nnz_of(h, l) * k;
 }
 
 void residual_op(H_t &h, int l, int lo, const void *x, const void *b, void *r, int k) {
   launch_stencil(view(h, l, lo), x, b, r, k, 1, h.stream);
   h.launches++;
-  if (!lo && l < 16) h.applies_accum[l] += k;
+  h.cost += nnz_of(h, l) * k;
 }
 
 void dense_apply(H_t &h, int lo, const void *b, void *x, int k) {
   const Level &C = h.lv[h.L - 1];
   launch_dense_apply(lo ? h.t32 : h.t64, lo ? C.Ainv32.p : C.Ainv64.p, b, x, (int)C.n, k, h.stream);
   h.launches++;
+  h.cost += (double)C.n * C.n * k;
 }
 
 void multidot(H_t &h, Krylov &K, const void *V, int nvec, const void *w, int k, void *out) {
@@ -272,6 +312,8 @@ int fgmres(H_t &h, Krylov &K, int l, int lo, const void *b, void *x, int k, doub
   }
 }
 
+void fine_hooks(H_t &h, void *x, const void *b, int k);
+
 // One multigrid cycle (Remark 4.1) on levels l..L in FP64 (lo = 0) or FP32 (lo = 1):
 // red-black block GS pre-smoothing from x = 0, residual, restriction, coarse
 // correction (dense inverse on level L, recursion for a V-cycle, or kcycle_its
@@ -287,18 +329,21 @@ void cycle(H_t &h, int lo, int l, const void *b, void *x, int k) {
   Level &Lv = h.lv[l];
   DType t = lo ? h.t32 : h.t64;
   size_t blk = Lv.n * (size_t)k;
+  (void)blk;
+  (void)t;
   CycleBufs &cb = h.cyc[lo][l];
   CycleBufs &cn = h.cyc[lo][l + 1];
-  launch_fill_zero(t, x, blk, s);
   StencilView A = view(h, l, lo);
+  if (h.prm.smooth_pre < 1) launch_fill_zero(t, x, blk, s);
   for (int it = 0; it < h.prm.smooth_pre; ++it) {
-    launch_rbgs_half(A, x, b, k, 0, s);
-    launch_rbgs_half(A, x, b, k, 1, s);
+    launch_rbgs_sweep(A, x, b, k, 0, it == 0, s);
     h.launches += 2;
+    h.cost += nnz_of(h, l) * k;
   }
   residual_op(h, l, lo, x, b, cb.r.p, k);
   launch_restrict(pview(h, l, lo), cb.r.p, cn.b.p, k, s);
   h.launches++;
+  h.cost += 2.0 * (double)Lv.n * Lv.dc * k;     // restriction and the prolongation below: nnz(P) each
   if (l + 1 == last) {
     dense_apply(h, lo, cn.b.p, cn.x.p, k);
   } else if (h.prm.cycle == MLMC_CYCLE_V) {
@@ -309,25 +354,83 @@ void cycle(H_t &h, int lo, int l, const void *b, void *x, int k) {
   }
   launch_prolong_add(pview(h, l, lo), cn.x.p, x, k, s);
   h.launches++;
+  if (l == 0 && lo == 1) fine_hooks(h, x, b, k);
   for (int it = 0; it < h.prm.smooth_post; ++it) {
-    launch_rbgs_half(A, x, b, k, 1, s);
-    launch_rbgs_half(A, x, b, k, 0, s);
+    launch_rbgs_sweep(A, x, b, k, 1, 0, s);
     h.launches += 2;
+    h.cost += nnz_of(h, l) * k;
   }
 }
 
-// FP64 preconditioner of the outer solve on level l: one cycle in FP64, or
-// (mixed) the same cycle in FP32 between two precision conversions.
-Precond outer_precond(H_t &h, int l, int k) {
-  if (h.prm.precision == MLMC_PREC_FP64) {
-    return [&h, l, k](const void *v, void *z) { cycle(h, 0, l, v, z, k); };
+// FP64 preconditioner of the outer solve on level l.  With inner_its > 0 it
+// is `inner_its` steps of FGMRES in the cycle precision preconditioned by the
+// cycle (no host synchronisation); else one cycle.  In the mixed form the
+// input is rounded to FP32 and the result widened back to FP64; the outer
+// FP64 FGMRES with its FP64 true residual recovers full accuracy.
+// Replays (capturing on first use) the inner solve on the fixed buffers
+// cyc[lo][l].b -> cyc[lo][l].x as one CUDA graph: it has no host
+// synchronisation, so the whole fixed-length FGMRES with its cycles is one launch.
+void inner_graph(H_t &h, int lo, int l, int k, const std::function<void()> &body) {
+  GraphEntry *ge = nullptr;
+  for (auto &g : h.graphs)
+    if (g.level == l && g.k == k && g.net == h.net_on && g.exec) ge = &g;
+  if (!ge) {
+    GraphEntry g;
+    g.level = l;
+    g.k = k;
+    g.net = h.net_on;
+    double c0 = h.cost;
+    uint64_t n0 = h.launches;
+    cudaGraph_t graph = nullptr;
+    check_cuda(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(h.stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    check_cuda(cudaStreamEndCapture(h.stream, &graph), "end capture");
+    cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    check_cuda(e, "graph instantiate");
+    g.cost = h.cost - c0;
+    g.launches = h.launches - n0;
+    h.cost = c0;
+    h.launches = n0;
+    h.graphs.push_back(g);
+    ge = &h.graphs.back();
   }
-  return [&h, l, k](const void *v, void *z) {
-    CycleBufs &cb = h.cyc[1][l];
+  check_cuda(cudaGraphLaunch(ge->exec, h.stream), "graph launch");
+  h.cost += ge->cost;
+  h.launches += ge->launches;
+}
+
+// FP64 preconditioner of the outer solve on level l.  With inner_its > 0 it
+// is `inner_its` steps of FGMRES in the cycle precision preconditioned by the
+// cycle (no host synchronisation, replayed as a CUDA graph); else one cycle.
+// In the mixed form the input is rounded to FP32 and the result widened back
+// to FP64; the outer FP64 FGMRES with its FP64 true residual recovers full
+// accuracy.
+Precond outer_precond(H_t &h, int l, int k) {
+  const int lo = h.prm.precision == MLMC_PREC_MIXED_FP32 ? 1 : 0;
+  const int nin = h.prm.inner_its;
+  auto inner = [&h, l, k, lo, nin](const void *b, void *x) {
+    if (nin > 0) {
+      Precond M = [&h, l, k, lo](const void *v, void *z) { cycle(h, lo, l, v, z, k); };
+      fgmres(h, *h.inner[lo][l], l, lo, b, x, k, 0.0, nin, nin, M, false, nullptr);
+    } else {
+      cycle(h, lo, l, b, x, k);
+    }
+  };
+  return [&h, l, k, lo, inner](const void *v, void *z) {
+    CycleBufs &cb = h.cyc[lo][l];
     size_t cnt = h.lv[l].n * (size_t)k;
-    launch_convert(h.t32, cb.b.p, h.t64, v, cnt, h.stream);
-    cycle(h, 1, l, cb.b.p, cb.x.p, k);
-    launch_convert(h.t64, z, h.t32, cb.x.p, cnt, h.stream);
+    DType t = lo ? h.t32 : h.t64;
+    launch_convert(t, cb.b.p, h.t64, v, cnt, h.stream);
+    if (h.prm.graphs && !h.capturing) inner_graph(h, lo, l, k, [&] { inner(cb.b.p, cb.x.p); });
+    else inner(cb.b.p, cb.x.p);
+    launch_convert(h.t64, z, t, cb.x.p, cnt, h.stream);
     h.launches += 2;
   };
 }
@@ -341,6 +444,14 @@ int solve_level(H_t &h, int l, const void *b, void *x, int k, double tol, bool *
   }
   int its = fgmres(h, *h.outer[l], l, 0, b, x, k, tol, 0, h.prm.max_iter, outer_precond(h, l, k),
                    h.prm.reorth != 0, conv);
+  if (conv && !*conv && h.net_on) {
+    // the plain smoother is the fallback: repeat the solve without the network
+    h.net_on = 0;
+    its += fgmres(h, *h.outer[l], l, 0, b, x, k, tol, 0, h.prm.max_iter, outer_precond(h, l, k),
+                  h.prm.reorth != 0, conv);
+    h.net_on = 1;
+    h.net_fallbacks++;
+  }
   if (l < 16) {
     h.iters_accum[l] += its;
     h.solves_accum[l] += 1;
@@ -349,6 +460,122 @@ int solve_level(H_t &h, int l, const void *b, void *x, int k, double tol, bool *
 }
 
 uint64_t key_hi(int purpose, int level) { return ((uint64_t)purpose << 8) | (uint64_t)level; }
+
+// ----------------------------------------------------------------- learned correction
+// Network c0 -> 16 -> 16 -> c0 (3x3 taps, ReLU, no bias) on the fine lattice,
+// FP32; weights concatenated [W1 | W2 | W3], each [c_out][c_in][3][3].
+const int NET_CH = 16;
+
+int net_weights(int c0) { return 9 * (NET_CH * c0 + NET_CH * NET_CH + c0 * NET_CH); }
+
+void net_alloc(H_t &h) {
+  const Level &F = h.lv[0];
+  if (h.net_c0 == 0) {
+    h.net_c0 = F.d * (h.complex_op ? 2 : 1);
+    h.net_nw = net_weights(h.net_c0);
+    h.netW.alloc(h.net_nw * sizeof(float));
+    h.netG.alloc(h.net_nw * sizeof(float));
+    h.netM.alloc(h.net_nw * sizeof(float));
+    h.netV.alloc(h.net_nw * sizeof(float));
+    h.netPart.alloc((size_t)conv_weight_blocks() * NET_CH * NET_CH * 9 * sizeof(float));
+    h.lcol.alloc(2 * (size_t)h.kmax * 16);
+    h.lalpha.alloc((size_t)h.kmax * sizeof(double));
+  }
+  if (h.net_alloc_k < h.kmax) {
+    size_t big = F.nsite * (size_t)NET_CH * h.kmax * sizeof(float);
+    size_t small = F.nsite * (size_t)h.net_c0 * h.kmax * sizeof(float);
+    h.act0.alloc(small);
+    h.act1.alloc(big);
+    h.act2.alloc(big);
+    h.act3.alloc(small);
+    h.g1.alloc(big);
+    h.g2.alloc(big);
+    h.net_alloc_k = h.kmax;
+  }
+}
+
+const float *netW1(H_t &h) { return h.netW.as<float>(); }
+const float *netW2(H_t &h) { return h.netW.as<float>() + 9 * NET_CH * h.net_c0; }
+const float *netW3(H_t &h) { return h.netW.as<float>() + 9 * (NET_CH * h.net_c0 + NET_CH * NET_CH); }
+
+// act3 = net(r) in channel layout; act0..act2 keep the activations
+void net_forward(H_t &h, const void *r, int k) {
+  const Level &F = h.lv[0];
+  cudaStream_t s = h.stream;
+  int per = h.periodic || h.complex_op;
+  launch_to_channels(h.t32, r, h.act0.as<float>(), (int)F.nsite, F.d, k, s);
+  launch_conv_fwd(h.net_c0, NET_CH, true, h.act0.as<float>(), netW1(h), h.act1.as<float>(), F.nx, F.ny, k, per, s);
+  launch_conv_fwd(NET_CH, NET_CH, true, h.act1.as<float>(), netW2(h), h.act2.as<float>(), F.nx, F.ny, k, per, s);
+  launch_conv_fwd(NET_CH, h.net_c0, false, h.act2.as<float>(), netW3(h), h.act3.as<float>(), F.nx, F.ny, k, per, s);
+  h.launches += 4;
+}
+
+// Loss mean_c ||A net(r_c) - r_c||^2 / ||r_c||^2 over the block and (grad = 1)
+// its weight gradients in netG.  Uses the FP32 cycle buffers of level 0 as scratch.
+double net_loss_grad(H_t &h, const void *r, int k, bool grad, bool read_loss) {
+  const Level &F = h.lv[0];
+  cudaStream_t s = h.stream;
+  int per = h.periodic || h.complex_op;
+  size_t cnt = F.n * (size_t)k;
+  void *E = h.cyc[1][0].x.p, *Tt = h.cyc[1][0].b.p;
+  net_forward(h, r, k);
+  launch_fill_zero(h.t32, E, cnt, s);
+  launch_add_from_channels(h.t32, E, h.act3.as<float>(), (int)F.nsite, F.d, k, s);
+  residual_op(h, 0, 1, E, r, Tt, k);                             // t = r - A e
+  Krylov &K = *h.outer[0];
+  const size_t as = acc_size(h);
+  char *nr2 = h.lcol.as<char>(), *nt2 = nr2 + (size_t)k * as;
+  launch_multidot(h.t32, r, cnt, 1, r, F.n, k, K.partials.p, multidot_parts(F.n, k), nr2, C64, s);
+  launch_multidot(h.t32, Tt, cnt, 1, Tt, F.n, k, K.partials.p, multidot_parts(F.n, k), nt2, C64, s);
+  h.launches += 6;
+  double loss = 0.0;
+  if (read_loss) {
+    std::vector<char> buf(2 * (size_t)k * as);
+    check_cuda(cudaMemcpyAsync(buf.data(), nr2, 2 * (size_t)k * as, cudaMemcpyDeviceToHost, s), "D2H loss");
+    check_cuda(cudaStreamSynchronize(s), "sync");
+    for (int c = 0; c < k; ++c) {
+      double a2 = *(double *)(buf.data() + c * as), t2 = *(double *)(buf.data() + (k + c) * as);
+      if (a2 > 0) loss += t2 / a2 / k;
+    }
+  }
+  if (!grad) return loss;
+  // g = -2 A^H t / (||r||^2 k);  A^H = J A J for the Wilson operator (J A = A^* J), A for the Laplacian
+  if (h.complex_op) launch_spin_flip(h.t32, Tt, (int)F.nsite, F.d, k, s);
+  apply_op(h, 0, 1, Tt, E, k);
+  if (h.complex_op) launch_spin_flip(h.t32, E, (int)F.nsite, F.d, k, s);
+  launch_col_factor(h.complex_op, nr2, h.lalpha.as<double>(), -2.0 / k, k, s);
+  launch_scale_cols(h.t32, E, E, h.lalpha.p, 0, F.n, k, s);
+  float *g3 = h.act3.as<float>();     // reuse: the output activations are no longer needed
+  launch_to_channels(h.t32, E, g3, (int)F.nsite, F.d, k, s);
+  float *G = h.netG.as<float>();
+  float *G1 = G, *G2 = G + 9 * NET_CH * h.net_c0, *G3 = G2 + 9 * NET_CH * NET_CH;
+  launch_conv_bwd_weight(NET_CH, h.net_c0, h.act2.as<float>(), g3, h.netPart.as<float>(), G3, 1.f, F.nx, F.ny, k, per, s);
+  launch_conv_bwd_data(NET_CH, h.net_c0, g3, netW3(h), h.act2.as<float>(), h.g2.as<float>(), F.nx, F.ny, k, per, s);
+  launch_conv_bwd_weight(NET_CH, NET_CH, h.act1.as<float>(), h.g2.as<float>(), h.netPart.as<float>(), G2, 1.f, F.nx, F.ny, k, per, s);
+  launch_conv_bwd_data(NET_CH, NET_CH, h.g2.as<float>(), netW2(h), h.act1.as<float>(), h.g1.as<float>(), F.nx, F.ny, k, per, s);
+  launch_conv_bwd_weight(h.net_c0, NET_CH, h.act0.as<float>(), h.g1.as<float>(), h.netPart.as<float>(), G1, 1.f, F.nx, F.ny, k, per, s);
+  h.launches += 16;
+  return loss;
+}
+
+// Fine-level hooks of the FP32 cycle, after the coarse-grid correction:
+// capture the residual (training data) and/or apply x += net(b - A x).
+void fine_hooks(H_t &h, void *x, const void *b, int k) {
+  if (h.capturing && h.capture_n < h.capture_blocks && k == h.kmax) {
+    const Level &F = h.lv[0];
+    char *slot = h.capture.as<char>() + h.capture_n * F.n * (size_t)k * dtype_size(h.t32);
+    residual_op(h, 0, 1, x, b, slot, k);
+    h.capture_n++;
+  }
+  if (h.net_on) {
+    const Level &F = h.lv[0];
+    void *r = h.cyc[1][0].r.p;
+    residual_op(h, 0, 1, x, b, r, k);
+    net_forward(h, r, k);
+    launch_add_from_channels(h.t32, x, h.act3.as<float>(), (int)F.nsite, F.d, k, h.stream);
+    h.launches++;
+  }
+}
 
 // ----------------------------------------------------------------- setup
 void filter(H_t &h, int l, void *V, void *tmp, void *tmp2, int ntv, int kind, int sweeps, double omega) {
@@ -455,8 +682,11 @@ void validate(const mlmc_operator_desc *op, const mlmc_hierarchy_params *p) {
   if (p->max_iter < 1) fail(MLMC_ERR_INVALID_ARG, "max_iter must be positive");
   if (p->cycle == MLMC_CYCLE_K && (p->kcycle_its < 1 || p->kcycle_its > 8))
     fail(MLMC_ERR_INVALID_ARG, "kcycle_its must be in 1..8");
+  if (p->inner_its < 0 || p->inner_its > 32) fail(MLMC_ERR_INVALID_ARG, "inner_its must be in 0..32");
   if (p->precision != MLMC_PREC_FP64 && p->precision != MLMC_PREC_MIXED_FP32)
     fail(MLMC_ERR_INVALID_ARG, "unknown precision");
+  if ((double)op->nx * op->ny * (op->kind == MLMC_OP_WILSON2D ? 2 : 1) * p->block >= 2147483648.0)
+    fail(MLMC_ERR_UNSUPPORTED, "n * block must stay below 2^31 (32-bit kernel indexing)");
   long nx = op->nx, ny = op->ny;
   for (int l = 0; l + 1 < p->levels; ++l) {
     if (nx % p->agg_x || ny % p->agg_y) fail(MLMC_ERR_INVALID_ARG, "lattice not divisible by the aggregates");
@@ -465,16 +695,25 @@ void validate(const mlmc_operator_desc *op, const mlmc_hierarchy_params *p) {
     ny /= p->agg_y;
   }
   int dc = p->n_tv * (p->spin_split ? 2 : 1);
-  if (dc != 1 && dc != 2 && dc != 4 && dc != 8 && dc != 16)
-    fail(MLMC_ERR_UNSUPPORTED, "coarse dofs per site must be 1, 2, 4, 8 or 16");
+  if (dc != 1 && dc != 2 && dc != 4 && dc != 8)
+    fail(MLMC_ERR_UNSUPPORTED, "coarse dofs per site must be 1, 2, 4 or 8");
   if (nx * ny * dc > 8192) fail(MLMC_ERR_INVALID_ARG, "coarsest level larger than 8192 unknowns");
 }
 
 void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p, cudaStream_t stream) {
   validate(op, p);
+  if (!stream) {
+    // stream capture is not allowed on the legacy default stream: use a private
+    // blocking stream (ordered with the legacy stream; every call synchronises it)
+    check_cuda(cudaStreamCreate(&h.own_stream), "stream create");
+    stream = h.own_stream;
+  }
   h.stream = stream;
   h.prm = *p;
   h.complex_op = op->kind == MLMC_OP_WILSON2D;
+  h.const_laplace = op->kind == MLMC_OP_LAPLACE2D;
+  h.periodic = op->periodic ? 1 : 0;
+  h.laplace_diag = 4.0 + op->shift;
   h.t64 = h.complex_op ? C64 : F64;
   h.t32 = h.complex_op ? C32 : F32;
   h.L = p->levels;
@@ -536,6 +775,12 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
     if (l + 1 < h.L) {
       h.outer[l].reset(new Krylov());
       alloc_krylov(h, *h.outer[l], h.t64, h.lv[l].n, k, p->fgmres_restart);
+      if (p->inner_its > 0) {
+        int lo = mixed ? 1 : 0;
+        h.inner[lo].resize(h.L);
+        h.inner[lo][l].reset(new Krylov());
+        alloc_krylov(h, *h.inner[lo][l], lo ? h.t32 : h.t64, h.lv[l].n, k, p->inner_its);
+      }
     }
   }
   h.dots.alloc(2 * (size_t)k * 16);
@@ -784,11 +1029,13 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
     if (!(p->eps > 0.0) || !(p->tol > 0.0)) fail(MLMC_ERR_INVALID_ARG, "eps and tol must be positive");
     if (p->form != MLMC_FORM_SIMPLIFIED) fail(MLMC_ERR_UNSUPPORTED, "only the simplified form (Remark 4.3) is built");
     if (p->noise == MLMC_NOISE_Z4 && !h->complex_op) fail(MLMC_ERR_INVALID_ARG, "Z4 noise needs a complex operator");
+    if (p->allocation != MLMC_ALLOC_RHO && p->allocation != MLMC_ALLOC_OPTIMAL)
+      fail(MLMC_ERR_INVALID_ARG, "unknown allocation");
     H_t &H = *h;
     const int L = H.L, nd = L - 1;
     std::memset(r, 0, sizeof(*r));
     r->levels = L;
-    for (int l = 0; l < 16; ++l) H.iters_accum[l] = H.solves_accum[l] = H.applies_accum[l] = 0.0;
+    for (int l = 0; l < 16; ++l) H.iters_accum[l] = H.solves_accum[l] = 0.0;
     auto t0 = std::chrono::steady_clock::now();
     mlmc_c64 TL;
     {
@@ -799,6 +1046,8 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
       check_cuda(cudaStreamSynchronize(H.stream), "sync");
     }
     r->coarse_term = TL;
+    // Remark 4.2 cost of the exact term: inversion of A_L (n_L^3)
+    r->cost_nnz[nd] = std::pow((double)H.lv[L - 1].n, 3.0);
     // five warm-up estimates from the warm-up stream (Sec. 5)
     std::vector<mlmc_c64> tmp(std::max(5, H.kmax));
     double warm[5];
@@ -820,52 +1069,97 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
     for (double v : warm) ms += (v - mean) * (v - mean) / 5.0;
     double tau = mean - std::sqrt(ms);
     r->tau = tau;
-    double wsum = 0.0;
-    for (int l = 0; l < nd; ++l) wsum += p->weights[l];
+    const double target = p->eps * std::fabs(tau);            // standard error of the estimate
     const int minN = p->min_samples > 0 ? p->min_samples : 5;
     const int maxN = p->max_samples > 0 ? p->max_samples : (1 << 24);
+    // per-level state: accumulators live on the device ({N, mean re, mean im, M2} x levels)
+    DevBuf accs;
+    accs.alloc((size_t)nd * 4 * sizeof(double));
+    check_cuda(cudaMemsetAsync(accs.p, 0, (size_t)nd * 4 * sizeof(double), H.stream), "memset acc");
+    std::vector<double> st((size_t)nd * 4, 0.0), cost(nd, 0.0), secs(nd, 0.0);
+    auto draw = [&](int l) {   // one block of samples on level difference l
+      auto tl = std::chrono::steady_clock::now();
+      double c0 = H.cost;
+      int k = std::min(H.kmax, maxN - (int)st[4 * l]);
+      if (k <= 0) return false;
+      bool conv = true;
+      sample_block(H, l, p->noise, p->seed, (uint64_t)st[4 * l], k, p->tol, MLMC_PURPOSE_NOISE, &conv);
+      if (!conv) fail(MLMC_ERR_NOT_CONVERGED, "level solve did not converge");
+      launch_accumulate(H.samples.p, k, accs.as<double>() + 4 * l, H.stream);
+      H.launches++;
+      check_cuda(cudaMemcpyAsync(&st[4 * l], accs.as<double>() + 4 * l, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 H.stream), "D2H acc");
+      check_cuda(cudaStreamSynchronize(H.stream), "sync");
+      cost[l] += H.cost - c0;
+      secs[l] += std::chrono::duration<double>(std::chrono::steady_clock::now() - tl).count();
+      return true;
+    };
+    auto var = [&](int l) { double N = st[4 * l]; return N > 1 ? st[4 * l + 3] / (N - 1) : INFINITY; };
+    std::vector<double> w(nd, 0.0);
+    if (p->allocation == MLMC_ALLOC_RHO) {
+      // Sec. 5: rho_l = sqrt(w_l) eps |tau|; sample each level until its standard error meets rho_l
+      double wsum = 0.0;
+      for (int l = 0; l < nd; ++l) wsum += p->weights[l];
+      for (int l = 0; l < nd; ++l) {
+        w[l] = wsum > 0.0 ? p->weights[l] / wsum : 1.0 / nd;
+        double rho = std::sqrt(w[l]) * target;
+        while (draw(l)) {
+          double N = st[4 * l];
+          if (N >= minN && std::sqrt(var(l) / N) <= rho) break;
+        }
+      }
+    } else {
+      // Sec. 2: minimise sum N_l C_l subject to sum V_l / N_l = (eps tau)^2, i.e.
+      // N_l = (eps tau)^-2 sqrt(V_l / C_l) sum_j sqrt(V_j C_j), with V_l and C_l (cost
+      // model per sample) estimated from the samples drawn so far; one pilot block per level.
+      for (int l = 0; l < nd; ++l) draw(l);
+      for (int round = 0; round < 100000; ++round) {
+        double S = 0.0;
+        for (int l = 0; l < nd; ++l) S += std::sqrt(var(l) * cost[l] / st[4 * l]);
+        bool more = false;
+        double tot = 0.0;
+        for (int l = 0; l < nd; ++l) {
+          double Cl = cost[l] / st[4 * l];
+          double want = std::max((double)minN, std::ceil(std::sqrt(var(l) / Cl) * S / (target * target)));
+          w[l] = std::sqrt(var(l) * Cl) / S;
+          tot += var(l) / st[4 * l];
+          if (st[4 * l] < want && st[4 * l] < maxN) {
+            more = true;
+            draw(l);
+          }
+        }
+        if (!more && tot <= target * target) break;
+        if (!more) {             // variances grew: add a block where it reduces the variance most per cost
+          int best = 0;
+          double gain = -1.0;
+          for (int l = 0; l < nd; ++l) {
+            double N = st[4 * l], k = std::min(H.kmax, maxN - (int)N);
+            if (k <= 0) continue;
+            double g = (var(l) / N - var(l) / (N + k)) / (cost[l] / N * k);
+            if (g > gain) { gain = g; best = l; }
+          }
+          if (gain < 0.0) break;
+          draw(best);
+        }
+      }
+    }
     double var_sum = 0.0;
     mlmc_c64 total = TL;
     for (int l = 0; l < nd; ++l) {
-      double w = wsum > 0.0 ? p->weights[l] : 1.0 / nd;
-      double rho = std::sqrt(w) * p->eps * std::fabs(tau);
-      auto tl = std::chrono::steady_clock::now();
-      check_cuda(cudaMemsetAsync(H.acc.p, 0, 4 * sizeof(double), H.stream), "memset acc");
-      double acc[4] = {0, 0, 0, 0};
-      for (;;) {
-        int k = std::min(H.kmax, maxN - (int)acc[0]);
-        if (k <= 0) break;
-        bool conv = true;
-        sample_block(H, l, p->noise, p->seed, (uint64_t)acc[0], k, p->tol, MLMC_PURPOSE_NOISE, &conv);
-        if (!conv) fail(MLMC_ERR_NOT_CONVERGED, "level solve did not converge");
-        launch_accumulate(H.samples.p, k, H.acc.as<double>(), H.stream);
-        H.launches++;
-        check_cuda(cudaMemcpyAsync(acc, H.acc.p, sizeof(acc), cudaMemcpyDeviceToHost, H.stream), "D2H acc");
-        check_cuda(cudaStreamSynchronize(H.stream), "sync");
-        double N = acc[0];
-        double var = N > 1 ? acc[3] / (N - 1) : INFINITY;
-        if (N >= minN && std::sqrt(var / N) <= rho) break;
-      }
-      double N = acc[0];
-      double var = N > 1 ? acc[3] / (N - 1) : 0.0;
+      double N = st[4 * l];
+      double v = N > 1 ? st[4 * l + 3] / (N - 1) : 0.0;
       r->n_samples[l] = (int)N;
-      r->mean[l].re = acc[1];
-      r->mean[l].im = acc[2];
-      r->variance[l] = var;
-      r->seconds[l] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tl).count();
-      total.re += acc[1];
-      total.im += acc[2];
-      if (N > 0) var_sum += var / N;
-    }
-    for (int l = 0; l < nd && l < 16; ++l) {
+      r->mean[l].re = st[4 * l + 1];
+      r->mean[l].im = st[4 * l + 2];
+      r->variance[l] = v;
+      r->seconds[l] = secs[l];
+      r->cost_nnz[l] = cost[l];
+      r->weights_used[l] = w[l];
+      total.re += st[4 * l + 1];
+      total.im += st[4 * l + 2];
+      if (N > 0) var_sum += v / N;
       double solves = H.solves_accum[l];
       r->iters[l] = solves > 0 ? H.iters_accum[l] / solves : 0.0;
-    }
-    // cost model (Sec. 5): nnz-weighted operator products per level
-    for (int l = 0; l < L && l < 16; ++l) {
-      const Level &Lv = H.lv[l];
-      double nnz = (double)Lv.nsite * 5.0 * Lv.d * Lv.d;
-      r->cost_nnz[l] = H.applies_accum[l] * nnz;
     }
     r->trace = total;
     r->std_err = std::sqrt(var_sum);
@@ -880,8 +1174,9 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
     if (k < 1 || k > h->kmax || reps < 1) fail(MLMC_ERR_INVALID_ARG, "bad k or reps");
     H_t &H = *h;
     int l = level - 1;
-    int lo = which == 1 ? 1 : (which == 2 ? (H.prm.precision == MLMC_PREC_MIXED_FP32) : 0);
-    if (lo && H.prm.precision != MLMC_PREC_MIXED_FP32) fail(MLMC_ERR_INVALID_ARG, "FP32 kernels need the mixed form");
+    int lo = which == 0 ? 0 : (H.prm.precision == MLMC_PREC_MIXED_FP32 ? 1 : 0);
+    if (which == 1 && !lo) fail(MLMC_ERR_INVALID_ARG, "FP32 kernels need the mixed form");
+    if (which < 0 || which > 4) fail(MLMC_ERR_INVALID_ARG, "unknown kernel family");
     if (which == 2 && l == H.L - 1) fail(MLMC_ERR_INVALID_ARG, "no smoother on the coarsest level");
     const Level &Lv = H.lv[l];
     DType t = lo ? H.t32 : H.t64;
@@ -893,10 +1188,25 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
     cudaEvent_t e0, e1;
     check_cuda(cudaEventCreate(&e0), "event");
     check_cuda(cudaEventCreate(&e1), "event");
+    const int nvec = 4;      // which 3 / 4: basis vectors of a mid-length inner Arnoldi step
+    DevBuf Vb, part, outb;
+    if (which >= 3) {
+      Vb.alloc((size_t)nvec * Lv.n * k * es);
+      for (int v = 0; v < nvec; ++v)
+        launch_noise(H.complex_op, 2 + v, 0, 0, Lv.n, k, t, Vb.as<char>() + (size_t)v * Lv.n * k * es, H.stream);
+      part.alloc((size_t)multidot_parts(Lv.n, k) * nvec * k * 16);
+      outb.alloc((size_t)nvec * k * 16);
+      launch_fill_zero(F64, outb.p, (size_t)nvec * k * (H.complex_op ? 2 : 1), H.stream);
+    }
     auto body = [&] {
       if (which == 2) {
-        launch_rbgs_half(view(H, l, lo), y, x, k, 0, H.stream);
-        launch_rbgs_half(view(H, l, lo), y, x, k, 1, H.stream);
+        launch_rbgs_sweep(view(H, l, lo), y, x, k, 0, 0, H.stream);
+      } else if (which == 3) {
+        launch_multidot(t, Vb.p, Lv.n * (size_t)k, nvec, x, Lv.n, k, part.p, multidot_parts(Lv.n, k), outb.p,
+                        H.complex_op ? C64 : F64, H.stream);
+      } else if (which == 4) {
+        launch_multiaxpy(t, y, Vb.p, Lv.n * (size_t)k, nvec, outb.p, H.complex_op ? C64 : F64, k, -1e-30, Lv.n, k,
+                         H.stream);
       } else {
         launch_stencil(view(H, l, lo), x, nullptr, y, k, 0, H.stream);
       }
@@ -914,7 +1224,11 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
     bool const_coef = l == 0 && !H.complex_op;      // Example 5.1 stencil has no matrix to read
     double coefb = const_coef ? 0.0 : (double)Lv.nsite * 5 * Lv.d * Lv.d * es;
     double bytes;
-    if (which == 2) {
+    if (which == 3 || which == 4) {
+      // multi-dot reads nvec basis blocks and w; multi-AXPY also writes w
+      bytes = (which == 3 ? nvec + 1.0 : nvec + 2.0) * vec;
+      if (ms_per_launch) *ms_per_launch = ms / reps;
+    } else if (which == 2) {
       // one sweep = two half-sweeps: each reads b and x on its colour, the
       // other colour's x as neighbours, writes x on its colour: 2 passes over
       // x plus b, plus the coefficient and inverse blocks
@@ -926,6 +1240,138 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
       if (ms_per_launch) *ms_per_launch = ms / reps;
     }
     if (bytes_per_launch) *bytes_per_launch = bytes;
+  });
+}
+
+int mlmc_learned_set(mlmc_hierarchy *h, const float *weights, int enable) {
+  return translate([&] {
+    need(h);
+    if (h->prm.precision != MLMC_PREC_MIXED_FP32) fail(MLMC_ERR_UNSUPPORTED, "the learned correction runs in the mixed form");
+    net_alloc(*h);
+    if (weights)
+      check_cuda(cudaMemcpyAsync(h->netW.p, weights, h->net_nw * sizeof(float), cudaMemcpyHostToDevice, h->stream), "H2D W");
+    check_cuda(cudaStreamSynchronize(h->stream), "sync");
+    h->net_on = enable ? 1 : 0;
+  });
+}
+
+int mlmc_learned_apply(mlmc_hierarchy *h, const void *r, void *e, int k) {
+  return translate([&] {
+    need(h);
+    if (h->prm.precision != MLMC_PREC_MIXED_FP32) fail(MLMC_ERR_UNSUPPORTED, "the learned correction runs in the mixed form");
+    if (!r || !e || k < 1 || k > h->kmax) fail(MLMC_ERR_INVALID_ARG, "bad block");
+    net_alloc(*h);
+    const Level &F = h->lv[0];
+    net_forward(*h, r, k);
+    launch_fill_zero(h->t32, e, F.n * (size_t)k, h->stream);
+    launch_add_from_channels(h->t32, e, h->act3.as<float>(), (int)F.nsite, F.d, k, h->stream);
+    check_cuda(cudaStreamSynchronize(h->stream), "sync");
+  });
+}
+
+int mlmc_learned_grad(mlmc_hierarchy *h, const void *r, int k, double *loss, float *grad_out) {
+  return translate([&] {
+    need(h);
+    if (h->prm.precision != MLMC_PREC_MIXED_FP32) fail(MLMC_ERR_UNSUPPORTED, "the learned correction runs in the mixed form");
+    if (!r || k < 1 || k > h->kmax) fail(MLMC_ERR_INVALID_ARG, "bad block");
+    net_alloc(*h);
+    double l = net_loss_grad(*h, r, k, true, true);
+    if (loss) *loss = l;
+    if (grad_out)
+      check_cuda(cudaMemcpyAsync(grad_out, h->netG.p, h->net_nw * sizeof(float), cudaMemcpyDeviceToHost, h->stream), "D2H G");
+    check_cuda(cudaStreamSynchronize(h->stream), "sync");
+  });
+}
+
+int mlmc_learned_train(mlmc_hierarchy *h, const mlmc_train_params *p, float *weights_out, mlmc_train_report *rep) {
+  return translate([&] {
+    need(h);
+    if (!p) fail(MLMC_ERR_INVALID_ARG, "null training parameters");
+    if (h->prm.precision != MLMC_PREC_MIXED_FP32) fail(MLMC_ERR_UNSUPPORTED, "the learned correction runs in the mixed form");
+    if (p->n_pairs < 2 || p->epochs < 1 || !(p->lr > 0.0) || !(p->tol > 0.0)) fail(MLMC_ERR_INVALID_ARG, "bad training parameters");
+    H_t &H = *h;
+    net_alloc(H);
+    const Level &F = H.lv[0];
+    const int k = H.kmax;
+    cudaStream_t s = H.stream;
+    mlmc_train_report R;
+    std::memset(&R, 0, sizeof(R));
+    R.n_weights = H.net_nw;
+    // 1) residual/error pairs from plain solves (net off)
+    auto t0 = std::chrono::steady_clock::now();
+    size_t blocks = ((size_t)p->n_pairs + k - 1) / k;
+    if (blocks < 2) blocks = 2;
+    H.capture.alloc(blocks * F.n * (size_t)k * dtype_size(H.t32));
+    H.capture_blocks = blocks;
+    H.capture_n = 0;
+    int was_on = H.net_on;
+    H.net_on = 0;
+    H.capturing = 1;
+    for (uint64_t solve = 0; H.capture_n < H.capture_blocks && solve < 100000; ++solve) {
+      launch_noise(H.complex_op ? 1 : 0, p->seed, key_hi(MLMC_PURPOSE_TRAIN, 1), solve * k, F.n, k, H.t64, H.xs[0].p, s);
+      bool conv = true;
+      solve_level(H, 0, H.xs[0].p, H.ys[0].p, k, p->tol, &conv);
+    }
+    H.capturing = 0;
+    check_cuda(cudaStreamSynchronize(s), "sync");
+    R.seconds_capture = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    R.blocks = (int)blocks;
+    R.pairs = (int)(blocks * k);
+    // 2) initial weights
+    if (p->init_weights) {
+      check_cuda(cudaMemcpyAsync(H.netW.p, p->init_weights, H.net_nw * sizeof(float), cudaMemcpyHostToDevice, s), "H2D W");
+    } else {
+      // Rademacher signs (Philox, purpose TRAIN, level 0) scaled by sqrt(2 / fan_in) / 2 per layer
+      DevBuf tmp;
+      tmp.alloc(H.net_nw * sizeof(double));
+      launch_noise(0, p->seed, key_hi(MLMC_PURPOSE_TRAIN, 0), 0, (size_t)H.net_nw, 1, F64, tmp.p, s);
+      std::vector<double> hw(H.net_nw);
+      check_cuda(cudaMemcpyAsync(hw.data(), tmp.p, H.net_nw * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+      check_cuda(cudaStreamSynchronize(s), "sync");
+      std::vector<float> w(H.net_nw);
+      int c0 = H.net_c0;
+      int n1 = 9 * NET_CH * c0, n2 = 9 * NET_CH * NET_CH;
+      for (int i = 0; i < H.net_nw; ++i) {
+        int fan_in = i < n1 ? 9 * c0 : 9 * NET_CH;
+        (void)n2;
+        w[i] = (float)(hw[i] * 0.5 * std::sqrt(2.0 / fan_in));
+      }
+      check_cuda(cudaMemcpyAsync(H.netW.p, w.data(), H.net_nw * sizeof(float), cudaMemcpyHostToDevice, s), "H2D W");
+    }
+    check_cuda(cudaMemsetAsync(H.netM.p, 0, H.net_nw * sizeof(float), s), "memset");
+    check_cuda(cudaMemsetAsync(H.netV.p, 0, H.net_nw * sizeof(float), s), "memset");
+    H.net_step = 0;
+    // 3) Adam over the training blocks; the last block (at least 10%) is held out
+    size_t nval = std::max<size_t>(1, blocks / 10);
+    size_t ntrain = blocks - nval;
+    auto blk = [&](size_t i) { return H.capture.as<char>() + i * F.n * (size_t)k * dtype_size(H.t32); };
+    auto t1 = std::chrono::steady_clock::now();
+    for (int ep = 0; ep < p->epochs; ++ep) {
+      double sum = 0.0;
+      for (size_t i = 0; i < ntrain; ++i) {
+        bool rd = (ep == 0 || ep == p->epochs - 1);
+        sum += net_loss_grad(H, blk(i), k, true, rd);
+        launch_adam(H.netW.as<float>(), H.netG.as<float>(), H.netM.as<float>(), H.netV.as<float>(), H.net_nw,
+                    (float)p->lr, ++H.net_step, s);
+        H.launches++;
+      }
+      if (ep == 0) R.loss_first = sum / ntrain;
+      if (ep == p->epochs - 1) R.loss_last = sum / ntrain;
+    }
+    double val = 0.0;
+    for (size_t i = ntrain; i < blocks; ++i) val += net_loss_grad(H, blk(i), k, false, true);
+    R.val_loss = val / nval;
+    check_cuda(cudaStreamSynchronize(s), "sync");
+    R.seconds_train = std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+    R.epochs = p->epochs;
+    H.capture.release();
+    H.capture_blocks = H.capture_n = 0;
+    H.net_on = (p->enable && R.val_loss < 1.0) ? 1 : (p->enable ? 0 : was_on);
+    R.enabled = H.net_on;
+    if (weights_out)
+      check_cuda(cudaMemcpyAsync(weights_out, H.netW.p, H.net_nw * sizeof(float), cudaMemcpyDeviceToHost, s), "D2H W");
+    check_cuda(cudaStreamSynchronize(s), "sync");
+    if (rep) *rep = R;
   });
 }
 

@@ -79,6 +79,7 @@ template <> __host__ __device__ inline cdouble cvt<cdouble, cdouble>(cdouble a) 
 template <> __host__ __device__ inline cfloat cvt<cfloat, cfloat>(cfloat a) { return a; }
 template <> __host__ __device__ inline cdouble cvt<cdouble, cfloat>(cfloat a) { return {(double)a.re, (double)a.im}; }
 template <> __host__ __device__ inline cfloat cvt<cfloat, cdouble>(cdouble a) { return {(float)a.re, (float)a.im}; }
+template <> __host__ __device__ inline float cvt<float, cfloat>(cfloat a) { return a.re; }
 
 template <class T> struct dtype_of;
 template <> struct dtype_of<double> { static const DType v = F64; };
@@ -120,6 +121,9 @@ struct StencilView {
   DType t;            // element type of coef / dinv
   const void *coef;   // [nsite][5][d][d]
   const void *dinv;   // [nsite][d][d] inverse of the self block (smoother), may be null
+  int const_laplace;  // 1: Example 5.1 operator, applied without reading coef
+  double diag;        //    its diagonal 4 + shift
+  int periodic;       //    0: Dirichlet
 };
 
 // Per-aggregate prolongation blocks P[agg][loc*d + a][q] with loc = jj*ax + ii.
@@ -158,6 +162,10 @@ void launch_stencil(const StencilView &A, const void *x, const void *b, void *y,
                     cudaStream_t s);
 // one red-black block Gauss-Seidel half-sweep over sites of `colour`
 void launch_rbgs_half(const StencilView &A, void *x, const void *b, int k, int colour, cudaStream_t s);
+// one full red-black sweep (order 0: red then black, 1: black then red).  x_zero = 1
+// means x holds zeros on entry (x need not be initialised: the kernels skip it).
+void launch_rbgs_sweep(const StencilView &A, void *x, const void *b, int k, int order, int x_zero,
+                       cudaStream_t s);
 // rc = P^* r
 void launch_restrict(const ProlongView &P, const void *r, void *rc, int k, cudaStream_t s);
 // x += P ec
@@ -199,4 +207,21 @@ void launch_build_laplace(double *coef, int nx, int ny, double shift, int period
 void launch_build_wilson(cdouble *coef, const cdouble *links, int nx, int ny, double mass, cudaStream_t s);
 // dense n x n matrix of a block stencil level (row-major)
 void launch_stencil_to_dense(const StencilView &A, void *dense, cudaStream_t s);
+}  // namespace mlmc
+
+namespace mlmc {
+// learned correction (kernels_learned.cu)
+void launch_to_channels(DType t, const void *x, float *a, int nsite, int d, int k, cudaStream_t s);
+void launch_add_from_channels(DType t, void *x, const float *a, int nsite, int d, int k, cudaStream_t s);
+void launch_conv_fwd(int ci, int co, bool relu, const float *in, const float *W, float *out, int nx, int ny, int k,
+                     int periodic, cudaStream_t s);
+void launch_conv_bwd_data(int ci, int co, const float *gout, const float *W, const float *act, float *gin, int nx,
+                          int ny, int k, int periodic, cudaStream_t s);
+int conv_weight_blocks();
+void launch_conv_bwd_weight(int ci, int co, const float *in, const float *gout, float *partial, float *grad,
+                            float scale, int nx, int ny, int k, int periodic, cudaStream_t s);
+void launch_adam(float *W, const float *g, float *m, float *v, int n, float lr, int step, cudaStream_t s);
+void launch_spin_flip(DType t, void *x, int nsite, int d, int k, cudaStream_t s);
+// alpha[c] = scale / |dot[c]| (real part), FP64 per-column factors from a column dot
+void launch_col_factor(int hc, const void *dot, double *alpha, double scale, int k, cudaStream_t s);
 }  // namespace mlmc

@@ -22,6 +22,7 @@ SETUP_SMOOTH, SETUP_INVERSE, SETUP_CONSTANT = 0, 1, 2
 PREC_FP64, PREC_MIXED_FP32 = 0, 1
 FORM_SIMPLIFIED, FORM_HAT = 0, 1
 CYCLE_V, CYCLE_K = 0, 1
+ALLOC_RHO, ALLOC_OPTIMAL = 0, 1
 
 
 class C64(ctypes.Structure):
@@ -43,13 +44,13 @@ class HierarchyParams(ctypes.Structure):
                 ("smooth_pre", ctypes.c_int), ("smooth_post", ctypes.c_int), ("cycle", ctypes.c_int),
                 ("kcycle_its", ctypes.c_int), ("fgmres_restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("block", ctypes.c_int), ("reorth", ctypes.c_int),
-                ("user_P", ctypes.c_void_p)]
+                ("inner_its", ctypes.c_int), ("graphs", ctypes.c_int), ("user_P", ctypes.c_void_p)]
 
 
 class EstimateParams(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("weights", ctypes.c_double * 16), ("noise", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("tol", ctypes.c_double), ("min_samples", ctypes.c_int),
-                ("max_samples", ctypes.c_int), ("form", ctypes.c_int)]
+                ("max_samples", ctypes.c_int), ("form", ctypes.c_int), ("allocation", ctypes.c_int)]
 
 
 class EstimateResult(ctypes.Structure):
@@ -57,7 +58,19 @@ class EstimateResult(ctypes.Structure):
                 ("coarse_term", C64), ("levels", ctypes.c_int), ("n_samples", ctypes.c_int * 16),
                 ("mean", C64 * 16), ("variance", ctypes.c_double * 16), ("iters", ctypes.c_double * 16),
                 ("seconds", ctypes.c_double * 16), ("cost_nnz", ctypes.c_double * 16),
-                ("seconds_total", ctypes.c_double)]
+                ("weights_used", ctypes.c_double * 16), ("seconds_total", ctypes.c_double)]
+
+
+class TrainParams(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int), ("epochs", ctypes.c_int), ("lr", ctypes.c_double), ("tol", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("init_weights", ctypes.c_void_p), ("enable", ctypes.c_int)]
+
+
+class TrainReport(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int), ("blocks", ctypes.c_int), ("epochs", ctypes.c_int), ("enabled", ctypes.c_int),
+                ("n_weights", ctypes.c_int), ("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double),
+                ("val_loss", ctypes.c_double), ("seconds_capture", ctypes.c_double),
+                ("seconds_train", ctypes.c_double)]
 
 
 class MLMCError(RuntimeError):
@@ -85,6 +98,10 @@ def _load():
         "mlmc_trace_estimate": [vp, ctypes.POINTER(EstimateParams), ctypes.POINTER(EstimateResult)],
         "mlmc_profile_kernel": [vp, i, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d)],
         "mlmc_launch_count": [vp, ctypes.POINTER(u64)],
+        "mlmc_learned_train": [vp, ctypes.POINTER(TrainParams), vp, ctypes.POINTER(TrainReport)],
+        "mlmc_learned_set": [vp, vp, i],
+        "mlmc_learned_apply": [vp, vp, vp, i],
+        "mlmc_learned_grad": [vp, vp, i, ctypes.POINTER(d), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -101,7 +118,7 @@ lib = _load()
 EXPORTED = ["mlmc_setup_hierarchy", "mlmc_destroy_hierarchy", "mlmc_level_info", "mlmc_get_prolongation",
             "mlmc_get_operator", "mlmc_apply", "mlmc_solve", "mlmc_noise", "mlmc_sample_level",
             "mlmc_coarse_trace_exact", "mlmc_trace_estimate", "mlmc_profile_kernel", "mlmc_launch_count",
-            "mlmc_last_error"]
+            "mlmc_last_error", "mlmc_learned_train", "mlmc_learned_set", "mlmc_learned_apply", "mlmc_learned_grad"]
 
 
 def check(status):
@@ -114,7 +131,7 @@ def default_params(**kw):
                         setup_sweeps=40, coarse_sweeps=20, setup_omega=2.0 / 3.0, setup_seed=0,
                         bootstrap=1, boot_iters=2, smooth_pre=1, smooth_post=1, cycle=CYCLE_K,
                         kcycle_its=2, fgmres_restart=30, max_iter=2000, precision=PREC_FP64, block=64,
-                        reorth=1, user_P=None)
+                        reorth=1, inner_its=0, graphs=1, user_P=None)
     for k, v in kw.items():
         if not hasattr(p, k):
             raise KeyError(k)
@@ -207,9 +224,9 @@ class Hierarchy:
         return complex(out.re, out.im)
 
     def trace_estimate(self, eps=1e-3, noise=NOISE_RADEMACHER, seed=0, tol=1e-10, weights=None, min_samples=5,
-                       max_samples=1 << 24, form=FORM_SIMPLIFIED):
+                       max_samples=1 << 24, form=FORM_SIMPLIFIED, allocation=ALLOC_RHO):
         p = EstimateParams(eps=eps, noise=noise, seed=seed, tol=tol, min_samples=min_samples,
-                           max_samples=max_samples, form=form)
+                           max_samples=max_samples, form=form, allocation=allocation)
         if weights is not None:
             for i, w in enumerate(weights):
                 p.weights[i] = w
@@ -221,6 +238,34 @@ class Hierarchy:
         ms, by = ctypes.c_double(), ctypes.c_double()
         check(lib.mlmc_profile_kernel(self.handle, which, level, k, reps, ctypes.byref(ms), ctypes.byref(by)))
         return ms.value, by.value
+
+    def net_weights(self):
+        c0 = self.level_info(1)[2] * (2 if self.complex else 1)
+        return 9 * (16 * c0 + 256 + c0 * 16)
+
+    def learned_train(self, n_pairs=10000, epochs=3, lr=1e-3, tol=1e-8, seed=0, init_weights=None, enable=1):
+        w0 = None
+        if init_weights is not None:
+            w0 = np.ascontiguousarray(init_weights, dtype=np.float32)
+        p = TrainParams(n_pairs=n_pairs, epochs=epochs, lr=lr, tol=tol, seed=seed,
+                        init_weights=None if w0 is None else w0.ctypes.data, enable=enable)
+        out = np.zeros(self.net_weights(), dtype=np.float32)
+        rep = TrainReport()
+        check(lib.mlmc_learned_train(self.handle, ctypes.byref(p), out.ctypes.data, ctypes.byref(rep)))
+        return out, {f: getattr(rep, f) for f, _ in TrainReport._fields_}
+
+    def learned_set(self, weights, enable=1):
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+        check(lib.mlmc_learned_set(self.handle, None if w is None else w.ctypes.data, enable))
+
+    def learned_apply(self, r_ptr, e_ptr, k):
+        check(lib.mlmc_learned_apply(self.handle, ctypes.c_void_p(r_ptr), ctypes.c_void_p(e_ptr), k))
+
+    def learned_grad(self, r_ptr, k):
+        loss = ctypes.c_double()
+        g = np.zeros(self.net_weights(), dtype=np.float32)
+        check(lib.mlmc_learned_grad(self.handle, ctypes.c_void_p(r_ptr), k, ctypes.byref(loss), g.ctypes.data))
+        return loss.value, g
 
     def launch_count(self):
         c = ctypes.c_uint64()
@@ -244,5 +289,6 @@ def result_dict(r):
         "iters": [r.iters[i] for i in range(L - 1)],
         "seconds": [r.seconds[i] for i in range(L - 1)],
         "cost_nnz": [r.cost_nnz[i] for i in range(L)],
+        "weights_used": [r.weights_used[i] for i in range(L - 1)],
         "seconds_total": r.seconds_total,
     }

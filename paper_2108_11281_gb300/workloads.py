@@ -36,6 +36,7 @@ LAPLACE_SMALL = dict(name="laplace2d-64x64-L2-const", kind="laplace", nx=64, ny=
 LAPLACE_1024 = dict(name="laplace2d-1024x1024-L4", kind="laplace", nx=1024, ny=1024, shift=0.0,
                     levels=4, n_tv=4, setup="smooth", sweeps=160, coarse_sweeps=20,
                     noise="rademacher", block=64, tol=1e-10, eps=1e-3)
+# mass from `python -m oracle.tune_mass 128 128 0.3 1`: sigma_min / sigma_max = 1.0015e-3
 WILSON_128 = dict(name="wilson2d-128x128-L3", kind="wilson", nx=128, ny=128, link_sd=0.3,
-                  link_seed=1, levels=3, n_tv=4, spin_split=True, setup="inverse", sweeps=20,
-                  noise="z4", block=32, tol=1e-10, eps=1e-3)
+                  link_seed=1, mass=-0.1317442871, levels=3, n_tv=4, spin_split=True, setup="inverse",
+                  sweeps=20, noise="z4", block=32, tol=1e-10, eps=1e-3)

@@ -1,0 +1,96 @@
+"""GPU learned correction against the FP64 oracle (oracle/learned.py).
+
+The network runs in FP32; forward values are compared to 1e-5 of the output
+scale and gradients to 1e-3 of the gradient scale (FP32 sums over 9*16 taps
+and all lattice sites)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import learned as NN
+from oracle.operators import laplace2d, wilson2d
+from paper_2108_11281_gb300.workloads import gauge_links
+
+
+@pytest.fixture(scope="module")
+def mlmc():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2108_11281_gb300 import mlmc as m
+    return m
+
+
+def make(mlmc, case, N=8, k=3):
+    if case == "wilson":
+        U = gauge_links(N, N, 0.3, 2)
+        prm = mlmc.default_params(levels=2, n_tv=2, spin_split=1, setup_kind=mlmc.SETUP_INVERSE, setup_sweeps=4,
+                                  setup_omega=1.0, precision=mlmc.PREC_MIXED_FP32, block=k, bootstrap=0)
+        h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.2, links=U)
+        A = wilson2d(N, N, 0.2, U)
+        return h, A, 2, True, True
+    prm = mlmc.default_params(levels=2, n_tv=1, setup_kind=mlmc.SETUP_CONSTANT, precision=mlmc.PREC_MIXED_FP32,
+                              block=k, bootstrap=0)
+    h = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, N, N, prm)
+    return h, laplace2d(N, N), 1, False, False
+
+
+def flat(Ws):
+    return np.concatenate([W.astype(np.float32).ravel() for W in Ws])
+
+
+@pytest.mark.parametrize("case", ["wilson", "laplace"])
+def test_forward_and_gradient_match_oracle(mlmc, case):
+    N, k = 8, 3
+    h, A, d, cplx, per = make(mlmc, case, N, k)
+    c0 = NN.channels_of(d, cplx)
+    Ws = [W.astype(np.float32).astype(np.float64) for W in NN.init_weights(c0, 9)]
+    h.learned_set(flat(Ws), enable=0)
+    n = N * N * d
+    g = torch.Generator().manual_seed(0)
+    if cplx:
+        R = torch.complex(torch.randn(n, k, generator=g), torch.randn(n, k, generator=g)).to(torch.complex64).cuda()
+    else:
+        R = torch.randn(n, k, generator=g, dtype=torch.float32).cuda()
+    E = torch.zeros_like(R)
+    h.learned_apply(R.data_ptr(), E.data_ptr(), k)
+    Rn = R.cpu().numpy().astype(np.complex128 if cplx else np.float64)
+    En = E.cpu().numpy()
+    for c in range(k):
+        ref, _ = NN.forward(Rn[:, c], Ws, N, N, d, cplx, per)
+        assert np.abs(En[:, c] - ref).max() <= 1e-5 * np.abs(ref).max()
+    loss, grad = h.learned_grad(R.data_ptr(), k)
+    ref_loss, ref_g = NN.loss_and_grad(A, Rn, Ws, N, N, d, cplx, per)
+    ref_flat = np.concatenate([x.ravel() for x in ref_g])
+    assert abs(loss - ref_loss) <= 1e-4 * abs(ref_loss)
+    assert np.abs(grad - ref_flat).max() <= 1e-3 * np.abs(ref_flat).max()
+    h.close()
+
+
+def test_training_on_gpu_and_gain(mlmc):
+    """Train on residuals captured from plain solves of a 32x32 Wilson operator; the
+    network must lower its training loss, solves with it must still meet the FP64
+    tolerance, and the iteration counts with and without it are reported."""
+    N, k = 32, 16
+    U = gauge_links(N, N, 0.3, 4)
+    prm = mlmc.default_params(levels=3, n_tv=2, spin_split=1, setup_kind=mlmc.SETUP_INVERSE, setup_sweeps=8,
+                              coarse_sweeps=4, setup_omega=1.0, precision=mlmc.PREC_MIXED_FP32, block=k,
+                              smooth_pre=1, smooth_post=1, inner_its=6, fgmres_restart=10)
+    h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.02, links=U)
+    W, rep = h.learned_train(n_pairs=32 * k, epochs=4, lr=2e-3, tol=1e-6, seed=1, enable=1)
+    assert rep["loss_last"] < rep["loss_first"]
+    assert np.isfinite(W).all() and rep["n_weights"] == W.size
+    n = N * N * 2
+    b = torch.complex(torch.randn(n, k, dtype=torch.float64), torch.randn(n, k, dtype=torch.float64)).cuda()
+    x = torch.zeros_like(b)
+    its_net = h.solve(1, b.data_ptr(), x.data_ptr(), k, 1e-10)
+    A = wilson2d(N, N, 0.02, U)
+    bn, xn = b.cpu().numpy(), x.cpu().numpy()
+    assert (np.linalg.norm(bn - A @ xn, axis=0) / np.linalg.norm(bn, axis=0)).max() <= 1e-10
+    h.learned_set(None, enable=0)
+    its_plain = h.solve(1, b.data_ptr(), x.data_ptr(), k, 1e-10)
+    print("learned: val_loss %.3f, outer iterations with net %d, without %d" % (rep["val_loss"], its_net, its_plain))
+    h.close()

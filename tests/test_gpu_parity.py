@@ -239,3 +239,39 @@ def test_trace_estimate_matches_oracle(mlmc):
     assert abs(r["trace"] - ref.trace) <= 1e-9 * abs(ref.trace)
     assert abs(r["std_err"] - ref.std_err) <= 1e-6 * ref.std_err
     h.close()
+
+
+def test_optimal_allocation_estimate(mlmc):
+    """Sec. 2 optimal allocation: the total variance meets (eps tau)^2 and the
+    estimate equals the oracle's mean of the same samples (same N_l, same noise)."""
+    N = 32
+    h = laplace_h(mlmc, N, 3, block=16, n_tv=4, setup_sweeps=20, coarse_sweeps=10, smooth_pre=1, smooth_post=1)
+    r = mlmc.result_dict(h.trace_estimate(eps=1e-2, noise=mlmc.NOISE_RADEMACHER, seed=2, tol=1e-12,
+                                          allocation=mlmc.ALLOC_OPTIMAL))
+    target = 1e-2 * abs(r["tau"])
+    assert r["std_err"] <= target * (1 + 1e-12)
+    assert all(n >= 5 for n in r["n_samples"])
+    assert abs(sum(r["weights_used"]) - 1.0) < 1e-12
+    # the same samples, drawn by the GPU itself one level at a time, give the same means
+    for l, n in enumerate(r["n_samples"], start=1):
+        s, _ = h.sample_level(l, mlmc.NOISE_RADEMACHER, 2, 0, n, 1e-12)
+        assert abs(s.mean() - r["mean"][l - 1]) <= 1e-9 * abs(r["mean"][l - 1])
+    h.close()
+
+
+def test_wilson_estimate_matches_oracle(mlmc):
+    """Z4 estimate on a 16x16 Wilson operator (imported P): same N_l and estimate as the oracle."""
+    N = 16
+    U = gauge_links(N, N, 0.3, 11)
+    S = wilson2d(N, N, 0.05, U)
+    lv = build_hierarchy(S, N, N, 2, SetupParams(levels=3, n_tv=2, spin_split=True, kind="inverse", sweeps=6,
+                                                 coarse_sweeps=4, omega=1.0, noise_kind="z4"))
+    prm = mlmc.default_params(levels=3, n_tv=2, spin_split=1, block=8, smooth_pre=2, smooth_post=2)
+    h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.05, links=U, user_P=[lv[0].P_blocks, lv[1].P_blocks])
+    r = mlmc.result_dict(h.trace_estimate(eps=3e-2, noise=mlmc.NOISE_Z4, seed=5, tol=1e-12,
+                                          weights=[0.4, 0.6]))
+    ref = E.trace_estimate(lv, "z4", seed=5, eps=3e-2, block=8, weights=[0.4, 0.6])
+    assert r["n_samples"] == ref.n_samples
+    assert abs(r["trace"] - ref.trace) <= 1e-9 * abs(ref.trace)
+    assert abs(r["trace"].imag) <= 1e-6 * abs(r["trace"])          # J-symmetry: the trace is real
+    h.close()

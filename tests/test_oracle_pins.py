@@ -267,3 +267,48 @@ def test_small_laplace_estimate_against_closed_form():
     assert abs(res.trace.real - exact) <= 4 * res.std_err
     assert np.isclose(res.coarse_term, np.trace(np.linalg.inv(h[1].A.toarray())), rtol=1e-12)
     assert all(n >= 5 for n in res.n_samples)
+
+
+# ---------------------------------------------------------------- learned correction (no paper basis)
+@pytest.mark.parametrize("case", ["wilson", "laplace"])
+def test_learned_gradient_matches_finite_differences(case):
+    """The network's loss gradient (oracle/learned.py) against central differences in FP64."""
+    from oracle import learned as NN
+    rng = np.random.default_rng(3)
+    if case == "wilson":
+        A = wilson2d(4, 4, 0.2, gauge_links(4, 4, 0.3, 1))
+        d, cplx, per, n = 2, True, True, 32
+        R = rng.normal(size=(n, 2)) + 1j * rng.normal(size=(n, 2))
+    else:
+        A = laplace2d(4, 4)
+        d, cplx, per, n = 1, False, False, 16
+        R = rng.normal(size=(n, 2))
+    Ws = NN.init_weights(NN.channels_of(d, cplx), 5)
+    _, G = NN.loss_and_grad(A, R, Ws, 4, 4, d, cplx, per)
+    h = 1e-6
+    for li, idx in [(0, (1, 0, 2, 1)), (1, (5, 7, 1, 1)), (2, (0, 3, 0, 2))]:
+        Wp = [W.copy() for W in Ws]
+        Wm = [W.copy() for W in Ws]
+        Wp[li][idx] += h
+        Wm[li][idx] -= h
+        fd = (NN.loss_and_grad(A, R, Wp, 4, 4, d, cplx, per)[0] - NN.loss_and_grad(A, R, Wm, 4, 4, d, cplx, per)[0]) / (2 * h)
+        assert abs(fd - G[li][idx]) <= 1e-6 * max(abs(fd), 1e-3)
+
+
+def test_learned_linear_special_case():
+    """With every pre-activation positive the network is the linear map W3*W2*W1: a
+    single-tap identity chain must reproduce its input exactly (net(r) = r)."""
+    from oracle import learned as NN
+    c0 = 4
+    W1 = np.zeros((16, c0, 3, 3)); W2 = np.zeros((16, 16, 3, 3)); W3 = np.zeros((c0, 16, 3, 3))
+    for c in range(c0):
+        W1[c, c, 1, 1] = 1.0
+        W1[c + c0, c, 1, 1] = -1.0          # ReLU(x) - ReLU(-x) = x
+        W2[c, c, 1, 1] = 1.0
+        W2[c + c0, c + c0, 1, 1] = 1.0
+        W3[c, c, 1, 1] = 1.0
+        W3[c, c + c0, 1, 1] = -1.0
+    rng = np.random.default_rng(1)
+    r = rng.normal(size=32) + 1j * rng.normal(size=32)
+    e, _ = NN.forward(r, [W1, W2, W3], 4, 4, 2, True, True)
+    assert np.allclose(e, r, atol=1e-15)
