@@ -39,11 +39,18 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--profile-sample", action="store_true",
+                    help="for ncu only: after setup, one warm block and one profiled 64-sample block per level "
+                         "difference inside cudaProfilerStart/Stop; prints no bench line")
+    ap.add_argument("--profile-nx", type=int, default=0,
+                    help="with --profile-sample: lattice side for a smaller capture (default: the workload's)")
+    ap.add_argument("--alloc", default="optimal", choices=["optimal", "rho"],
+                    help="Sec. 2 optimal allocation (default) or the Sec. 5 equal rho split")
     return ap.parse_args()
 
 
@@ -200,10 +207,36 @@ def config_dict(form):
             "l2": "inputs larger than L2 (a 64-column level-1 block is 512 MiB in FP64)"}
 
 
+def profile_sample(args):
+    """One block per level difference inside cudaProfilerStart/Stop (ncu launch lists / captures)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2108_11281_gb300 import mlmc
+    w = dict(WORKLOAD)
+    if args.profile_nx:
+        w["nx"] = w["ny"] = args.profile_nx
+    prm = hierarchy_params(mlmc, mlmc.PREC_MIXED_FP32)
+    h = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, w["nx"], w["ny"], prm,
+                       stream=torch.cuda.current_stream().cuda_stream)
+    for lvl in range(1, w["levels"]):
+        h.sample_level(lvl, mlmc.NOISE_RADEMACHER, 0, 0, w["block"], w["tol_mixed"])
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for lvl in range(1, w["levels"]):
+        h.sample_level(lvl, mlmc.NOISE_RADEMACHER, 0, w["block"], w["block"], w["tol_mixed"])
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    h.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_sample:
+        profile_sample(args)
         return
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -221,8 +254,11 @@ def main():
     h = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, w["nx"], w["ny"], hierarchy_params(mlmc, mlmc.PREC_MIXED_FP32),
                        stream=stream)
 
+    alloc = mlmc.ALLOC_OPTIMAL if args.alloc == "optimal" else mlmc.ALLOC_RHO
+
     def step(hh, tol, seed):
-        return mlmc.result_dict(hh.trace_estimate(eps=w["eps"], noise=mlmc.NOISE_RADEMACHER, seed=seed, tol=tol))
+        return mlmc.result_dict(hh.trace_estimate(eps=w["eps"], noise=mlmc.NOISE_RADEMACHER, seed=seed, tol=tol,
+                                                  allocation=alloc))
 
     seed = w["seed"] + 1000 * rank          # replicas draw disjoint noise
     for _ in range(args.warmup):
@@ -278,12 +314,12 @@ def main():
         h.close()
         h64 = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, w["nx"], w["ny"], hierarchy_params(mlmc, mlmc.PREC_FP64),
                              stream=stream)
-        step(h64, w["tol_fp64"], seed)
         torch.cuda.synchronize()
         t = time.time()
         r64 = step(h64, w["tol_fp64"], seed)
         torch.cuda.synchronize()
-        fp64 = {"seconds": time.time() - t, "trace": r64["trace"].real, "std_err": r64["std_err"],
+        fp64 = {"seconds": time.time() - t, "unit": "s (one estimate, same allocation and noise)",
+                "trace": r64["trace"].real, "std_err": r64["std_err"],
                 "n_samples": r64["n_samples"], "iters": r64["iters"]}
         h64.close()
     else:
@@ -307,7 +343,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
-                "config": config_dict("mixed: FP32 K-cycle under FP64 FGMRES"),
+                "config": dict(config_dict("mixed: FP32 K-cycle under FP64 FGMRES"), allocation=args.alloc),
                 "clocks": sampler.summary(local), "gpu_launches": int(launches), "wall_s_timed": wall,
                 "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": ctypes.sizeof(mlmc.EstimateResult),

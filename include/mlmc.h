@@ -182,6 +182,14 @@ int mlmc_noise(int noise, uint64_t seed, int level, int purpose, uint64_t first,
 int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, uint64_t first,
                       int n_samples, double tol, mlmc_c64 *out_samples, int *out_iters);
 
+/* Column dots out[c] = sum_i conj(x[i][c]) y[i][c] of two device blocks [n][k]
+ * (the x_j^* y_j products of the difference samples, Remark 4.3), in FP64:
+ * double (complex = 0) or interleaved complex double (complex = 1) inputs; out
+ * is device memory of k doubles or k complex doubles.  Summation order is
+ * fixed (per-column partial sums over 608 row chunks, then a fixed tree).
+ * Allocates and frees its scratch (608 x k partial sums) on every call; k <= 256. */
+int mlmc_column_dots(int complex_data, const void *x, const void *y, int n, int k, void *out, void *stream);
+
 /* tr(A_L^{-1}) from the FP64 dense inverse (Remark 4.2). */
 int mlmc_coarse_trace_exact(mlmc_hierarchy *h, mlmc_c64 *out);
 

@@ -1010,6 +1010,19 @@ int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, ui
   });
 }
 
+int mlmc_column_dots(int complex_data, const void *x, const void *y, int n, int k, void *out, void *stream) {
+  return translate([&] {
+    if (!x || !y || !out || n < 1 || k < 1 || k > 256) fail(MLMC_ERR_INVALID_ARG, "bad column-dot arguments (k must be in 1..256)");
+    cudaStream_t s = (cudaStream_t)stream;
+    DType t = complex_data ? C64 : F64;
+    int parts = multidot_parts((size_t)n, k);
+    DevBuf part;
+    part.alloc((size_t)parts * k * (complex_data ? 16 : 8));
+    launch_multidot(t, x, (size_t)n * k, 1, y, (size_t)n, k, part.p, parts, out, t, s);
+    check_cuda(cudaStreamSynchronize(s), "sync");
+  });
+}
+
 int mlmc_coarse_trace_exact(mlmc_hierarchy *h, mlmc_c64 *out) {
   return translate([&] {
     need(h);

@@ -102,6 +102,7 @@ def _load():
         "mlmc_learned_set": [vp, vp, i],
         "mlmc_learned_apply": [vp, vp, vp, i],
         "mlmc_learned_grad": [vp, vp, i, ctypes.POINTER(d), vp],
+        "mlmc_column_dots": [i, vp, vp, i, i, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -118,7 +119,8 @@ lib = _load()
 EXPORTED = ["mlmc_setup_hierarchy", "mlmc_destroy_hierarchy", "mlmc_level_info", "mlmc_get_prolongation",
             "mlmc_get_operator", "mlmc_apply", "mlmc_solve", "mlmc_noise", "mlmc_sample_level",
             "mlmc_coarse_trace_exact", "mlmc_trace_estimate", "mlmc_profile_kernel", "mlmc_launch_count",
-            "mlmc_last_error", "mlmc_learned_train", "mlmc_learned_set", "mlmc_learned_apply", "mlmc_learned_grad"]
+            "mlmc_last_error", "mlmc_learned_train", "mlmc_learned_set", "mlmc_learned_apply", "mlmc_learned_grad",
+            "mlmc_column_dots"]
 
 
 def check(status):
@@ -276,6 +278,11 @@ class Hierarchy:
 def noise(kind, seed, level, purpose, first, n, k, complex_out, out_ptr, stream=0):
     check(lib.mlmc_noise(kind, seed, level, purpose, first, n, k, complex_out, ctypes.c_void_p(out_ptr),
                          ctypes.c_void_p(stream)))
+
+
+def column_dots(complex_data, x_ptr, y_ptr, n, k, out_ptr, stream=0):
+    check(lib.mlmc_column_dots(int(complex_data), ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), n, k,
+                               ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream)))
 
 
 def result_dict(r):
