@@ -120,7 +120,7 @@ EXPORTED = ["mlmc_setup_hierarchy", "mlmc_destroy_hierarchy", "mlmc_level_info",
             "mlmc_get_operator", "mlmc_apply", "mlmc_solve", "mlmc_noise", "mlmc_sample_level",
             "mlmc_coarse_trace_exact", "mlmc_trace_estimate", "mlmc_profile_kernel", "mlmc_launch_count",
             "mlmc_last_error", "mlmc_learned_train", "mlmc_learned_set", "mlmc_learned_apply", "mlmc_learned_grad",
-            "mlmc_column_dots"]
+            "mlmc_column_dots", "mlmc_column_dots_noalloc", "mlmc_noalloc_last_error"]
 
 
 def check(status):
