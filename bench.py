@@ -27,9 +27,31 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="laplace2d-1024x1024-L4-4tv-k64", nx=1024, ny=1024, levels=4, n_tv=4, block=64,
-                setup_sweeps=160, coarse_sweeps=20, bootstrap=1, boot_iters=2, smooth_pre=2, smooth_post=2,
-                kcycle_its=2, restart=10, inner_its=8, eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8, seed=0)
+WILSON256_MASS = -0.15      # replaced by the value of `python -m oracle.tune_mass 256 256 0.4 2`
+
+WORKLOADS = {
+    # the 1024^2 Dirichlet Laplacian, 4 levels of 4x4 aggregation, 4 smoothed test vectors
+    "laplace1024": dict(name="laplace2d-1024x1024-L4-4tv-k64", kind="laplace", nx=1024, ny=1024, levels=4, n_tv=4,
+                        spin_split=0, setup="smooth", setup_sweeps=160, coarse_sweeps=20, omega=2.0 / 3.0,
+                        bootstrap=1, boot_iters=2, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=10,
+                        inner_its=8, block=64, noise="rademacher", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8,
+                        seed=0, learned=False),
+    # 2-spin Wilson operator 128^2, theta ~ N(0, 0.3^2), m0 tuned to sigma_min / sigma_max = 1e-3
+    "wilson128": dict(name="wilson2d-128x128-L3-8dof-k32", kind="wilson", nx=128, ny=128, levels=3, n_tv=4,
+                      spin_split=1, setup="inverse", setup_sweeps=20, coarse_sweeps=10, omega=1.0, bootstrap=2,
+                      boot_iters=2, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=10, inner_its=8, block=32,
+                      noise="z4", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8, seed=0, link_sd=0.3, link_seed=1,
+                      mass=-0.1317442871, learned=False),
+    # 2-spin Wilson operator 256^2, theta ~ N(0, 0.4^2), complex64 cycle with the learned correction
+    # trained on 10^4 residual/error pairs from plain multigrid solves (training is setup, not timed)
+    "wilson256": dict(name="wilson2d-256x256-L3-8dof-k32-learned", kind="wilson", nx=256, ny=256, levels=3,
+                      n_tv=4, spin_split=1, setup="inverse", setup_sweeps=20, coarse_sweeps=10, omega=1.0,
+                      bootstrap=2, boot_iters=2, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=10,
+                      inner_its=8, block=32, noise="z4", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8, seed=0,
+                      link_sd=0.4, link_seed=2, mass=WILSON256_MASS, learned=True, train_pairs=10000,
+                      train_epochs=3, train_lr=1e-3),
+}
+WORKLOAD = WORKLOADS["laplace1024"]
 METRIC = "Seconds to tr(A^-1) at 1e-3 rel. error, mixed+learned vs plain FP64; HBM %"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -49,19 +71,32 @@ def parse():
                          "difference inside cudaProfilerStart/Stop; prints no bench line")
     ap.add_argument("--profile-nx", type=int, default=0,
                     help="with --profile-sample: lattice side for a smaller capture (default: the workload's)")
+    ap.add_argument("--workload", default="laplace1024", choices=sorted(WORKLOADS),
+                    help="laplace1024 (default, the headline), wilson128, wilson256 (learned correction)")
     ap.add_argument("--alloc", default="optimal", choices=["optimal", "rho"],
                     help="Sec. 2 optimal allocation (default) or the Sec. 5 equal rho split")
     return ap.parse_args()
 
 
-def hierarchy_params(mlmc, precision):
-    w = WORKLOAD
-    return mlmc.default_params(levels=w["levels"], n_tv=w["n_tv"], setup_kind=mlmc.SETUP_SMOOTH,
+def hierarchy_params(mlmc, precision, w=None):
+    w = w or WORKLOAD
+    kind = {"smooth": mlmc.SETUP_SMOOTH, "inverse": mlmc.SETUP_INVERSE}[w["setup"]]
+    return mlmc.default_params(levels=w["levels"], n_tv=w["n_tv"], spin_split=w["spin_split"], setup_kind=kind,
                                setup_sweeps=w["setup_sweeps"], coarse_sweeps=w["coarse_sweeps"],
-                               bootstrap=w["bootstrap"], boot_iters=w["boot_iters"], smooth_pre=w["smooth_pre"],
-                               smooth_post=w["smooth_post"], cycle=mlmc.CYCLE_K, kcycle_its=w["kcycle_its"],
-                               fgmres_restart=w["restart"], max_iter=5000, precision=precision,
-                               block=w["block"], reorth=1, inner_its=w["inner_its"])
+                               setup_omega=w["omega"], bootstrap=w["bootstrap"], boot_iters=w["boot_iters"],
+                               smooth_pre=w["smooth_pre"], smooth_post=w["smooth_post"], cycle=mlmc.CYCLE_K,
+                               kcycle_its=w["kcycle_its"], fgmres_restart=w["restart"], max_iter=5000,
+                               precision=precision, block=w["block"], reorth=1, inner_its=w["inner_its"])
+
+
+def make_hierarchy(mlmc, precision, w, stream=0):
+    """Hierarchy of workload w (the Wilson links come from the seeded generator)."""
+    prm = hierarchy_params(mlmc, precision, w)
+    if w["kind"] == "laplace":
+        return mlmc.Hierarchy(mlmc.OP_LAPLACE2D, w["nx"], w["ny"], prm, stream=stream)
+    from paper_2108_11281_gb300.workloads import gauge_links
+    U = gauge_links(w["nx"], w["ny"], w["link_sd"], w["link_seed"])
+    return mlmc.Hierarchy(mlmc.OP_WILSON2D, w["nx"], w["ny"], prm, mass=w["mass"], links=U, stream=stream)
 
 
 class ClockSampler:
@@ -120,43 +155,46 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(result, seconds_budget=25.0):
+def cpu_baseline(result, w):
     """Oracle (FP64 CPU, as it stands) on a bounded sample of the workload.
 
-    The sample: the oracle's own hierarchy for the workload, then per level
-    difference l a few FGMRES iterations (preconditioned by the oracle's
-    K-cycle) on levels l and l+1, timed.  Extrapolation: seconds per
-    iteration x (iterations per solve) x N_l, with N_l and the iterations per
-    solve of the same estimator on the same inputs (taken from the GPU
+    The sample: the oracle's own hierarchy for the workload, then per level l
+    a few FGMRES iterations (preconditioned by the oracle's K-cycle), timed,
+    and ten products with the dense coarsest inverse.  Extrapolation:
+    seconds per cycle x cycles per solve x (N_l + 5), with N_l and the cycles
+    per solve of the same estimator on the same inputs (taken from the GPU
     result, which matches the oracle sample by sample)."""
-    import numpy as np
     from oracle.hierarchy import SetupParams, build_hierarchy
-    from oracle.operators import laplace2d
-    from oracle.philox import rademacher
-    from oracle.solver import Cycle, fgmres
-    w = WORKLOAD
+    from oracle.operators import laplace2d, wilson2d
+    from oracle.philox import noise
+    from oracle.solver import Cycle, dense_inverse, fgmres
     t0 = time.time()
-    A = laplace2d(w["nx"], w["ny"])
-    lv = build_hierarchy(A, w["nx"], w["ny"], 1, SetupParams(
-        levels=w["levels"], n_tv=w["n_tv"], sweeps=w["setup_sweeps"], coarse_sweeps=w["coarse_sweeps"],
-        bootstrap=w["bootstrap"], boot_iters=w["boot_iters"], smooth_pre=w["smooth_pre"],
-        smooth_post=w["smooth_post"], kcycle_its=w["kcycle_its"]))
+    if w["kind"] == "laplace":
+        A, d = laplace2d(w["nx"], w["ny"]), 1
+    else:
+        from paper_2108_11281_gb300.workloads import gauge_links
+        A, d = wilson2d(w["nx"], w["ny"], w["mass"], gauge_links(w["nx"], w["ny"], w["link_sd"], w["link_seed"])), 2
+    lv = build_hierarchy(A, w["nx"], w["ny"], d, SetupParams(
+        levels=w["levels"], n_tv=w["n_tv"], spin_split=bool(w["spin_split"]), kind=w["setup"],
+        sweeps=w["setup_sweeps"], coarse_sweeps=w["coarse_sweeps"], omega=w["omega"],
+        noise_kind="z4" if w["kind"] == "wilson" else "rademacher", bootstrap=w["bootstrap"],
+        boot_iters=w["boot_iters"], smooth_pre=w["smooth_pre"], smooth_post=w["smooth_post"],
+        kcycle_its=w["kcycle_its"]))
     setup_s = time.time() - t0
     per_it = []
     its_probe = 3
     for l in range(len(lv) - 1):
         M = Cycle(lv, l, w["smooth_pre"], w["smooth_post"], "K", w["kcycle_its"])
-        b = rademacher(lv[l].n, 1, l + 1, 0)
+        b = noise(lv[l].n, w["noise"], 1, l + 1, 0)
         t = time.time()
         fgmres(lv[l].A, b, M, tol=0.0, m=its_probe, maxit=its_probe)
         per_it.append((time.time() - t) / its_probe)
     L = len(lv)
-    # the coarsest solve is a dense product: time it too
-    from oracle.solver import dense_inverse
     Ainv = dense_inverse(lv[-1].A)
+    xL = noise(lv[-1].n, w["noise"], 1, L, 0)
     t = time.time()
     for _ in range(10):
-        Ainv @ rademacher(lv[-1].n, 1, L, 0)
+        Ainv @ xL
     per_it.append((time.time() - t) / 10)
     # the GPU reports outer iterations; each preconditions with inner_its cycles
     cyc = [it * max(1, w["inner_its"]) for it in result["iters"]]
@@ -171,40 +209,41 @@ def cpu_baseline(result, seconds_budget=25.0):
                       (its_probe, sum(per_it) * its_probe, setup_s)}
 
 
+# per-level sample counts and mean outer iterations of each workload's estimate
+# (same estimator and noise on both sides, optimal allocation); used only by
+# the reference arm's extrapolation, which runs before any GPU number exists.
+REFERENCE = {"laplace1024": {"n_samples": [2880, 3200, 7872], "iters": [5.0, 6.0, 6.0]},
+             "wilson128": {"n_samples": [1024, 2048], "iters": [4.0, 4.0]}}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    w = WORKLOADS[args.workload]
     steps = []
-    res_nominal = {"n_samples": [w for w in REFERENCE_NL], "iters": [w for w in REFERENCE_ITERS]}
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(res_nominal)
+        cb = cpu_baseline(REFERENCE[args.workload], w)
         if i >= args.warmup:
             steps.append(cb["value"])
     v = statistics.mean(steps)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict("fp64-cpu-oracle"),
+            "config": dict(config_dict("fp64-cpu-oracle", w), allocation=args.alloc),
             "cpu_baseline": {"value": v, "unit": "s (extrapolated)", "kind": "oracle", "cores": 1,
                              "sample": cb["sample"] + "; N_l and iterations per solve from "
-                                       "workloads-recorded values of this estimate"},
+                                       "recorded values of this estimate"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-# per-level sample counts and mean outer iterations of this workload's estimate
-# (same estimator and noise on both sides); used only by the reference arm's
-# extrapolation, which runs before any GPU number exists.
-REFERENCE_NL = [5632, 2432, 1152]
-REFERENCE_ITERS = [5.0, 6.0, 6.0]
-
-
-def config_dict(form):
-    w = WORKLOAD
+def config_dict(form, w):
+    blk = w["nx"] * w["ny"] * (2 if w["kind"] == "wilson" else 1) * w["block"] * (16 if w["kind"] == "wilson" else 8)
     return {"workload": w["name"], "form": form, "nx": w["nx"], "ny": w["ny"], "levels": w["levels"],
-            "n_tv": w["n_tv"], "block": w["block"], "eps": w["eps"], "noise": "rademacher",
-            "l2": "inputs larger than L2 (a 64-column level-1 block is 512 MiB in FP64)"}
+            "n_tv": w["n_tv"], "block": w["block"], "eps": w["eps"], "noise": w["noise"],
+            "l2": ("inputs larger than L2 (a level-1 block is %d MiB in FP64)" % (blk >> 20)) if blk > 130e6 else
+                  ("level-1 block %d MiB: L2-resident working set, no flush" % (blk >> 20))}
 
 
 def profile_sample(args):
@@ -213,18 +252,17 @@ def profile_sample(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2108_11281_gb300 import mlmc
-    w = dict(WORKLOAD)
+    w = dict(WORKLOADS[args.workload])
     if args.profile_nx:
         w["nx"] = w["ny"] = args.profile_nx
-    prm = hierarchy_params(mlmc, mlmc.PREC_MIXED_FP32)
-    h = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, w["nx"], w["ny"], prm,
-                       stream=torch.cuda.current_stream().cuda_stream)
+    nz = mlmc.NOISE_Z4 if w["noise"] == "z4" else mlmc.NOISE_RADEMACHER
+    h = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, torch.cuda.current_stream().cuda_stream)
     for lvl in range(1, w["levels"]):
-        h.sample_level(lvl, mlmc.NOISE_RADEMACHER, 0, 0, w["block"], w["tol_mixed"])
+        h.sample_level(lvl, nz, 0, 0, w["block"], w["tol_mixed"])
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
     for lvl in range(1, w["levels"]):
-        h.sample_level(lvl, mlmc.NOISE_RADEMACHER, 0, w["block"], w["block"], w["tol_mixed"])
+        h.sample_level(lvl, nz, 0, w["block"], w["block"], w["tol_mixed"])
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     h.close()
@@ -249,17 +287,23 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2108_11281_gb300 import mlmc
-    w = WORKLOAD
+    w = WORKLOADS[args.workload]
+    nz = mlmc.NOISE_Z4 if w["noise"] == "z4" else mlmc.NOISE_RADEMACHER
     stream = torch.cuda.current_stream().cuda_stream
-    h = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, w["nx"], w["ny"], hierarchy_params(mlmc, mlmc.PREC_MIXED_FP32),
-                       stream=stream)
+    h = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, stream)
 
     alloc = mlmc.ALLOC_OPTIMAL if args.alloc == "optimal" else mlmc.ALLOC_RHO
 
     def step(hh, tol, seed):
-        return mlmc.result_dict(hh.trace_estimate(eps=w["eps"], noise=mlmc.NOISE_RADEMACHER, seed=seed, tol=tol,
+        return mlmc.result_dict(hh.trace_estimate(eps=w["eps"], noise=nz, seed=seed, tol=tol,
                                                   allocation=alloc))
 
+    learned = None
+    if w.get("learned"):
+        t = time.time()
+        _, rep = h.learned_train(n_pairs=w["train_pairs"], epochs=w["train_epochs"], lr=w["train_lr"],
+                                 tol=w["tol_mixed"], seed=7, enable=1)
+        learned = dict(rep, seconds_total=time.time() - t)
     seed = w["seed"] + 1000 * rank          # replicas draw disjoint noise
     for _ in range(args.warmup):
         res = step(h, w["tol_mixed"], seed)
@@ -309,11 +353,21 @@ def main():
                 "achieved": dom["gbs"], "peak": peak, "unit": "GB/s", "frac": dom["gbs"] / peak,
                 "peak_source": peak_kind, "traffic": None, "kernels": kern}
 
+    if learned is not None and rank == 0:
+        # the same mixed estimate without the network (plain multigrid smoother)
+        h.learned_set(None, enable=0)
+        torch.cuda.synchronize()
+        t = time.time()
+        rp = step(h, w["tol_mixed"], seed)
+        torch.cuda.synchronize()
+        learned["plain_mixed_seconds"] = time.time() - t
+        learned["plain_mixed_iters"] = rp["iters"]
+        learned["with_net_iters"] = res["iters"]
+        learned["with_net_seconds"] = t_step
     fp64 = None
     if not args.no_fp64_form and rank == 0:
         h.close()
-        h64 = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, w["nx"], w["ny"], hierarchy_params(mlmc, mlmc.PREC_FP64),
-                             stream=stream)
+        h64 = make_hierarchy(mlmc, mlmc.PREC_FP64, w, stream)
         torch.cuda.synchronize()
         t = time.time()
         r64 = step(h64, w["tol_fp64"], seed)
@@ -328,8 +382,7 @@ def main():
     # end to end through the C ABI: setup from the host descriptor + estimate + result read-back
     torch.cuda.synchronize()
     t = time.time()
-    he = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, w["nx"], w["ny"], hierarchy_params(mlmc, mlmc.PREC_MIXED_FP32),
-                        stream=stream)
+    he = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, stream)
     step(he, w["tol_mixed"], seed)
     he.close()
     torch.cuda.synchronize()
@@ -337,22 +390,23 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(res)
+        cpu = cpu_baseline(res, w)
     if rank == 0:
         import ctypes
         line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
-                "config": dict(config_dict("mixed: FP32 K-cycle under FP64 FGMRES"), allocation=args.alloc),
+                "config": dict(config_dict("mixed: FP32 K-cycle under FP64 FGMRES", w), allocation=args.alloc),
                 "clocks": sampler.summary(local), "gpu_launches": int(launches), "wall_s_timed": wall,
-                "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 0,
+                "e2e": {"value": e2e, "unit": "s",
+                        "h2d_bytes_per_step": 0 if w["kind"] == "laplace" else 2 * w["nx"] * w["ny"] * 16,
                         "d2h_bytes_per_step": ctypes.sizeof(mlmc.EstimateResult),
                         "includes": "hierarchy setup from the host descriptor + estimate + result read-back"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "result": {"trace": res["trace"].real, "std_err": res["std_err"], "tau": res["tau"],
                            "coarse_term": res["coarse_term"].real, "n_samples": res["n_samples"],
                            "iters": res["iters"], "seconds_per_level": res["seconds"]},
-                "fp64_form": fp64}
+                "fp64_form": fp64, "learned": learned}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -106,6 +106,7 @@ typedef struct {
                           steps in the cycle precision (each preconditioned by one cycle);
                           0: by one cycle                                                      */
   int graphs;          /* 1: replay each inner solve as a captured CUDA graph                   */
+  int coarse_smooth;   /* > 0: pre- and post-smoothing sweeps on levels >= 2 (else as level 1) */
   const void *const *user_P; /* optional, host: user_P[l-1] = P_l as blocks [agg][ax*ay*d][dc]
                           (double, or mlmc_c64 for complex operators); columns must be
                           orthonormal.  Replaces the test-vector setup.  NULL = build P.      */

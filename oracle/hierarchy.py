@@ -60,6 +60,7 @@ class SetupParams:
     smooth_pre: int = 1           # red-black GS sweeps of the cycle used by the bootstrap
     smooth_post: int = 1
     kcycle_its: int = 2
+    coarse_smooth: int = 0        # > 0: sweeps on levels >= 2 in that cycle
 
 
 def tv_count(params, lvl):
@@ -194,7 +195,8 @@ def build_hierarchy(A1, nx, ny, d, params: SetupParams):
     V = level1_test_vectors(base.A, base.n, params)
     levels = _coarsen(base, V, params)
     for _ in range(params.bootstrap if params.kind != "constant" else 0):
-        M = Cycle(levels, 0, params.smooth_pre, params.smooth_post, "K", params.kcycle_its)
+        M = Cycle(levels, 0, params.smooth_pre, params.smooth_post, "K", params.kcycle_its,
+                  coarse_smooth=params.coarse_smooth)
         for _ in range(params.boot_iters):
             V = np.stack([V[:, t] - M(base.A @ V[:, t]) for t in range(V.shape[1])], axis=1)
         levels = _coarsen(base, V, params)

@@ -106,9 +106,10 @@ class Cycle:
                  x += P_l ec; x = post-smooth(x, b).
     """
 
-    def __init__(self, levels, first=0, pre=1, post=1, kind="K", kcycle_its=2, coarse_inv=None):
+    def __init__(self, levels, first=0, pre=1, post=1, kind="K", kcycle_its=2, coarse_inv=None, coarse_smooth=0):
         self.levels, self.first = levels, first
         self.pre, self.post = pre, post
+        self.coarse_smooth = coarse_smooth      # > 0: sweeps on every level below the finest
         self.kind, self.kits = kind, kcycle_its
         self.smoothers = [RedBlackGS(L) if i < len(levels) - 1 else None
                           for i, L in enumerate(levels)]
@@ -119,7 +120,9 @@ class Cycle:
         if l == last:
             return self.coarse_inv @ b
         L = self.levels[l]
-        x = self.smoothers[l].pre(np.zeros_like(b), b, self.pre)
+        pre = self.coarse_smooth if (l > 0 and self.coarse_smooth > 0) else self.pre
+        post = self.coarse_smooth if (l > 0 and self.coarse_smooth > 0) else self.post
+        x = self.smoothers[l].pre(np.zeros_like(b), b, pre)
         r = b - L.A @ x
         rc = L.P.conj().T @ r
         if l + 1 == last or self.kind == "V":
@@ -128,7 +131,7 @@ class Cycle:
             ec, _, _ = fgmres(self.levels[l + 1].A, rc, lambda v: self.cycle(l + 1, v),
                               tol=0.0, m=self.kits, maxit=self.kits)
         x = x + L.P @ ec
-        return self.smoothers[l].post(x, b, self.post)
+        return self.smoothers[l].post(x, b, post)
 
     def __call__(self, b):
         return self.cycle(self.first, b)

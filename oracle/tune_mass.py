@@ -5,7 +5,7 @@ generator.  sigma_max by power iteration on S^* S, sigma_min by inverse
 iteration on S^* S with sparse-LU solves; bisection on m.  The workloads
 record the printed masses.
 
-usage: python -m oracle.tune_mass NX NY LINK_SD LINK_SEED [TARGET]
+usage: python -m oracle.tune_mass NX NY LINK_SD LINK_SEED [TARGET [LO HI SCAN]]
 """
 import sys
 
@@ -16,7 +16,7 @@ from .operators import wilson2d
 from paper_2108_11281_gb300.workloads import gauge_links
 
 
-def sigma_extremes(S, iters=60, seed=0):
+def sigma_extremes(S, iters=30, seed=0):
     rng = np.random.default_rng(seed)
     n = S.shape[0]
     v = rng.normal(size=n) + 1j * rng.normal(size=n)
@@ -46,7 +46,10 @@ def tune(nx, ny, sd, seed, target=1e-3, lo=-0.4, hi=0.1, scan=21, steps=30):
         return smin / smax
 
     grid = np.linspace(lo, hi, scan)
-    vals = [ratio_of(m) for m in grid]
+    vals = []
+    for m in grid:
+        vals.append(ratio_of(m))
+        print("scan m %.4f ratio %.3e" % (m, vals[-1]), flush=True)
     i = int(np.argmin(vals))
     a, b = grid[max(i - 1, 0)], grid[min(i + 1, scan - 1)]
     for _ in range(40):                      # golden-section refinement of the dip
@@ -76,5 +79,6 @@ if __name__ == "__main__":
     a = sys.argv[1:]
     nx, ny, sd, seed = int(a[0]), int(a[1]), float(a[2]), int(a[3])
     target = float(a[4]) if len(a) > 4 else 1e-3
-    m, ratio = tune(nx, ny, sd, seed, target)
+    rng = dict(lo=float(a[5]), hi=float(a[6]), scan=int(a[7])) if len(a) > 7 else {}
+    m, ratio = tune(nx, ny, sd, seed, target, **rng)
     print("mass %.10f ratio %.4e" % (m, ratio))

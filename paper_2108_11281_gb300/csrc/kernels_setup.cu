@@ -300,43 +300,93 @@ void launch_trace(DType t, const void *A, int n, void *out, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ dense coarsest apply
-// Y[i][c] = sum_j Ainv[i][j] B[j][c].  32 x 32 output tile per block, j in
-// steps of 32 staged through shared memory.
+// Y[i][c] = sum_j Ainv[i][j] B[j][c].  64 x 32 output tiles, 128 threads with
+// a 4 x 4 register tile each, j in steps of 16 through shared memory; the j
+// range is split over `splits` blocks (grid.z) writing partial tiles that a
+// second kernel adds in split order.
+constexpr int DA_BM = 64, DA_BN = 32, DA_BK = 16;
+
 template <class T>
-__global__ void k_dense_apply(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ Y, int n, int k) {
-  __shared__ T As[32][33];
-  __shared__ T Bs[32][33];
-  int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 32 x 8 threads
-  int row0 = blockIdx.y * 32, col0 = blockIdx.x * 32;
-  T acc[4];
+__global__ void __launch_bounds__(128) k_dense_apply(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ Y,
+                                                     int n, int k, int jchunk) {
+  __shared__ T As[DA_BK][DA_BM + 1];
+  __shared__ T Bs[DA_BK][DA_BN];
+  const int tx = threadIdx.x % 8, ty = threadIdx.x / 8;        // 8 x 16 threads, 4 x 4 outputs each
+  const int row0 = blockIdx.y * DA_BM, col0 = blockIdx.x * DA_BN;
+  const int j_begin = blockIdx.z * jchunk, j_end = min(n, j_begin + jchunk);
+  T acc[4][4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) acc[u] = zero<T>();
-  for (int j0 = 0; j0 < n; j0 += 32) {
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int r = ty + 8 * u;
-      As[r][tx] = (row0 + r < n && j0 + tx < n) ? A[(size_t)(row0 + r) * n + j0 + tx] : zero<T>();
-      Bs[r][tx] = (j0 + r < n && col0 + tx < k) ? B[(size_t)(j0 + r) * k + col0 + tx] : zero<T>();
+    for (int b = 0; b < 4; ++b) acc[a][b] = zero<T>();
+  for (int j0 = j_begin; j0 < j_end; j0 += DA_BK) {
+    for (int e = threadIdx.x; e < DA_BK * DA_BM; e += 128) {
+      int r = e / DA_BK, jj = e % DA_BK;
+      int gi = row0 + r, gj = j0 + jj;
+      As[jj][r] = (gi < n && gj < j_end) ? A[(size_t)gi * n + gj] : zero<T>();
+    }
+    for (int e = threadIdx.x; e < DA_BK * DA_BN; e += 128) {
+      int jj = e / DA_BN, c = e % DA_BN;
+      int gj = j0 + jj, gc = col0 + c;
+      Bs[jj][c] = (gj < j_end && gc < k) ? B[(size_t)gj * k + gc] : zero<T>();
     }
     __syncthreads();
-#pragma unroll 8
-    for (int jj = 0; jj < 32; ++jj) {
-      T b = Bs[jj][tx];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] = acc[u] + As[ty + 8 * u][jj] * b;
+    for (int jj = 0; jj < DA_BK; ++jj) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[jj][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[jj][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = acc[a][b] + av[a] * bv[b];
     }
     __syncthreads();
   }
+  T *Yz = Y + (size_t)blockIdx.z * n * k;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    int r = row0 + ty + 8 * u, c = col0 + tx;
-    if (r < n && c < k) Y[(size_t)r * k + c] = acc[u];
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int r = row0 + ty * 4 + a, c = col0 + tx * 4 + b;
+      if (r < n && c < k) Yz[(size_t)r * k + c] = acc[a][b];
+    }
+}
+
+template <class T>
+__global__ void k_dense_sum(const T *part, int splits, size_t count, T *Y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    T s = part[i];
+    for (int z = 1; z < splits; ++z) s = s + part[(size_t)z * count + i];
+    Y[i] = s;
   }
 }
 
-void launch_dense_apply(DType t, const void *Ainv, const void *B, void *Y, int n, int k, cudaStream_t s) {
-  dim3 g((k + 31) / 32, (n + 31) / 32);
-  MLMC_DISPATCH(t, T, k_dense_apply<T><<<g, 256, 0, s>>>((const T *)Ainv, (const T *)B, (T *)Y, n, k));
+int dense_apply_splits(int n, int k) {
+  int tiles = ((k + DA_BN - 1) / DA_BN) * ((n + DA_BM - 1) / DA_BM);
+  int s = 152 / (tiles > 0 ? tiles : 1);
+  if (s > 8) s = 8;
+  if (s < 1) s = 1;
+  while (s > 1 && n / s < 4 * DA_BK) --s;
+  return s;
+}
+
+void launch_dense_apply(DType t, const void *Ainv, const void *B, void *Y, int n, int k, void *part, cudaStream_t s) {
+  int splits = part ? dense_apply_splits(n, k) : 1;
+  int jchunk = (n + splits - 1) / splits;
+  jchunk = (jchunk + DA_BK - 1) / DA_BK * DA_BK;
+  dim3 g((k + DA_BN - 1) / DA_BN, (n + DA_BM - 1) / DA_BM, splits);
+  MLMC_DISPATCH(t, T, {
+    if (splits == 1) {
+      k_dense_apply<T><<<g, 128, 0, s>>>((const T *)Ainv, (const T *)B, (T *)Y, n, k, jchunk);
+    } else {
+      k_dense_apply<T><<<g, 128, 0, s>>>((const T *)Ainv, (const T *)B, (T *)part, n, k, jchunk);
+      size_t cnt = (size_t)n * k;
+      k_dense_sum<T><<<grid_for(cnt, 256), 256, 0, s>>>((const T *)part, splits, cnt, (T *)Y);
+    }
+  });
   MLMC_LAUNCH_CHECK("k_dense_apply");
 }
 

@@ -15,77 +15,124 @@ namespace mlmc {
 
 // ------------------------------------------------------------------ restriction / prolongation
 // rc[I][q][c] = sum_{loc,a} conj(P[I][loc*d + a][q]) r[site(I,loc)][a][c]
-template <class T, int DC>
-__global__ void k_restrict(const T *__restrict__ P, const T *__restrict__ r, T *__restrict__ rc, int nx,
-                           int ny, int d, int ax, int ay, int k) {
+// One thread per (aggregate, VEC consecutive columns), 16-byte packs when k allows.
+template <class T, int VEC> struct alignas(sizeof(T) * VEC) TPack { T v[VEC]; };
+
+template <class T, int DC, int VEC>
+__global__ void __launch_bounds__(128) k_restrict(const T *__restrict__ P, const T *__restrict__ r, T *__restrict__ rc,
+                                                  int nx, int ny, int d, int ax, int ay, int kv) {
+  typedef TPack<T, VEC> V;
   int ncx = nx / ax, ncy = ny / ay;
-  const unsigned total = (unsigned)ncx * ncy * k;
+  const unsigned total = (unsigned)ncx * ncy * kv;
   int m = ax * ay * d;
+  const V *R = (const V *)r;
+  V *RC = (V *)rc;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int I = (int)(t / (unsigned)k);
-    const int c = (int)(t - (unsigned)I * k);
+    const int I = (int)(t / (unsigned)kv);
+    const int c = (int)(t - (unsigned)I * kv);
     int bi = I % ncx, bj = I / ncx;
-    T acc[DC];
+    T acc[DC][VEC];
 #pragma unroll
-    for (int q = 0; q < DC; ++q) acc[q] = zero<T>();
+    for (int q = 0; q < DC; ++q)
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) acc[q][u] = zero<T>();
     const T *PI = P + (size_t)I * m * DC;
     for (int jj = 0; jj < ay; ++jj)
       for (int ii = 0; ii < ax; ++ii) {
         int s = (bj * ay + jj) * nx + bi * ax + ii;
         int loc = jj * ax + ii;
         for (int a = 0; a < d; ++a) {
-          T xv = r[((size_t)s * d + a) * k + c];
+          V xv = R[((size_t)s * d + a) * kv + c];
           const T *Pr = PI + (size_t)(loc * d + a) * DC;
 #pragma unroll
-          for (int q = 0; q < DC; ++q) acc[q] = acc[q] + conj(Pr[q]) * xv;
+          for (int q = 0; q < DC; ++q) {
+            T pq = conj(Pr[q]);
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) acc[q][u] = acc[q][u] + pq * xv.v[u];
+          }
         }
       }
 #pragma unroll
-    for (int q = 0; q < DC; ++q) rc[((size_t)I * DC + q) * k + c] = acc[q];
-  }
-}
-
-// x[s][a][c] += sum_q P[I(s)][loc(s)*d + a][q] ec[I][q][c]
-template <class T, int DC>
-__global__ void k_prolong_add(const T *__restrict__ P, const T *__restrict__ ec, T *__restrict__ x, int nx,
-                              int ny, int d, int ax, int ay, int k) {
-  int ncx = nx / ax;
-  const unsigned total = (unsigned)nx * ny * k;
-  int m = ax * ay * d;
-  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int s = (int)(t / (unsigned)k);
-    const int c = (int)(t - (unsigned)s * k);
-    int i = s % nx, j = s / nx;
-    int I = (j / ay) * ncx + i / ax;
-    int loc = (j % ay) * ax + (i % ax);
-    T e[DC];
+    for (int q = 0; q < DC; ++q) {
+      V o;
 #pragma unroll
-    for (int q = 0; q < DC; ++q) e[q] = ec[((size_t)I * DC + q) * k + c];
-    const T *PI = P + (size_t)I * m * DC;
-    for (int a = 0; a < d; ++a) {
-      const T *Pr = PI + (size_t)(loc * d + a) * DC;
-      T acc = zero<T>();
-#pragma unroll
-      for (int q = 0; q < DC; ++q) acc = acc + Pr[q] * e[q];
-      size_t o = ((size_t)s * d + a) * k + c;
-      x[o] = x[o] + acc;
+      for (int u = 0; u < VEC; ++u) o.v[u] = acc[q][u];
+      RC[((size_t)I * DC + q) * kv + c] = o;
     }
   }
 }
 
+// x[s][a][c] += sum_q P[I(s)][loc(s)*d + a][q] ec[I][q][c]
+template <class T, int DC, int VEC>
+__global__ void __launch_bounds__(256) k_prolong_add(const T *__restrict__ P, const T *__restrict__ ec, T *__restrict__ x,
+                                                     int nx, int ny, int d, int ax, int ay, int kv) {
+  typedef TPack<T, VEC> V;
+  int ncx = nx / ax;
+  const unsigned total = (unsigned)nx * ny * kv;
+  int m = ax * ay * d;
+  const V *E = (const V *)ec;
+  V *X = (V *)x;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int s = (int)(t / (unsigned)kv);
+    const int c = (int)(t - (unsigned)s * kv);
+    int i = s % nx, j = s / nx;
+    int I = (j / ay) * ncx + i / ax;
+    int loc = (j % ay) * ax + (i % ax);
+    V e[DC];
+#pragma unroll
+    for (int q = 0; q < DC; ++q) e[q] = E[((size_t)I * DC + q) * kv + c];
+    const T *PI = P + (size_t)I * m * DC;
+    for (int a = 0; a < d; ++a) {
+      const T *Pr = PI + (size_t)(loc * d + a) * DC;
+      size_t o = ((size_t)s * d + a) * kv + c;
+      V xv = X[o];
+#pragma unroll
+      for (int q = 0; q < DC; ++q) {
+        T pq = Pr[q];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) xv.v[u] = xv.v[u] + pq * e[q].v[u];
+      }
+      X[o] = xv;
+    }
+  }
+}
+
+template <class T> struct tr_vec { static const int v = 1; };
+template <> struct tr_vec<float> { static const int v = 4; };
+template <> struct tr_vec<double> { static const int v = 2; };
+template <> struct tr_vec<cfloat> { static const int v = 2; };
+
+template <class T, int DC>
+static void restrict_go(const ProlongView &P, const void *r, void *rc, int k, cudaStream_t s) {
+  constexpr int VW = tr_vec<T>::v;
+  const int vec = (VW > 1 && k % VW == 0) ? VW : 1;
+  const int kv = k / vec;
+  unsigned g = grid_for((size_t)(P.nx / P.ax) * (P.ny / P.ay) * kv, 128, (size_t)1 << 20);
+  if (vec == VW && VW > 1)
+    k_restrict<T, DC, VW><<<g, 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d, P.ax, P.ay, kv);
+  else
+    k_restrict<T, DC, 1><<<g, 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d, P.ax, P.ay, kv);
+}
+
+template <class T, int DC>
+static void prolong_go(const ProlongView &P, const void *ec, void *x, int k, cudaStream_t s) {
+  constexpr int VW = tr_vec<T>::v;
+  const int vec = (VW > 1 && k % VW == 0) ? VW : 1;
+  const int kv = k / vec;
+  unsigned g = grid_for((size_t)P.nx * P.ny * kv, 256, (size_t)1 << 20);
+  if (vec == VW && VW > 1)
+    k_prolong_add<T, DC, VW><<<g, 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx, P.ny, P.d, P.ax, P.ay, kv);
+  else
+    k_prolong_add<T, DC, 1><<<g, 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx, P.ny, P.d, P.ax, P.ay, kv);
+}
+
 void launch_restrict(const ProlongView &P, const void *r, void *rc, int k, cudaStream_t s) {
-  size_t total = (size_t)(P.nx / P.ax) * (P.ny / P.ay) * k;
-  unsigned g = grid_for(total, 128, (size_t)1 << 20);
-  MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC,
-    k_restrict<T, DC><<<g, 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d, P.ax, P.ay, k)));
+  MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC, restrict_go<T, DC>(P, r, rc, k, s)));
   MLMC_LAUNCH_CHECK("k_restrict");
 }
 
 void launch_prolong_add(const ProlongView &P, const void *ec, void *x, int k, cudaStream_t s) {
-  size_t total = (size_t)P.nx * P.ny * k;
-  unsigned g = grid_for(total, 256, (size_t)1 << 20);
-  MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC,
-    k_prolong_add<T, DC><<<g, 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx, P.ny, P.d, P.ax, P.ay, k)));
+  MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC, prolong_go<T, DC>(P, ec, x, k, s)));
   MLMC_LAUNCH_CHECK("k_prolong_add");
 }
 

@@ -172,42 +172,61 @@ int multidot_parts(size_t rows, int k) {
   return (int)(p < 1 ? 1 : p);
 }
 
-// partial[part][v][c] = sum over rows of chunk `part` of conj(V_v[row][c]) * w[row][c]
-template <class T>
-__global__ void __launch_bounds__(DOT_THREADS) k_multidot_partial(const T *V, size_t vstride, int nvec,
+// partial[part][v][c] = sum over rows of chunk `part` of conj(V_v[row][c]) * w[row][c].
+// Each thread owns VEC consecutive columns (16-byte loads when k allows);
+// the block covers 256 / (k / VEC) rows per step.
+template <class T, int VEC> struct alignas(sizeof(T) * VEC) DPack { T v[VEC]; };
+
+template <class T, int VEC>
+__global__ void __launch_bounds__(DOT_THREADS, 4) k_multidot_partial(const T *V, size_t vstride, int nvec,
                                                                   const T *w, size_t rows, int k,
                                                                   typename acc_of<T>::type *partial) {
   typedef typename acc_of<T>::type A;
-  __shared__ A red[DOT_THREADS];
-  const int slots = DOT_THREADS / k;          // rows handled per step
+  typedef DPack<T, VEC> P;
+  __shared__ A red[DOT_THREADS * VEC];
+  const int kv = k / VEC;
+  const int slots = DOT_THREADS / kv;          // rows handled per step
   const int tid = threadIdx.x;
-  const int col = tid % k, slot = tid / k;
+  const int cv = tid % kv, slot = tid / kv;
   const bool live = slot < slots;
   const int part = blockIdx.x, nparts = gridDim.x;
   size_t chunk = (rows + nparts - 1) / nparts;
   size_t r0 = (size_t)part * chunk, r1 = r0 + chunk < rows ? r0 + chunk : rows;
-  for (int v0 = 0; v0 < nvec; v0 += DOT_MAXV) {
-    T acc[DOT_MAXV];
+  const P *Wp = (const P *)w;
+  const P *Vp = (const P *)V;
+  const size_t vs = vstride / VEC;
+  constexpr int MV = (int)(64 / (sizeof(T) * VEC)) < DOT_MAXV ? (int)(64 / (sizeof(T) * VEC)) : DOT_MAXV;
+  for (int v0 = 0; v0 < nvec; v0 += MV) {
+    T acc[MV][VEC];
 #pragma unroll
-    for (int v = 0; v < DOT_MAXV; ++v) acc[v] = zero<T>();
+    for (int v = 0; v < MV; ++v)
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) acc[v][u] = zero<T>();
     if (live) {
-#pragma unroll 4
+#pragma unroll 2
       for (size_t r = r0 + slot; r < r1; r += slots) {
-        T wv = w[r * k + col];
+        P wv = Wp[r * kv + cv];
 #pragma unroll
-        for (int v = 0; v < DOT_MAXV; ++v)
-          if (v0 + v < nvec) acc[v] = acc[v] + dotc_l(V[(size_t)(v0 + v) * vstride + r * k + col], wv);
+        for (int v = 0; v < MV; ++v)
+          if (v0 + v < nvec) {
+            P xv = Vp[(size_t)(v0 + v) * vs + r * kv + cv];
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) acc[v][u] = acc[v][u] + dotc_l(xv.v[u], wv.v[u]);
+          }
       }
     }
 #pragma unroll
-    for (int v = 0; v < DOT_MAXV; ++v) {
+    for (int v = 0; v < MV; ++v) {
       if (v0 + v >= nvec) break;
-      red[tid] = live ? widen(acc[v]) : zero<A>();
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) red[tid * VEC + u] = live ? widen(acc[v][u]) : zero<A>();
       __syncthreads();
+      // column c = cv * VEC + u lives at red[(slot * kv + cv) * VEC + u]
       if (tid < k) {
-        A s = red[tid];
-        for (int sl = 1; sl < slots; ++sl) s = addd(s, red[sl * k + tid]);
-        partial[((size_t)part * nvec + v0 + v) * k + tid] = s;
+        const int c = tid, cvv = c / VEC, u = c % VEC;
+        A sum = red[cvv * VEC + u];
+        for (int sl = 1; sl < slots; ++sl) sum = addd(sum, red[(sl * kv + cvv) * VEC + u]);
+        partial[((size_t)part * nvec + v0 + v) * k + c] = sum;
       }
       __syncthreads();
     }
@@ -239,8 +258,13 @@ void launch_multidot(DType t, const void *V, size_t vstride, int nvec, const voi
   (void)out_t;
   MLMC_DISPATCH(t, T, {
     typedef typename acc_of<T>::type A;
-    k_multidot_partial<T><<<nparts, DOT_THREADS, 0, s>>>((const T *)V, vstride, nvec, (const T *)w, rows, k,
-                                                          (A *)partials);
+    constexpr int VW = sizeof(T) == 4 ? 2 : (16 / (int)sizeof(T) > 0 ? 16 / (int)sizeof(T) : 1);
+    if (VW > 1 && k % VW == 0 && vstride % VW == 0)
+      k_multidot_partial<T, VW><<<nparts, DOT_THREADS, 0, s>>>((const T *)V, vstride, nvec, (const T *)w, rows, k,
+                                                               (A *)partials);
+    else
+      k_multidot_partial<T, 1><<<nparts, DOT_THREADS, 0, s>>>((const T *)V, vstride, nvec, (const T *)w, rows, k,
+                                                              (A *)partials);
     MLMC_LAUNCH_CHECK("k_multidot_partial");
     int tot = nvec * k;
     k_multidot_reduce<A><<<(tot * 32 + 255) / 256, 256, 0, s>>>((const A *)partials, nparts, nvec, k, (A *)out);
@@ -252,23 +276,35 @@ void launch_multidot(DType t, const void *V, size_t vstride, int nvec, const voi
 // w[r][c] += sign * sum_v V_v[r][c] * h[v*hstride + c]   (h is FP64 / complex FP64)
 // The grid is a multiple of k threads wide, so each thread keeps one column c
 // for its whole grid-stride loop (no per-element division).
-template <class T, class H>
+template <class T, class H, int VEC>
 __global__ void __launch_bounds__(256) k_multiaxpy(T *__restrict__ w, const T *__restrict__ V, size_t vstride, int nvec,
                                                    const H *__restrict__ h, size_t hstride, double sign, size_t total, int k) {
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  typedef DPack<T, VEC> P;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;       // in packs; a multiple of k / VEC
   const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  const int c = (int)(t0 % k);
-  T hv[8];   // coefficients rounded to the storage precision: FP32 lanes for FP32 blocks
+  const int kv = k / VEC;
+  const int cv = (int)(t0 % kv);
+  const size_t totv = total / VEC, vs = vstride / VEC;
+  P *W = (P *)w;
+  const P *Vp = (const P *)V;
+  T hv[8][VEC];   // coefficients rounded to the storage precision: FP32 lanes for FP32 blocks
   for (int v0 = 0; v0 < nvec; v0 += 8) {
     const int nv = nvec - v0 < 8 ? nvec - v0 : 8;
 #pragma unroll
-    for (int v = 0; v < 8; ++v) hv[v] = v < nv ? cvt<T, H>(rmul(sign, h[(size_t)(v0 + v) * hstride + c])) : zero<T>();
-    for (size_t i = t0; i < total; i += stride) {
-      T acc = w[i];
+    for (int v = 0; v < 8; ++v)
+#pragma unroll
+      for (int u = 0; u < VEC; ++u)
+        hv[v][u] = v < nv ? cvt<T, H>(rmul(sign, h[(size_t)(v0 + v) * hstride + cv * VEC + u])) : zero<T>();
+    for (size_t i = t0; i < totv; i += stride) {
+      P acc = W[i];
 #pragma unroll
       for (int v = 0; v < 8; ++v)
-        if (v < nv) acc = acc + V[(size_t)(v0 + v) * vstride + i] * hv[v];
-      w[i] = acc;
+        if (v < nv) {
+          P x = Vp[(size_t)(v0 + v) * vs + i];
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) acc.v[u] = acc.v[u] + x.v[u] * hv[v][u];
+        }
+      W[i] = acc;
     }
   }
 }
@@ -285,17 +321,29 @@ static unsigned column_grid(size_t total, int k) {
   return (unsigned)g;
 }
 
+template <class T, class H>
+static void multiaxpy_go(void *w, const void *V, size_t vstride, int nvec, const void *h, size_t hstride, double sign,
+                         size_t total, int k, cudaStream_t s) {
+  constexpr int VW = 16 / (int)sizeof(T) > 0 ? 16 / (int)sizeof(T) : 1;
+  if (VW > 1 && k % VW == 0 && vstride % VW == 0) {
+    unsigned g = column_grid(total / VW, k / VW);
+    k_multiaxpy<T, H, VW><<<g, 256, 0, s>>>((T *)w, (const T *)V, vstride, nvec, (const H *)h, hstride, sign, total, k);
+  } else {
+    unsigned g = column_grid(total, k);
+    k_multiaxpy<T, H, 1><<<g, 256, 0, s>>>((T *)w, (const T *)V, vstride, nvec, (const H *)h, hstride, sign, total, k);
+  }
+}
+
 void launch_multiaxpy(DType t, void *w, const void *V, size_t vstride, int nvec, const void *h,
                       DType h_t, size_t hstride, double sign, size_t rows, int k, cudaStream_t s) {
   size_t total = rows * (size_t)k;
-  unsigned g = column_grid(total, k);
   (void)h_t;
   if (nvec <= 0) return;
   switch (t) {
-    case F64: k_multiaxpy<double, double><<<g, 256, 0, s>>>((double *)w, (const double *)V, vstride, nvec, (const double *)h, hstride, sign, total, k); break;
-    case F32: k_multiaxpy<float, double><<<g, 256, 0, s>>>((float *)w, (const float *)V, vstride, nvec, (const double *)h, hstride, sign, total, k); break;
-    case C64: k_multiaxpy<cdouble, cdouble><<<g, 256, 0, s>>>((cdouble *)w, (const cdouble *)V, vstride, nvec, (const cdouble *)h, hstride, sign, total, k); break;
-    case C32: k_multiaxpy<cfloat, cdouble><<<g, 256, 0, s>>>((cfloat *)w, (const cfloat *)V, vstride, nvec, (const cdouble *)h, hstride, sign, total, k); break;
+    case F64: multiaxpy_go<double, double>(w, V, vstride, nvec, h, hstride, sign, total, k, s); break;
+    case F32: multiaxpy_go<float, double>(w, V, vstride, nvec, h, hstride, sign, total, k, s); break;
+    case C64: multiaxpy_go<cdouble, cdouble>(w, V, vstride, nvec, h, hstride, sign, total, k, s); break;
+    case C32: multiaxpy_go<cfloat, cdouble>(w, V, vstride, nvec, h, hstride, sign, total, k, s); break;
   }
   MLMC_LAUNCH_CHECK("k_multiaxpy");
 }

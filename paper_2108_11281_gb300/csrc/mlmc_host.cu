@@ -69,6 +69,7 @@ struct Level {
   int ax = 0, ay = 0, dc = 0;              // aggregation towards the next level
   DevBuf P64, P32;
   DevBuf Ainv64, Ainv32;                   // coarsest level only
+  DevBuf dense_part;                       // split-j partial products of the coarsest apply
 };
 
 // Workspace of one batched FGMRES (one level, one element type).
@@ -223,7 +224,7 @@ void residual_op(H_t &h, int l, int lo, const void *x, const void *b, void *r, i
 
 void dense_apply(H_t &h, int lo, const void *b, void *x, int k) {
   const Level &C = h.lv[h.L - 1];
-  launch_dense_apply(lo ? h.t32 : h.t64, lo ? C.Ainv32.p : C.Ainv64.p, b, x, (int)C.n, k, h.stream);
+  launch_dense_apply(lo ? h.t32 : h.t64, lo ? C.Ainv32.p : C.Ainv64.p, b, x, (int)C.n, k, C.dense_part.p, h.stream);
   h.launches++;
   h.cost += (double)C.n * C.n * k;
 }
@@ -334,8 +335,10 @@ void cycle(H_t &h, int lo, int l, const void *b, void *x, int k) {
   CycleBufs &cb = h.cyc[lo][l];
   CycleBufs &cn = h.cyc[lo][l + 1];
   StencilView A = view(h, l, lo);
-  if (h.prm.smooth_pre < 1) launch_fill_zero(t, x, blk, s);
-  for (int it = 0; it < h.prm.smooth_pre; ++it) {
+  const int npre = (l > 0 && h.prm.coarse_smooth > 0) ? h.prm.coarse_smooth : h.prm.smooth_pre;
+  const int npost = (l > 0 && h.prm.coarse_smooth > 0) ? h.prm.coarse_smooth : h.prm.smooth_post;
+  if (npre < 1) launch_fill_zero(t, x, blk, s);
+  for (int it = 0; it < npre; ++it) {
     launch_rbgs_sweep(A, x, b, k, 0, it == 0, s);
     h.launches += 2;
     h.cost += nnz_of(h, l) * k;
@@ -355,7 +358,7 @@ void cycle(H_t &h, int lo, int l, const void *b, void *x, int k) {
   launch_prolong_add(pview(h, l, lo), cn.x.p, x, k, s);
   h.launches++;
   if (l == 0 && lo == 1) fine_hooks(h, x, b, k);
-  for (int it = 0; it < h.prm.smooth_post; ++it) {
+  for (int it = 0; it < npost; ++it) {
     launch_rbgs_sweep(A, x, b, k, 1, 0, s);
     h.launches += 2;
     h.cost += nnz_of(h, l) * k;
@@ -743,6 +746,10 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
       }
     } else {
       Lv.Ainv64.alloc(Lv.n * Lv.n * es);
+      size_t most = 0;     // the split count depends on the column count of a call
+      for (int kk = 1; kk <= std::max(p->block, p->n_tv); ++kk)
+        most = std::max(most, (size_t)dense_apply_splits((int)Lv.n, kk) * kk);
+      Lv.dense_part.alloc(most * Lv.n * es);
       if (mixed) Lv.Ainv32.alloc(Lv.n * Lv.n * es32);
     }
   }

@@ -184,7 +184,9 @@ void launch_gauss_jordan(DType t, const void *A, void *Ainv, void *work, int n, 
                          void *colbuf, cudaStream_t s);
 void launch_trace(DType t, const void *A, int n, void *out /* FP64 (complex) */, cudaStream_t s);
 // Y = Ainv * B  (n x n times n x k, row-major / [row][k])
-void launch_dense_apply(DType t, const void *Ainv, const void *B, void *Y, int n, int k, cudaStream_t s);
+// part: scratch of dense_apply_splits(n, k) * n * k elements (or null: no split of j)
+void launch_dense_apply(DType t, const void *Ainv, const void *B, void *Y, int n, int k, void *part, cudaStream_t s);
+int dense_apply_splits(int n, int k);
 }  // namespace mlmc
 
 namespace mlmc {

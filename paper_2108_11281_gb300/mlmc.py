@@ -44,7 +44,8 @@ class HierarchyParams(ctypes.Structure):
                 ("smooth_pre", ctypes.c_int), ("smooth_post", ctypes.c_int), ("cycle", ctypes.c_int),
                 ("kcycle_its", ctypes.c_int), ("fgmres_restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("block", ctypes.c_int), ("reorth", ctypes.c_int),
-                ("inner_its", ctypes.c_int), ("graphs", ctypes.c_int), ("user_P", ctypes.c_void_p)]
+                ("inner_its", ctypes.c_int), ("graphs", ctypes.c_int), ("coarse_smooth", ctypes.c_int),
+                ("user_P", ctypes.c_void_p)]
 
 
 class EstimateParams(ctypes.Structure):
@@ -133,7 +134,7 @@ def default_params(**kw):
                         setup_sweeps=40, coarse_sweeps=20, setup_omega=2.0 / 3.0, setup_seed=0,
                         bootstrap=1, boot_iters=2, smooth_pre=1, smooth_post=1, cycle=CYCLE_K,
                         kcycle_its=2, fgmres_restart=30, max_iter=2000, precision=PREC_FP64, block=64,
-                        reorth=1, inner_its=0, graphs=1, user_P=None)
+                        reorth=1, inner_its=0, graphs=1, coarse_smooth=0, user_P=None)
     for k, v in kw.items():
         if not hasattr(p, k):
             raise KeyError(k)
