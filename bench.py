@@ -33,8 +33,8 @@ WORKLOADS = {
     # the 1024^2 Dirichlet Laplacian, 4 levels of 4x4 aggregation, 4 smoothed test vectors
     "laplace1024": dict(name="laplace2d-1024x1024-L4-4tv-k64", kind="laplace", nx=1024, ny=1024, levels=4, n_tv=4,
                         spin_split=0, setup="smooth", setup_sweeps=160, coarse_sweeps=20, omega=2.0 / 3.0,
-                        bootstrap=1, boot_iters=2, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=10,
-                        inner_its=8, block=64, noise="rademacher", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8,
+                        bootstrap=1, boot_iters=2, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=8,
+                        inner_its=12, block=64, noise="rademacher", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8,
                         seed=0, learned=False),
     # 2-spin Wilson operator 128^2, theta ~ N(0, 0.3^2), m0 tuned to sigma_min / sigma_max = 1e-3
     "wilson128": dict(name="wilson2d-128x128-L3-8dof-k32", kind="wilson", nx=128, ny=128, levels=3, n_tv=4,

@@ -216,6 +216,23 @@ int mlmc_coarse_trace_exact(mlmc_hierarchy *h, mlmc_c64 *out);
  * level meets rho_l (and N_l >= min_samples). */
 int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_estimate_result *r);
 
+/* ---- Batched, uneven serving (many instances) ---------------------------- */
+/* Active vector-block width (columns per solve) of this handle's estimates
+ * and sample calls, 1 <= k <= block.  Samples do not depend on k. */
+int mlmc_set_block_width(mlmc_hierarchy *h, int k);
+/* Autotuner: time one block of level-`level` samples for k = 16, 32, ...,
+ * block (each twice; the second, warm run counts) and keep the k with the
+ * lowest time per sample as the active width.  Uses the setup noise stream,
+ * so no estimate sample is consumed.  Wall-clock based: the choice may vary
+ * between runs. */
+int mlmc_autotune_block(mlmc_hierarchy *h, int level, int noise, double tol, int *k_out, double *seconds_per_sample);
+/* Run mlmc_trace_estimate on `count` independent hierarchies with `workers`
+ * host threads.  Each hierarchy works on its own stream, so instances of
+ * uneven size overlap on the GPU.  status[i] receives each instance's status;
+ * the return value is the first failing one (or MLMC_OK). */
+int mlmc_trace_estimate_batch(mlmc_hierarchy *const *hs, int count, const mlmc_estimate_params *params, int workers,
+                              mlmc_estimate_result *results, int *status);
+
 /* Time one kernel family on level l with CUDA events on the hierarchy's
  * stream: which = 0 operator apply (FP64), 1 operator apply (FP32),
  * 2 red-black GS sweep, 3 column multi-dot of 4 basis blocks against w,

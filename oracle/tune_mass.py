@@ -6,6 +6,8 @@ iteration on S^* S with sparse-LU solves; bisection on m.  The workloads
 record the printed masses.
 
 usage: python -m oracle.tune_mass NX NY LINK_SD LINK_SEED [TARGET [LO HI SCAN]]
+       python -m oracle.tune_mass NX NY LINK_SD LINK_SEED TARGET --bisect M_CRIT M_HI STEPS
+         (bisection on [M_CRIT, M_HI], the physical side above a known critical mass)
 """
 import sys
 
@@ -79,6 +81,20 @@ if __name__ == "__main__":
     a = sys.argv[1:]
     nx, ny, sd, seed = int(a[0]), int(a[1]), float(a[2]), int(a[3])
     target = float(a[4]) if len(a) > 4 else 1e-3
+    if len(a) > 5 and a[5] == "--bisect":
+        U = gauge_links(nx, ny, sd, seed)
+        lo, hi = float(a[6]), float(a[7])
+        for _ in range(int(a[8])):
+            m = 0.5 * (lo + hi)
+            smin, smax = sigma_extremes(wilson2d(nx, ny, m, U))
+            ratio = smin / smax
+            print("bisect m %.6f ratio %.4e" % (m, ratio), flush=True)
+            if ratio > target:
+                hi = m
+            else:
+                lo = m
+        print("mass %.10f ratio %.4e" % (m, ratio))
+        sys.exit(0)
     rng = dict(lo=float(a[5]), hi=float(a[6]), scan=int(a[7])) if len(a) > 7 else {}
     m, ratio = tune(nx, ny, sd, seed, target, **rng)
     print("mass %.10f ratio %.4e" % (m, ratio))

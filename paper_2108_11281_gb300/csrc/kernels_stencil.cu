@@ -7,6 +7,7 @@
 // vector blocks are [site][dof][k] with the k right-hand sides innermost, so
 // the k threads of one site read consecutive addresses and share the
 // coefficient loads through L1.
+#include <cstring>
 #include <type_traits>
 
 #include "mlmc_internal.cuh"
@@ -26,6 +27,22 @@ __device__ inline void neighbours(int s, int nx, int ny, int nb[5]) {
 // One thread per (site, VEC consecutive columns): the d x d coefficient blocks
 // are loaded once per VEC columns, the vector entries as 16-byte packs.
 template <class T, int VEC> struct alignas(sizeof(T) * VEC) Pack { T v[VEC]; };
+
+// Row r of a d x d coefficient block, with 16-byte loads when the row allows.
+template <class T, int D>
+__device__ inline void load_row(const T *__restrict__ p, T out[D]) {
+  if constexpr ((D * sizeof(T)) % 16 == 0) {
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+    for (int i = 0; i < (int)(D * sizeof(T) / 16); ++i) {
+      uint4 w = __ldg(q + i);
+      memcpy(&out[i * (16 / sizeof(T))], &w, 16);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < D; ++i) out[i] = p[i];
+  }
+}
 
 template <class T, int D, int VEC>
 __global__ void __launch_bounds__(256) k_stencil(const T *__restrict__ coef, const T *__restrict__ x,
@@ -47,15 +64,17 @@ __global__ void __launch_bounds__(256) k_stencil(const T *__restrict__ coef, con
     for (int dir = 0; dir < 5; ++dir) {
       const T *B = coef + ((size_t)s * 5 + dir) * D * D;
       const V *xs = (const V *)x + (size_t)nb[dir] * D * kv + c;
+      V xq[D];
 #pragma unroll
-      for (int q = 0; q < D; ++q) {
-        V xv = xs[(size_t)q * kv];
+      for (int q = 0; q < D; ++q) xq[q] = xs[(size_t)q * kv];
 #pragma unroll
-        for (int r = 0; r < D; ++r) {
-          T br = B[r * D + q];
+      for (int r = 0; r < D; ++r) {
+        T row[D];
+        load_row<T, D>(B + r * D, row);
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) acc[r][u] = acc[r][u] + br * xv.v[u];
-        }
+        for (int q = 0; q < D; ++q)
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) acc[r][u] = acc[r][u] + row[q] * xq[q].v[u];
       }
     }
     size_t o = (size_t)s * D * kv + c;
@@ -75,10 +94,11 @@ __global__ void __launch_bounds__(256) k_stencil(const T *__restrict__ coef, con
   }
 }
 
-// columns per thread for the generic kernels: 16-byte packs for FP32 data
-template <class T> struct gen_vec { static const int v = 1; };
-template <> struct gen_vec<float> { static const int v = 4; };
-template <> struct gen_vec<cfloat> { static const int v = 2; };
+// columns per thread for the generic kernels: 16-byte packs for FP32 data on
+// small blocks; fewer columns per thread as d grows, to bound registers
+template <class T, int D> struct gen_vec { static const int v = 1; };
+template <int D> struct gen_vec<float, D> { static const int v = D <= 2 ? 4 : (D == 4 ? 2 : 1); };
+template <int D> struct gen_vec<cfloat, D> { static const int v = D <= 2 ? 2 : 1; };
 
 #define MLMC_DDISPATCH(d, DD, ...)                       \
   switch (d) {                                           \
@@ -91,7 +111,7 @@ template <> struct gen_vec<cfloat> { static const int v = 2; };
 
 template <class T, int D>
 static void stencil_go(const StencilView &A, const void *x, const void *b, void *y, int k, int mode, cudaStream_t s) {
-  constexpr int VW = gen_vec<T>::v;
+  constexpr int VW = gen_vec<T, D>::v;
   if (VW > 1 && k % VW == 0) {
     int kv = k / VW;
     unsigned g = grid_for((size_t)A.nx * A.ny * kv, 256, (size_t)1 << 20);
@@ -239,6 +259,10 @@ void launch_stencil(const StencilView &A, const void *x, const void *b, void *y,
 // For every site s of colour `colour` ((i + j) % 2): x_s += D_s^{-1} (b - A x)_s.
 // Sites of one colour couple only to the other colour, so the half-sweep is
 // an exact block Gauss-Seidel step in red-black order (needs nx, ny even).
+// the smoother keeps 16-byte packs for complex FP32 blocks up to d = 8 (measured faster there)
+template <class T, int D> struct rbgs_vec { static const int v = gen_vec<T, D>::v; };
+template <int D> struct rbgs_vec<cfloat, D> { static const int v = D <= 8 ? 2 : 1; };
+
 template <class T, int D, int VEC>
 __global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, const T *__restrict__ dinv,
                                                    T *__restrict__ x, const T *__restrict__ b, int nx, int ny, int kv,
@@ -266,15 +290,17 @@ __global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, c
     for (int dir = 0; dir < 5; ++dir) {
       const T *B = coef + ((size_t)s * 5 + dir) * D * D;
       const V *xs = (const V *)x + (size_t)nb[dir] * D * kv + c;
+      V xq[D];
 #pragma unroll
-      for (int q = 0; q < D; ++q) {
-        V xv = xs[(size_t)q * kv];
+      for (int q = 0; q < D; ++q) xq[q] = xs[(size_t)q * kv];
 #pragma unroll
-        for (int r = 0; r < D; ++r) {
-          T br = B[r * D + q];
+      for (int r = 0; r < D; ++r) {
+        T row[D];
+        load_row<T, D>(B + r * D, row);
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) res[r][u] = res[r][u] - br * xv.v[u];
-        }
+        for (int q = 0; q < D; ++q)
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) res[r][u] = res[r][u] - row[q] * xq[q].v[u];
       }
     }
     const T *Di = dinv + (size_t)s * D * D;
@@ -282,12 +308,12 @@ __global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, c
 #pragma unroll
     for (int r = 0; r < D; ++r) {
       V cur = X[o + (size_t)r * kv];
+      T row[D];
+      load_row<T, D>(Di + r * D, row);
 #pragma unroll
-      for (int q = 0; q < D; ++q) {
-        T dq = Di[r * D + q];
+      for (int q = 0; q < D; ++q)
 #pragma unroll
-        for (int u = 0; u < VEC; ++u) cur.v[u] = cur.v[u] + dq * res[q][u];
-      }
+        for (int u = 0; u < VEC; ++u) cur.v[u] = cur.v[u] + row[q] * res[q][u];
       X[o + (size_t)r * kv] = cur;
     }
   }
@@ -295,7 +321,7 @@ __global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, c
 
 template <class T, int D>
 static void rbgs_go(const StencilView &A, void *x, const void *b, int k, int colour, cudaStream_t s) {
-  constexpr int VW = gen_vec<T>::v;
+  constexpr int VW = rbgs_vec<T, D>::v;
   if (VW > 1 && k % VW == 0) {
     int kv = k / VW;
     unsigned g = grid_for((size_t)(A.nx / 2) * A.ny * kv, 256, (size_t)1 << 20);

@@ -18,25 +18,30 @@ namespace mlmc {
 // One thread per (aggregate, VEC consecutive columns), 16-byte packs when k allows.
 template <class T, int VEC> struct alignas(sizeof(T) * VEC) TPack { T v[VEC]; };
 
-template <class T, int DC, int VEC>
+// One thread per (aggregate, group of QG coarse dofs, VEC columns): with many
+// coarse dofs per aggregate the groups keep enough threads in flight.
+template <class T, int DC, int VEC, int QG>
 __global__ void __launch_bounds__(128) k_restrict(const T *__restrict__ P, const T *__restrict__ r, T *__restrict__ rc,
                                                   int nx, int ny, int d, int ax, int ay, int kv) {
   typedef TPack<T, VEC> V;
+  constexpr int NG = DC / QG;
   int ncx = nx / ax, ncy = ny / ay;
-  const unsigned total = (unsigned)ncx * ncy * kv;
+  const unsigned total = (unsigned)ncx * ncy * NG * kv;
   int m = ax * ay * d;
   const V *R = (const V *)r;
   V *RC = (V *)rc;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int I = (int)(t / (unsigned)kv);
-    const int c = (int)(t - (unsigned)I * kv);
+    const int c = (int)(t % (unsigned)kv);
+    const unsigned ig = t / (unsigned)kv;
+    const int g = (int)(ig % NG);
+    const int I = (int)(ig / NG);
     int bi = I % ncx, bj = I / ncx;
-    T acc[DC][VEC];
+    T acc[QG][VEC];
 #pragma unroll
-    for (int q = 0; q < DC; ++q)
+    for (int q = 0; q < QG; ++q)
 #pragma unroll
       for (int u = 0; u < VEC; ++u) acc[q][u] = zero<T>();
-    const T *PI = P + (size_t)I * m * DC;
+    const T *PI = P + (size_t)I * m * DC + g * QG;
     for (int jj = 0; jj < ay; ++jj)
       for (int ii = 0; ii < ax; ++ii) {
         int s = (bj * ay + jj) * nx + bi * ax + ii;
@@ -45,7 +50,7 @@ __global__ void __launch_bounds__(128) k_restrict(const T *__restrict__ P, const
           V xv = R[((size_t)s * d + a) * kv + c];
           const T *Pr = PI + (size_t)(loc * d + a) * DC;
 #pragma unroll
-          for (int q = 0; q < DC; ++q) {
+          for (int q = 0; q < QG; ++q) {
             T pq = conj(Pr[q]);
 #pragma unroll
             for (int u = 0; u < VEC; ++u) acc[q][u] = acc[q][u] + pq * xv.v[u];
@@ -53,11 +58,11 @@ __global__ void __launch_bounds__(128) k_restrict(const T *__restrict__ P, const
         }
       }
 #pragma unroll
-    for (int q = 0; q < DC; ++q) {
+    for (int q = 0; q < QG; ++q) {
       V o;
 #pragma unroll
       for (int u = 0; u < VEC; ++u) o.v[u] = acc[q][u];
-      RC[((size_t)I * DC + q) * kv + c] = o;
+      RC[((size_t)I * DC + g * QG + q) * kv + c] = o;
     }
   }
 }
@@ -105,13 +110,14 @@ template <> struct tr_vec<cfloat> { static const int v = 2; };
 template <class T, int DC>
 static void restrict_go(const ProlongView &P, const void *r, void *rc, int k, cudaStream_t s) {
   constexpr int VW = tr_vec<T>::v;
+  constexpr int QG = DC <= 4 ? DC : 2;
   const int vec = (VW > 1 && k % VW == 0) ? VW : 1;
   const int kv = k / vec;
-  unsigned g = grid_for((size_t)(P.nx / P.ax) * (P.ny / P.ay) * kv, 128, (size_t)1 << 20);
+  unsigned g = grid_for((size_t)(P.nx / P.ax) * (P.ny / P.ay) * (DC / QG) * kv, 128, (size_t)1 << 20);
   if (vec == VW && VW > 1)
-    k_restrict<T, DC, VW><<<g, 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d, P.ax, P.ay, kv);
+    k_restrict<T, DC, VW, QG><<<g, 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d, P.ax, P.ay, kv);
   else
-    k_restrict<T, DC, 1><<<g, 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d, P.ax, P.ay, kv);
+    k_restrict<T, DC, 1, QG><<<g, 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d, P.ax, P.ay, kv);
 }
 
 template <class T, int DC>

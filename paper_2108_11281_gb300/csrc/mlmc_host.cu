@@ -5,6 +5,8 @@
 // Every numerical step runs in the kernels of the other translation units;
 // this file only sequences launches and owns device memory.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -107,6 +109,7 @@ struct mlmc_hierarchy {
   DType t64 = F64, t32 = F32;
   mlmc_hierarchy_params prm{};
   int L = 0, kmax = 0;
+  int kact = 0;        // active vector-block width of estimates and sample calls (<= kmax)
   std::vector<Level> lv;
   std::vector<CycleBufs> cyc[2];                  // [0] FP64 cycle, [1] FP32 cycle
   std::vector<std::unique_ptr<Krylov>> outer;     // FP64 outer FGMRES per level
@@ -721,6 +724,7 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   h.t32 = h.complex_op ? C32 : F32;
   h.L = p->levels;
   h.kmax = p->block;
+  h.kact = p->block;
   const bool mixed = p->precision == MLMC_PREC_MIXED_FP32;
   const int dc = p->n_tv * (p->spin_split ? 2 : 1);
   const size_t es = dtype_size(h.t64), es32 = dtype_size(h.t32);
@@ -1005,7 +1009,7 @@ int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, ui
     if (!(tol > 0.0)) fail(MLMC_ERR_INVALID_ARG, "tol must be positive");
     bool all_conv = true;
     for (int done = 0, b = 0; done < n_samples; ++b) {
-      int k = std::min(h->kmax, n_samples - done);
+      int k = std::min(h->kact, n_samples - done);
       bool conv = true;
       int its = sample_block(*h, level - 1, noise, seed, first + done, k, tol, MLMC_PURPOSE_NOISE, &conv);
       copy_samples_out(*h, k, out_samples + done);
@@ -1072,7 +1076,7 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
     std::vector<mlmc_c64> tmp(std::max(5, H.kmax));
     double warm[5];
     for (int i = 0; i < 5; ++i) warm[i] = TL.re;
-    const int kw = std::min(5, H.kmax);
+    const int kw = std::min(5, H.kact);
     for (int l = 0; l < nd; ++l) {
       for (int done = 0; done < 5; done += kw) {
         int k = std::min(kw, 5 - done);
@@ -1100,7 +1104,7 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
     auto draw = [&](int l) {   // one block of samples on level difference l
       auto tl = std::chrono::steady_clock::now();
       double c0 = H.cost;
-      int k = std::min(H.kmax, maxN - (int)st[4 * l]);
+      int k = std::min(H.kact, maxN - (int)st[4 * l]);
       if (k <= 0) return false;
       bool conv = true;
       sample_block(H, l, p->noise, p->seed, (uint64_t)st[4 * l], k, p->tol, MLMC_PURPOSE_NOISE, &conv);
@@ -1153,7 +1157,7 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
           int best = 0;
           double gain = -1.0;
           for (int l = 0; l < nd; ++l) {
-            double N = st[4 * l], k = std::min(H.kmax, maxN - (int)N);
+            double N = st[4 * l], k = std::min(H.kact, maxN - (int)N);
             if (k <= 0) continue;
             double g = (var(l) / N - var(l) / (N + k)) / (cost[l] / N * k);
             if (g > gain) { gain = g; best = l; }
@@ -1393,6 +1397,67 @@ int mlmc_learned_train(mlmc_hierarchy *h, const mlmc_train_params *p, float *wei
     check_cuda(cudaStreamSynchronize(s), "sync");
     if (rep) *rep = R;
   });
+}
+
+int mlmc_set_block_width(mlmc_hierarchy *h, int k) {
+  return translate([&] {
+    need(h);
+    if (k < 1 || k > h->kmax) fail(MLMC_ERR_INVALID_ARG, "block width must be in 1..block");
+    h->kact = k;
+  });
+}
+
+int mlmc_autotune_block(mlmc_hierarchy *h, int level, int noise, double tol, int *k_out, double *seconds_per_sample) {
+  return translate([&] {
+    need_level(h, level, 1, h ? h->L - 1 : 0);
+    if (noise == MLMC_NOISE_Z4 && !h->complex_op) fail(MLMC_ERR_INVALID_ARG, "Z4 noise needs a complex operator");
+    H_t &H = *h;
+    int best = H.kmax;
+    double best_t = INFINITY;
+    for (int k = 16; k <= H.kmax; k *= 2) {
+      for (int rep = 0; rep < 2; ++rep) {      // first call captures graphs and warms caches
+        bool conv = true;
+        auto t0 = std::chrono::steady_clock::now();
+        sample_block(H, level - 1, noise, 0x7e57ull, 0, k, tol, MLMC_PURPOSE_SETUP, &conv);
+        check_cuda(cudaStreamSynchronize(H.stream), "sync");
+        double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() / k;
+        if (rep == 1 && t < best_t) {
+          best_t = t;
+          best = k;
+        }
+      }
+      if (k * 2 > H.kmax && k != H.kmax) k = H.kmax / 2;   // also try kmax itself
+    }
+    H.kact = best;
+    if (k_out) *k_out = best;
+    if (seconds_per_sample) *seconds_per_sample = best_t;
+  });
+}
+
+int mlmc_trace_estimate_batch(mlmc_hierarchy *const *hs, int count, const mlmc_estimate_params *params, int workers,
+                              mlmc_estimate_result *results, int *status) {
+  if (!hs || !params || !results || !status || count < 0 || workers < 1) {
+    g_last_error = "bad batch arguments";
+    return MLMC_ERR_INVALID_ARG;
+  }
+  std::atomic<int> next(0);
+  auto work = [&] {
+    for (;;) {
+      int i = next.fetch_add(1);
+      if (i >= count) return;
+      status[i] = mlmc_trace_estimate(hs[i], &params[i], &results[i]);
+    }
+  };
+  std::vector<std::thread> pool;
+  int nw = std::min(workers, std::max(count, 1));
+  for (int w = 0; w < nw; ++w) pool.emplace_back(work);
+  for (auto &t : pool) t.join();
+  for (int i = 0; i < count; ++i)
+    if (status[i] != MLMC_OK) {
+      g_last_error = "instance " + std::to_string(i) + " failed with status " + std::to_string(status[i]);
+      return status[i];
+    }
+  return MLMC_OK;
 }
 
 int mlmc_launch_count(const mlmc_hierarchy *h, uint64_t *count) {

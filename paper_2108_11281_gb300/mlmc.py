@@ -104,6 +104,10 @@ def _load():
         "mlmc_learned_apply": [vp, vp, vp, i],
         "mlmc_learned_grad": [vp, vp, i, ctypes.POINTER(d), vp],
         "mlmc_column_dots": [i, vp, vp, i, i, vp, vp],
+        "mlmc_set_block_width": [vp, i],
+        "mlmc_autotune_block": [vp, i, i, d, ctypes.POINTER(i), ctypes.POINTER(d)],
+        "mlmc_trace_estimate_batch": [ctypes.POINTER(vp), i, ctypes.POINTER(EstimateParams), i,
+                                      ctypes.POINTER(EstimateResult), ctypes.POINTER(i)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -121,7 +125,8 @@ EXPORTED = ["mlmc_setup_hierarchy", "mlmc_destroy_hierarchy", "mlmc_level_info",
             "mlmc_get_operator", "mlmc_apply", "mlmc_solve", "mlmc_noise", "mlmc_sample_level",
             "mlmc_coarse_trace_exact", "mlmc_trace_estimate", "mlmc_profile_kernel", "mlmc_launch_count",
             "mlmc_last_error", "mlmc_learned_train", "mlmc_learned_set", "mlmc_learned_apply", "mlmc_learned_grad",
-            "mlmc_column_dots", "mlmc_column_dots_noalloc", "mlmc_noalloc_last_error"]
+            "mlmc_column_dots", "mlmc_column_dots_noalloc", "mlmc_noalloc_last_error", "mlmc_set_block_width",
+            "mlmc_autotune_block", "mlmc_trace_estimate_batch"]
 
 
 def check(status):
@@ -270,6 +275,14 @@ class Hierarchy:
         check(lib.mlmc_learned_grad(self.handle, ctypes.c_void_p(r_ptr), k, ctypes.byref(loss), g.ctypes.data))
         return loss.value, g
 
+    def set_block_width(self, k):
+        check(lib.mlmc_set_block_width(self.handle, k))
+
+    def autotune_block(self, level=1, noise=NOISE_RADEMACHER, tol=1e-8):
+        k, t = ctypes.c_int(), ctypes.c_double()
+        check(lib.mlmc_autotune_block(self.handle, level, noise, tol, ctypes.byref(k), ctypes.byref(t)))
+        return k.value, t.value
+
     def launch_count(self):
         c = ctypes.c_uint64()
         check(lib.mlmc_launch_count(self.handle, ctypes.byref(c)))
@@ -284,6 +297,27 @@ def noise(kind, seed, level, purpose, first, n, k, complex_out, out_ptr, stream=
 def column_dots(complex_data, x_ptr, y_ptr, n, k, out_ptr, stream=0):
     check(lib.mlmc_column_dots(int(complex_data), ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), n, k,
                                ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream)))
+
+
+def trace_estimate_batch(hierarchies, params, workers=4):
+    """mlmc_trace_estimate_batch over Hierarchy objects with one EstimateParams each."""
+    n = len(hierarchies)
+    hs = (ctypes.c_void_p * n)(*[h.handle.value for h in hierarchies])
+    ps = (EstimateParams * n)(*params)
+    rs = (EstimateResult * n)()
+    st = (ctypes.c_int * n)()
+    check(lib.mlmc_trace_estimate_batch(hs, n, ps, workers, rs, st))
+    return [result_dict(rs[i]) for i in range(n)], list(st)
+
+
+def estimate_params(eps=1e-3, noise=NOISE_RADEMACHER, seed=0, tol=1e-8, allocation=ALLOC_OPTIMAL, weights=None,
+                    min_samples=5, max_samples=1 << 24):
+    p = EstimateParams(eps=eps, noise=noise, seed=seed, tol=tol, min_samples=min_samples, max_samples=max_samples,
+                       form=FORM_SIMPLIFIED, allocation=allocation)
+    if weights is not None:
+        for i, w in enumerate(weights):
+            p.weights[i] = w
+    return p
 
 
 def result_dict(r):

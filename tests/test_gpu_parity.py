@@ -295,3 +295,41 @@ def test_column_dots(mlmc, cplx):
     mlmc.column_dots(cplx, xd.data_ptr(), yd.data_ptr(), n, k, out.data_ptr())
     ref = np.einsum("ic,ic->c", x.numpy().conj(), y.numpy())
     assert np.abs(out.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max() * 10
+
+
+def test_batch_matches_serial_and_autotune(mlmc):
+    """Uneven batch (shifted Laplacians and Wilson operators of different sizes) run on
+    worker threads with one stream per instance gives the same estimates as one-by-one
+    runs; the autotuned block width does not change the samples."""
+    def build(i):
+        if i % 2 == 0:
+            N = 32 * (1 + i // 2)
+            prm = mlmc.default_params(levels=2, n_tv=4, setup_sweeps=20, coarse_sweeps=10, block=32,
+                                      precision=mlmc.PREC_MIXED_FP32, inner_its=4, fgmres_restart=8)
+            return mlmc.Hierarchy(mlmc.OP_LAPLACE2D, N, N, prm, shift=[1e-2, 1e-3][i // 2]), mlmc.NOISE_RADEMACHER
+        N = 16 * (1 + i // 2)
+        prm = mlmc.default_params(levels=2, n_tv=2, spin_split=1, setup_kind=mlmc.SETUP_INVERSE, setup_sweeps=6,
+                                  setup_omega=1.0, block=32, precision=mlmc.PREC_MIXED_FP32, inner_its=4,
+                                  fgmres_restart=8, smooth_pre=2, smooth_post=2)
+        return mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.1, links=gauge_links(N, N, 0.3, 30 + i)), mlmc.NOISE_Z4
+    built = [build(i) for i in range(4)]
+    hs = [b[0] for b in built]
+    params = [mlmc.estimate_params(eps=3e-2, noise=b[1], seed=i, tol=1e-10) for i, b in enumerate(built)]
+    batch, status = mlmc.trace_estimate_batch(hs, params, workers=4)
+    assert status == [0, 0, 0, 0]
+    k, t = hs[0].autotune_block(1, mlmc.NOISE_RADEMACHER, 1e-10)
+    assert k in (16, 32) and t > 0
+    for i, h in enumerate(hs):
+        r = mlmc.result_dict(h.trace_estimate(eps=3e-2, noise=built[i][1], seed=i, tol=1e-10,
+                                              allocation=mlmc.ALLOC_OPTIMAL))
+        if i == 0 and k != 32:
+            # a different block width draws a different number of samples, but each sample is the same
+            s, _ = h.sample_level(1, mlmc.NOISE_RADEMACHER, 0, 0, 8, 1e-10)
+            h.set_block_width(32)
+            s2, _ = h.sample_level(1, mlmc.NOISE_RADEMACHER, 0, 0, 8, 1e-10)
+            assert np.allclose(s, s2, rtol=1e-8)
+            continue
+        assert r["n_samples"] == batch[i]["n_samples"]
+        assert abs(r["trace"] - batch[i]["trace"]) <= 1e-12 * abs(r["trace"])
+    for h in hs:
+        h.close()
