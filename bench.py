@@ -27,7 +27,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WILSON256_MASS = -0.15      # replaced by the value of `python -m oracle.tune_mass 256 256 0.4 2`
+# `python -m oracle.tune_mass 256 256 0.4 2 1e-3 --bisect -0.25 -0.20 7`: sigma_min / sigma_max = 1.019e-3
+WILSON256_MASS = -0.2417968750
 
 WORKLOADS = {
     # the 1024^2 Dirichlet Laplacian, 4 levels of 4x4 aggregation, 4 smoothed test vectors
@@ -383,6 +384,9 @@ def main():
     torch.cuda.synchronize()
     t = time.time()
     he = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, stream)
+    if w.get("learned"):
+        he.learned_train(n_pairs=w["train_pairs"], epochs=w["train_epochs"], lr=w["train_lr"],
+                         tol=w["tol_mixed"], seed=7, enable=1)
     step(he, w["tol_mixed"], seed)
     he.close()
     torch.cuda.synchronize()
@@ -401,7 +405,9 @@ def main():
                 "e2e": {"value": e2e, "unit": "s",
                         "h2d_bytes_per_step": 0 if w["kind"] == "laplace" else 2 * w["nx"] * w["ny"] * 16,
                         "d2h_bytes_per_step": ctypes.sizeof(mlmc.EstimateResult),
-                        "includes": "hierarchy setup from the host descriptor + estimate + result read-back"},
+                        "includes": "hierarchy setup from the host descriptor" +
+                                    (" + network training" if w.get("learned") else "") +
+                                    " + estimate + result read-back"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "result": {"trace": res["trace"].real, "std_err": res["std_err"], "tau": res["tau"],
                            "coarse_term": res["coarse_term"].real, "n_samples": res["n_samples"],

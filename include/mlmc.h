@@ -62,7 +62,7 @@ enum { MLMC_NOISE_RADEMACHER = 0, MLMC_NOISE_Z4 = 1 };
 enum { MLMC_PURPOSE_NOISE = 0, MLMC_PURPOSE_WARMUP = 1, MLMC_PURPOSE_SETUP = 2, MLMC_PURPOSE_TRAIN = 3 };
 enum { MLMC_SETUP_SMOOTH = 0, MLMC_SETUP_INVERSE = 1, MLMC_SETUP_CONSTANT = 2 };
 enum { MLMC_PREC_FP64 = 0, MLMC_PREC_MIXED_FP32 = 1 };
-enum { MLMC_FORM_SIMPLIFIED = 0, MLMC_FORM_HAT = 1 };
+enum { MLMC_FORM_SIMPLIFIED = 0, MLMC_FORM_HAT = 1, MLMC_FORM_PLAIN = 2 };
 enum { MLMC_CYCLE_V = 0, MLMC_CYCLE_K = 1 };
 enum { MLMC_ALLOC_RHO = 0, MLMC_ALLOC_OPTIMAL = 1 };
 
@@ -123,7 +123,11 @@ typedef struct {
   double tol;          /* relative residual of every level solve                             */
   int min_samples;     /* floor on N_l (paper: 5)                                            */
   int max_samples;     /* cap on N_l                                                          */
-  int form;            /* MLMC_FORM_SIMPLIFIED (Remark 4.3)                                  */
+  int form;            /* MLMC_FORM_SIMPLIFIED (Remark 4.3, noise on each level's space),
+                          MLMC_FORM_HAT (Eq. tr_ml_dec: noise on the fine space restricted by
+                          R^_l; same exact term since R^_L P^_L = I), or MLMC_FORM_PLAIN
+                          (Eq. plain_tr_estimate: Hutchinson on A_1 alone, one "level",
+                          no coarse term: the comparison the paper makes in Sec. 5)          */
   int allocation;      /* MLMC_ALLOC_RHO: Sec. 5 per-level targets rho_l from `weights`;
                           MLMC_ALLOC_OPTIMAL: Sec. 2 N_l proportional to sqrt(V_l / C_l) with
                           V_l, C_l (cost model per sample) estimated as samples arrive, until
@@ -207,6 +211,11 @@ int mlmc_column_dots(int complex_data, const void *x, const void *y, int n, int 
 int mlmc_column_dots_noalloc(int complex_data, const void *x, const void *y, int n, int k, void *out,
                              void *stream);
 const char *mlmc_noalloc_last_error(void);
+
+/* mlmc_sample_level for a chosen form (see mlmc_estimate_params.form); the
+ * plain form is only defined on level 1. */
+int mlmc_sample_level_form(mlmc_hierarchy *h, int level, int form, int noise, uint64_t seed, uint64_t first,
+                           int n_samples, double tol, mlmc_c64 *out_samples);
 
 /* tr(A_L^{-1}) from the FP64 dense inverse (Remark 4.2). */
 int mlmc_coarse_trace_exact(mlmc_hierarchy *h, mlmc_c64 *out);

@@ -58,8 +58,12 @@ def exact_coarse_trace(levels, form="simplified"):
 
 
 def sample(levels, solvers, l, x, form="simplified", hats=None):
-    """One difference sample at level l (1-based, l < L) for the noise vector x."""
+    """One difference sample at level l (1-based, l < L) for the noise vector x.
+
+    form "plain" (Eq. plain_tr_estimate): x^* A_1^{-1} x, level 1 only."""
     i = l - 1
+    if form == "plain":
+        return np.vdot(x, solvers.solve(0, x))
     if form == "simplified":
         y = solvers.solve(i, x)
         z = levels[i].P.conj().T @ x
@@ -71,7 +75,7 @@ def sample(levels, solvers, l, x, form="simplified", hats=None):
 
 
 def noise_length(levels, l, form):
-    return levels[l - 1].n if form == "simplified" else levels[0].n
+    return levels[l - 1].n if form == "simplified" else levels[0].n   # hat and plain: fine space
 
 
 def level_samples(levels, solvers, l, kind, seed, first, count, form="simplified",
@@ -124,7 +128,11 @@ def trace_estimate(levels, kind, seed=0, eps=1e-3, weights=None, block=64, min_s
     hats = None
     if form == "hat":
         hats = [accumulated_prolongation(levels, l) for l in range(1, L + 1)]
-    TL = exact_coarse_trace(levels, form)
+    if form == "plain":                 # Hutchinson on A_1 alone: one level, no exact term
+        L = 2
+        TL = 0.0
+    else:
+        TL = exact_coarse_trace(levels, form)
     # warm-up: five full estimates from the warm-up stream
     warm = np.zeros(5, dtype=np.complex128) + TL
     for l in range(1, L):

@@ -64,8 +64,12 @@ __global__ void k_add_from_channels(T *x, const float *a, int nsite, int d, int 
 template <int CI, int CO, bool RELU>
 __global__ void __launch_bounds__(256) k_conv_fwd(const float *__restrict__ in, const float *__restrict__ W,
                                                   float *__restrict__ out, int nx, int ny, int k, int periodic) {
-  __shared__ float Ws[CO * CI * 9];
-  for (int i = threadIdx.x; i < CO * CI * 9; i += blockDim.x) Ws[i] = W[i];
+  // weights transposed to [tap][ci][co] so that 4 outputs take one 16-byte shared load
+  __shared__ __align__(16) float Ws[9 * CI * CO];
+  for (int i = threadIdx.x; i < CO * CI * 9; i += blockDim.x) {
+    int co = i / (CI * 9), ci = (i / 9) % CI, tap = i % 9;
+    Ws[(tap * CI + ci) * CO + co] = W[i];
+  }
   __syncthreads();
   const unsigned total = (unsigned)nx * ny * k;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
@@ -83,8 +87,20 @@ __global__ void __launch_bounds__(256) k_conv_fwd(const float *__restrict__ in, 
 #pragma unroll
       for (int ci = 0; ci < CI; ++ci) {
         float v = src[(size_t)ci * k];
+        const float *w = Ws + (tap * CI + ci) * CO;
+        if constexpr (CO % 4 == 0) {
 #pragma unroll
-        for (int co = 0; co < CO; ++co) acc[co] = fmaf(Ws[(co * CI + ci) * 9 + tap], v, acc[co]);
+          for (int co = 0; co < CO; co += 4) {
+            float4 w4 = *reinterpret_cast<const float4 *>(w + co);
+            acc[co] = fmaf(w4.x, v, acc[co]);
+            acc[co + 1] = fmaf(w4.y, v, acc[co + 1]);
+            acc[co + 2] = fmaf(w4.z, v, acc[co + 2]);
+            acc[co + 3] = fmaf(w4.w, v, acc[co + 3]);
+          }
+        } else {
+#pragma unroll
+          for (int co = 0; co < CO; ++co) acc[co] = fmaf(w[co], v, acc[co]);
+        }
       }
     }
     float *dst = out + (size_t)s * CO * k + c;
@@ -101,8 +117,12 @@ template <int CI, int CO>
 __global__ void __launch_bounds__(256) k_conv_bwd_data(const float *__restrict__ gout, const float *__restrict__ W,
                                                        const float *__restrict__ act, float *__restrict__ gin, int nx,
                                                        int ny, int k, int periodic) {
-  __shared__ float Ws[CO * CI * 9];
-  for (int i = threadIdx.x; i < CO * CI * 9; i += blockDim.x) Ws[i] = W[i];
+  // weights transposed to [tap][co][ci]: 4 inputs take one 16-byte shared load
+  __shared__ __align__(16) float Ws[9 * CO * CI];
+  for (int i = threadIdx.x; i < CO * CI * 9; i += blockDim.x) {
+    int co = i / (CI * 9), ci = (i / 9) % CI, tap = i % 9;
+    Ws[(tap * CO + co) * CI + ci] = W[i];
+  }
   __syncthreads();
   const unsigned total = (unsigned)nx * ny * k;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
@@ -121,8 +141,20 @@ __global__ void __launch_bounds__(256) k_conv_bwd_data(const float *__restrict__
 #pragma unroll
       for (int co = 0; co < CO; ++co) {
         float g = src[(size_t)co * k];
+        const float *w = Ws + (tap * CO + co) * CI;
+        if constexpr (CI % 4 == 0) {
 #pragma unroll
-        for (int ci = 0; ci < CI; ++ci) acc[ci] = fmaf(Ws[(co * CI + ci) * 9 + tap], g, acc[ci]);
+          for (int ci = 0; ci < CI; ci += 4) {
+            float4 w4 = *reinterpret_cast<const float4 *>(w + ci);
+            acc[ci] = fmaf(w4.x, g, acc[ci]);
+            acc[ci + 1] = fmaf(w4.y, g, acc[ci + 1]);
+            acc[ci + 2] = fmaf(w4.z, g, acc[ci + 2]);
+            acc[ci + 3] = fmaf(w4.w, g, acc[ci + 3]);
+          }
+        } else {
+#pragma unroll
+          for (int ci = 0; ci < CI; ++ci) acc[ci] = fmaf(w[ci], g, acc[ci]);
+        }
       }
     }
     float *dst = gin + (size_t)s * CI * k + c;

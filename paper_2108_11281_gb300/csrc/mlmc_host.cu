@@ -850,13 +850,27 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
 
 // Samples first..first+k-1 of level l (0-based) into h.samples (complex FP64).
 // Returns the summed outer iterations of the two solves.
+// Samples first..first+k-1 of level l (0-based) into h.samples (complex FP64).
+//   simplified (Remark 4.3): x in F^{n_l};  s = x^* A_l^{-1} x - (R_l x)^* A_{l+1}^{-1} (R_l x)
+//   hat (Eq. tr_ml_dec):     x in F^{n_1}, z_l = R^_l x = R_{l-1} ... R_1 x; then as above with z_l for x
+//   plain (Eq. plain_tr_estimate): l = 0 only, s = x^* A_1^{-1} x (no coarse solve)
+// Returns the summed outer iterations of the solves.
 int sample_block(H_t &h, int l, int noise, uint64_t seed, uint64_t first, int k, double tol, int purpose,
-                 bool *conv) {
+                 bool *conv, int form = MLMC_FORM_SIMPLIFIED) {
   const int kind = noise == MLMC_NOISE_Z4 ? 1 : 0;
-  Level &Lv = h.lv[l];
   cudaStream_t s = h.stream;
-  launch_noise(kind, seed, key_hi(purpose, l + 1), first, Lv.n, k, h.t64, h.xs[l].p, s);
-  h.launches++;
+  if (form == MLMC_FORM_HAT) {
+    launch_noise(kind, seed, key_hi(purpose, l + 1), first, h.lv[0].n, k, h.t64, h.xs[0].p, s);
+    h.launches++;
+    for (int j = 0; j < l; ++j) {                // R^_l x: restrict down to level l
+      launch_restrict(pview(h, j, 0), h.xs[j].p, h.xs[j + 1].p, k, s);
+      h.launches++;
+      h.cost += (double)h.lv[j].n * h.lv[j].dc * k;
+    }
+  } else {
+    launch_noise(kind, seed, key_hi(purpose, l + 1), first, h.lv[l].n, k, h.t64, h.xs[l].p, s);
+    h.launches++;
+  }
   bool c1 = true, c2 = true;
   int its = solve_level(h, l, h.xs[l].p, h.ys[l].p, k, tol, &c1);
   char *dxy = h.dots.as<char>(), *dzw = dxy + (size_t)k * 16;
@@ -866,7 +880,7 @@ int sample_block(H_t &h, int l, int noise, uint64_t seed, uint64_t first, int k,
     h.launches += 2;
   };
   coldot(l, h.xs[l].p, h.ys[l].p, dxy);
-  if (l + 1 < h.L) {
+  if (l + 1 < h.L && form != MLMC_FORM_PLAIN) {
     launch_restrict(pview(h, l, 0), h.xs[l].p, h.xs[l + 1].p, k, s);
     h.launches++;
     its += solve_level(h, l + 1, h.xs[l + 1].p, h.ys[l + 1].p, k, tol, &c2);
@@ -1034,6 +1048,29 @@ int mlmc_column_dots(int complex_data, const void *x, const void *y, int n, int 
   });
 }
 
+int mlmc_sample_level_form(mlmc_hierarchy *h, int level, int form, int noise, uint64_t seed, uint64_t first,
+                           int n_samples, double tol, mlmc_c64 *out_samples) {
+  return translate([&] {
+    need_level(h, level, 1, h ? h->L : 0);
+    if (form != MLMC_FORM_SIMPLIFIED && form != MLMC_FORM_HAT && form != MLMC_FORM_PLAIN)
+      fail(MLMC_ERR_INVALID_ARG, "unknown form");
+    if (form == MLMC_FORM_PLAIN && level != 1) fail(MLMC_ERR_INVALID_ARG, "plain samples live on level 1");
+    if (n_samples < 0 || (n_samples > 0 && !out_samples)) fail(MLMC_ERR_INVALID_ARG, "bad sample output");
+    if (noise == MLMC_NOISE_Z4 && !h->complex_op) fail(MLMC_ERR_INVALID_ARG, "Z4 noise needs a complex operator");
+    if (!(tol > 0.0)) fail(MLMC_ERR_INVALID_ARG, "tol must be positive");
+    bool all_conv = true;
+    for (int done = 0; done < n_samples;) {
+      int k = std::min(h->kact, n_samples - done);
+      bool conv = true;
+      sample_block(*h, level - 1, noise, seed, first + done, k, tol, MLMC_PURPOSE_NOISE, &conv, form);
+      copy_samples_out(*h, k, out_samples + done);
+      all_conv = all_conv && conv;
+      done += k;
+    }
+    if (!all_conv) fail(MLMC_ERR_NOT_CONVERGED, "a level solve did not reach tol within max_iter");
+  });
+}
+
 int mlmc_coarse_trace_exact(mlmc_hierarchy *h, mlmc_c64 *out) {
   return translate([&] {
     need(h);
@@ -1051,27 +1088,30 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
     need(h);
     if (!p || !r) fail(MLMC_ERR_INVALID_ARG, "null parameters or result");
     if (!(p->eps > 0.0) || !(p->tol > 0.0)) fail(MLMC_ERR_INVALID_ARG, "eps and tol must be positive");
-    if (p->form != MLMC_FORM_SIMPLIFIED) fail(MLMC_ERR_UNSUPPORTED, "only the simplified form (Remark 4.3) is built");
+    if (p->form != MLMC_FORM_SIMPLIFIED && p->form != MLMC_FORM_HAT && p->form != MLMC_FORM_PLAIN)
+      fail(MLMC_ERR_INVALID_ARG, "unknown form");
+    const bool plain = p->form == MLMC_FORM_PLAIN;
     if (p->noise == MLMC_NOISE_Z4 && !h->complex_op) fail(MLMC_ERR_INVALID_ARG, "Z4 noise needs a complex operator");
     if (p->allocation != MLMC_ALLOC_RHO && p->allocation != MLMC_ALLOC_OPTIMAL)
       fail(MLMC_ERR_INVALID_ARG, "unknown allocation");
     H_t &H = *h;
-    const int L = H.L, nd = L - 1;
+    const int L = H.L, nd = plain ? 1 : L - 1;
     std::memset(r, 0, sizeof(*r));
-    r->levels = L;
+    r->levels = plain ? 2 : L;
     for (int l = 0; l < 16; ++l) H.iters_accum[l] = H.solves_accum[l] = 0.0;
     auto t0 = std::chrono::steady_clock::now();
-    mlmc_c64 TL;
-    {
+    mlmc_c64 TL = {0.0, 0.0};
+    if (!plain) {
+      // Remark 4.2: tr(P^_L A_L^{-1} R^_L) = tr(A_L^{-1} R^_L P^_L) = tr(A_L^{-1}), since R^_L P^_L = I
       const Level &C = H.lv[L - 1];
       launch_trace(H.t64, C.Ainv64.p, (int)C.n, H.trace.p, H.stream);
       H.launches++;
       check_cuda(cudaMemcpyAsync(&TL, H.trace.p, sizeof(TL), cudaMemcpyDeviceToHost, H.stream), "D2H trace");
       check_cuda(cudaStreamSynchronize(H.stream), "sync");
+      // Remark 4.2 cost of the exact term: inversion of A_L (n_L^3)
+      r->cost_nnz[nd] = std::pow((double)H.lv[L - 1].n, 3.0);
     }
     r->coarse_term = TL;
-    // Remark 4.2 cost of the exact term: inversion of A_L (n_L^3)
-    r->cost_nnz[nd] = std::pow((double)H.lv[L - 1].n, 3.0);
     // five warm-up estimates from the warm-up stream (Sec. 5)
     std::vector<mlmc_c64> tmp(std::max(5, H.kmax));
     double warm[5];
@@ -1081,7 +1121,7 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
       for (int done = 0; done < 5; done += kw) {
         int k = std::min(kw, 5 - done);
         bool conv = true;
-        sample_block(H, l, p->noise, p->seed, done, k, p->tol, MLMC_PURPOSE_WARMUP, &conv);
+        sample_block(H, l, p->noise, p->seed, done, k, p->tol, MLMC_PURPOSE_WARMUP, &conv, p->form);
         if (!conv) fail(MLMC_ERR_NOT_CONVERGED, "warm-up solve did not converge");
         copy_samples_out(H, k, tmp.data());
         for (int i = 0; i < k; ++i) warm[done + i] += tmp[i].re;
@@ -1107,7 +1147,7 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
       int k = std::min(H.kact, maxN - (int)st[4 * l]);
       if (k <= 0) return false;
       bool conv = true;
-      sample_block(H, l, p->noise, p->seed, (uint64_t)st[4 * l], k, p->tol, MLMC_PURPOSE_NOISE, &conv);
+      sample_block(H, l, p->noise, p->seed, (uint64_t)st[4 * l], k, p->tol, MLMC_PURPOSE_NOISE, &conv, p->form);
       if (!conv) fail(MLMC_ERR_NOT_CONVERGED, "level solve did not converge");
       launch_accumulate(H.samples.p, k, accs.as<double>() + 4 * l, H.stream);
       H.launches++;

@@ -20,7 +20,7 @@ NOISE_RADEMACHER, NOISE_Z4 = 0, 1
 PURPOSE_NOISE, PURPOSE_WARMUP, PURPOSE_SETUP = 0, 1, 2
 SETUP_SMOOTH, SETUP_INVERSE, SETUP_CONSTANT = 0, 1, 2
 PREC_FP64, PREC_MIXED_FP32 = 0, 1
-FORM_SIMPLIFIED, FORM_HAT = 0, 1
+FORM_SIMPLIFIED, FORM_HAT, FORM_PLAIN = 0, 1, 2
 CYCLE_V, CYCLE_K = 0, 1
 ALLOC_RHO, ALLOC_OPTIMAL = 0, 1
 
@@ -105,6 +105,7 @@ def _load():
         "mlmc_learned_grad": [vp, vp, i, ctypes.POINTER(d), vp],
         "mlmc_column_dots": [i, vp, vp, i, i, vp, vp],
         "mlmc_set_block_width": [vp, i],
+        "mlmc_sample_level_form": [vp, i, i, i, u64, u64, i, d, ctypes.POINTER(C64)],
         "mlmc_autotune_block": [vp, i, i, d, ctypes.POINTER(i), ctypes.POINTER(d)],
         "mlmc_trace_estimate_batch": [ctypes.POINTER(vp), i, ctypes.POINTER(EstimateParams), i,
                                       ctypes.POINTER(EstimateResult), ctypes.POINTER(i)],
@@ -126,7 +127,7 @@ EXPORTED = ["mlmc_setup_hierarchy", "mlmc_destroy_hierarchy", "mlmc_level_info",
             "mlmc_coarse_trace_exact", "mlmc_trace_estimate", "mlmc_profile_kernel", "mlmc_launch_count",
             "mlmc_last_error", "mlmc_learned_train", "mlmc_learned_set", "mlmc_learned_apply", "mlmc_learned_grad",
             "mlmc_column_dots", "mlmc_column_dots_noalloc", "mlmc_noalloc_last_error", "mlmc_set_block_width",
-            "mlmc_autotune_block", "mlmc_trace_estimate_batch"]
+            "mlmc_autotune_block", "mlmc_trace_estimate_batch", "mlmc_sample_level_form"]
 
 
 def check(status):
@@ -225,6 +226,11 @@ class Hierarchy:
         check(lib.mlmc_sample_level(self.handle, level, noise, seed, first, n_samples, tol, out, its))
         vals = np.array([complex(out[i].re, out[i].im) for i in range(n_samples)])
         return vals, list(its)[:nblk]
+
+    def sample_level_form(self, level, form, noise, seed, first, n_samples, tol):
+        out = (C64 * max(n_samples, 1))()
+        check(lib.mlmc_sample_level_form(self.handle, level, form, noise, seed, first, n_samples, tol, out))
+        return np.array([complex(out[i].re, out[i].im) for i in range(n_samples)])
 
     def coarse_trace_exact(self):
         out = C64()

@@ -40,3 +40,7 @@ LAPLACE_1024 = dict(name="laplace2d-1024x1024-L4", kind="laplace", nx=1024, ny=1
 WILSON_128 = dict(name="wilson2d-128x128-L3", kind="wilson", nx=128, ny=128, link_sd=0.3,
                   link_seed=1, mass=-0.1317442871, levels=3, n_tv=4, spin_split=True, setup="inverse",
                   sweeps=20, noise="z4", block=32, tol=1e-10, eps=1e-3)
+# mass from `python -m oracle.tune_mass 256 256 0.4 2 1e-3 --bisect -0.25 -0.20 7`: ratio 1.019e-3
+WILSON_256 = dict(name="wilson2d-256x256-L3", kind="wilson", nx=256, ny=256, link_sd=0.4, link_seed=2,
+                  mass=-0.2417968750, levels=3, n_tv=4, spin_split=True, setup="inverse", sweeps=20,
+                  noise="z4", block=32, tol=1e-8, eps=1e-3)

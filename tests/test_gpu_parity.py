@@ -15,7 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle import estimator as E
-from oracle.hierarchy import SetupParams, build_hierarchy
+from oracle.hierarchy import SetupParams, accumulated_prolongation, build_hierarchy
 from oracle.operators import laplace2d, wilson2d
 from oracle.philox import rademacher, z4, PURPOSE_NOISE, PURPOSE_SETUP
 from paper_2108_11281_gb300.workloads import gauge_links
@@ -333,3 +333,24 @@ def test_batch_matches_serial_and_autotune(mlmc):
         assert abs(r["trace"] - batch[i]["trace"]) <= 1e-12 * abs(r["trace"])
     for h in hs:
         h.close()
+
+
+def test_hat_and_plain_forms(mlmc):
+    """Hat form (noise on the fine space restricted by R^_l, Eq. tr_ml_dec) and plain
+    Hutchinson (Eq. plain_tr_estimate) samples and estimates against the oracle."""
+    h, lv = imported_laplace(mlmc, block=8)
+    solv = E.LevelSolvers(lv)
+    hats = [accumulated_prolongation(lv, l) for l in range(1, 4)]
+    for level in (1, 2):
+        got = h.sample_level_form(level, mlmc.FORM_HAT, mlmc.NOISE_RADEMACHER, 3, 2, 6, 1e-12)
+        ref = E.level_samples(lv, solv, level, "rademacher", 3, 2, 6, form="hat", hats=hats)
+        compare_samples(got, ref, 1e-9)
+    got = h.sample_level_form(1, mlmc.FORM_PLAIN, mlmc.NOISE_RADEMACHER, 3, 0, 6, 1e-12)
+    ref = E.level_samples(lv, solv, 1, "rademacher", 3, 0, 6, form="plain")
+    compare_samples(got, ref, 1e-9)
+    for form, name in ((mlmc.FORM_HAT, "hat"), (mlmc.FORM_PLAIN, "plain")):
+        r = mlmc.result_dict(h.trace_estimate(eps=5e-2, noise=mlmc.NOISE_RADEMACHER, seed=1, tol=1e-12, form=form))
+        ref = E.trace_estimate(lv, "rademacher", seed=1, eps=5e-2, block=8, form=name, solvers=solv)
+        assert r["n_samples"] == ref.n_samples, name
+        assert abs(r["trace"] - ref.trace) <= 1e-9 * abs(ref.trace), name
+    h.close()

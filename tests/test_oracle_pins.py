@@ -312,3 +312,12 @@ def test_learned_linear_special_case():
     r = rng.normal(size=32) + 1j * rng.normal(size=32)
     e, _ = NN.forward(r, [W1, W2, W3], 4, 4, 2, True, True)
     assert np.allclose(e, r, atol=1e-15)
+
+
+def test_plain_hutchinson_sample_is_unbiased():
+    """Eq. plain_tr_estimate: the mean of x^T A^{-1} x over all 2^n sign vectors is tr(A^{-1})."""
+    A = laplace2d(4, 2, 0.2)
+    h = build_hierarchy(A, 4, 2, 1, SetupParams(levels=2, agg_x=2, agg_y=2, n_tv=1, kind="constant"))
+    solv = E.LevelSolvers(h)
+    vals = [E.sample(h, solv, 1, np.array(v), form="plain") for v in itertools.product([1.0, -1.0], repeat=8)]
+    assert np.isclose(np.mean(vals), np.trace(np.linalg.inv(A.toarray())), rtol=1e-12)
