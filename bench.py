@@ -72,7 +72,7 @@ def parse():
                          "difference inside cudaProfilerStart/Stop; prints no bench line")
     ap.add_argument("--profile-nx", type=int, default=0,
                     help="with --profile-sample: lattice side for a smaller capture (default: the workload's)")
-    ap.add_argument("--workload", default="laplace1024", choices=sorted(WORKLOADS),
+    ap.add_argument("--workload", default="laplace1024", choices=sorted(WORKLOADS) + ["batch48"],
                     help="laplace1024 (default, the headline), wilson128, wilson256 (learned correction)")
     ap.add_argument("--alloc", default="optimal", choices=["optimal", "rho"],
                     help="Sec. 2 optimal allocation (default) or the Sec. 5 equal rho split")
@@ -269,10 +269,101 @@ def profile_sample(args):
     h.close()
 
 
+def batch_instances(seed=2026):
+    """48 uneven instances (seeded): 24 shifted Dirichlet Laplacians, sides 256..2048,
+    shift ~ U[1e-4, 1e-1]; 24 Wilson operators, sides 64..256, theta ~ N(0, 0.3^2),
+    mass -0.10 (above the critical mass, about -0.14 at this link spread); per level
+    difference a sample budget ~ U{16..128}."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(48):
+        lap = i < 24
+        side = int(rng.choice([256, 512, 1024, 2048] if lap else [64, 128, 256]))
+        levels = 1
+        s_ = side
+        while s_ > 16 and s_ % 4 == 0 and (s_ // 4) >= 2:
+            s_ //= 4
+            levels += 1
+        if levels < 2:
+            levels = 2
+        inst = dict(kind="laplace" if lap else "wilson", side=side, levels=levels, index=i,
+                    n_fixed=[int(rng.integers(16, 129)) for _ in range(levels - 1)])
+        if lap:
+            inst["shift"] = float(rng.uniform(1e-4, 1e-1))
+        else:
+            inst["link_seed"] = 100 + i
+        out.append(inst)
+    return out
+
+
+def run_batch(args):
+    """Config 5: the 48 instances through a pool of worker threads; each worker builds the
+    hierarchy (mixed form), autotunes the block width, runs the fixed-budget estimate and
+    frees the hierarchy.  Value: seconds for the whole batch."""
+    import threading
+    from concurrent.futures import ThreadPoolExecutor
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2108_11281_gb300 import mlmc
+    from paper_2108_11281_gb300.workloads import gauge_links
+    insts = batch_instances()
+    base = WORKLOADS["laplace1024"]
+    wb = WORKLOADS["wilson128"]
+
+    def one(inst):
+        t0 = time.time()
+        if inst["kind"] == "laplace":
+            w = dict(base, nx=inst["side"], ny=inst["side"], levels=inst["levels"])
+            w["block"] = 128 if inst["side"] <= 512 else (64 if inst["side"] <= 1024 else 32)
+            prm = hierarchy_params(mlmc, mlmc.PREC_MIXED_FP32, w)
+            h = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, inst["side"], inst["side"], prm, shift=inst["shift"])
+            nz = mlmc.NOISE_RADEMACHER
+        else:
+            w = dict(wb, nx=inst["side"], ny=inst["side"], levels=inst["levels"], block=128)
+            prm = hierarchy_params(mlmc, mlmc.PREC_MIXED_FP32, w)
+            U = gauge_links(inst["side"], inst["side"], 0.3, inst["link_seed"])
+            h = mlmc.Hierarchy(mlmc.OP_WILSON2D, inst["side"], inst["side"], prm, mass=-0.10, links=U)
+            nz = mlmc.NOISE_Z4
+        t_setup = time.time() - t0
+        k, _ = h.autotune_block(1, nz, 1e-8)
+        t1 = time.time()
+        r = mlmc.result_dict(h.trace_estimate(noise=nz, seed=inst["index"], tol=1e-8, allocation=mlmc.ALLOC_FIXED,
+                                              n_fixed=inst["n_fixed"]))
+        t_est = time.time() - t1
+        launches = h.launch_count()
+        h.close()
+        return dict(index=inst["index"], kind=inst["kind"], side=inst["side"], block=k, setup_s=t_setup,
+                    estimate_s=t_est, total_s=time.time() - t0, trace=r["trace"].real, std_err=r["std_err"],
+                    n_samples=r["n_samples"], launches=launches)
+
+    workers = 4
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        one(insts[0])
+    torch.cuda.synchronize()
+    t0 = time.time()
+    with ThreadPoolExecutor(workers) as ex:
+        res = list(ex.map(one, insts))
+    torch.cuda.synchronize()
+    wall = time.time() - t0
+    line = {"metric": METRIC, "value": wall, "unit": "s (48-instance batch)", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
+            "config": {"workload": "batch48-uneven", "workers": workers, "instances": len(insts),
+                       "allocation": "fixed budget per level ~ U{16..128}", "form": "mixed"},
+            "instances_per_s": len(insts) / wall, "gpu_launches": int(sum(r["launches"] for r in res)),
+            "sum_instance_seconds": sum(r["total_s"] for r in res), "instances": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch48":
+        run_batch(args)
         return
     if args.profile_sample:
         profile_sample(args)

@@ -64,7 +64,7 @@ enum { MLMC_SETUP_SMOOTH = 0, MLMC_SETUP_INVERSE = 1, MLMC_SETUP_CONSTANT = 2 };
 enum { MLMC_PREC_FP64 = 0, MLMC_PREC_MIXED_FP32 = 1 };
 enum { MLMC_FORM_SIMPLIFIED = 0, MLMC_FORM_HAT = 1, MLMC_FORM_PLAIN = 2 };
 enum { MLMC_CYCLE_V = 0, MLMC_CYCLE_K = 1 };
-enum { MLMC_ALLOC_RHO = 0, MLMC_ALLOC_OPTIMAL = 1 };
+enum { MLMC_ALLOC_RHO = 0, MLMC_ALLOC_OPTIMAL = 1, MLMC_ALLOC_FIXED = 2 };
 
 /* Fine operator A = A_1 (Examples 5.1 and 5.3).  Sites s = j*nx + i. */
 typedef struct {
@@ -131,7 +131,10 @@ typedef struct {
   int allocation;      /* MLMC_ALLOC_RHO: Sec. 5 per-level targets rho_l from `weights`;
                           MLMC_ALLOC_OPTIMAL: Sec. 2 N_l proportional to sqrt(V_l / C_l) with
                           V_l, C_l (cost model per sample) estimated as samples arrive, until
-                          sum V_l / N_l <= (eps tau)^2                                         */
+                          sum V_l / N_l <= (eps tau)^2;
+                          MLMC_ALLOC_FIXED: exactly n_fixed[l] samples on level difference l
+                          (serving requests with a fixed sample budget; eps unused)            */
+  int n_fixed[16];
 } mlmc_estimate_params;
 
 typedef struct {

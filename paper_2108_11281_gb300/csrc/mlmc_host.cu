@@ -1092,8 +1092,11 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
       fail(MLMC_ERR_INVALID_ARG, "unknown form");
     const bool plain = p->form == MLMC_FORM_PLAIN;
     if (p->noise == MLMC_NOISE_Z4 && !h->complex_op) fail(MLMC_ERR_INVALID_ARG, "Z4 noise needs a complex operator");
-    if (p->allocation != MLMC_ALLOC_RHO && p->allocation != MLMC_ALLOC_OPTIMAL)
+    if (p->allocation != MLMC_ALLOC_RHO && p->allocation != MLMC_ALLOC_OPTIMAL && p->allocation != MLMC_ALLOC_FIXED)
       fail(MLMC_ERR_INVALID_ARG, "unknown allocation");
+    if (p->allocation == MLMC_ALLOC_FIXED)
+      for (int l = 0; l < h->L - 1; ++l)
+        if (p->n_fixed[l] < 2) fail(MLMC_ERR_INVALID_ARG, "n_fixed must be >= 2 on every level difference");
     H_t &H = *h;
     const int L = H.L, nd = plain ? 1 : L - 1;
     std::memset(r, 0, sizeof(*r));
@@ -1160,7 +1163,26 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
     };
     auto var = [&](int l) { double N = st[4 * l]; return N > 1 ? st[4 * l + 3] / (N - 1) : INFINITY; };
     std::vector<double> w(nd, 0.0);
-    if (p->allocation == MLMC_ALLOC_RHO) {
+    if (p->allocation == MLMC_ALLOC_FIXED) {
+      for (int l = 0; l < nd; ++l) {
+        w[l] = 0.0;
+        while (st[4 * l] < p->n_fixed[l]) {
+          int k = std::min(H.kact, p->n_fixed[l] - (int)st[4 * l]);
+          auto tl = std::chrono::steady_clock::now();
+          double c0 = H.cost;
+          bool conv = true;
+          sample_block(H, l, p->noise, p->seed, (uint64_t)st[4 * l], k, p->tol, MLMC_PURPOSE_NOISE, &conv, p->form);
+          if (!conv) fail(MLMC_ERR_NOT_CONVERGED, "level solve did not converge");
+          launch_accumulate(H.samples.p, k, accs.as<double>() + 4 * l, H.stream);
+          H.launches++;
+          check_cuda(cudaMemcpyAsync(&st[4 * l], accs.as<double>() + 4 * l, 4 * sizeof(double),
+                                     cudaMemcpyDeviceToHost, H.stream), "D2H acc");
+          check_cuda(cudaStreamSynchronize(H.stream), "sync");
+          cost[l] += H.cost - c0;
+          secs[l] += std::chrono::duration<double>(std::chrono::steady_clock::now() - tl).count();
+        }
+      }
+    } else if (p->allocation == MLMC_ALLOC_RHO) {
       // Sec. 5: rho_l = sqrt(w_l) eps |tau|; sample each level until its standard error meets rho_l
       double wsum = 0.0;
       for (int l = 0; l < nd; ++l) wsum += p->weights[l];

@@ -22,7 +22,7 @@ SETUP_SMOOTH, SETUP_INVERSE, SETUP_CONSTANT = 0, 1, 2
 PREC_FP64, PREC_MIXED_FP32 = 0, 1
 FORM_SIMPLIFIED, FORM_HAT, FORM_PLAIN = 0, 1, 2
 CYCLE_V, CYCLE_K = 0, 1
-ALLOC_RHO, ALLOC_OPTIMAL = 0, 1
+ALLOC_RHO, ALLOC_OPTIMAL, ALLOC_FIXED = 0, 1, 2
 
 
 class C64(ctypes.Structure):
@@ -51,7 +51,8 @@ class HierarchyParams(ctypes.Structure):
 class EstimateParams(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("weights", ctypes.c_double * 16), ("noise", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("tol", ctypes.c_double), ("min_samples", ctypes.c_int),
-                ("max_samples", ctypes.c_int), ("form", ctypes.c_int), ("allocation", ctypes.c_int)]
+                ("max_samples", ctypes.c_int), ("form", ctypes.c_int), ("allocation", ctypes.c_int),
+                ("n_fixed", ctypes.c_int * 16)]
 
 
 class EstimateResult(ctypes.Structure):
@@ -238,9 +239,12 @@ class Hierarchy:
         return complex(out.re, out.im)
 
     def trace_estimate(self, eps=1e-3, noise=NOISE_RADEMACHER, seed=0, tol=1e-10, weights=None, min_samples=5,
-                       max_samples=1 << 24, form=FORM_SIMPLIFIED, allocation=ALLOC_RHO):
+                       max_samples=1 << 24, form=FORM_SIMPLIFIED, allocation=ALLOC_RHO, n_fixed=None):
         p = EstimateParams(eps=eps, noise=noise, seed=seed, tol=tol, min_samples=min_samples,
                            max_samples=max_samples, form=form, allocation=allocation)
+        if n_fixed is not None:
+            for i, n in enumerate(n_fixed):
+                p.n_fixed[i] = n
         if weights is not None:
             for i, w in enumerate(weights):
                 p.weights[i] = w
@@ -317,9 +321,12 @@ def trace_estimate_batch(hierarchies, params, workers=4):
 
 
 def estimate_params(eps=1e-3, noise=NOISE_RADEMACHER, seed=0, tol=1e-8, allocation=ALLOC_OPTIMAL, weights=None,
-                    min_samples=5, max_samples=1 << 24):
+                    min_samples=5, max_samples=1 << 24, n_fixed=None):
     p = EstimateParams(eps=eps, noise=noise, seed=seed, tol=tol, min_samples=min_samples, max_samples=max_samples,
                        form=FORM_SIMPLIFIED, allocation=allocation)
+    if n_fixed is not None:
+        for i, n in enumerate(n_fixed):
+            p.n_fixed[i] = n
     if weights is not None:
         for i, w in enumerate(weights):
             p.weights[i] = w
