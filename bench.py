@@ -34,20 +34,20 @@ WORKLOADS = {
     # the 1024^2 Dirichlet Laplacian, 4 levels of 4x4 aggregation, 4 smoothed test vectors
     "laplace1024": dict(name="laplace2d-1024x1024-L4-4tv-k64", kind="laplace", nx=1024, ny=1024, levels=4, n_tv=4,
                         spin_split=0, setup="smooth", setup_sweeps=160, coarse_sweeps=20, omega=2.0 / 3.0,
-                        bootstrap=1, boot_iters=2, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=8,
+                        bootstrap=2, boot_iters=5, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=8,
                         inner_its=12, block=64, noise="rademacher", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8,
                         seed=0, learned=False),
     # 2-spin Wilson operator 128^2, theta ~ N(0, 0.3^2), m0 tuned to sigma_min / sigma_max = 1e-3
     "wilson128": dict(name="wilson2d-128x128-L3-8dof-k32", kind="wilson", nx=128, ny=128, levels=3, n_tv=4,
-                      spin_split=1, setup="inverse", setup_sweeps=20, coarse_sweeps=10, omega=1.0, bootstrap=2,
-                      boot_iters=2, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=10, inner_its=8, block=32,
+                      spin_split=1, setup="inverse", setup_sweeps=20, coarse_sweeps=10, omega=1.0, bootstrap=4,
+                      boot_iters=4, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=10, inner_its=8, block=32,
                       noise="z4", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8, seed=0, link_sd=0.3, link_seed=1,
                       mass=-0.1317442871, learned=False),
     # 2-spin Wilson operator 256^2, theta ~ N(0, 0.4^2), complex64 cycle with the learned correction
     # trained on 10^4 residual/error pairs from plain multigrid solves (training is setup, not timed)
     "wilson256": dict(name="wilson2d-256x256-L3-8dof-k32-learned", kind="wilson", nx=256, ny=256, levels=3,
                       n_tv=4, spin_split=1, setup="inverse", setup_sweeps=20, coarse_sweeps=10, omega=1.0,
-                      bootstrap=2, boot_iters=2, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=10,
+                      bootstrap=4, boot_iters=4, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=10,
                       inner_its=8, block=32, noise="z4", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8, seed=0,
                       link_sd=0.4, link_seed=2, mass=WILSON256_MASS, learned=True, train_pairs=10000,
                       train_epochs=3, train_lr=1e-3),
@@ -62,7 +62,7 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--profile-sample", action="store_true",
                     help="for ncu only: after setup, one warm block and one profiled 64-sample block per level "
                          "difference inside cudaProfilerStart/Stop; prints no bench line")
+    ap.add_argument("--profile-kernel", default="", choices=["", "multidot", "multiaxpy", "rbgs", "stencil"],
+                    help="with --profile-sample: instead of sample blocks, the one kernel launch the bench's "
+                         "roofline measures (3 warm launches, then 1), inside cudaProfilerStart/Stop")
     ap.add_argument("--profile-nx", type=int, default=0,
                     help="with --profile-sample: lattice side for a smaller capture (default: the workload's)")
     ap.add_argument("--workload", default="laplace1024", choices=sorted(WORKLOADS) + ["batch48"],
@@ -258,6 +261,15 @@ def profile_sample(args):
         w["nx"] = w["ny"] = args.profile_nx
     nz = mlmc.NOISE_Z4 if w["noise"] == "z4" else mlmc.NOISE_RADEMACHER
     h = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, torch.cuda.current_stream().cuda_stream)
+    if args.profile_kernel:
+        which = {"stencil": 1, "rbgs": 2, "multidot": 3, "multiaxpy": 4}[args.profile_kernel]
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        h.profile_kernel(which, 1, w["block"], 1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        h.close()
+        return
     for lvl in range(1, w["levels"]):
         h.sample_level(lvl, nz, 0, 0, w["block"], w["tol_mixed"])
     torch.cuda.synchronize()
@@ -355,6 +367,17 @@ def run_batch(args):
             "instances_per_s": len(insts) / wall, "gpu_launches": int(sum(r["launches"] for r in res)),
             "sum_instance_seconds": sum(r["total_s"] for r in res), "instances": res}
     print(json.dumps(line), flush=True)
+
+
+def closed_form(w):
+    """Example 5.1: tr(A^{-1}) = sum over the eigenvalues 4 + shift - 2cos(i pi/(N+1)) - 2cos(j pi/(N+1))
+    (Dirichlet Laplacian; None for other operators)."""
+    if w["kind"] != "laplace":
+        return None
+    import numpy as np
+    cx = 2 * np.cos(np.arange(1, w["nx"] + 1) * np.pi / (w["nx"] + 1))
+    cy = 2 * np.cos(np.arange(1, w["ny"] + 1) * np.pi / (w["ny"] + 1))
+    return float(np.sum(1.0 / (4.0 + w.get("shift", 0.0) - cy[:, None] - cx[None, :])))
 
 
 def main():
@@ -501,6 +524,7 @@ def main():
                                     " + estimate + result read-back"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "result": {"trace": res["trace"].real, "std_err": res["std_err"], "tau": res["tau"],
+                           "closed_form": closed_form(w),
                            "coarse_term": res["coarse_term"].real, "n_samples": res["n_samples"],
                            "iters": res["iters"], "seconds_per_level": res["seconds"]},
                 "fp64_form": fp64, "learned": learned}

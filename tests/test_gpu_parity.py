@@ -110,16 +110,17 @@ def projector_distance(Pa, Pb):
     return max(np.abs(a @ a.conj().T - b @ b.conj().T).max() for a, b in zip(Pa, Pb))
 
 
-@pytest.mark.parametrize("case", ["laplace", "wilson"])
+@pytest.mark.parametrize("case", ["laplace", "wilson", "laplace-boot3"])
 def test_setup_matches_oracle(mlmc, case):
     """GPU test vectors, bootstrap, MGS and Galerkin reproduce the oracle's hierarchy
     (same algorithm, FP64; agreement to rounding amplified by the setup's conditioning)."""
-    if case == "laplace":
+    if case.startswith("laplace"):
         N = 64
-        kw = dict(levels=3, n_tv=4, setup_sweeps=20, coarse_sweeps=10, bootstrap=1, boot_iters=2)
+        nb, ni = (1, 2) if case == "laplace" else (2, 3)
+        kw = dict(levels=3, n_tv=4, setup_sweeps=20, coarse_sweeps=10, bootstrap=nb, boot_iters=ni)
         h = laplace_h(mlmc, N, block=8, **kw)
         A = laplace2d(N, N)
-        sp_ = SetupParams(levels=3, n_tv=4, sweeps=20, coarse_sweeps=10, bootstrap=1, boot_iters=2)
+        sp_ = SetupParams(levels=3, n_tv=4, sweeps=20, coarse_sweeps=10, bootstrap=nb, boot_iters=ni)
         lv = build_hierarchy(A, N, N, 1, sp_)
     else:
         N = 16
