@@ -216,8 +216,9 @@ def cpu_baseline(result, w):
 # per-level sample counts and mean outer iterations of each workload's estimate
 # (same estimator and noise on both sides, optimal allocation); used only by
 # the reference arm's extrapolation, which runs before any GPU number exists.
-REFERENCE = {"laplace1024": {"n_samples": [2880, 3200, 7872], "iters": [5.0, 6.0, 6.0]},
-             "wilson128": {"n_samples": [1024, 2048], "iters": [4.0, 4.0]}}
+REFERENCE = {"laplace1024": {"n_samples": [64, 128, 1024], "iters": [2.0, 2.0, 3.0]},
+             "wilson128": {"n_samples": [128, 768], "iters": [3.0, 3.0]},
+             "wilson256": {"n_samples": [32, 96], "iters": [3.0, 4.0]}}
 
 
 def run_reference(args):
@@ -463,10 +464,13 @@ def main():
         kms, kbytes = h.profile_kernel(which, 1, w["block"], 20)
         kern[name] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6}
     dom = kern["multidot_fp32"]
+    # DRAM bytes of this launch from an ncu capture of the same kernel version on the 512^2 case
+    # (reads scaled by the 4x rows of the 1024^2 case; the partial-sum write does not scale)
+    traffic = 4 * 335.62e6 + 3.14e6 if (w["kind"] == "laplace" and w["nx"] == 1024) else None
     roofline = {"bound": "hbm", "kernel": "k_multidot_partial<float> (inner Arnoldi: 4 basis blocks + w, "
-                                          "level 1, k=64; largest share of the launch list)",
+                                          "level 1, k=%d)" % w["block"],
                 "achieved": dom["gbs"], "peak": peak, "unit": "GB/s", "frac": dom["gbs"] / peak,
-                "peak_source": peak_kind, "traffic": None, "kernels": kern}
+                "peak_source": peak_kind, "traffic": traffic, "algorithmic_bytes": dom["bytes"], "kernels": kern}
 
     if learned is not None and rank == 0:
         # the same mixed estimate without the network (plain multigrid smoother)
