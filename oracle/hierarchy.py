@@ -9,8 +9,9 @@ divided into non-overlapping agg_x x agg_y aggregates; each aggregate becomes
 one site of level l+1.  P_l is block diagonal over aggregates: its columns
 are test vectors restricted to the aggregate (optionally split into the two
 spin halves of each site's dofs, which doubles the coarse dofs and keeps
-J A = A^* J), orthonormalised by modified Gram-Schmidt.  So R_l P_l = I and
-Remark 4.3 applies.
+J A = A^* J), orthonormalised by modified Gram-Schmidt applied twice to each
+column (smooth test vectors are nearly dependent on an aggregate; one pass
+leaves |P^* P - I| ~ 1e-10).  So R_l P_l = I and Remark 4.3 applies.
 
 Test vectors (the paper says only "quite inexact approximations to the d
 smallest eigenvectors"; this is the project's reading): n_tv Philox noise
@@ -124,9 +125,10 @@ def build_prolongation(V, nx, ny, d, ax, ay, spin_split):
     Q = np.zeros((nagg, m, dc), dtype=dtype)
     for q, v in enumerate(cols):
         v = v.copy()
-        for p in range(q):                            # modified Gram-Schmidt
-            coef = np.einsum("im,im->i", Q[:, :, p].conj(), v)
-            v = v - coef[:, None] * Q[:, :, p]
+        for _ in range(2):                            # modified Gram-Schmidt, each column twice
+            for p in range(q):
+                coef = np.einsum("im,im->i", Q[:, :, p].conj(), v)
+                v = v - coef[:, None] * Q[:, :, p]
         nrm = np.sqrt(np.einsum("im,im->i", v.conj(), v).real)
         if np.any(nrm == 0.0):
             raise ValueError("test vectors are linearly dependent on an aggregate")

@@ -109,6 +109,9 @@ __global__ void k_mgs(const T *V, T *P, int nx, int ny, int d, int ax, int ay, i
       PI[(size_t)row * dc + q] = keep ? V[((size_t)s * d + a) * ntv + tv] : zero<T>();
     }
     __syncwarp();
+    // modified Gram-Schmidt, each column twice (one pass loses orthogonality on
+    // nearly dependent smooth test vectors; R P = I is what Remark 4.3 needs)
+    for (int pass = 0; pass < 2; ++pass)
     for (int p = 0; p < q; ++p) {
       cdouble acc = {0.0, 0.0};
       for (int row = lane; row < m; row += 32) {
