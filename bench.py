@@ -35,12 +35,14 @@ WORKLOADS = {
     "laplace1024": dict(name="laplace2d-1024x1024-L4-4tv-k64", kind="laplace", nx=1024, ny=1024, levels=4, n_tv=4,
                         spin_split=0, setup="smooth", setup_sweeps=160, coarse_sweeps=20, omega=2.0 / 3.0,
                         bootstrap=2, boot_iters=5, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=8,
-                        inner_its=12, block=64, noise="rademacher", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8,
+                        inner_its=12, block=64, coarse_block=128, noise="rademacher", eps=1e-3, tol_fp64=1e-10,
+                        tol_mixed=1e-8,
                         seed=0, learned=False),
     # 2-spin Wilson operator 128^2, theta ~ N(0, 0.3^2), m0 tuned to sigma_min / sigma_max = 1e-3
     "wilson128": dict(name="wilson2d-128x128-L3-8dof-k32", kind="wilson", nx=128, ny=128, levels=3, n_tv=4,
                       spin_split=1, setup="inverse", setup_sweeps=20, coarse_sweeps=10, omega=1.0, bootstrap=4,
                       boot_iters=4, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=10, inner_its=8, block=32,
+                      coarse_block=128,
                       noise="z4", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8, seed=0, link_sd=0.3, link_seed=1,
                       mass=-0.1317442871, learned=False),
     # 2-spin Wilson operator 256^2, theta ~ N(0, 0.4^2), complex64 cycle with the learned correction
@@ -48,8 +50,8 @@ WORKLOADS = {
     "wilson256": dict(name="wilson2d-256x256-L3-8dof-k32-learned", kind="wilson", nx=256, ny=256, levels=3,
                       n_tv=4, spin_split=1, setup="inverse", setup_sweeps=20, coarse_sweeps=10, omega=1.0,
                       bootstrap=4, boot_iters=4, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=10,
-                      inner_its=8, block=32, noise="z4", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8, seed=0,
-                      link_sd=0.4, link_seed=2, mass=WILSON256_MASS, learned=True, train_pairs=10000,
+                      inner_its=8, block=32, coarse_block=128, noise="z4", eps=1e-3, tol_fp64=1e-10,
+                      tol_mixed=1e-8, seed=0, link_sd=0.4, link_seed=2, mass=WILSON256_MASS, learned=True, train_pairs=10000,
                       train_epochs=3, train_lr=1e-3),
 }
 WORKLOAD = WORKLOADS["laplace1024"]
@@ -90,7 +92,8 @@ def hierarchy_params(mlmc, precision, w=None):
                                setup_omega=w["omega"], bootstrap=w["bootstrap"], boot_iters=w["boot_iters"],
                                smooth_pre=w["smooth_pre"], smooth_post=w["smooth_post"], cycle=mlmc.CYCLE_K,
                                kcycle_its=w["kcycle_its"], fgmres_restart=w["restart"], max_iter=5000,
-                               precision=precision, block=w["block"], reorth=1, inner_its=w["inner_its"])
+                               precision=precision, block=w["block"], reorth=1, inner_its=w["inner_its"],
+                               coarse_block=w.get("coarse_block", 0))
 
 
 def make_hierarchy(mlmc, precision, w, stream=0):

@@ -107,6 +107,8 @@ typedef struct {
                           0: by one cycle                                                      */
   int graphs;          /* 1: replay each inner solve as a captured CUDA graph                   */
   int coarse_smooth;   /* > 0: pre- and post-smoothing sweeps on levels >= 2 (else as level 1) */
+  int coarse_block;    /* > 0: vector-block width of samples on level differences >= 2 (their
+                          solves are small, so wider blocks fill the GPU); 0 = block          */
   const void *const *user_P; /* optional, host: user_P[l-1] = P_l as blocks [agg][ax*ay*d][dc]
                           (double, or mlmc_c64 for complex operators); columns must be
                           orthonormal.  Replaces the test-vector setup.  NULL = build P.      */
@@ -223,9 +225,11 @@ int mlmc_sample_level_form(mlmc_hierarchy *h, int level, int form, int noise, ui
 /* tr(A_L^{-1}) from the FP64 dense inverse (Remark 4.2). */
 int mlmc_coarse_trace_exact(mlmc_hierarchy *h, mlmc_c64 *out);
 
-/* The Sec. 5 procedure: exact coarse term, tau from five warm-up estimates,
- * rho_l split, per-level sampling in blocks until the standard error of every
- * level meets rho_l (and N_l >= min_samples). */
+/* The Sec. 5 procedure: exact coarse term; the first block of every level
+ * difference, whose samples 0..4 (plus the exact term) are the five full
+ * estimates that give tau = mean - rms deviation; then sampling in blocks
+ * until every level meets its target (rho_l split, Sec. 2 optimal allocation,
+ * or a fixed budget), with N_l >= min_samples. */
 int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_estimate_result *r);
 
 /* ---- Batched, uneven serving (many instances) ---------------------------- */

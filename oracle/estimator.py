@@ -17,10 +17,12 @@ variance sum_l V_l / N_l with V_l the unbiased sample variance of |s - mean|^2
 (complex variance convention of Sec. 3).
 
 Stopping rule (Sec. 5): five full estimates t_1..t_5 (one sample per level
-difference plus the exact term, drawn from the warm-up noise stream) give
-tau = mean(t) - rms(t - mean(t)) (real parts); rho_l = sqrt(w_l) eps |tau| with
-sum w_l = 1 (default w_l = 1/(L-1)); level l draws blocks of `block` samples
-until N_l >= 5 and the standard error sqrt(V_l / N_l) <= rho_l.
+difference plus the exact term) give tau = mean(t) - rms(t - mean(t)) (real
+parts).  They are samples 0..4 of each level's noise stream, taken from the
+first block every level draws, and they also count in the level means.
+rho_l = sqrt(w_l) eps |tau| with sum w_l = 1 (default w_l = 1/(L-1)); level l
+then draws further blocks of `block` samples until N_l >= 5 and the standard
+error sqrt(V_l / N_l) <= rho_l.
 """
 from dataclasses import dataclass, field
 from typing import List, Optional
@@ -133,21 +135,25 @@ def trace_estimate(levels, kind, seed=0, eps=1e-3, weights=None, block=64, min_s
         TL = 0.0
     else:
         TL = exact_coarse_trace(levels, form)
-    # warm-up: five full estimates from the warm-up stream
-    warm = np.zeros(5, dtype=np.complex128) + TL
+    # first block of every level; its first five samples give the five full estimates of tau
+    acc = [Accumulator() for _ in range(L - 1)]
     for l in range(1, L):
-        warm += level_samples(levels, solvers, l, kind, seed, 0, 5, form, PURPOSE_WARMUP, hats)
+        while acc[l - 1].n < 5:
+            a = acc[l - 1]
+            a.add(level_samples(levels, solvers, l, kind, seed, a.n, block, form, PURPOSE_NOISE, hats))
+    warm = np.zeros(5, dtype=np.complex128) + TL
+    for a in acc:
+        warm += np.asarray(a.values[:5])
     tr = warm.real
     tau = tr.mean() - np.sqrt(np.mean((tr - tr.mean()) ** 2))
     w = np.full(L - 1, 1.0 / (L - 1)) if weights is None else np.asarray(weights, dtype=float)
     rho = np.sqrt(w) * eps * abs(tau)
-    acc = [Accumulator() for _ in range(L - 1)]
     for l in range(1, L):
         a = acc[l - 1]
         while a.n < max_samples:
-            a.add(level_samples(levels, solvers, l, kind, seed, a.n, block, form, PURPOSE_NOISE, hats))
             if a.n >= min_samples and np.sqrt(a.var() / a.n) <= rho[l - 1]:
                 break
+            a.add(level_samples(levels, solvers, l, kind, seed, a.n, block, form, PURPOSE_NOISE, hats))
     est = TL + sum(a.mean() for a in acc)
     se = np.sqrt(sum(a.var() / a.n for a in acc))
     return EstimateResult(est, se, tau, TL, [a.n for a in acc], [a.mean() for a in acc],

@@ -110,6 +110,8 @@ struct mlmc_hierarchy {
   mlmc_hierarchy_params prm{};
   int L = 0, kmax = 0;
   int kact = 0;        // active vector-block width of estimates and sample calls (<= kmax)
+  int kwide = 0;       // vector-block width of samples drawn on level differences >= 2 (coarse levels)
+  int kbig = 0;        // max(kmax, kwide): sizes of the per-column scratch
   std::vector<Level> lv;
   std::vector<CycleBufs> cyc[2];                  // [0] FP64 cycle, [1] FP32 cycle
   std::vector<std::unique_ptr<Krylov>> outer;     // FP64 outer FGMRES per level
@@ -131,7 +133,7 @@ struct mlmc_hierarchy {
     if (own_stream) cudaStreamDestroy(own_stream);
   }
   std::vector<DevBuf> xs, ys;                     // sample blocks per level (FP64)
-  DevBuf dots, samples, acc, err, trace;
+  DevBuf dots, dots_part, samples, acc, err, trace;
   uint64_t launches = 0;
   double iters_accum[16] = {0}, solves_accum[16] = {0};
   double cost = 0.0;   // Sec. 5 cost model: running sum of nnz(B) over products B x (per column)
@@ -681,6 +683,7 @@ void validate(const mlmc_operator_desc *op, const mlmc_hierarchy_params *p) {
   if (p->levels < 2 || p->levels > 16) fail(MLMC_ERR_INVALID_ARG, "levels must be in 2..16");
   if (p->agg_x < 1 || p->agg_y < 1) fail(MLMC_ERR_INVALID_ARG, "bad aggregate shape");
   if (p->block < 1 || p->block > 256) fail(MLMC_ERR_INVALID_ARG, "block must be in 1..256");
+  if (p->coarse_block < 0 || p->coarse_block > 256) fail(MLMC_ERR_INVALID_ARG, "coarse_block must be in 0..256");
   if (p->n_tv < 1 || p->n_tv > 16) fail(MLMC_ERR_INVALID_ARG, "n_tv must be in 1..16");
   if (p->setup_kind == MLMC_SETUP_CONSTANT && (p->n_tv != 1 || p->spin_split))
     fail(MLMC_ERR_INVALID_ARG, "constant setup needs n_tv = 1 and no spin split");
@@ -691,7 +694,8 @@ void validate(const mlmc_operator_desc *op, const mlmc_hierarchy_params *p) {
   if (p->inner_its < 0 || p->inner_its > 32) fail(MLMC_ERR_INVALID_ARG, "inner_its must be in 0..32");
   if (p->precision != MLMC_PREC_FP64 && p->precision != MLMC_PREC_MIXED_FP32)
     fail(MLMC_ERR_INVALID_ARG, "unknown precision");
-  if ((double)op->nx * op->ny * (op->kind == MLMC_OP_WILSON2D ? 2 : 1) * p->block >= 2147483648.0)
+  if ((double)op->nx * op->ny * (op->kind == MLMC_OP_WILSON2D ? 2 : 1) * std::max(p->block, p->coarse_block) >=
+      2147483648.0)
     fail(MLMC_ERR_UNSUPPORTED, "n * block must stay below 2^31 (32-bit kernel indexing)");
   long nx = op->nx, ny = op->ny;
   for (int l = 0; l + 1 < p->levels; ++l) {
@@ -725,6 +729,8 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   h.L = p->levels;
   h.kmax = p->block;
   h.kact = p->block;
+  h.kwide = p->coarse_block > 0 ? p->coarse_block : p->block;
+  h.kbig = std::max(h.kmax, h.kwide);
   const bool mixed = p->precision == MLMC_PREC_MIXED_FP32;
   const int dc = p->n_tv * (p->spin_split ? 2 : 1);
   const size_t es = dtype_size(h.t64), es32 = dtype_size(h.t32);
@@ -751,7 +757,7 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
     } else {
       Lv.Ainv64.alloc(Lv.n * Lv.n * es);
       size_t most = 0;     // the split count depends on the column count of a call
-      for (int kk = 1; kk <= std::max(p->block, p->n_tv); ++kk)
+      for (int kk = 1; kk <= std::max(std::max(p->block, p->coarse_block), p->n_tv); ++kk)
         most = std::max(most, (size_t)dense_apply_splits((int)Lv.n, kk) * kk);
       Lv.dense_part.alloc(most * Lv.n * es);
       if (mixed) Lv.Ainv32.alloc(Lv.n * Lv.n * es32);
@@ -760,12 +766,15 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   // workspaces.  The FP64 cycle serves the solves in the FP64 form; in the
   // mixed form it only serves the setup bootstrap (n_tv columns) and the
   // FP32 cycle serves the solves.
+  // Level 0 holds blocks of `block` columns; levels >= 1 also serve the wider
+  // coarse-level samples (`coarse_block` columns).
   const int k = h.kmax;
+  auto width = [&](int l) { return l == 0 ? h.kmax : h.kbig; };
   for (int lo = 0; lo < (mixed ? 2 : 1); ++lo) {
     DType t = lo ? h.t32 : h.t64;
-    int kc = (lo == 0 && mixed) ? p->n_tv : std::max(k, p->n_tv);
     h.cyc[lo].resize(h.L);
     for (int l = 0; l < h.L; ++l) {
+      int kc = (lo == 0 && mixed) ? p->n_tv : std::max(width(l), p->n_tv);
       CycleBufs &cb = h.cyc[lo][l];
       size_t bytes = h.lv[l].n * (size_t)kc * dtype_size(t);
       cb.b.alloc(bytes);
@@ -781,21 +790,23 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   h.xs.resize(h.L);
   h.ys.resize(h.L);
   for (int l = 0; l < h.L; ++l) {
-    h.xs[l].alloc(h.lv[l].n * (size_t)k * es);
-    h.ys[l].alloc(h.lv[l].n * (size_t)k * es);
+    h.xs[l].alloc(h.lv[l].n * (size_t)width(l) * es);
+    h.ys[l].alloc(h.lv[l].n * (size_t)width(l) * es);
     if (l + 1 < h.L) {
       h.outer[l].reset(new Krylov());
-      alloc_krylov(h, *h.outer[l], h.t64, h.lv[l].n, k, p->fgmres_restart);
+      alloc_krylov(h, *h.outer[l], h.t64, h.lv[l].n, width(l), p->fgmres_restart);
       if (p->inner_its > 0) {
         int lo = mixed ? 1 : 0;
         h.inner[lo].resize(h.L);
         h.inner[lo][l].reset(new Krylov());
-        alloc_krylov(h, *h.inner[lo][l], lo ? h.t32 : h.t64, h.lv[l].n, k, p->inner_its);
+        alloc_krylov(h, *h.inner[lo][l], lo ? h.t32 : h.t64, h.lv[l].n, width(l), p->inner_its);
       }
     }
   }
-  h.dots.alloc(2 * (size_t)k * 16);
-  h.samples.alloc((size_t)k * 16);
+  (void)k;
+  h.dots.alloc(2 * (size_t)h.kbig * 16);
+  h.dots_part.alloc((size_t)multidot_parts(h.lv[0].n, h.kbig) * h.kbig * 16);   // sample-dot partial sums
+  h.samples.alloc((size_t)h.kbig * 16);
   h.acc.alloc(4 * sizeof(double));
   h.err.alloc(sizeof(int));
   h.trace.alloc(2 * sizeof(double));
@@ -876,7 +887,7 @@ int sample_block(H_t &h, int l, int noise, uint64_t seed, uint64_t first, int k,
   char *dxy = h.dots.as<char>(), *dzw = dxy + (size_t)k * 16;
   auto coldot = [&](int lev, const void *a, const void *b, void *out) {
     launch_multidot(h.t64, a, h.lv[lev].n * (size_t)k, 1, b, h.lv[lev].n, k,
-                    h.outer[0]->partials.p, multidot_parts(h.lv[lev].n, k), out, h.complex_op ? C64 : F64, s);
+                    h.dots_part.p, multidot_parts(h.lv[lev].n, k), out, h.complex_op ? C64 : F64, s);
     h.launches += 2;
   };
   coldot(l, h.xs[l].p, h.ys[l].p, dxy);
@@ -1022,8 +1033,9 @@ int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, ui
     if (noise == MLMC_NOISE_Z4 && !h->complex_op) fail(MLMC_ERR_INVALID_ARG, "Z4 noise needs a complex operator");
     if (!(tol > 0.0)) fail(MLMC_ERR_INVALID_ARG, "tol must be positive");
     bool all_conv = true;
+    const int kl = level == 1 ? h->kact : h->kwide;
     for (int done = 0, b = 0; done < n_samples; ++b) {
-      int k = std::min(h->kact, n_samples - done);
+      int k = std::min(kl, n_samples - done);
       bool conv = true;
       int its = sample_block(*h, level - 1, noise, seed, first + done, k, tol, MLMC_PURPOSE_NOISE, &conv);
       copy_samples_out(*h, k, out_samples + done);
@@ -1059,8 +1071,9 @@ int mlmc_sample_level_form(mlmc_hierarchy *h, int level, int form, int noise, ui
     if (noise == MLMC_NOISE_Z4 && !h->complex_op) fail(MLMC_ERR_INVALID_ARG, "Z4 noise needs a complex operator");
     if (!(tol > 0.0)) fail(MLMC_ERR_INVALID_ARG, "tol must be positive");
     bool all_conv = true;
+    const int kl = level == 1 ? h->kact : h->kwide;
     for (int done = 0; done < n_samples;) {
-      int k = std::min(h->kact, n_samples - done);
+      int k = std::min(kl, n_samples - done);
       bool conv = true;
       sample_block(*h, level - 1, noise, seed, first + done, k, tol, MLMC_PURPOSE_NOISE, &conv, form);
       copy_samples_out(*h, k, out_samples + done);
@@ -1096,7 +1109,7 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
       fail(MLMC_ERR_INVALID_ARG, "unknown allocation");
     if (p->allocation == MLMC_ALLOC_FIXED)
       for (int l = 0; l < h->L - 1; ++l)
-        if (p->n_fixed[l] < 2) fail(MLMC_ERR_INVALID_ARG, "n_fixed must be >= 2 on every level difference");
+        if (p->n_fixed[l] < 5) fail(MLMC_ERR_INVALID_ARG, "n_fixed must be >= 5 on every level difference");
     H_t &H = *h;
     const int L = H.L, nd = plain ? 1 : L - 1;
     std::memset(r, 0, sizeof(*r));
@@ -1115,43 +1128,33 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
       r->cost_nnz[nd] = std::pow((double)H.lv[L - 1].n, 3.0);
     }
     r->coarse_term = TL;
-    // five warm-up estimates from the warm-up stream (Sec. 5)
-    std::vector<mlmc_c64> tmp(std::max(5, H.kmax));
-    double warm[5];
-    for (int i = 0; i < 5; ++i) warm[i] = TL.re;
-    const int kw = std::min(5, H.kact);
-    for (int l = 0; l < nd; ++l) {
-      for (int done = 0; done < 5; done += kw) {
-        int k = std::min(kw, 5 - done);
-        bool conv = true;
-        sample_block(H, l, p->noise, p->seed, done, k, p->tol, MLMC_PURPOSE_WARMUP, &conv, p->form);
-        if (!conv) fail(MLMC_ERR_NOT_CONVERGED, "warm-up solve did not converge");
-        copy_samples_out(H, k, tmp.data());
-        for (int i = 0; i < k; ++i) warm[done + i] += tmp[i].re;
-      }
-    }
-    double mean = 0.0;
-    for (double v : warm) mean += v / 5.0;
-    double ms = 0.0;
-    for (double v : warm) ms += (v - mean) * (v - mean) / 5.0;
-    double tau = mean - std::sqrt(ms);
-    r->tau = tau;
-    const double target = p->eps * std::fabs(tau);            // standard error of the estimate
     const int minN = p->min_samples > 0 ? p->min_samples : 5;
     const int maxN = p->max_samples > 0 ? p->max_samples : (1 << 24);
+    auto cap = [&](int l) { return p->allocation == MLMC_ALLOC_FIXED ? p->n_fixed[l] : maxN; };
     // per-level state: accumulators live on the device ({N, mean re, mean im, M2} x levels)
     DevBuf accs;
     accs.alloc((size_t)nd * 4 * sizeof(double));
     check_cuda(cudaMemsetAsync(accs.p, 0, (size_t)nd * 4 * sizeof(double), H.stream), "memset acc");
     std::vector<double> st((size_t)nd * 4, 0.0), cost(nd, 0.0), secs(nd, 0.0);
-    auto draw = [&](int l) {   // one block of samples on level difference l
+    std::vector<mlmc_c64> tmp(std::max(5, H.kbig));
+    double warm[5];
+    for (int i = 0; i < 5; ++i) warm[i] = TL.re;
+    auto width = [&](int l) { return l == 0 ? H.kact : H.kwide; };
+    // one block of samples on level difference l; samples 0..4 also enter the five
+    // full estimates that define tau
+    auto draw = [&](int l) {
       auto tl = std::chrono::steady_clock::now();
       double c0 = H.cost;
-      int k = std::min(H.kact, maxN - (int)st[4 * l]);
+      int N0 = (int)st[4 * l];
+      int k = std::min(width(l), cap(l) - N0);
       if (k <= 0) return false;
       bool conv = true;
-      sample_block(H, l, p->noise, p->seed, (uint64_t)st[4 * l], k, p->tol, MLMC_PURPOSE_NOISE, &conv, p->form);
+      sample_block(H, l, p->noise, p->seed, (uint64_t)N0, k, p->tol, MLMC_PURPOSE_NOISE, &conv, p->form);
       if (!conv) fail(MLMC_ERR_NOT_CONVERGED, "level solve did not converge");
+      if (N0 < 5) {
+        copy_samples_out(H, k, tmp.data());
+        for (int i = N0; i < std::min(5, N0 + k); ++i) warm[i] += tmp[i - N0].re;
+      }
       launch_accumulate(H.samples.p, k, accs.as<double>() + 4 * l, H.stream);
       H.launches++;
       check_cuda(cudaMemcpyAsync(&st[4 * l], accs.as<double>() + 4 * l, 4 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -1162,26 +1165,22 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
       return true;
     };
     auto var = [&](int l) { double N = st[4 * l]; return N > 1 ? st[4 * l + 3] / (N - 1) : INFINITY; };
+    // Sec. 5: five full estimates (one sample per level difference plus the exact term);
+    // they are samples 0..4 of every level's stream, drawn with each level's first block
+    for (int l = 0; l < nd; ++l)
+      while (st[4 * l] < 5)
+        if (!draw(l)) fail(MLMC_ERR_INVALID_ARG, "fewer than five samples allowed on a level");
+    double mean = 0.0;
+    for (double v : warm) mean += v / 5.0;
+    double ms = 0.0;
+    for (double v : warm) ms += (v - mean) * (v - mean) / 5.0;
+    double tau = mean - std::sqrt(ms);
+    r->tau = tau;
+    const double target = p->eps * std::fabs(tau);            // standard error of the estimate
     std::vector<double> w(nd, 0.0);
     if (p->allocation == MLMC_ALLOC_FIXED) {
-      for (int l = 0; l < nd; ++l) {
-        w[l] = 0.0;
-        while (st[4 * l] < p->n_fixed[l]) {
-          int k = std::min(H.kact, p->n_fixed[l] - (int)st[4 * l]);
-          auto tl = std::chrono::steady_clock::now();
-          double c0 = H.cost;
-          bool conv = true;
-          sample_block(H, l, p->noise, p->seed, (uint64_t)st[4 * l], k, p->tol, MLMC_PURPOSE_NOISE, &conv, p->form);
-          if (!conv) fail(MLMC_ERR_NOT_CONVERGED, "level solve did not converge");
-          launch_accumulate(H.samples.p, k, accs.as<double>() + 4 * l, H.stream);
-          H.launches++;
-          check_cuda(cudaMemcpyAsync(&st[4 * l], accs.as<double>() + 4 * l, 4 * sizeof(double),
-                                     cudaMemcpyDeviceToHost, H.stream), "D2H acc");
-          check_cuda(cudaStreamSynchronize(H.stream), "sync");
-          cost[l] += H.cost - c0;
-          secs[l] += std::chrono::duration<double>(std::chrono::steady_clock::now() - tl).count();
-        }
-      }
+      for (int l = 0; l < nd; ++l)
+        while (st[4 * l] < p->n_fixed[l]) draw(l);
     } else if (p->allocation == MLMC_ALLOC_RHO) {
       // Sec. 5: rho_l = sqrt(w_l) eps |tau|; sample each level until its standard error meets rho_l
       double wsum = 0.0;
@@ -1189,16 +1188,17 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
       for (int l = 0; l < nd; ++l) {
         w[l] = wsum > 0.0 ? p->weights[l] / wsum : 1.0 / nd;
         double rho = std::sqrt(w[l]) * target;
-        while (draw(l)) {
+        for (;;) {
           double N = st[4 * l];
           if (N >= minN && std::sqrt(var(l) / N) <= rho) break;
+          if (!draw(l)) break;
         }
       }
     } else {
       // Sec. 2: minimise sum N_l C_l subject to sum V_l / N_l = (eps tau)^2, i.e.
       // N_l = (eps tau)^-2 sqrt(V_l / C_l) sum_j sqrt(V_j C_j), with V_l and C_l (cost
-      // model per sample) estimated from the samples drawn so far; one pilot block per level.
-      for (int l = 0; l < nd; ++l) draw(l);
+      // model per sample) estimated from the samples drawn so far (the first block of
+      // every level is the pilot).
       for (int round = 0; round < 100000; ++round) {
         double S = 0.0;
         for (int l = 0; l < nd; ++l) S += std::sqrt(var(l) * cost[l] / st[4 * l]);
@@ -1219,7 +1219,7 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
           int best = 0;
           double gain = -1.0;
           for (int l = 0; l < nd; ++l) {
-            double N = st[4 * l], k = std::min(H.kact, maxN - (int)N);
+            double N = st[4 * l], k = std::min(width(l), maxN - (int)N);
             if (k <= 0) continue;
             double g = (var(l) / N - var(l) / (N + k)) / (cost[l] / N * k);
             if (g > gain) { gain = g; best = l; }

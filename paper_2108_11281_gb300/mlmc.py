@@ -45,7 +45,7 @@ class HierarchyParams(ctypes.Structure):
                 ("kcycle_its", ctypes.c_int), ("fgmres_restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("block", ctypes.c_int), ("reorth", ctypes.c_int),
                 ("inner_its", ctypes.c_int), ("graphs", ctypes.c_int), ("coarse_smooth", ctypes.c_int),
-                ("user_P", ctypes.c_void_p)]
+                ("coarse_block", ctypes.c_int), ("user_P", ctypes.c_void_p)]
 
 
 class EstimateParams(ctypes.Structure):
@@ -141,7 +141,7 @@ def default_params(**kw):
                         setup_sweeps=40, coarse_sweeps=20, setup_omega=2.0 / 3.0, setup_seed=0,
                         bootstrap=1, boot_iters=2, smooth_pre=1, smooth_post=1, cycle=CYCLE_K,
                         kcycle_its=2, fgmres_restart=30, max_iter=2000, precision=PREC_FP64, block=64,
-                        reorth=1, inner_its=0, graphs=1, coarse_smooth=0, user_P=None)
+                        reorth=1, inner_its=0, graphs=1, coarse_smooth=0, coarse_block=0, user_P=None)
     for k, v in kw.items():
         if not hasattr(p, k):
             raise KeyError(k)
@@ -222,7 +222,8 @@ class Hierarchy:
 
     def sample_level(self, level, noise, seed, first, n_samples, tol):
         out = (C64 * max(n_samples, 1))()
-        nblk = (n_samples + self.params.block - 1) // self.params.block
+        width = self.params.block if level == 1 or self.params.coarse_block <= 0 else self.params.coarse_block
+        nblk = (n_samples + width - 1) // width
         its = (ctypes.c_int * max(nblk, 1))()
         check(lib.mlmc_sample_level(self.handle, level, noise, seed, first, n_samples, tol, out, its))
         vals = np.array([complex(out[i].re, out[i].im) for i in range(n_samples)])
