@@ -277,7 +277,7 @@ void launch_multidot(DType t, const void *V, size_t vstride, int nvec, const voi
 // The grid is a multiple of k threads wide, so each thread keeps one column c
 // for its whole grid-stride loop (no per-element division).
 template <class T, class H, int VEC>
-__global__ void __launch_bounds__(256) k_multiaxpy(T *__restrict__ w, const T *__restrict__ V, size_t vstride, int nvec,
+__global__ void __launch_bounds__(256, 4) k_multiaxpy(T *__restrict__ w, const T *__restrict__ V, size_t vstride, int nvec,
                                                    const H *__restrict__ h, size_t hstride, double sign, size_t total, int k) {
   typedef DPack<T, VEC> P;
   const size_t stride = (size_t)gridDim.x * blockDim.x;       // in packs; a multiple of k / VEC
@@ -324,7 +324,8 @@ static unsigned column_grid(size_t total, int k) {
 template <class T, class H>
 static void multiaxpy_go(void *w, const void *V, size_t vstride, int nvec, const void *h, size_t hstride, double sign,
                          size_t total, int k, cudaStream_t s) {
-  constexpr int VW = 16 / (int)sizeof(T) > 0 ? 16 / (int)sizeof(T) : 1;
+  // 8-byte packs for FP32 (16-byte for wider types): bounds the coefficient registers
+  constexpr int VW = sizeof(T) == 4 ? 2 : (16 / (int)sizeof(T) > 0 ? 16 / (int)sizeof(T) : 1);
   if (VW > 1 && k % VW == 0 && vstride % VW == 0) {
     unsigned g = column_grid(total / VW, k / VW);
     k_multiaxpy<T, H, VW><<<g, 256, 0, s>>>((T *)w, (const T *)V, vstride, nvec, (const H *)h, hstride, sign, total, k);
