@@ -37,6 +37,8 @@ class Level:
     d: int
     P: Optional[sp.csr_matrix] = None       # n_l x n_{l+1}; None on the coarsest level
     P_blocks: Optional[np.ndarray] = None   # [aggregate][loc*d + a][q], same entries as P
+    colours: int = 2                        # site colours of the Gauss-Seidel smoother: 2 for
+                                            # nearest-neighbour stencils, 4 for 9-point stencils
 
     @property
     def n(self):

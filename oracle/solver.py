@@ -47,18 +47,24 @@ def dense_inverse(A):
     return sla.lu_solve(lu, np.eye(Ad.shape[0], dtype=Ad.dtype))
 
 
-def site_colour(nx, ny, d):
-    """Red (0) / black (1) colour of every dof: parity of i + j of its site."""
+def site_colour(nx, ny, d, colours=2):
+    """Colour of every dof.  2 colours: red (0) / black (1) = parity of i + j of
+    its site.  4 colours (9-point stencils, whose diagonal neighbours share the
+    red-black colour): (i mod 2) + 2 (j mod 2)."""
     j, i = np.divmod(np.arange(nx * ny), nx)
-    return np.repeat((i + j) % 2, d)
+    c = (i + j) % 2 if colours == 2 else (i % 2) + 2 * (j % 2)
+    return np.repeat(c, d)
 
 
 class RedBlackGS:
-    """Block Gauss-Seidel in red-black site order on one level.
+    """Block Gauss-Seidel in multi-colour site order on one level (red-black for
+    nearest-neighbour stencils, four colours for 9-point stencils).
 
-    A half-sweep over colour c sets, for every site s of colour c,
+    A partial sweep over colour c sets, for every site s of colour c,
         x_s <- x_s + D_s^{-1} (b - A x)_s,     D_s = the d x d diagonal block,
     which equals solving the site's row block exactly given its neighbours.
+    Pre-smoothing visits the colours in increasing order, post-smoothing in
+    decreasing order.
     """
 
     def __init__(self, level):
@@ -74,8 +80,9 @@ class RedBlackGS:
         bj = np.repeat(np.arange(nsite) * d, d * d) + np.tile(np.tile(np.arange(d), d), nsite)
         self.Dinv = sp.csr_matrix((inv.ravel(), (bi, bj)), shape=A.shape)
         self.A = A
-        colour = site_colour(level.nx, level.ny, d)
-        self.mask = [(colour == 0).astype(float), (colour == 1).astype(float)]
+        self.ncol = getattr(level, "colours", 2)
+        colour = site_colour(level.nx, level.ny, d, self.ncol)
+        self.mask = [(colour == c).astype(float) for c in range(self.ncol)]
 
     def half(self, x, b, c):
         upd = self.Dinv @ (b - self.A @ x)
@@ -84,14 +91,14 @@ class RedBlackGS:
 
     def pre(self, x, b, sweeps):
         for _ in range(sweeps):
-            x = self.half(x, b, 0)
-            x = self.half(x, b, 1)
+            for c in range(self.ncol):
+                x = self.half(x, b, c)
         return x
 
     def post(self, x, b, sweeps):
         for _ in range(sweeps):
-            x = self.half(x, b, 1)
-            x = self.half(x, b, 0)
+            for c in reversed(range(self.ncol)):
+                x = self.half(x, b, c)
         return x
 
 

@@ -321,3 +321,104 @@ def test_plain_hutchinson_sample_is_unbiased():
     solv = E.LevelSolvers(h)
     vals = [E.sample(h, solv, 1, np.array(v), form="plain") for v in itertools.product([1.0, -1.0], repeat=8)]
     assert np.isclose(np.mean(vals), np.trace(np.linalg.inv(A.toarray())), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- the paper's bilinear Laplace hierarchy
+
+def _table1_rows():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_laplace_hierarchy.txt")
+    rows = []
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if line:
+            rows.append((int(line[0]), int(line[1]), int(line[2]), float(line[3])))
+    return rows
+
+
+def test_bilinear_hierarchy_table1_sizes_and_nnz():
+    """Table 1: n_l and nnz(L^N_l) of the Example 5.1 hierarchy (bilinear P, Galerkin,
+    N_{l+1} = floor(N_l/2), N_L = 15) for N = 63, 127, 255, 511."""
+    from oracle.bilinear import build_bilinear_hierarchy
+    rows = _table1_rows()
+    for N in sorted({r[0] for r in rows}):
+        mine = [r for r in rows if r[0] == N]
+        lv = build_bilinear_hierarchy(N, len(mine))
+        for (_, l, n_l, nnz_printed), L in zip(mine, lv):
+            assert L.n == n_l
+            assert float("%.2e" % L.A.nnz) == nnz_printed, (N, l, L.A.nnz)
+
+
+def _tri(n, off, diag):
+    return sp.diags([off * np.ones(n - 1), diag * np.ones(n), off * np.ones(n - 1)], [-1, 0, 1])
+
+
+@pytest.mark.parametrize("shift", [0.0, 0.05])
+def test_bilinear_galerkin_operators_closed_form(shift):
+    """Galerkin coarse operators of Example 5.1 under bilinear P, derived by hand:
+    A_1 = T (x) I + I (x) T (+ s I (x) I) with T = tridiag(-1, 2, -1); P = p (x) p, so
+    A_l = T_l (x) M_l + M_l (x) T_l + s M_l (x) M_l with T_{l+1} = p^T T_l p = T_l / 2
+    (at every size, also next to the Dirichlet edge) and M_{l+1} = p^T M_l p, where
+    p^T tridiag(a, b) p = tridiag(b/4 + a, 3b/2 + 2a); M_1 = I."""
+    from oracle.bilinear import build_bilinear_hierarchy
+    lv = build_bilinear_hierarchy(63, 4, shift)
+    t_scale, (a, b) = 1.0, (0.0, 1.0)
+    for L in lv:
+        n = L.nx
+        T = t_scale * _tri(n, -1.0, 2.0)
+        M = _tri(n, a, b)
+        ref = sp.kron(T, M) + sp.kron(M, T) + shift * sp.kron(M, M)
+        assert abs(L.A - ref).max() <= 1e-13
+        t_scale, (a, b) = t_scale / 2.0, (b / 4.0 + a, 1.5 * b + 2.0 * a)
+    # interior 9-point stencil of level 2 (shift 0): [-1/4 -1/2 -1/4; -1/2 3 -1/2; -1/4 -1/2 -1/4]
+    A2 = build_bilinear_hierarchy(15, 2)[1].A.toarray()
+    c = 3 * 7 + 3
+    assert np.allclose([A2[c, c], A2[c, c + 1], A2[c, c + 7], A2[c, c + 8], A2[c, c - 6]],
+                       [3.0, -0.5, -0.5, -0.25, -0.25], atol=1e-15)
+
+
+def test_bilinear_four_colour_gauss_seidel_is_well_defined():
+    """9-point stencils couple diagonal neighbours: the 4-colour order (i mod 2, j mod 2)
+    leaves no coupling inside a colour (so each partial sweep solves its rows exactly),
+    while red-black would not; and R P != I, so the simplified form does not apply."""
+    from oracle.bilinear import build_bilinear_hierarchy
+    from oracle.solver import site_colour
+    lv = build_bilinear_hierarchy(31, 3)
+    for L in lv[1:]:
+        r, c = L.A.nonzero()
+        off = r != c
+        col4 = site_colour(L.nx, L.ny, 1, 4)
+        col2 = site_colour(L.nx, L.ny, 1, 2)
+        assert np.all(col4[r[off]] != col4[c[off]])
+        assert np.any(col2[r[off]] == col2[c[off]])
+    RP = (lv[0].P.T @ lv[0].P).toarray()
+    assert np.abs(RP - np.eye(RP.shape[0])).max() > 0.1
+
+
+def test_bilinear_hat_telescoping_against_closed_form():
+    """Eq. tr_ml_dec with the exact term of Remark 4.2, tr(A_L^{-1} R^_L P^_L): the hat-form
+    level differences plus that term equal the closed-form tr(A^{-1}) of Example 5.1."""
+    from oracle.bilinear import build_bilinear_hierarchy
+    N = 31
+    lv = build_bilinear_hierarchy(N, 3)
+    hats = [accumulated_prolongation(lv, l).toarray() for l in range(1, 4)]
+    inv = [np.linalg.inv(L.A.toarray()) for L in lv]
+    diffs = [np.trace(hats[i] @ inv[i] @ hats[i].T) - np.trace(hats[i + 1] @ inv[i + 1] @ hats[i + 1].T)
+             for i in range(2)]
+    exact = E.exact_coarse_trace(lv, "hat")
+    assert np.isclose(sum(diffs) + exact, laplace_trace_inverse_closed_form(N, 0.0), rtol=1e-12)
+    assert not np.isclose(exact, np.trace(inv[-1]), rtol=1e-3)     # R^ P^ != I matters
+
+
+def test_bilinear_multigrid_reaches_exact_solve():
+    """FGMRES with the multigrid cycle on the bilinear hierarchy (red-black GS on the
+    5-point fine level, 4-colour GS on the 9-point coarse levels) reaches the exact solve."""
+    from oracle.bilinear import build_bilinear_hierarchy
+    lv = build_bilinear_hierarchy(63, 3)
+    for cycle in ("V", "K"):
+        M = Cycle(lv, 0, 1, 1, cycle, 2)
+        b = rademacher(lv[0].n, 0, 1, 0)
+        x, its, res = fgmres(lv[0].A, b, M, tol=1e-11, m=30)
+        assert res <= 1e-11 and its < 30
+        ref = exact_solver(lv[0].A)(b)
+        assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
