@@ -72,13 +72,16 @@ def parse():
     ap.add_argument("--profile-sample", action="store_true",
                     help="for ncu only: after setup, one warm block and one profiled 64-sample block per level "
                          "difference inside cudaProfilerStart/Stop; prints no bench line")
-    ap.add_argument("--profile-kernel", default="", choices=["", "multidot", "multiaxpy", "rbgs", "stencil"],
+    ap.add_argument("--profile-kernel", default="", choices=["", "multidot", "multiaxpy", "rbgs", "stencil", "dense"],
                     help="with --profile-sample: instead of sample blocks, the one kernel launch the bench's "
                          "roofline measures (3 warm launches, then 1), inside cudaProfilerStart/Stop")
     ap.add_argument("--profile-nx", type=int, default=0,
                     help="with --profile-sample: lattice side for a smaller capture (default: the workload's)")
     ap.add_argument("--workload", default="laplace1024", choices=sorted(WORKLOADS) + ["batch48"],
                     help="laplace1024 (default, the headline), wilson128, wilson256 (learned correction)")
+    ap.add_argument("--eps-sweep", action="store_true",
+                    help="MLMC vs plain Hutchinson (Eq. plain_tr_estimate) over eps = 10^-1 .. 10^-3 on the "
+                         "workload: seconds, device-counted cost (Sec. 5 model) and N per method; one JSON line")
     ap.add_argument("--alloc", default="optimal", choices=["optimal", "rho"],
                     help="Sec. 2 optimal allocation (default) or the Sec. 5 equal rho split")
     return ap.parse_args()
@@ -220,7 +223,7 @@ def cpu_baseline(result, w):
 # (same estimator and noise on both sides, optimal allocation); used only by
 # the reference arm's extrapolation, which runs before any GPU number exists.
 REFERENCE = {"laplace1024": {"n_samples": [64, 128, 1024], "iters": [2.0, 2.0, 3.0]},
-             "wilson128": {"n_samples": [128, 768], "iters": [3.0, 3.0]},
+             "wilson128": {"n_samples": [128, 896], "iters": [3.0, 3.0]},
              "wilson256": {"n_samples": [32, 96], "iters": [3.0, 4.0]}}
 
 
@@ -266,10 +269,11 @@ def profile_sample(args):
     nz = mlmc.NOISE_Z4 if w["noise"] == "z4" else mlmc.NOISE_RADEMACHER
     h = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, torch.cuda.current_stream().cuda_stream)
     if args.profile_kernel:
-        which = {"stencil": 1, "rbgs": 2, "multidot": 3, "multiaxpy": 4}[args.profile_kernel]
+        which = {"stencil": 1, "rbgs": 2, "multidot": 3, "multiaxpy": 4, "dense": 5}[args.profile_kernel]
+        level, kk = (w["levels"], w.get("coarse_block") or w["block"]) if which == 5 else (1, w["block"])
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        h.profile_kernel(which, 1, w["block"], 1)
+        h.profile_kernel(which, level, kk, 1)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         h.close()
@@ -283,6 +287,37 @@ def profile_sample(args):
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     h.close()
+
+
+def eps_sweep(args):
+    """Time-to-trace and arithmetic cost of MLMC (simplified form, Sec. 2 optimal allocation) and
+    of plain Hutchinson on the fine operator, for eps = 10^-1, 10^-1.5, ..., 10^-3 (the study of
+    the paper's Fig. 5 and Sec. 5 cost model), on one GPU with the same solver, noise and seed."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2108_11281_gb300 import mlmc
+    w = WORKLOADS[args.workload]
+    nz = mlmc.NOISE_Z4 if w["noise"] == "z4" else mlmc.NOISE_RADEMACHER
+    h = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, torch.cuda.current_stream().cuda_stream)
+    rows = []
+    for e in (1.0, 1.5, 2.0, 2.5, 3.0):
+        eps = 10.0 ** -e
+        row = {"eps": eps}
+        for name, form in (("mlmc", mlmc.FORM_SIMPLIFIED), ("plain", mlmc.FORM_PLAIN)):
+            torch.cuda.synchronize()
+            t = time.time()
+            r = mlmc.result_dict(h.trace_estimate(eps=eps, noise=nz, seed=w["seed"], tol=w["tol_mixed"],
+                                                  form=form, allocation=mlmc.ALLOC_OPTIMAL))
+            torch.cuda.synchronize()
+            row[name] = {"seconds": time.time() - t, "trace": r["trace"].real, "std_err": r["std_err"],
+                         "n_samples": r["n_samples"], "cost_nnz": float(sum(r["cost_nnz"]))}
+        row["cost_ratio_plain_over_mlmc"] = row["plain"]["cost_nnz"] / row["mlmc"]["cost_nnz"]
+        row["time_ratio_plain_over_mlmc"] = row["plain"]["seconds"] / row["mlmc"]["seconds"]
+        rows.append(row)
+    h.close()
+    print(json.dumps({"eps_sweep": rows, "workload": w["name"], "closed_form": closed_form(w),
+                      "form": "mixed: FP32 K-cycle under FP64 FGMRES", "allocation": "optimal"}), flush=True)
 
 
 def batch_instances(seed=2026):
@@ -395,6 +430,9 @@ def main():
     if args.profile_sample:
         profile_sample(args)
         return
+    if args.eps_sweep:
+        eps_sweep(args)
+        return
     import torch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -466,6 +504,15 @@ def main():
                         ("stencil_fp64", 0)):
         kms, kbytes = h.profile_kernel(which, 1, w["block"], 20)
         kern[name] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6}
+    # the coarsest dense apply of the FP32 cycle (tensor cores vs CUDA cores), k = the coarse block
+    nxL, nyL, dL = h.level_info(w["levels"])
+    nL, kc = nxL * nyL * dL, (w.get("coarse_block") or w["block"])
+    for name, wk in (("dense_apply_tc", mlmc.DENSE_TC), ("dense_apply_simt", mlmc.DENSE_SIMT)):
+        h.set_dense_kernel(wk)
+        kms, kbytes = h.profile_kernel(5, w["levels"], kc, 20)
+        flops = (8.0 if w["kind"] == "wilson" else 2.0) * nL * nL * kc
+        kern[name] = {"ms": kms, "bytes": kbytes, "flops": flops, "tflops": flops / kms / 1e9, "n": nL, "k": kc}
+    h.set_dense_kernel(mlmc.DENSE_TC)
     dom = kern["multidot_fp32"]
     # DRAM bytes of this launch from an ncu capture of the same kernel version on the 512^2 case
     # (reads scaled by the 4x rows of the 1024^2 case; the partial-sum write does not scale)

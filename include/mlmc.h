@@ -222,6 +222,26 @@ const char *mlmc_noalloc_last_error(void);
 int mlmc_sample_level_form(mlmc_hierarchy *h, int level, int form, int noise, uint64_t seed, uint64_t first,
                            int n_samples, double tol, mlmc_c64 *out_samples);
 
+/* ---- Coarsest-level dense apply (Sec. 4: the coarsest system is solved
+ * directly; the FP32 cycle applies the inverse A_L^-1 computed at setup) ---
+ * Y = A B for FP32 data on the device: A n x n row-major, B and Y n x k with
+ * the k columns innermost (complex_data: complex64 interleaved (re, im)).
+ * which = MLMC_DENSE_TC runs the tcgen05 tensor-core kernel (three TF32
+ * products per term, FP32 accuracy; every mbarrier wait bounded, a wait that
+ * gives up returns MLMC_ERR_TIMEOUT and leaves Y unspecified); MLMC_DENSE_SIMT
+ * the CUDA-core kernel.  MLMC_DENSE_TC_WITHHOLD exercises the timeout path:
+ * the tensor-core kernel issues no MMA, its first wait runs out after about
+ * 1 ms, and the call returns MLMC_ERR_TIMEOUT with the context intact.
+ * Any n >= 1, 1 <= k <= 4096; pointers 16-byte aligned (else
+ * MLMC_ERR_INVALID_ARG).  The call allocates its scratch, runs on `stream`
+ * and is synchronous on return. */
+enum { MLMC_DENSE_SIMT = 0, MLMC_DENSE_TC = 1, MLMC_DENSE_TC_WITHHOLD = 2 };
+int mlmc_dense_apply(int complex_data, const void *A, const void *B, void *Y, int n, int k, int which, void *stream);
+/* Kernel of the FP32 cycle's coarsest apply for this handle (default
+ * MLMC_DENSE_TC; the FP64 cycle always uses the CUDA-core kernel, GB300's
+ * FP64 tensor rate being far below its FP32 one). */
+int mlmc_set_dense_kernel(mlmc_hierarchy *h, int which);
+
 /* tr(A_L^{-1}) from the FP64 dense inverse (Remark 4.2). */
 int mlmc_coarse_trace_exact(mlmc_hierarchy *h, mlmc_c64 *out);
 
@@ -252,9 +272,12 @@ int mlmc_trace_estimate_batch(mlmc_hierarchy *const *hs, int count, const mlmc_e
 /* Time one kernel family on level l with CUDA events on the hierarchy's
  * stream: which = 0 operator apply (FP64), 1 operator apply (FP32),
  * 2 red-black GS sweep, 3 column multi-dot of 4 basis blocks against w,
- * 4 multi-AXPY of 4 basis blocks into w (2-4 in the cycle precision).
+ * 4 multi-AXPY of 4 basis blocks into w, 5 coarsest dense apply
+ * Y = A_L^-1 B (level = L, k <= max(block, coarse_block); the kernel chosen
+ * by mlmc_set_dense_kernel) (2-5 in the cycle precision).
  * Reports the average launch time and the algorithmic bytes one launch must
- * move. */
+ * move (for 5: the dense inverse once plus B and Y; its FLOPs are
+ * 2 n_L^2 k real, 8 n_L^2 k complex). */
 int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps,
                         double *ms_per_launch, double *bytes_per_launch);
 

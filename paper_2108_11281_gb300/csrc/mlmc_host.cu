@@ -117,6 +117,7 @@ struct mlmc_hierarchy {
   std::vector<std::unique_ptr<Krylov>> outer;     // FP64 outer FGMRES per level
   std::vector<std::unique_ptr<Krylov>> inner[2];  // fixed-length inner FGMRES per level, [0] FP64 [1] FP32
   int const_laplace = 0, periodic = 0;
+  int dense_tc = 1;    // coarsest apply of the FP32 cycle on the tensor cores (else the SIMT kernel)
   double laplace_diag = 4.0;
   // learned correction on the fine level (FP32 cycle only)
   int net_on = 0, net_c0 = 0, net_nw = 0, net_alloc_k = 0, net_step = 0, net_fallbacks = 0;
@@ -229,8 +230,15 @@ void residual_op(H_t &h, int l, int lo, const void *x, const void *b, void *r, i
 
 void dense_apply(H_t &h, int lo, const void *b, void *x, int k) {
   const Level &C = h.lv[h.L - 1];
-  launch_dense_apply(lo ? h.t32 : h.t64, lo ? C.Ainv32.p : C.Ainv64.p, b, x, (int)C.n, k, C.dense_part.p, h.stream);
-  h.launches++;
+  if (lo && h.dense_tc && dense_apply_tc_ok(h.t32, (int)C.n, k)) {
+    launch_dense_apply_tc(h.t32, C.Ainv32.p, b, x, (int)C.n, k, C.dense_part.p, C.dense_part.bytes, h.err.as<int>(),
+                          h.stream);
+    h.launches += dense_apply_tc_part_bytes(h.t32, (int)C.n, k) ? 2 : 1;
+  } else {
+    launch_dense_apply(lo ? h.t32 : h.t64, lo ? C.Ainv32.p : C.Ainv64.p, b, x, (int)C.n, k, C.dense_part.p,
+                       h.stream);
+    h.launches++;
+  }
   h.cost += (double)C.n * C.n * k;
 }
 
@@ -606,8 +614,21 @@ void check_err(H_t &h, const char *what) {
   int e = 0;
   check_cuda(cudaMemcpyAsync(&e, h.err.p, sizeof(int), cudaMemcpyDeviceToHost, h.stream), "D2H err");
   check_cuda(cudaStreamSynchronize(h.stream), "sync");
+  if (e == MLMC_ERR_TIMEOUT) fail(MLMC_ERR_TIMEOUT, std::string(what) + ": a bounded tensor-core wait gave up");
   if (e) fail(MLMC_ERR_SINGULAR, std::string(what) + ": singular block or dependent test vectors (code " +
                                       std::to_string(e) + ")");
+}
+
+// The tensor-core coarsest apply records MLMC_ERR_TIMEOUT in h.err when one of
+// its bounded waits gives up; the entry points that run solves report it.
+void check_timeout(H_t &h) {
+  int e = 0;
+  check_cuda(cudaMemcpyAsync(&e, h.err.p, sizeof(int), cudaMemcpyDeviceToHost, h.stream), "D2H err");
+  check_cuda(cudaStreamSynchronize(h.stream), "sync");
+  if (e == MLMC_ERR_TIMEOUT) {
+    check_cuda(cudaMemsetAsync(h.err.p, 0, sizeof(int), h.stream), "memset err");
+    fail(MLMC_ERR_TIMEOUT, "a bounded tensor-core wait in the coarsest apply gave up");
+  }
 }
 
 // Levels 2..L from the level-1 test vectors (or from user-supplied P).
@@ -759,7 +780,11 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
       size_t most = 0;     // the split count depends on the column count of a call
       for (int kk = 1; kk <= std::max(std::max(p->block, p->coarse_block), p->n_tv); ++kk)
         most = std::max(most, (size_t)dense_apply_splits((int)Lv.n, kk) * kk);
-      Lv.dense_part.alloc(most * Lv.n * es);
+      size_t part_bytes = most * Lv.n * es;
+      if (mixed)
+        for (int kk = 1; kk <= std::max(std::max(p->block, p->coarse_block), p->n_tv); ++kk)
+          part_bytes = std::max(part_bytes, dense_apply_tc_part_bytes(dtype_lower(h.t64), (int)Lv.n, kk));
+      Lv.dense_part.alloc(part_bytes);
       if (mixed) Lv.Ainv32.alloc(Lv.n * Lv.n * es32);
     }
   }
@@ -1009,6 +1034,7 @@ int mlmc_solve(mlmc_hierarchy *h, int level, const void *b, void *x, int k, doub
     int its = solve_level(*h, level - 1, b, x, k, tol, &conv);
     check_cuda(cudaStreamSynchronize(h->stream), "sync");
     if (iters) *iters = its;
+    check_timeout(*h);
     if (!conv) fail(MLMC_ERR_NOT_CONVERGED, "solve did not reach tol within max_iter");
   });
 }
@@ -1043,6 +1069,7 @@ int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, ui
       all_conv = all_conv && conv;
       done += k;
     }
+    check_timeout(*h);
     if (!all_conv) fail(MLMC_ERR_NOT_CONVERGED, "a level solve did not reach tol within max_iter");
   });
 }
@@ -1080,7 +1107,43 @@ int mlmc_sample_level_form(mlmc_hierarchy *h, int level, int form, int noise, ui
       all_conv = all_conv && conv;
       done += k;
     }
+    check_timeout(*h);
     if (!all_conv) fail(MLMC_ERR_NOT_CONVERGED, "a level solve did not reach tol within max_iter");
+  });
+}
+
+int mlmc_dense_apply(int complex_data, const void *A, const void *B, void *Y, int n, int k, int which,
+                     void *stream) {
+  return translate([&] {
+    if (!A || !B || !Y || n < 1 || k < 1 || k > 4096) fail(MLMC_ERR_INVALID_ARG, "bad dense apply arguments");
+    if (which != MLMC_DENSE_SIMT && which != MLMC_DENSE_TC && which != MLMC_DENSE_TC_WITHHOLD)
+      fail(MLMC_ERR_INVALID_ARG, "unknown dense kernel");
+    if ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)Y)) & 15)
+      fail(MLMC_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+    const DType t = complex_data ? C32 : F32;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf part, err;
+    err.alloc(sizeof(int));
+    check_cuda(cudaMemsetAsync(err.p, 0, sizeof(int), s), "memset err");
+    if (which != MLMC_DENSE_SIMT) {
+      part.alloc(dense_apply_tc_part_bytes(t, n, k));
+      launch_dense_apply_tc(t, A, B, Y, n, k, part.p, part.bytes, err.as<int>(), s, which == MLMC_DENSE_TC_WITHHOLD);
+    } else {
+      part.alloc((size_t)dense_apply_splits(n, k) * n * k * dtype_size(t));
+      launch_dense_apply(t, A, B, Y, n, k, part.p, s);
+    }
+    int e = 0;
+    check_cuda(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H err");
+    check_cuda(cudaStreamSynchronize(s), "sync");
+    if (e == MLMC_ERR_TIMEOUT) fail(MLMC_ERR_TIMEOUT, "a bounded tensor-core wait gave up");
+  });
+}
+
+int mlmc_set_dense_kernel(mlmc_hierarchy *h, int which) {
+  return translate([&] {
+    need(h);
+    if (which != MLMC_DENSE_SIMT && which != MLMC_DENSE_TC) fail(MLMC_ERR_INVALID_ARG, "unknown dense kernel");
+    h->dense_tc = which == MLMC_DENSE_TC ? 1 : 0;
   });
 }
 
@@ -1229,6 +1292,7 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
         }
       }
     }
+    check_timeout(H);
     double var_sum = 0.0;
     mlmc_c64 total = TL;
     for (int l = 0; l < nd; ++l) {
@@ -1257,12 +1321,13 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
                         double *bytes_per_launch) {
   return translate([&] {
     need_level(h, level, 1, h ? h->L : 0);
-    if (k < 1 || k > h->kmax || reps < 1) fail(MLMC_ERR_INVALID_ARG, "bad k or reps");
+    if (k < 1 || k > (which == 5 ? h->kbig : h->kmax) || reps < 1) fail(MLMC_ERR_INVALID_ARG, "bad k or reps");
     H_t &H = *h;
     int l = level - 1;
     int lo = which == 0 ? 0 : (H.prm.precision == MLMC_PREC_MIXED_FP32 ? 1 : 0);
     if (which == 1 && !lo) fail(MLMC_ERR_INVALID_ARG, "FP32 kernels need the mixed form");
-    if (which < 0 || which > 4) fail(MLMC_ERR_INVALID_ARG, "unknown kernel family");
+    if (which < 0 || which > 5) fail(MLMC_ERR_INVALID_ARG, "unknown kernel family");
+    if (which == 5 && l != H.L - 1) fail(MLMC_ERR_INVALID_ARG, "the dense apply lives on the coarsest level");
     if (which == 2 && l == H.L - 1) fail(MLMC_ERR_INVALID_ARG, "no smoother on the coarsest level");
     const Level &Lv = H.lv[l];
     DType t = lo ? H.t32 : H.t64;
@@ -1290,6 +1355,8 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
       } else if (which == 3) {
         launch_multidot(t, Vb.p, Lv.n * (size_t)k, nvec, x, Lv.n, k, part.p, multidot_parts(Lv.n, k), outb.p,
                         H.complex_op ? C64 : F64, H.stream);
+      } else if (which == 5) {
+        dense_apply(H, lo, x, y, k);
       } else if (which == 4) {
         launch_multiaxpy(t, y, Vb.p, Lv.n * (size_t)k, nvec, outb.p, H.complex_op ? C64 : F64, k, -1e-30, Lv.n, k,
                          H.stream);
@@ -1310,7 +1377,11 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
     bool const_coef = l == 0 && !H.complex_op;      // Example 5.1 stencil has no matrix to read
     double coefb = const_coef ? 0.0 : (double)Lv.nsite * 5 * Lv.d * Lv.d * es;
     double bytes;
-    if (which == 3 || which == 4) {
+    if (which == 5) {
+      // the dense inverse once, the block in, the block out
+      bytes = (double)Lv.n * Lv.n * es + 2.0 * vec;
+      if (ms_per_launch) *ms_per_launch = ms / reps;
+    } else if (which == 3 || which == 4) {
       // multi-dot reads nvec basis blocks and w; multi-AXPY also writes w
       bytes = (which == 3 ? nvec + 1.0 : nvec + 2.0) * vec;
       if (ms_per_launch) *ms_per_launch = ms / reps;

@@ -187,6 +187,15 @@ void launch_trace(DType t, const void *A, int n, void *out /* FP64 (complex) */,
 // part: scratch of dense_apply_splits(n, k) * n * k elements (or null: no split of j)
 void launch_dense_apply(DType t, const void *Ainv, const void *B, void *Y, int n, int k, void *part, cudaStream_t s);
 int dense_apply_splits(int n, int k);
+// Tensor-core (tcgen05, 3xTF32) variant for FP32 / complex-FP32 data, any n, k >= 1.
+// part: dense_apply_tc_part_bytes(t, n, k) bytes of K-slice partials (none needed
+// when that is 0); err: device int that receives MLMC_ERR_TIMEOUT if a bounded
+// wait gives up.  Pointers 16-byte aligned.  withhold != 0: test mode that
+// issues no MMA, so the first bounded wait runs out (about 1 ms).
+bool dense_apply_tc_ok(DType t, int n, int k);
+size_t dense_apply_tc_part_bytes(DType t, int n, int k);
+void launch_dense_apply_tc(DType t, const void *Ainv, const void *B, void *Y, int n, int k, void *part,
+                           size_t part_bytes, int *err, cudaStream_t s, int withhold = 0);
 }  // namespace mlmc
 
 namespace mlmc {

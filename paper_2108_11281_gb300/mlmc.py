@@ -23,6 +23,7 @@ PREC_FP64, PREC_MIXED_FP32 = 0, 1
 FORM_SIMPLIFIED, FORM_HAT, FORM_PLAIN = 0, 1, 2
 CYCLE_V, CYCLE_K = 0, 1
 ALLOC_RHO, ALLOC_OPTIMAL, ALLOC_FIXED = 0, 1, 2
+DENSE_SIMT, DENSE_TC, DENSE_TC_WITHHOLD = 0, 1, 2
 
 
 class C64(ctypes.Structure):
@@ -110,6 +111,8 @@ def _load():
         "mlmc_autotune_block": [vp, i, i, d, ctypes.POINTER(i), ctypes.POINTER(d)],
         "mlmc_trace_estimate_batch": [ctypes.POINTER(vp), i, ctypes.POINTER(EstimateParams), i,
                                       ctypes.POINTER(EstimateResult), ctypes.POINTER(i)],
+        "mlmc_dense_apply": [i, vp, vp, vp, i, i, i, vp],
+        "mlmc_set_dense_kernel": [vp, i],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -128,7 +131,8 @@ EXPORTED = ["mlmc_setup_hierarchy", "mlmc_destroy_hierarchy", "mlmc_level_info",
             "mlmc_coarse_trace_exact", "mlmc_trace_estimate", "mlmc_profile_kernel", "mlmc_launch_count",
             "mlmc_last_error", "mlmc_learned_train", "mlmc_learned_set", "mlmc_learned_apply", "mlmc_learned_grad",
             "mlmc_column_dots", "mlmc_column_dots_noalloc", "mlmc_noalloc_last_error", "mlmc_set_block_width",
-            "mlmc_autotune_block", "mlmc_trace_estimate_batch", "mlmc_sample_level_form"]
+            "mlmc_autotune_block", "mlmc_trace_estimate_batch", "mlmc_sample_level_form", "mlmc_dense_apply",
+            "mlmc_set_dense_kernel"]
 
 
 def check(status):
@@ -289,6 +293,9 @@ class Hierarchy:
     def set_block_width(self, k):
         check(lib.mlmc_set_block_width(self.handle, k))
 
+    def set_dense_kernel(self, which):
+        check(lib.mlmc_set_dense_kernel(self.handle, which))
+
     def autotune_block(self, level=1, noise=NOISE_RADEMACHER, tol=1e-8):
         k, t = ctypes.c_int(), ctypes.c_double()
         check(lib.mlmc_autotune_block(self.handle, level, noise, tol, ctypes.byref(k), ctypes.byref(t)))
@@ -308,6 +315,12 @@ def noise(kind, seed, level, purpose, first, n, k, complex_out, out_ptr, stream=
 def column_dots(complex_data, x_ptr, y_ptr, n, k, out_ptr, stream=0):
     check(lib.mlmc_column_dots(int(complex_data), ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), n, k,
                                ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream)))
+
+
+def dense_apply(complex_data, a_ptr, b_ptr, y_ptr, n, k, which=DENSE_TC, stream=0):
+    """Y = A B in FP32 / complex64 on the device (the coarsest-level apply of the FP32 cycle)."""
+    check(lib.mlmc_dense_apply(int(complex_data), ctypes.c_void_p(a_ptr), ctypes.c_void_p(b_ptr),
+                               ctypes.c_void_p(y_ptr), n, k, which, ctypes.c_void_p(stream)))
 
 
 def trace_estimate_batch(hierarchies, params, workers=4):
