@@ -38,6 +38,14 @@ WORKLOADS = {
                         inner_its=12, block=64, coarse_block=128, noise="rademacher", eps=1e-3, tol_fp64=1e-10,
                         tol_mixed=1e-8,
                         seed=0, learned=False),
+    # the paper's own hierarchy for Example 5.1 (Sec. 5, Table 1): bilinear P, N_{l+1} = (N_l - 1)/2,
+    # Galerkin 9-point coarse levels down to N_L = 15; the hat form of the estimator (R P != I)
+    "laplace1023bil": dict(name="laplace2d-1023x1023-bilinear-L7-k64", kind="laplace", transfer="bilinear",
+                           form="hat", nx=1023, ny=1023, levels=7, n_tv=1, spin_split=0, setup="smooth",
+                           setup_sweeps=0, coarse_sweeps=0, omega=2.0 / 3.0, bootstrap=0, boot_iters=0,
+                           smooth_pre=1, smooth_post=1, kcycle_its=2, restart=8, inner_its=8, block=64,
+                           coarse_block=128, noise="rademacher", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8,
+                           seed=0, learned=False),
     # 2-spin Wilson operator 128^2, theta ~ N(0, 0.3^2), m0 tuned to sigma_min / sigma_max = 1e-3
     "wilson128": dict(name="wilson2d-128x128-L3-8dof-k32", kind="wilson", nx=128, ny=128, levels=3, n_tv=4,
                       spin_split=1, setup="inverse", setup_sweeps=20, coarse_sweeps=10, omega=1.0, bootstrap=4,
@@ -96,7 +104,9 @@ def hierarchy_params(mlmc, precision, w=None):
                                smooth_pre=w["smooth_pre"], smooth_post=w["smooth_post"], cycle=mlmc.CYCLE_K,
                                kcycle_its=w["kcycle_its"], fgmres_restart=w["restart"], max_iter=5000,
                                precision=precision, block=w["block"], reorth=1, inner_its=w["inner_its"],
-                               coarse_block=w.get("coarse_block", 0))
+                               coarse_block=w.get("coarse_block", 0),
+                               transfer=(mlmc.TRANSFER_BILINEAR if w.get("transfer") == "bilinear"
+                                         else mlmc.TRANSFER_AGGREGATION))
 
 
 def make_hierarchy(mlmc, precision, w, stream=0):
@@ -184,12 +194,16 @@ def cpu_baseline(result, w):
     else:
         from paper_2108_11281_gb300.workloads import gauge_links
         A, d = wilson2d(w["nx"], w["ny"], w["mass"], gauge_links(w["nx"], w["ny"], w["link_sd"], w["link_seed"])), 2
-    lv = build_hierarchy(A, w["nx"], w["ny"], d, SetupParams(
-        levels=w["levels"], n_tv=w["n_tv"], spin_split=bool(w["spin_split"]), kind=w["setup"],
-        sweeps=w["setup_sweeps"], coarse_sweeps=w["coarse_sweeps"], omega=w["omega"],
-        noise_kind="z4" if w["kind"] == "wilson" else "rademacher", bootstrap=w["bootstrap"],
-        boot_iters=w["boot_iters"], smooth_pre=w["smooth_pre"], smooth_post=w["smooth_post"],
-        kcycle_its=w["kcycle_its"]))
+    if w.get("transfer") == "bilinear":
+        from oracle.bilinear import build_bilinear_hierarchy
+        lv = build_bilinear_hierarchy(w["nx"], w["levels"])
+    else:
+        lv = build_hierarchy(A, w["nx"], w["ny"], d, SetupParams(
+            levels=w["levels"], n_tv=w["n_tv"], spin_split=bool(w["spin_split"]), kind=w["setup"],
+            sweeps=w["setup_sweeps"], coarse_sweeps=w["coarse_sweeps"], omega=w["omega"],
+            noise_kind="z4" if w["kind"] == "wilson" else "rademacher", bootstrap=w["bootstrap"],
+            boot_iters=w["boot_iters"], smooth_pre=w["smooth_pre"], smooth_post=w["smooth_post"],
+            kcycle_its=w["kcycle_its"]))
     setup_s = time.time() - t0
     per_it = []
     its_probe = 3
@@ -224,7 +238,8 @@ def cpu_baseline(result, w):
 # the reference arm's extrapolation, which runs before any GPU number exists.
 REFERENCE = {"laplace1024": {"n_samples": [64, 128, 1024], "iters": [2.0, 2.0, 3.0]},
              "wilson128": {"n_samples": [128, 896], "iters": [3.0, 3.0]},
-             "wilson256": {"n_samples": [32, 96], "iters": [3.0, 4.0]}}
+             "wilson256": {"n_samples": [32, 96], "iters": [3.0, 4.0]},
+             "laplace1023bil": {"n_samples": [64, 128, 128, 128, 128, 256], "iters": [2.0, 3.0, 2.0, 2.0, 2.0, 2.0]}}
 
 
 def run_reference(args):
@@ -278,12 +293,13 @@ def profile_sample(args):
         torch.cuda.profiler.stop()
         h.close()
         return
+    form = mlmc.FORM_HAT if w.get("form") == "hat" else mlmc.FORM_SIMPLIFIED
     for lvl in range(1, w["levels"]):
-        h.sample_level(lvl, nz, 0, 0, w["block"], w["tol_mixed"])
+        h.sample_level_form(lvl, form, nz, 0, 0, w["block"], w["tol_mixed"])
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
     for lvl in range(1, w["levels"]):
-        h.sample_level(lvl, nz, 0, w["block"], w["block"], w["tol_mixed"])
+        h.sample_level_form(lvl, form, nz, 0, w["block"], w["block"], w["tol_mixed"])
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     h.close()
@@ -304,7 +320,8 @@ def eps_sweep(args):
     for e in (1.0, 1.5, 2.0, 2.5, 3.0):
         eps = 10.0 ** -e
         row = {"eps": eps}
-        for name, form in (("mlmc", mlmc.FORM_SIMPLIFIED), ("plain", mlmc.FORM_PLAIN)):
+        mlmc_form = mlmc.FORM_HAT if w.get("form") == "hat" else mlmc.FORM_SIMPLIFIED
+        for name, form in (("mlmc", mlmc_form), ("plain", mlmc.FORM_PLAIN)):
             torch.cuda.synchronize()
             t = time.time()
             r = mlmc.result_dict(h.trace_estimate(eps=eps, noise=nz, seed=w["seed"], tol=w["tol_mixed"],
@@ -451,9 +468,11 @@ def main():
 
     alloc = mlmc.ALLOC_OPTIMAL if args.alloc == "optimal" else mlmc.ALLOC_RHO
 
+    form = mlmc.FORM_HAT if w.get("form") == "hat" else mlmc.FORM_SIMPLIFIED
+
     def step(hh, tol, seed):
         return mlmc.result_dict(hh.trace_estimate(eps=w["eps"], noise=nz, seed=seed, tol=tol,
-                                                  allocation=alloc))
+                                                  allocation=alloc, form=form))
 
     learned = None
     if w.get("learned"):

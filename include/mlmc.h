@@ -65,6 +65,7 @@ enum { MLMC_PREC_FP64 = 0, MLMC_PREC_MIXED_FP32 = 1 };
 enum { MLMC_FORM_SIMPLIFIED = 0, MLMC_FORM_HAT = 1, MLMC_FORM_PLAIN = 2 };
 enum { MLMC_CYCLE_V = 0, MLMC_CYCLE_K = 1 };
 enum { MLMC_ALLOC_RHO = 0, MLMC_ALLOC_OPTIMAL = 1, MLMC_ALLOC_FIXED = 2 };
+enum { MLMC_TRANSFER_AGGREGATION = 0, MLMC_TRANSFER_BILINEAR = 1 };
 
 /* Fine operator A = A_1 (Examples 5.1 and 5.3).  Sites s = j*nx + i. */
 typedef struct {
@@ -112,6 +113,13 @@ typedef struct {
   const void *const *user_P; /* optional, host: user_P[l-1] = P_l as blocks [agg][ax*ay*d][dc]
                           (double, or mlmc_c64 for complex operators); columns must be
                           orthonormal.  Replaces the test-vector setup.  NULL = build P.      */
+  int transfer;        /* MLMC_TRANSFER_AGGREGATION (above), or MLMC_TRANSFER_BILINEAR: the
+                          paper's hierarchy for Example 5.1 (Sec. 5): Dirichlet Laplacian with
+                          N_l = 2 N_{l+1} + 1 (every side above the coarsest odd), P_l bilinear
+                          interpolation, R_l = P_l^T, Galerkin 9-point coarse operators
+                          smoothed by 4-colour Gauss-Seidel.  R P != I, so samples and
+                          estimates need MLMC_FORM_HAT (or MLMC_FORM_PLAIN); agg_*, n_tv,
+                          spin_split, setup_*, bootstrap and user_P are ignored.           */
 } mlmc_hierarchy_params;
 
 typedef struct mlmc_hierarchy mlmc_hierarchy;
@@ -167,11 +175,18 @@ void mlmc_destroy_hierarchy(mlmc_hierarchy *h);
 
 /* Level sizes: lattice nx, ny and dofs per site d of level l (1-based). */
 int mlmc_level_info(const mlmc_hierarchy *h, int level, int *nx, int *ny, int *d);
+/* Stencil taps of level l's operator as returned by mlmc_get_operator: 5
+ * (nearest-neighbour blocks) or 9 (the 9-point coarse levels of the bilinear
+ * hierarchy: taps 0 self, 1 +x, 2 -x, 3 +y, 4 -y, 5 (+x,+y), 6 (-x,+y),
+ * 7 (+x,-y), 8 (-x,-y)). */
+int mlmc_level_taps(const mlmc_hierarchy *h, int level, int *taps);
 
-/* Copy P_l (level l < L) to host as blocks [agg][ax*ay*d][dc] (FP64 / c64). */
+/* Copy P_l (level l < L) to host as blocks [agg][ax*ay*d][dc] (FP64 / c64).
+ * MLMC_ERR_UNSUPPORTED for the bilinear hierarchy (P is applied, not stored). */
 int mlmc_get_prolongation(const mlmc_hierarchy *h, int level, void *host_out);
-/* Copy the block stencil of A_l to host as [site][5][d][d] (FP64 / c64);
- * directions 0 self, 1 +x, 2 -x, 3 +y, 4 -y (periodic indexing). */
+/* Copy the block stencil of A_l to host as [site][taps][d][d] (FP64 / c64);
+ * 5 taps: directions 0 self, 1 +x, 2 -x, 3 +y, 4 -y (periodic indexing);
+ * 9 taps: see mlmc_level_taps (Dirichlet). */
 int mlmc_get_operator(const mlmc_hierarchy *h, int level, void *host_out);
 
 /* y = A_l x for a device block of k columns (FP64 / c64). */
@@ -242,7 +257,8 @@ int mlmc_dense_apply(int complex_data, const void *A, const void *B, void *Y, in
  * FP64 tensor rate being far below its FP32 one). */
 int mlmc_set_dense_kernel(mlmc_hierarchy *h, int which);
 
-/* tr(A_L^{-1}) from the FP64 dense inverse (Remark 4.2). */
+/* The exact coarsest term of the estimator (Remark 4.2), tr(A_L^{-1} R^_L P^_L)
+ * from the FP64 dense inverse: tr(A_L^{-1}) when R^_L P^_L = I (aggregation). */
 int mlmc_coarse_trace_exact(mlmc_hierarchy *h, mlmc_c64 *out);
 
 /* The Sec. 5 procedure: exact coarse term; the first block of every level
@@ -273,8 +289,9 @@ int mlmc_trace_estimate_batch(mlmc_hierarchy *const *hs, int count, const mlmc_e
  * stream: which = 0 operator apply (FP64), 1 operator apply (FP32),
  * 2 red-black GS sweep, 3 column multi-dot of 4 basis blocks against w,
  * 4 multi-AXPY of 4 basis blocks into w, 5 coarsest dense apply
- * Y = A_L^-1 B (level = L, k <= max(block, coarse_block); the kernel chosen
- * by mlmc_set_dense_kernel) (2-5 in the cycle precision).
+ * Y = A_L^-1 B (level = L; the kernel chosen by mlmc_set_dense_kernel)
+ * (2-5 in the cycle precision).  k <= block on level 1, k <= max(block,
+ * coarse_block) on the coarser levels.
  * Reports the average launch time and the algorithmic bytes one launch must
  * move (for 5: the dense inverse once plus B and Y; its FLOPs are
  * 2 n_L^2 k real, 8 n_L^2 k complex). */

@@ -170,11 +170,12 @@ __global__ void __launch_bounds__(256) k_laplace_rbgs(T *__restrict__ x, const T
                                                       int kv, T dinv, int periodic, int colour, int other_zero) {
   typedef Pack<T, VEC> V;
   const int j = blockIdx.y;
-  const int hx = nx >> 1;
+  const int i0 = (j + colour) & 1;
+  const int hx = (nx - i0 + 1) >> 1;      // sites of this colour in row j (odd nx too)
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= hx * kv) return;
   const int m = t / kv, c = t - (t / kv) * kv;
-  const int i = 2 * m + ((j + colour) & 1);
+  const int i = 2 * m + i0;
   const int s = j * nx + i;
   V *X = (V *)x;
   V acc = ((const V *)b)[(size_t)s * kv + c];
@@ -229,7 +230,7 @@ static void launch_laplace_rbgs(const StencilView &A, void *x, const void *b, in
     typedef decltype(tag) T;
     constexpr int VEC = decltype(vtag)::value;
     int kv = k / VEC;
-    dim3 g(((A.nx / 2) * kv + 255) / 256, A.ny);
+    dim3 g((((A.nx + 1) / 2) * kv + 255) / 256, A.ny);
     k_laplace_rbgs<T, VEC><<<g, 256, 0, s>>>((T *)x, (const T *)b, A.nx, A.ny, kv, (T)(1.0 / A.diag), A.periodic,
                                              colour, other_zero);
   };
@@ -249,6 +250,10 @@ void launch_stencil(const StencilView &A, const void *x, const void *b, void *y,
                     cudaStream_t s) {
   if (A.const_laplace) {
     launch_laplace(A, x, b, y, k, mode, s);
+    return;
+  }
+  if (A.taps == 9) {
+    launch_stencil9(A, x, b, y, k, mode, s);
     return;
   }
   MLMC_DISPATCH(A.t, T, MLMC_DDISPATCH(A.d, D, stencil_go<T, D>(A, x, b, y, k, mode, s)));
@@ -337,6 +342,7 @@ void launch_rbgs_half(const StencilView &A, void *x, const void *b, int k, int c
     launch_laplace_rbgs(A, x, b, k, colour, 0, s);
     return;
   }
+  if (A.taps == 9) throw cuda_error{cudaErrorInvalidValue, "9-point stencils are smoothed in four colours"};
   MLMC_DISPATCH(A.t, T, MLMC_DDISPATCH(A.d, D, rbgs_go<T, D>(A, x, b, k, colour, s)));
   MLMC_LAUNCH_CHECK("k_rbgs_half");
 }
@@ -347,6 +353,10 @@ void launch_rbgs_sweep(const StencilView &A, void *x, const void *b, int k, int 
   if (A.const_laplace) {
     launch_laplace_rbgs(A, x, b, k, first, x_zero, s);
     launch_laplace_rbgs(A, x, b, k, 1 - first, 0, s);
+    return;
+  }
+  if (A.taps == 9) {
+    launch_gs9_sweep(A, x, b, k, order, x_zero, s);
     return;
   }
   if (x_zero) MLMC_CUDA(cudaMemsetAsync(x, 0, (size_t)A.nx * A.ny * A.d * k * dtype_size(A.t), s));

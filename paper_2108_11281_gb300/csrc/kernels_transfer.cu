@@ -133,11 +133,19 @@ static void prolong_go(const ProlongView &P, const void *ec, void *x, int k, cud
 }
 
 void launch_restrict(const ProlongView &P, const void *r, void *rc, int k, cudaStream_t s) {
+  if (P.bilinear) {
+    launch_restrict_bilinear(P.t, r, rc, (P.nx - 1) / 2, (P.ny - 1) / 2, k, s);
+    return;
+  }
   MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC, restrict_go<T, DC>(P, r, rc, k, s)));
   MLMC_LAUNCH_CHECK("k_restrict");
 }
 
 void launch_prolong_add(const ProlongView &P, const void *ec, void *x, int k, cudaStream_t s) {
+  if (P.bilinear) {
+    launch_prolong_bilinear(P.t, ec, x, P.nx, P.ny, k, s);
+    return;
+  }
   MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC, prolong_go<T, DC>(P, ec, x, k, s)));
   MLMC_LAUNCH_CHECK("k_prolong_add");
 }

@@ -70,6 +70,7 @@ struct Level {
   DevBuf coef64, dinv64, coef32, dinv32;   // block stencil and inverse self blocks
   int ax = 0, ay = 0, dc = 0;              // aggregation towards the next level
   DevBuf P64, P32;
+  int taps = 5;                            // 5: block stencil; 9: 9-point scalar stencil (bilinear levels >= 2)
   DevBuf Ainv64, Ainv32;                   // coarsest level only
   DevBuf dense_part;                       // split-j partial products of the coarsest apply
 };
@@ -118,6 +119,8 @@ struct mlmc_hierarchy {
   std::vector<std::unique_ptr<Krylov>> inner[2];  // fixed-length inner FGMRES per level, [0] FP64 [1] FP32
   int const_laplace = 0, periodic = 0;
   int dense_tc = 1;    // coarsest apply of the FP32 cycle on the tensor cores (else the SIMT kernel)
+  int bilinear = 0;    // the Example 5.1 hierarchy of Sec. 5: bilinear P, Galerkin 9-point levels
+  double coarse_term_hat = 0.0;   // bilinear: tr(A_L^{-1} R^_L P^_L) (Remark 4.2), computed at setup
   double laplace_diag = 4.0;
   // learned correction on the fine level (FP32 cycle only)
   int net_on = 0, net_c0 = 0, net_nw = 0, net_alloc_k = 0, net_step = 0, net_fallbacks = 0;
@@ -158,6 +161,7 @@ StencilView view(const H_t &h, int l, int lo) {
   v.const_laplace = (l == 0 && h.const_laplace) ? 1 : 0;
   v.diag = h.laplace_diag;
   v.periodic = h.periodic;
+  v.taps = L.taps;
   return v;
 }
 
@@ -172,6 +176,7 @@ ProlongView pview(const H_t &h, int l, int lo) {
   v.dc = L.dc;
   v.t = lo ? h.t32 : h.t64;
   v.P = lo ? L.P32.p : L.P64.p;
+  v.bilinear = h.bilinear;
   return v;
 }
 
@@ -213,7 +218,14 @@ double nnz_of(const H_t &h, int l) {
   const Level &L = h.lv[l];
   if (l == 0 && h.const_laplace) return 5.0 * L.n - (h.periodic ? 0.0 : 2.0 * (L.nx + L.ny));
   if (l == 0 && h.complex_op) return 9.0 * L.n;
+  if (L.taps == 9) return (3.0 * L.nx - 2.0) * (3.0 * L.ny - 2.0);      // Table 1: (3 N_l - 2)^2
   return 5.0 * L.nsite * L.d * L.d;
+}
+
+// nnz(P_l): the cost-model weight of one restriction or prolongation per column
+double nnz_P(const H_t &h, int l) {
+  if (h.bilinear) return 9.0 * (double)h.lv[l + 1].n;     // three 1-D weights per coarse point and direction
+  return (double)h.lv[l].n * h.lv[l].dc;
 }
 
 void apply_op(H_t &h, int l, int lo, const void *x, void *y, int k) {
@@ -359,7 +371,7 @@ void cycle(H_t &h, int lo, int l, const void *b, void *x, int k) {
   residual_op(h, l, lo, x, b, cb.r.p, k);
   launch_restrict(pview(h, l, lo), cb.r.p, cn.b.p, k, s);
   h.launches++;
-  h.cost += 2.0 * (double)Lv.n * Lv.dc * k;     // restriction and the prolongation below: nnz(P) each
+  h.cost += 2.0 * nnz_P(h, l) * k;              // restriction and the prolongation below: nnz(P) each
   if (l + 1 == last) {
     dense_apply(h, lo, cn.b.p, cn.x.p, k);
   } else if (h.prm.cycle == MLMC_CYCLE_V) {
@@ -683,7 +695,7 @@ void build_levels(H_t &h, const void *V1, const void *const *user_P) {
   if (h.prm.precision == MLMC_PREC_MIXED_FP32) {
     for (int l = 0; l < h.L; ++l) {
       Level &Lv = h.lv[l];
-      launch_convert(h.t32, Lv.coef32.p, h.t64, Lv.coef64.p, Lv.nsite * 5 * Lv.d * Lv.d, h.stream);
+      launch_convert(h.t32, Lv.coef32.p, h.t64, Lv.coef64.p, Lv.nsite * Lv.taps * Lv.d * Lv.d, h.stream);
       if (l + 1 < h.L) {
         launch_convert(h.t32, Lv.dinv32.p, h.t64, Lv.dinv64.p, Lv.nsite * Lv.d * Lv.d, h.stream);
         size_t pc = (size_t)(Lv.nx / Lv.ax) * (Lv.ny / Lv.ay) * Lv.ax * Lv.ay * Lv.d * Lv.dc;
@@ -696,12 +708,170 @@ void build_levels(H_t &h, const void *V1, const void *const *user_P) {
   }
 }
 
+// ----------------------------------------------------------------- bilinear hierarchy (Sec. 5, Example 5.1)
+// 9-point stencils on the host, taps 0 self, 1 +x, 2 -x, 3 +y, 4 -y, 5 (+x,+y),
+// 6 (-x,+y), 7 (+x,-y), 8 (-x,-y), row-major over sites s = j*nx + i.
+const int kTapDx[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+const int kTapDy[9] = {0, 0, 0, 1, -1, 1, 1, -1, -1};
+
+int tap_of(int dx, int dy) {
+  for (int q = 0; q < 9; ++q)
+    if (kTapDx[q] == dx && kTapDy[q] == dy) return q;
+  return -1;
+}
+
+// A_c = P^T A P for bilinear P from the ((nx-1)/2) x ((ny-1)/2) grid: coarse
+// point (I, J) sits on fine (2I+1, 2J+1) with 1-D weights 1 (centre), 1/2 (+-1).
+std::vector<double> galerkin9(const std::vector<double> &Af, int nx, int ny) {
+  const int ncx = (nx - 1) / 2, ncy = (ny - 1) / 2;
+  std::vector<double> Ac((size_t)ncx * ncy * 9, 0.0);
+  auto w1 = [](int a) { return a == 0 ? 1.0 : 0.5; };
+  for (int J = 0; J < ncy; ++J)
+    for (int I = 0; I < ncx; ++I) {
+      double *row = &Ac[((size_t)J * ncx + I) * 9];
+      for (int b = -1; b <= 1; ++b)
+        for (int a = -1; a <= 1; ++a) {
+          const int px = 2 * I + 1 + a, py = 2 * J + 1 + b;
+          const double wp = w1(a) * w1(b);
+          const double *ap = &Af[((size_t)py * nx + px) * 9];
+          for (int q = 0; q < 9; ++q) {
+            const int qx = px + kTapDx[q], qy = py + kTapDy[q];
+            if (qx < 0 || qx >= nx || qy < 0 || qy >= ny || ap[q] == 0.0) continue;
+            for (int J2 = J - 1; J2 <= J + 1; ++J2)
+              for (int I2 = I - 1; I2 <= I + 1; ++I2) {
+                if (I2 < 0 || I2 >= ncx || J2 < 0 || J2 >= ncy) continue;
+                const int ex = qx - (2 * I2 + 1), ey = qy - (2 * J2 + 1);
+                if (ex < -1 || ex > 1 || ey < -1 || ey > 1) continue;
+                row[tap_of(I2 - I, J2 - J)] += wp * ap[q] * w1(ex) * w1(ey);
+              }
+          }
+        }
+    }
+  return Ac;
+}
+
+// Levels 2..L by Galerkin coarsening with bilinear P (host, FP64), their smoother
+// diagonals, the coarsest inverse, and the exact term of the hat form,
+// tr(A_L^{-1} R^_L P^_L) = sum_ij (A_L^{-1})_ij M_ji with M = R^_L P^_L obtained by
+// coarsening the identity the same way (M is symmetric: R = P^T).
+void build_bilinear(H_t &h, const mlmc_operator_desc *op) {
+  const int L = h.L;
+  std::vector<double> A, M;
+  {
+    const int nx = h.lv[0].nx, ny = h.lv[0].ny;
+    A.assign((size_t)nx * ny * 9, 0.0);
+    M.assign((size_t)nx * ny * 9, 0.0);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        double *a = &A[((size_t)j * nx + i) * 9];
+        a[0] = 4.0 + op->shift;
+        for (int q = 1; q <= 4; ++q) {
+          const int ii = i + kTapDx[q], jj = j + kTapDy[q];
+          if (ii >= 0 && ii < nx && jj >= 0 && jj < ny) a[q] = -1.0;
+        }
+        M[((size_t)j * nx + i) * 9] = 1.0;
+      }
+  }
+  const size_t es = sizeof(double);
+  for (int l = 0; l + 1 < L; ++l) {
+    A = galerkin9(A, h.lv[l].nx, h.lv[l].ny);
+    M = galerkin9(M, h.lv[l].nx, h.lv[l].ny);
+    Level &C = h.lv[l + 1];
+    check_cuda(cudaMemcpyAsync(C.coef64.p, A.data(), A.size() * es, cudaMemcpyHostToDevice, h.stream), "H2D coef");
+    if (l + 2 < L) {
+      std::vector<double> dinv(C.nsite);
+      for (size_t s = 0; s < C.nsite; ++s) {
+        if (A[s * 9] == 0.0) fail(MLMC_ERR_SINGULAR, "zero diagonal in a Galerkin level");
+        dinv[s] = 1.0 / A[s * 9];
+      }
+      check_cuda(cudaMemcpyAsync(C.dinv64.p, dinv.data(), dinv.size() * es, cudaMemcpyHostToDevice, h.stream),
+                 "H2D dinv");
+      check_cuda(cudaStreamSynchronize(h.stream), "sync");   // dinv leaves scope
+    }
+    check_cuda(cudaStreamSynchronize(h.stream), "sync");     // A and M are reassigned next
+  }
+  launch_block_inverse(h.t64, h.lv[0].coef64.p, h.lv[0].dinv64.p, (int)h.lv[0].nsite, 1, h.err.as<int>(), h.stream);
+  h.launches++;
+  check_err(h, "setup (smoother diagonal)");
+  // coarsest: dense matrix from the 9-point stencil, Gauss-Jordan inverse (Remark 4.2)
+  Level &C = h.lv[L - 1];
+  const int nxL = C.nx, nyL = C.ny, n = (int)C.n;
+  {
+    std::vector<double> dense((size_t)n * n, 0.0);
+    for (int j = 0; j < nyL; ++j)
+      for (int i = 0; i < nxL; ++i)
+        for (int q = 0; q < 9; ++q) {
+          const int ii = i + kTapDx[q], jj = j + kTapDy[q];
+          if (ii < 0 || ii >= nxL || jj < 0 || jj >= nyL) continue;
+          dense[((size_t)j * nxL + i) * n + (size_t)jj * nxL + ii] = A[((size_t)j * nxL + i) * 9 + q];
+        }
+    DevBuf dd, work, col;
+    dd.alloc(dense.size() * es);
+    work.alloc((size_t)n * 2 * n * es);
+    col.alloc((size_t)n * es);
+    check_cuda(cudaMemcpyAsync(dd.p, dense.data(), dense.size() * es, cudaMemcpyHostToDevice, h.stream), "H2D dense");
+    launch_gauss_jordan(h.t64, dd.p, C.Ainv64.p, work.p, n, h.err.as<int>(), col.p, h.stream);
+    h.launches += 5 + 2 * n + 2;
+    check_err(h, "coarsest inverse");
+    std::vector<double> Ainv((size_t)n * n);
+    check_cuda(cudaMemcpyAsync(Ainv.data(), C.Ainv64.p, Ainv.size() * es, cudaMemcpyDeviceToHost, h.stream), "D2H Ainv");
+    check_cuda(cudaStreamSynchronize(h.stream), "sync");
+    double tr = 0.0;
+    for (int j = 0; j < nyL; ++j)
+      for (int i = 0; i < nxL; ++i)
+        for (int q = 0; q < 9; ++q) {
+          const int ii = i + kTapDx[q], jj = j + kTapDy[q];
+          if (ii < 0 || ii >= nxL || jj < 0 || jj >= nyL) continue;
+          const size_t r = (size_t)j * nxL + i, c = (size_t)jj * nxL + ii;
+          tr += Ainv[r * n + c] * M[r * 9 + q];
+        }
+    h.coarse_term_hat = tr;
+  }
+  if (h.prm.precision == MLMC_PREC_MIXED_FP32) {
+    for (int l = 0; l < L; ++l) {
+      Level &Lv = h.lv[l];
+      launch_convert(h.t32, Lv.coef32.p, h.t64, Lv.coef64.p, Lv.nsite * Lv.taps, h.stream);
+      if (l + 1 < L) launch_convert(h.t32, Lv.dinv32.p, h.t64, Lv.dinv64.p, Lv.nsite, h.stream);
+      h.launches += 2;
+    }
+    launch_convert(h.t32, C.Ainv32.p, h.t64, C.Ainv64.p, C.n * C.n, h.stream);
+    h.launches++;
+  }
+}
+
 void validate(const mlmc_operator_desc *op, const mlmc_hierarchy_params *p) {
   if (!op || !p) fail(MLMC_ERR_INVALID_ARG, "null descriptor or parameters");
   if (op->kind != MLMC_OP_LAPLACE2D && op->kind != MLMC_OP_WILSON2D) fail(MLMC_ERR_INVALID_ARG, "unknown operator kind");
   if (op->nx < 2 || op->ny < 2) fail(MLMC_ERR_INVALID_ARG, "lattice too small");
   if (op->kind == MLMC_OP_WILSON2D && !op->links) fail(MLMC_ERR_INVALID_ARG, "Wilson operator needs links");
   if (p->levels < 2 || p->levels > 16) fail(MLMC_ERR_INVALID_ARG, "levels must be in 2..16");
+  if (p->transfer != MLMC_TRANSFER_AGGREGATION && p->transfer != MLMC_TRANSFER_BILINEAR)
+    fail(MLMC_ERR_INVALID_ARG, "unknown transfer");
+  if (p->transfer == MLMC_TRANSFER_BILINEAR) {
+    // Sec. 5, Example 5.1: Dirichlet Laplacian, N_{l+1} = (N_l - 1) / 2 with N_l odd
+    if (op->kind != MLMC_OP_LAPLACE2D || op->periodic)
+      fail(MLMC_ERR_UNSUPPORTED, "the bilinear hierarchy is built for the Dirichlet Laplacian (Example 5.1)");
+    if (p->block < 1 || p->block > 256) fail(MLMC_ERR_INVALID_ARG, "block must be in 1..256");
+    if (p->coarse_block < 0 || p->coarse_block > 256) fail(MLMC_ERR_INVALID_ARG, "coarse_block must be in 0..256");
+    if (p->fgmres_restart < 1 || p->fgmres_restart > 64) fail(MLMC_ERR_INVALID_ARG, "fgmres_restart must be in 1..64");
+    if (p->max_iter < 1) fail(MLMC_ERR_INVALID_ARG, "max_iter must be positive");
+    if (p->cycle == MLMC_CYCLE_K && (p->kcycle_its < 1 || p->kcycle_its > 8))
+      fail(MLMC_ERR_INVALID_ARG, "kcycle_its must be in 1..8");
+    if (p->inner_its < 0 || p->inner_its > 32) fail(MLMC_ERR_INVALID_ARG, "inner_its must be in 0..32");
+    if (p->precision != MLMC_PREC_FP64 && p->precision != MLMC_PREC_MIXED_FP32)
+      fail(MLMC_ERR_INVALID_ARG, "unknown precision");
+    if ((double)op->nx * op->ny * std::max(p->block, p->coarse_block) >= 2147483648.0)
+      fail(MLMC_ERR_UNSUPPORTED, "n * block must stay below 2^31 (32-bit kernel indexing)");
+    long nx = op->nx, ny = op->ny;
+    for (int l = 0; l + 1 < p->levels; ++l) {
+      if (nx % 2 == 0 || ny % 2 == 0 || nx < 3 || ny < 3)
+        fail(MLMC_ERR_INVALID_ARG, "bilinear coarsening needs odd sides >= 3 on every level above the coarsest");
+      nx = (nx - 1) / 2;
+      ny = (ny - 1) / 2;
+    }
+    if (nx * ny > 8192) fail(MLMC_ERR_INVALID_ARG, "coarsest level larger than 8192 unknowns");
+    return;
+  }
   if (p->agg_x < 1 || p->agg_y < 1) fail(MLMC_ERR_INVALID_ARG, "bad aggregate shape");
   if (p->block < 1 || p->block > 256) fail(MLMC_ERR_INVALID_ARG, "block must be in 1..256");
   if (p->coarse_block < 0 || p->coarse_block > 256) fail(MLMC_ERR_INVALID_ARG, "coarse_block must be in 0..256");
@@ -748,6 +918,7 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   h.t64 = h.complex_op ? C64 : F64;
   h.t32 = h.complex_op ? C32 : F32;
   h.L = p->levels;
+  h.bilinear = p->transfer == MLMC_TRANSFER_BILINEAR;
   h.kmax = p->block;
   h.kact = p->block;
   h.kwide = p->coarse_block > 0 ? p->coarse_block : p->block;
@@ -758,22 +929,29 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   h.lv.resize(h.L);
   for (int l = 0; l < h.L; ++l) {
     Level &Lv = h.lv[l];
-    Lv.nx = l == 0 ? op->nx : h.lv[l - 1].nx / p->agg_x;
-    Lv.ny = l == 0 ? op->ny : h.lv[l - 1].ny / p->agg_y;
-    Lv.d = l == 0 ? (h.complex_op ? 2 : 1) : dc;
+    if (h.bilinear) {
+      Lv.nx = l == 0 ? op->nx : (h.lv[l - 1].nx - 1) / 2;
+      Lv.ny = l == 0 ? op->ny : (h.lv[l - 1].ny - 1) / 2;
+      Lv.d = 1;
+      Lv.taps = l == 0 ? 5 : 9;
+    } else {
+      Lv.nx = l == 0 ? op->nx : h.lv[l - 1].nx / p->agg_x;
+      Lv.ny = l == 0 ? op->ny : h.lv[l - 1].ny / p->agg_y;
+      Lv.d = l == 0 ? (h.complex_op ? 2 : 1) : dc;
+    }
     Lv.nsite = (size_t)Lv.nx * Lv.ny;
     Lv.n = Lv.nsite * Lv.d;
-    Lv.coef64.alloc(Lv.nsite * 5 * Lv.d * Lv.d * es);
-    if (mixed) Lv.coef32.alloc(Lv.nsite * 5 * Lv.d * Lv.d * es32);
+    Lv.coef64.alloc(Lv.nsite * Lv.taps * Lv.d * Lv.d * es);
+    if (mixed) Lv.coef32.alloc(Lv.nsite * Lv.taps * Lv.d * Lv.d * es32);
     if (l + 1 < h.L) {
-      Lv.ax = p->agg_x;
-      Lv.ay = p->agg_y;
-      Lv.dc = dc;
+      Lv.ax = h.bilinear ? 2 : p->agg_x;
+      Lv.ay = h.bilinear ? 2 : p->agg_y;
+      Lv.dc = h.bilinear ? 1 : dc;
       Lv.dinv64.alloc(Lv.nsite * Lv.d * Lv.d * es);
-      Lv.P64.alloc(Lv.n * dc * es);
+      Lv.P64.alloc(h.bilinear ? 0 : Lv.n * dc * es);      // bilinear P has no stored entries
       if (mixed) {
         Lv.dinv32.alloc(Lv.nsite * Lv.d * Lv.d * es32);
-        Lv.P32.alloc(Lv.n * dc * es32);
+        Lv.P32.alloc(h.bilinear ? 0 : Lv.n * dc * es32);
       }
     } else {
       Lv.Ainv64.alloc(Lv.n * Lv.n * es);
@@ -815,7 +993,9 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   h.xs.resize(h.L);
   h.ys.resize(h.L);
   for (int l = 0; l < h.L; ++l) {
-    h.xs[l].alloc(h.lv[l].n * (size_t)width(l) * es);
+    // the hat form draws every level difference's noise on the fine level, so the
+    // fine noise block also takes the coarse-level width
+    h.xs[l].alloc(h.lv[l].n * (size_t)(l == 0 ? h.kbig : width(l)) * es);
     h.ys[l].alloc(h.lv[l].n * (size_t)width(l) * es);
     if (l + 1 < h.L) {
       h.outer[l].reset(new Krylov());
@@ -850,6 +1030,11 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   }
   h.launches++;
 
+  if (h.bilinear) {
+    build_bilinear(h, op);
+    check_cuda(cudaStreamSynchronize(h.stream), "sync");
+    return;
+  }
   if (p->user_P) {
     build_levels(h, nullptr, p->user_P);
     check_cuda(cudaStreamSynchronize(h.stream), "sync");
@@ -901,7 +1086,7 @@ int sample_block(H_t &h, int l, int noise, uint64_t seed, uint64_t first, int k,
     for (int j = 0; j < l; ++j) {                // R^_l x: restrict down to level l
       launch_restrict(pview(h, j, 0), h.xs[j].p, h.xs[j + 1].p, k, s);
       h.launches++;
-      h.cost += (double)h.lv[j].n * h.lv[j].dc * k;
+      h.cost += nnz_P(h, j) * k;
     }
   } else {
     launch_noise(kind, seed, key_hi(purpose, l + 1), first, h.lv[l].n, k, h.t64, h.xs[l].p, s);
@@ -995,10 +1180,19 @@ int mlmc_level_info(const mlmc_hierarchy *h, int level, int *nx, int *ny, int *d
   });
 }
 
+int mlmc_level_taps(const mlmc_hierarchy *h, int level, int *taps) {
+  return translate([&] {
+    need_level(h, level, 1, h ? h->L : 0);
+    if (!taps) fail(MLMC_ERR_INVALID_ARG, "null output");
+    *taps = h->lv[level - 1].taps;
+  });
+}
+
 int mlmc_get_prolongation(const mlmc_hierarchy *h, int level, void *host_out) {
   return translate([&] {
     need_level(h, level, 1, h ? h->L - 1 : 0);
     if (!host_out) fail(MLMC_ERR_INVALID_ARG, "null output");
+    if (h->bilinear) fail(MLMC_ERR_UNSUPPORTED, "bilinear P is not stored (it is applied by its stencil)");
     const Level &Lv = h->lv[level - 1];
     check_cuda(cudaMemcpyAsync(host_out, Lv.P64.p, Lv.n * Lv.dc * dtype_size(h->t64), cudaMemcpyDeviceToHost, h->stream), "D2H P");
     check_cuda(cudaStreamSynchronize(h->stream), "sync");
@@ -1010,7 +1204,7 @@ int mlmc_get_operator(const mlmc_hierarchy *h, int level, void *host_out) {
     need_level(h, level, 1, h ? h->L : 0);
     if (!host_out) fail(MLMC_ERR_INVALID_ARG, "null output");
     const Level &Lv = h->lv[level - 1];
-    check_cuda(cudaMemcpyAsync(host_out, Lv.coef64.p, Lv.nsite * 5 * Lv.d * Lv.d * dtype_size(h->t64),
+    check_cuda(cudaMemcpyAsync(host_out, Lv.coef64.p, Lv.nsite * Lv.taps * Lv.d * Lv.d * dtype_size(h->t64),
                                cudaMemcpyDeviceToHost, h->stream), "D2H coef");
     check_cuda(cudaStreamSynchronize(h->stream), "sync");
   });
@@ -1058,6 +1252,8 @@ int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, ui
     if (n_samples < 0 || (n_samples > 0 && !out_samples)) fail(MLMC_ERR_INVALID_ARG, "bad sample output");
     if (noise == MLMC_NOISE_Z4 && !h->complex_op) fail(MLMC_ERR_INVALID_ARG, "Z4 noise needs a complex operator");
     if (!(tol > 0.0)) fail(MLMC_ERR_INVALID_ARG, "tol must be positive");
+    if (h->bilinear && level < h->L)
+      fail(MLMC_ERR_INVALID_ARG, "the simplified form needs R P = I; use the hat form with a bilinear hierarchy");
     bool all_conv = true;
     const int kl = level == 1 ? h->kact : h->kwide;
     for (int done = 0, b = 0; done < n_samples; ++b) {
@@ -1094,6 +1290,8 @@ int mlmc_sample_level_form(mlmc_hierarchy *h, int level, int form, int noise, ui
     if (form != MLMC_FORM_SIMPLIFIED && form != MLMC_FORM_HAT && form != MLMC_FORM_PLAIN)
       fail(MLMC_ERR_INVALID_ARG, "unknown form");
     if (form == MLMC_FORM_PLAIN && level != 1) fail(MLMC_ERR_INVALID_ARG, "plain samples live on level 1");
+    if (form == MLMC_FORM_SIMPLIFIED && h->bilinear && level < h->L)
+      fail(MLMC_ERR_INVALID_ARG, "the simplified form needs R P = I; use the hat form with a bilinear hierarchy");
     if (n_samples < 0 || (n_samples > 0 && !out_samples)) fail(MLMC_ERR_INVALID_ARG, "bad sample output");
     if (noise == MLMC_NOISE_Z4 && !h->complex_op) fail(MLMC_ERR_INVALID_ARG, "Z4 noise needs a complex operator");
     if (!(tol > 0.0)) fail(MLMC_ERR_INVALID_ARG, "tol must be positive");
@@ -1151,6 +1349,11 @@ int mlmc_coarse_trace_exact(mlmc_hierarchy *h, mlmc_c64 *out) {
   return translate([&] {
     need(h);
     if (!out) fail(MLMC_ERR_INVALID_ARG, "null output");
+    if (h->bilinear) {
+      out->re = h->coarse_term_hat;
+      out->im = 0.0;
+      return;
+    }
     const Level &C = h->lv[h->L - 1];
     launch_trace(h->t64, C.Ainv64.p, (int)C.n, h->trace.p, h->stream);
     h->launches++;
@@ -1167,6 +1370,8 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
     if (p->form != MLMC_FORM_SIMPLIFIED && p->form != MLMC_FORM_HAT && p->form != MLMC_FORM_PLAIN)
       fail(MLMC_ERR_INVALID_ARG, "unknown form");
     const bool plain = p->form == MLMC_FORM_PLAIN;
+    if (p->form == MLMC_FORM_SIMPLIFIED && h->bilinear)
+      fail(MLMC_ERR_INVALID_ARG, "the simplified form needs R P = I; use the hat form with a bilinear hierarchy");
     if (p->noise == MLMC_NOISE_Z4 && !h->complex_op) fail(MLMC_ERR_INVALID_ARG, "Z4 noise needs a complex operator");
     if (p->allocation != MLMC_ALLOC_RHO && p->allocation != MLMC_ALLOC_OPTIMAL && p->allocation != MLMC_ALLOC_FIXED)
       fail(MLMC_ERR_INVALID_ARG, "unknown allocation");
@@ -1181,12 +1386,18 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
     auto t0 = std::chrono::steady_clock::now();
     mlmc_c64 TL = {0.0, 0.0};
     if (!plain) {
-      // Remark 4.2: tr(P^_L A_L^{-1} R^_L) = tr(A_L^{-1} R^_L P^_L) = tr(A_L^{-1}), since R^_L P^_L = I
+      // Remark 4.2: tr(P^_L A_L^{-1} R^_L) = tr(A_L^{-1} R^_L P^_L); = tr(A_L^{-1}) when R^_L P^_L = I
+      // (aggregation), else the setup's value (bilinear)
       const Level &C = H.lv[L - 1];
-      launch_trace(H.t64, C.Ainv64.p, (int)C.n, H.trace.p, H.stream);
-      H.launches++;
-      check_cuda(cudaMemcpyAsync(&TL, H.trace.p, sizeof(TL), cudaMemcpyDeviceToHost, H.stream), "D2H trace");
-      check_cuda(cudaStreamSynchronize(H.stream), "sync");
+      if (H.bilinear) {
+        TL.re = H.coarse_term_hat;
+        TL.im = 0.0;
+      } else {
+        launch_trace(H.t64, C.Ainv64.p, (int)C.n, H.trace.p, H.stream);
+        H.launches++;
+        check_cuda(cudaMemcpyAsync(&TL, H.trace.p, sizeof(TL), cudaMemcpyDeviceToHost, H.stream), "D2H trace");
+        check_cuda(cudaStreamSynchronize(H.stream), "sync");
+      }
       // Remark 4.2 cost of the exact term: inversion of A_L (n_L^3)
       r->cost_nnz[nd] = std::pow((double)H.lv[L - 1].n, 3.0);
     }
@@ -1321,7 +1532,8 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
                         double *bytes_per_launch) {
   return translate([&] {
     need_level(h, level, 1, h ? h->L : 0);
-    if (k < 1 || k > (which == 5 ? h->kbig : h->kmax) || reps < 1) fail(MLMC_ERR_INVALID_ARG, "bad k or reps");
+    // level 1 holds blocks of `block` columns, the coarser levels also the coarse-level blocks
+    if (k < 1 || k > (level > 1 ? h->kbig : h->kmax) || reps < 1) fail(MLMC_ERR_INVALID_ARG, "bad k or reps");
     H_t &H = *h;
     int l = level - 1;
     int lo = which == 0 ? 0 : (H.prm.precision == MLMC_PREC_MIXED_FP32 ? 1 : 0);
@@ -1375,7 +1587,7 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
     cudaEventDestroy(e1);
     double vec = (double)Lv.n * k * es;
     bool const_coef = l == 0 && !H.complex_op;      // Example 5.1 stencil has no matrix to read
-    double coefb = const_coef ? 0.0 : (double)Lv.nsite * 5 * Lv.d * Lv.d * es;
+    double coefb = const_coef ? 0.0 : (double)Lv.nsite * Lv.taps * Lv.d * Lv.d * es;
     double bytes;
     if (which == 5) {
       // the dense inverse once, the block in, the block out

@@ -124,6 +124,8 @@ struct StencilView {
   int const_laplace;  // 1: Example 5.1 operator, applied without reading coef
   double diag;        //    its diagonal 4 + shift
   int periodic;       //    0: Dirichlet
+  int taps;           // 5: the nearest-neighbour block stencil above; 9: a 9-point scalar
+                      //    stencil coef[site][9] (bilinear coarse levels, Dirichlet, d = 1)
 };
 
 // Per-aggregate prolongation blocks P[agg][loc*d + a][q] with loc = jj*ax + ii.
@@ -132,6 +134,7 @@ struct ProlongView {
   int ax, ay, dc;     // aggregate shape and coarse dofs
   DType t;
   const void *P;
+  int bilinear;       // 1: bilinear interpolation from the (nx-1)/2 x (ny-1)/2 grid (no P array)
 };
 
 // ----------------------------------------------------------------- launchers
@@ -173,6 +176,14 @@ void launch_prolong_add(const ProlongView &P, const void *ec, void *x, int k, cu
 // out = base + omega * D^{-1} (rhs - y), D = diagonal entries of the self blocks; base/rhs may be null
 void launch_jacobi_update(const StencilView &A, void *out, const void *base, const void *rhs,
                           const void *y, double omega, int k, cudaStream_t s);
+// bilinear hierarchy of Example 5.1 (kernels_bilinear.cu), real data, d = 1
+void launch_stencil9(const StencilView &A, const void *x, const void *b, void *y, int k, int mode, cudaStream_t s);
+// one 4-colour Gauss-Seidel sweep (order 0: colours 0..3, 1: 3..0); x_zero: x is zeroed first
+void launch_gs9_sweep(const StencilView &A, void *x, const void *b, int k, int order, int x_zero, cudaStream_t s);
+// rc = P^T r from the fine (2 nxc + 1) x (2 nyc + 1) grid
+void launch_restrict_bilinear(DType t, const void *r, void *rc, int nxc, int nyc, int k, cudaStream_t s);
+// x += P ec on the fine nx x ny grid
+void launch_prolong_bilinear(DType t, const void *ec, void *x, int nx, int ny, int k, cudaStream_t s);
 // setup kernels (kernels_setup.cu)
 void launch_block_inverse(DType t, const void *coef, void *dinv, int nsite, int d, int *err,
                           cudaStream_t s);

@@ -24,6 +24,7 @@ FORM_SIMPLIFIED, FORM_HAT, FORM_PLAIN = 0, 1, 2
 CYCLE_V, CYCLE_K = 0, 1
 ALLOC_RHO, ALLOC_OPTIMAL, ALLOC_FIXED = 0, 1, 2
 DENSE_SIMT, DENSE_TC, DENSE_TC_WITHHOLD = 0, 1, 2
+TRANSFER_AGGREGATION, TRANSFER_BILINEAR = 0, 1
 
 
 class C64(ctypes.Structure):
@@ -46,7 +47,7 @@ class HierarchyParams(ctypes.Structure):
                 ("kcycle_its", ctypes.c_int), ("fgmres_restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("block", ctypes.c_int), ("reorth", ctypes.c_int),
                 ("inner_its", ctypes.c_int), ("graphs", ctypes.c_int), ("coarse_smooth", ctypes.c_int),
-                ("coarse_block", ctypes.c_int), ("user_P", ctypes.c_void_p)]
+                ("coarse_block", ctypes.c_int), ("user_P", ctypes.c_void_p), ("transfer", ctypes.c_int)]
 
 
 class EstimateParams(ctypes.Structure):
@@ -112,6 +113,7 @@ def _load():
         "mlmc_trace_estimate_batch": [ctypes.POINTER(vp), i, ctypes.POINTER(EstimateParams), i,
                                       ctypes.POINTER(EstimateResult), ctypes.POINTER(i)],
         "mlmc_dense_apply": [i, vp, vp, vp, i, i, i, vp],
+        "mlmc_level_taps": [vp, i, ctypes.POINTER(i)],
         "mlmc_set_dense_kernel": [vp, i],
     }
     for name, args in sig.items():
@@ -132,7 +134,7 @@ EXPORTED = ["mlmc_setup_hierarchy", "mlmc_destroy_hierarchy", "mlmc_level_info",
             "mlmc_last_error", "mlmc_learned_train", "mlmc_learned_set", "mlmc_learned_apply", "mlmc_learned_grad",
             "mlmc_column_dots", "mlmc_column_dots_noalloc", "mlmc_noalloc_last_error", "mlmc_set_block_width",
             "mlmc_autotune_block", "mlmc_trace_estimate_batch", "mlmc_sample_level_form", "mlmc_dense_apply",
-            "mlmc_set_dense_kernel"]
+            "mlmc_set_dense_kernel", "mlmc_level_taps"]
 
 
 def check(status):
@@ -145,7 +147,8 @@ def default_params(**kw):
                         setup_sweeps=40, coarse_sweeps=20, setup_omega=2.0 / 3.0, setup_seed=0,
                         bootstrap=1, boot_iters=2, smooth_pre=1, smooth_post=1, cycle=CYCLE_K,
                         kcycle_its=2, fgmres_restart=30, max_iter=2000, precision=PREC_FP64, block=64,
-                        reorth=1, inner_its=0, graphs=1, coarse_smooth=0, coarse_block=0, user_P=None)
+                        reorth=1, inner_its=0, graphs=1, coarse_smooth=0, coarse_block=0, user_P=None,
+                        transfer=TRANSFER_AGGREGATION)
     for k, v in kw.items():
         if not hasattr(p, k):
             raise KeyError(k)
@@ -209,9 +212,15 @@ class Hierarchy:
         check(lib.mlmc_get_prolongation(self.handle, level, out.ctypes.data))
         return out
 
+    def level_taps(self, level):
+        t = ctypes.c_int()
+        check(lib.mlmc_level_taps(self.handle, level, ctypes.byref(t)))
+        return t.value
+
     def operator(self, level):
+        """[site][tap][d][d]: 5 block taps, or 9 scalar taps on the bilinear coarse levels."""
         nx, ny, d = self.level_info(level)
-        out = np.zeros((nx * ny, 5, d, d), dtype=np.complex128 if self.complex else np.float64)
+        out = np.zeros((nx * ny, self.level_taps(level), d, d), dtype=np.complex128 if self.complex else np.float64)
         check(lib.mlmc_get_operator(self.handle, level, out.ctypes.data))
         return out
 
