@@ -63,6 +63,9 @@ WORKLOADS = {
                       train_epochs=3, train_lr=1e-3),
 }
 WORKLOAD = WORKLOADS["laplace1024"]
+# ncu DRAM traffic (read + write bytes) per launch unit of the roofline kernel, keyed by
+# (workload, kernel row); only for the kernel version the capture was taken on
+TRAFFIC = {}
 METRIC = "Seconds to tr(A^-1) at 1e-3 rel. error, mixed+learned vs plain FP64; HBM %"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -80,7 +83,7 @@ def parse():
     ap.add_argument("--profile-sample", action="store_true",
                     help="for ncu only: after setup, one warm block and one profiled 64-sample block per level "
                          "difference inside cudaProfilerStart/Stop; prints no bench line")
-    ap.add_argument("--profile-kernel", default="", choices=["", "multidot", "multiaxpy", "rbgs", "stencil", "dense"],
+    ap.add_argument("--profile-kernel", default="", choices=["", "multidot", "multiaxpy", "rbgs", "rbgs2", "stencil", "dense"],
                     help="with --profile-sample: instead of sample blocks, the one kernel launch the bench's "
                          "roofline measures (3 warm launches, then 1), inside cudaProfilerStart/Stop")
     ap.add_argument("--profile-nx", type=int, default=0,
@@ -284,8 +287,12 @@ def profile_sample(args):
     nz = mlmc.NOISE_Z4 if w["noise"] == "z4" else mlmc.NOISE_RADEMACHER
     h = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, torch.cuda.current_stream().cuda_stream)
     if args.profile_kernel:
-        which = {"stencil": 1, "rbgs": 2, "multidot": 3, "multiaxpy": 4, "dense": 5}[args.profile_kernel]
-        level, kk = (w["levels"], w.get("coarse_block") or w["block"]) if which == 5 else (1, w["block"])
+        which = {"stencil": 1, "rbgs": 2, "rbgs2": 2, "multidot": 3, "multiaxpy": 4, "dense": 5}[args.profile_kernel]
+        level, kk = 1, w["block"]
+        if which == 5:
+            level, kk = w["levels"], w.get("coarse_block") or w["block"]
+        elif args.profile_kernel == "rbgs2":
+            level, kk = 2, w.get("coarse_block") or w["block"]
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
         h.profile_kernel(which, level, kk, 1)
@@ -523,6 +530,13 @@ def main():
                         ("stencil_fp64", 0)):
         kms, kbytes = h.profile_kernel(which, 1, w["block"], 20)
         kern[name] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6}
+    # the coarse-level smoother sweeps (block stencils, k = the coarse block)
+    kcb = w.get("coarse_block") or w["block"]
+    for lvl in range(2, w["levels"]):
+        kms, kbytes = h.profile_kernel(2, lvl, kcb, 20)
+        kern["rbgs_sweep_fp32_level%d" % lvl] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6, "k": kcb}
+        kms, kbytes = h.profile_kernel(1, lvl, kcb, 20)
+        kern["stencil_fp32_level%d" % lvl] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6, "k": kcb}
     # the coarsest dense apply of the FP32 cycle (tensor cores vs CUDA cores), k = the coarse block
     nxL, nyL, dL = h.level_info(w["levels"])
     nL, kc = nxL * nyL * dL, (w.get("coarse_block") or w["block"])
@@ -532,12 +546,16 @@ def main():
         flops = (8.0 if w["kind"] == "wilson" else 2.0) * nL * nL * kc
         kern[name] = {"ms": kms, "bytes": kbytes, "flops": flops, "tflops": flops / kms / 1e9, "n": nL, "k": kc}
     h.set_dense_kernel(mlmc.DENSE_TC)
-    dom = kern["multidot_fp32"]
-    # DRAM bytes of this launch from an ncu capture of the same kernel version on the 512^2 case
-    # (reads scaled by the 4x rows of the 1024^2 case; the partial-sum write does not scale)
-    traffic = 4 * 335.62e6 + 3.14e6 if (w["kind"] == "laplace" and w["nx"] == 1024) else None
-    roofline = {"bound": "hbm", "kernel": "k_multidot_partial<float> (inner Arnoldi: 4 basis blocks + w, "
-                                          "level 1, k=%d)" % w["block"],
+    # dominant kernel of the timed step (largest share of the step's ncu launch list): the
+    # coarse-level block Gauss-Seidel k_rbgs_half on level 2; one sweep = two launches
+    dom_name = "rbgs_sweep_fp32_level2" if w["levels"] > 2 else "multidot_fp32"
+    dom = kern[dom_name]
+    # DRAM bytes per sweep of this kernel version from an ncu capture (None until taken)
+    traffic = TRAFFIC.get((w["name"], dom_name))
+    label = ("k_rbgs_half (coarse-level red-black block GS, level 2, one sweep = 2 launches, k=%d)" % kcb
+             if dom_name != "multidot_fp32" else
+             "k_multidot_partial<float> (inner Arnoldi: 4 basis blocks + w, level 1, k=%d)" % w["block"])
+    roofline = {"bound": "hbm", "kernel": label,
                 "achieved": dom["gbs"], "peak": peak, "unit": "GB/s", "frac": dom["gbs"] / peak,
                 "peak_source": peak_kind, "traffic": traffic, "algorithmic_bytes": dom["bytes"], "kernels": kern}
 

@@ -261,9 +261,13 @@ void launch_stencil(const StencilView &A, const void *x, const void *b, void *y,
 }
 
 // ------------------------------------------------------------------ red-black block GS
-// For every site s of colour `colour` ((i + j) % 2): x_s += D_s^{-1} (b - A x)_s.
-// Sites of one colour couple only to the other colour, so the half-sweep is
-// an exact block Gauss-Seidel step in red-black order (needs nx, ny even).
+// For every site s of colour `colour` ((i + j) % 2):
+//   x_s = D_s^{-1} (b_s - sum over the 4 neighbour blocks A_{s,nb} x_nb),
+// the exact solve of the site's row block given its neighbours, so the old x_s
+// is not read.  Sites of one colour couple only to the other colour, so the
+// half-sweep is an exact block Gauss-Seidel step in red-black order (needs nx,
+// ny even).  other_zero = 1: the other colour holds zeros (not read), so the
+// first half-sweep from x = 0 needs no initialised x.
 // the smoother keeps 16-byte packs for complex FP32 blocks up to d = 8 (measured faster there)
 template <class T, int D> struct rbgs_vec { static const int v = gen_vec<T, D>::v; };
 template <int D> struct rbgs_vec<cfloat, D> { static const int v = D <= 8 ? 2 : 1; };
@@ -271,7 +275,7 @@ template <int D> struct rbgs_vec<cfloat, D> { static const int v = D <= 8 ? 2 : 
 template <class T, int D, int VEC>
 __global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, const T *__restrict__ dinv,
                                                    T *__restrict__ x, const T *__restrict__ b, int nx, int ny, int kv,
-                                                   int colour) {
+                                                   int colour, int other_zero) {
   typedef Pack<T, VEC> V;
   int hx = nx / 2;
   const unsigned total = (unsigned)hx * ny * kv;
@@ -291,49 +295,56 @@ __global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, c
 #pragma unroll
       for (int u = 0; u < VEC; ++u) res[r][u] = bb.v[u];
     }
+    if (!other_zero) {
 #pragma unroll
-    for (int dir = 0; dir < 5; ++dir) {
-      const T *B = coef + ((size_t)s * 5 + dir) * D * D;
-      const V *xs = (const V *)x + (size_t)nb[dir] * D * kv + c;
-      V xq[D];
+      for (int dir = 1; dir < 5; ++dir) {
+        const T *B = coef + ((size_t)s * 5 + dir) * D * D;
+        const V *xs = (const V *)x + (size_t)nb[dir] * D * kv + c;
+        V xq[D];
 #pragma unroll
-      for (int q = 0; q < D; ++q) xq[q] = xs[(size_t)q * kv];
+        for (int q = 0; q < D; ++q) xq[q] = xs[(size_t)q * kv];
 #pragma unroll
-      for (int r = 0; r < D; ++r) {
-        T row[D];
-        load_row<T, D>(B + r * D, row);
+        for (int r = 0; r < D; ++r) {
+          T row[D];
+          load_row<T, D>(B + r * D, row);
 #pragma unroll
-        for (int q = 0; q < D; ++q)
+          for (int q = 0; q < D; ++q)
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) res[r][u] = res[r][u] - row[q] * xq[q].v[u];
+            for (int u = 0; u < VEC; ++u) res[r][u] = res[r][u] - row[q] * xq[q].v[u];
+        }
       }
     }
     const T *Di = dinv + (size_t)s * D * D;
     V *X = (V *)x;
 #pragma unroll
     for (int r = 0; r < D; ++r) {
-      V cur = X[o + (size_t)r * kv];
+      V out;
       T row[D];
       load_row<T, D>(Di + r * D, row);
 #pragma unroll
+      for (int u = 0; u < VEC; ++u) out.v[u] = zero<T>();
+#pragma unroll
       for (int q = 0; q < D; ++q)
 #pragma unroll
-        for (int u = 0; u < VEC; ++u) cur.v[u] = cur.v[u] + row[q] * res[q][u];
-      X[o + (size_t)r * kv] = cur;
+        for (int u = 0; u < VEC; ++u) out.v[u] = out.v[u] + row[q] * res[q][u];
+      X[o + (size_t)r * kv] = out;
     }
   }
 }
 
 template <class T, int D>
-static void rbgs_go(const StencilView &A, void *x, const void *b, int k, int colour, cudaStream_t s) {
+static void rbgs_go(const StencilView &A, void *x, const void *b, int k, int colour, int other_zero,
+                    cudaStream_t s) {
   constexpr int VW = rbgs_vec<T, D>::v;
   if (VW > 1 && k % VW == 0) {
     int kv = k / VW;
     unsigned g = grid_for((size_t)(A.nx / 2) * A.ny * kv, 256, (size_t)1 << 20);
-    k_rbgs_half<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny, kv, colour);
+    k_rbgs_half<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny,
+                                            kv, colour, other_zero);
   } else {
     unsigned g = grid_for((size_t)(A.nx / 2) * A.ny * k, 256, (size_t)1 << 20);
-    k_rbgs_half<T, D, 1><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny, k, colour);
+    k_rbgs_half<T, D, 1><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny,
+                                           k, colour, other_zero);
   }
 }
 
@@ -343,7 +354,7 @@ void launch_rbgs_half(const StencilView &A, void *x, const void *b, int k, int c
     return;
   }
   if (A.taps == 9) throw cuda_error{cudaErrorInvalidValue, "9-point stencils are smoothed in four colours"};
-  MLMC_DISPATCH(A.t, T, MLMC_DDISPATCH(A.d, D, rbgs_go<T, D>(A, x, b, k, colour, s)));
+  MLMC_DISPATCH(A.t, T, MLMC_DDISPATCH(A.d, D, rbgs_go<T, D>(A, x, b, k, colour, 0, s)));
   MLMC_LAUNCH_CHECK("k_rbgs_half");
 }
 
@@ -359,8 +370,10 @@ void launch_rbgs_sweep(const StencilView &A, void *x, const void *b, int k, int 
     launch_gs9_sweep(A, x, b, k, order, x_zero, s);
     return;
   }
-  if (x_zero) MLMC_CUDA(cudaMemsetAsync(x, 0, (size_t)A.nx * A.ny * A.d * k * dtype_size(A.t), s));
-  launch_rbgs_half(A, x, b, k, first, s);
+  // x_zero: the first half-sweep reads no neighbours and the second none of its own
+  // old values, so x needs no initialisation
+  MLMC_DISPATCH(A.t, T, MLMC_DDISPATCH(A.d, D, rbgs_go<T, D>(A, x, b, k, first, x_zero ? 1 : 0, s)));
+  MLMC_LAUNCH_CHECK("k_rbgs_half");
   launch_rbgs_half(A, x, b, k, 1 - first, s);
 }
 

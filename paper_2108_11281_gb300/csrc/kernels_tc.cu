@@ -160,21 +160,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t idesc = tf32_idesc(ntile);
   constexpr uint32_t LBO = 128, SBO = (TC_BK / 4) * 128;
 
-  int issued = 0;      // K steps whose MMAs were committed (uniform over the CTA)
-  for (int t = 0; t < nsteps; ++t) {
-    const int buf = t & 1;
-    unsigned char *Ahi = smem + buf * sbytes, *Alo = Ahi + A_BYTES;
-    unsigned char *Bhi = Ahi + 2 * A_BYTES, *Blo = Bhi + bb;
-    if (t >= 2) {
-      // the MMAs of step t-2 read this stage: wait for their commit
-      if (!mbar_wait_bounded(&bars[buf], (uint32_t)(((t >> 1) - 1) & 1), wait_cycles)) failed = 1;
-      __syncthreads();
-      if (failed) break;
-    }
+  // One stage's tiles pass through registers: every thread first issues all its
+  // global loads (A: 8 float4; B^T: up to 8 (column, K quad) pairs of 4 scalars),
+  // and the loads of step t+1 are in flight while the MMAs of step t run.
+  constexpr int A_IT = TC_M * TC_BK / 4 / TC_THREADS;
+  constexpr int B_IT = TC_NT * (TC_BK / 4) / TC_THREADS;
+  float4 ra[A_IT];
+  float rb[B_IT][4];
+  auto load_stage = [&](int t) {
     const int j0 = j_begin + t * TC_BK;
     // A tile: float4 e4 -> row (e4>>6)*8 + (e4&7), K quad (e4>>3)&7; its core-matrix
     // offset is exactly 16*e4, so the 16-byte shared stores are dense.
-    for (int e4 = tid; e4 < TC_M * TC_BK / 4; e4 += TC_THREADS) {
+#pragma unroll
+    for (int it = 0; it < A_IT; ++it) {
+      const int e4 = tid + it * TC_THREADS;
       const int r = ((e4 >> 6) << 3) | (e4 & 7), kq = (e4 >> 3) & 7;
       const int gi = row0 + r, gj = j0 + 4 * kq;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -189,19 +188,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (gj + 3 < j_end) v.w = __ldg(src + 3);
         }
       }
-      split_store(Ahi, Alo, (uint32_t)e4 * 16, v);
+      ra[it] = v;
     }
-    // B^T tile: (column c, K quad kq) with c fastest; four K rows per thread, one
-    // 16-byte store of the (c, 4kq..4kq+3) core-matrix row.
-    for (int e = tid; e < ntile * (TC_BK / 4); e += TC_THREADS) {
+    // B^T tile: (column c, K quad kq) with c fastest; four K rows per pair.
+#pragma unroll
+    for (int it = 0; it < B_IT; ++it) {
+      const int e = tid + it * TC_THREADS;
       const int c = e % ntile, kq = e / ntile;
       const int gc = col0 + c;
-      float vv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int gj = j0 + 4 * kq + u;
         float x = 0.f;
-        if (gj < j_end && gc < nf) {
+        if (e < ntile * (TC_BK / 4) && gj < j_end && gc < nf) {
           if (!cplx) {
             x = __ldg(Bf + (size_t)gj * nf + gc);
           } else {
@@ -210,11 +209,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             else x = (gc & 1) ? __ldg(row + gc - 1) : -__ldg(row + gc + 1);
           }
         }
-        vv[u] = x;
+        rb[it][u] = x;
       }
-      const uint32_t off = (uint32_t)((((c >> 3) * (TC_BK / 4) + kq) << 7) + ((c & 7) << 4));
-      split_store(Bhi, Blo, off, make_float4(vv[0], vv[1], vv[2], vv[3]));
     }
+  };
+  auto store_stage = [&](unsigned char *Ahi, unsigned char *Alo, unsigned char *Bhi, unsigned char *Blo) {
+#pragma unroll
+    for (int it = 0; it < A_IT; ++it) split_store(Ahi, Alo, (uint32_t)(tid + it * TC_THREADS) * 16, ra[it]);
+#pragma unroll
+    for (int it = 0; it < B_IT; ++it) {
+      const int e = tid + it * TC_THREADS;
+      if (e >= ntile * (TC_BK / 4)) break;
+      const int c = e % ntile, kq = e / ntile;
+      const uint32_t off = (uint32_t)((((c >> 3) * (TC_BK / 4) + kq) << 7) + ((c & 7) << 4));
+      split_store(Bhi, Blo, off, make_float4(rb[it][0], rb[it][1], rb[it][2], rb[it][3]));
+    }
+  };
+
+  int issued = 0;      // K steps whose MMAs were committed (uniform over the CTA)
+  if (nsteps > 0) load_stage(0);
+  for (int t = 0; t < nsteps; ++t) {
+    const int buf = t & 1;
+    unsigned char *Ahi = smem + buf * sbytes, *Alo = Ahi + A_BYTES;
+    unsigned char *Bhi = Ahi + 2 * A_BYTES, *Blo = Bhi + bb;
+    if (t >= 2) {
+      // the MMAs of step t-2 read this stage: wait for their commit
+      if (!mbar_wait_bounded(&bars[buf], (uint32_t)(((t >> 1) - 1) & 1), wait_cycles)) failed = 1;
+      __syncthreads();
+      if (failed) break;
+    }
+    store_stage(Ahi, Alo, Bhi, Blo);
     // generic-proxy stores -> visible to the tensor core's async proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -234,6 +258,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mma_commit(&bars[buf]);
     }
     issued = t + 1;
+    if (t + 1 < nsteps) load_stage(t + 1);
   }
 
   // drain: the last commit of each stage that nobody waited for yet

@@ -1598,11 +1598,12 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
       bytes = (which == 3 ? nvec + 1.0 : nvec + 2.0) * vec;
       if (ms_per_launch) *ms_per_launch = ms / reps;
     } else if (which == 2) {
-      // one sweep = two half-sweeps: each reads b and x on its colour, the
-      // other colour's x as neighbours, writes x on its colour: 2 passes over
-      // x plus b, plus the coefficient and inverse blocks
+      // one sweep = two half-sweeps: each reads b on its colour and the other
+      // colour's x as neighbours and writes x on its colour (3 passes in all),
+      // plus the off-diagonal coefficient blocks and the inverse self blocks
       double dinvb = (double)Lv.nsite * Lv.d * Lv.d * es;
-      bytes = 3.0 * vec + (const_coef ? 0.0 : coefb + dinvb);
+      double offb = Lv.taps == 9 ? coefb * 8.0 / 9.0 : coefb * 4.0 / 5.0;
+      bytes = 3.0 * vec + (const_coef ? 0.0 : offb + dinvb);
       if (ms_per_launch) *ms_per_launch = ms / reps;
     } else {
       bytes = 2.0 * vec + coefb;
