@@ -65,7 +65,11 @@ WORKLOADS = {
 WORKLOAD = WORKLOADS["laplace1024"]
 # ncu DRAM traffic (read + write bytes) per launch unit of the roofline kernel, keyed by
 # (workload, kernel row); only for the kernel version the capture was taken on
-TRAFFIC = {}
+TRAFFIC = {
+    # k_rbgs_half<float,4,4>, level 2 (256^2 x 4, k = 128), both halves of one sweep:
+    # dram__bytes_read 149.44 + 149.43 MB, dram__bytes_write 40.31 + 37.25 MB (1 pass each)
+    ("laplace2d-1024x1024-L4-4tv-k64", "rbgs_sweep_fp32_level2"): 376.43e6,
+}
 METRIC = "Seconds to tr(A^-1) at 1e-3 rel. error, mixed+learned vs plain FP64; HBM %"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"

@@ -14,15 +14,6 @@
 
 namespace mlmc {
 
-__device__ inline void neighbours(int s, int nx, int ny, int nb[5]) {
-  int i = s % nx, j = s / nx;
-  nb[0] = s;
-  nb[1] = j * nx + (i + 1 == nx ? 0 : i + 1);
-  nb[2] = j * nx + (i == 0 ? nx - 1 : i - 1);
-  nb[3] = (j + 1 == ny ? 0 : j + 1) * nx + i;
-  nb[4] = (j == 0 ? ny - 1 : j - 1) * nx + i;
-}
-
 // ------------------------------------------------------------------ apply / residual
 // One thread per (site, VEC consecutive columns): the d x d coefficient blocks
 // are loaded once per VEC columns, the vector entries as 16-byte packs.
@@ -49,12 +40,17 @@ __global__ void __launch_bounds__(256) k_stencil(const T *__restrict__ coef, con
                                                  const T *__restrict__ b, T *__restrict__ y, int nx, int ny, int kv,
                                                  int mode) {
   typedef Pack<T, VEC> V;
-  const unsigned total = (unsigned)nx * ny * kv;
-  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int s = (int)(t / (unsigned)kv);
-    const int c = (int)(t - (unsigned)s * kv);
+  const int j = blockIdx.y;                 // grid.y = lattice row
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nx * kv) {
+    const int i = t / kv, c = t - (t / kv) * kv;
+    const int s = j * nx + i;
     int nb[5];
-    neighbours(s, nx, ny, nb);
+    nb[0] = s;
+    nb[1] = j * nx + (i + 1 == nx ? 0 : i + 1);
+    nb[2] = j * nx + (i == 0 ? nx - 1 : i - 1);
+    nb[3] = (j + 1 == ny ? 0 : j + 1) * nx + i;
+    nb[4] = (j == 0 ? ny - 1 : j - 1) * nx + i;
     T acc[D][VEC];
 #pragma unroll
     for (int r = 0; r < D; ++r)
@@ -97,7 +93,7 @@ __global__ void __launch_bounds__(256) k_stencil(const T *__restrict__ coef, con
 // columns per thread for the generic kernels: 16-byte packs for FP32 data on
 // small blocks; fewer columns per thread as d grows, to bound registers
 template <class T, int D> struct gen_vec { static const int v = 1; };
-template <int D> struct gen_vec<float, D> { static const int v = D <= 2 ? 4 : (D == 4 ? 2 : 1); };
+template <int D> struct gen_vec<float, D> { static const int v = D <= 4 ? 4 : 2; };
 template <int D> struct gen_vec<cfloat, D> { static const int v = D <= 2 ? 2 : 1; };
 
 #define MLMC_DDISPATCH(d, DD, ...)                       \
@@ -114,10 +110,10 @@ static void stencil_go(const StencilView &A, const void *x, const void *b, void 
   constexpr int VW = gen_vec<T, D>::v;
   if (VW > 1 && k % VW == 0) {
     int kv = k / VW;
-    unsigned g = grid_for((size_t)A.nx * A.ny * kv, 256, (size_t)1 << 20);
+    dim3 g((A.nx * kv + 255) / 256, A.ny);
     k_stencil<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, mode);
   } else {
-    unsigned g = grid_for((size_t)A.nx * A.ny * k, 256, (size_t)1 << 20);
+    dim3 g((A.nx * k + 255) / 256, A.ny);
     k_stencil<T, D, 1><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, k, mode);
   }
 }
@@ -269,24 +265,31 @@ void launch_stencil(const StencilView &A, const void *x, const void *b, void *y,
 // ny even).  other_zero = 1: the other colour holds zeros (not read), so the
 // first half-sweep from x = 0 needs no initialised x.
 // the smoother keeps 16-byte packs for complex FP32 blocks up to d = 8 (measured faster there)
-template <class T, int D> struct rbgs_vec { static const int v = gen_vec<T, D>::v; };
+// 16-byte packs where the block allows (measured on a level-2 shape, d = 4 FP32:
+// 16-byte packs on a row-per-block grid 0.095 ms per sweep, 8-byte packs 0.107 ms)
+template <class T, int D> struct rbgs_vec { static const int v = D <= 4 ? 16 / (int)sizeof(T) : 8 / (int)sizeof(T) > 0 ? 8 / (int)sizeof(T) : 1; };
 template <int D> struct rbgs_vec<cfloat, D> { static const int v = D <= 8 ? 2 : 1; };
+template <int D> struct rbgs_vec<cdouble, D> { static const int v = 1; };
 
+// grid.y = lattice row j; threads of a row cover (site m of the colour, VEC columns).
 template <class T, int D, int VEC>
 __global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, const T *__restrict__ dinv,
                                                    T *__restrict__ x, const T *__restrict__ b, int nx, int ny, int kv,
                                                    int colour, int other_zero) {
   typedef Pack<T, VEC> V;
-  int hx = nx / 2;
-  const unsigned total = (unsigned)hx * ny * kv;
-  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int idx = (int)(t / (unsigned)kv);
-    const int c = (int)(t - (unsigned)idx * kv);
-    int j = idx / hx, m = idx % hx;
-    int i = 2 * m + ((j + colour) & 1);
-    int s = j * nx + i;
+  const int j = blockIdx.y;
+  const int hx = nx / 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < hx * kv) {
+    const int m = t / kv, c = t - (t / kv) * kv;
+    const int i = 2 * m + ((j + colour) & 1);
+    const int s = j * nx + i;
     int nb[5];
-    neighbours(s, nx, ny, nb);
+    nb[0] = s;
+    nb[1] = j * nx + (i + 1 == nx ? 0 : i + 1);
+    nb[2] = j * nx + (i == 0 ? nx - 1 : i - 1);
+    nb[3] = (j + 1 == ny ? 0 : j + 1) * nx + i;
+    nb[4] = (j == 0 ? ny - 1 : j - 1) * nx + i;
     T res[D][VEC];
     size_t o = (size_t)s * D * kv + c;
 #pragma unroll
@@ -338,11 +341,11 @@ static void rbgs_go(const StencilView &A, void *x, const void *b, int k, int col
   constexpr int VW = rbgs_vec<T, D>::v;
   if (VW > 1 && k % VW == 0) {
     int kv = k / VW;
-    unsigned g = grid_for((size_t)(A.nx / 2) * A.ny * kv, 256, (size_t)1 << 20);
+    dim3 g(((A.nx / 2) * kv + 255) / 256, A.ny);
     k_rbgs_half<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny,
                                             kv, colour, other_zero);
   } else {
-    unsigned g = grid_for((size_t)(A.nx / 2) * A.ny * k, 256, (size_t)1 << 20);
+    dim3 g(((A.nx / 2) * k + 255) / 256, A.ny);
     k_rbgs_half<T, D, 1><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny,
                                            k, colour, other_zero);
   }
