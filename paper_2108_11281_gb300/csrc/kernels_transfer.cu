@@ -42,21 +42,35 @@ __global__ void __launch_bounds__(128) k_restrict(const T *__restrict__ P, const
 #pragma unroll
       for (int u = 0; u < VEC; ++u) acc[q][u] = zero<T>();
     const T *PI = P + (size_t)I * m * DC + g * QG;
-    for (int jj = 0; jj < ay; ++jj)
-      for (int ii = 0; ii < ax; ++ii) {
-        int s = (bj * ay + jj) * nx + bi * ax + ii;
-        int loc = jj * ax + ii;
-        for (int a = 0; a < d; ++a) {
-          V xv = R[((size_t)s * d + a) * kv + c];
-          const T *Pr = PI + (size_t)(loc * d + a) * DC;
+    // the aggregate's m = ax * ay * d fine entries, e = loc * d + a (the row of P), in
+    // batches of 8 loads issued before their products (the loads are independent;
+    // one load at a time left the small coarse-level launches latency-bound)
+    for (int e0 = 0; e0 < m; e0 += 8) {
+      V xv[8];
+#pragma unroll
+      for (int b8 = 0; b8 < 8; ++b8) {
+        const int e = e0 + b8;
+        if (e < m) {
+          const int loc = e / d, a = e - (e / d) * d;
+          const int jj = loc / ax, ii = loc - (loc / ax) * ax;
+          const int s = (bj * ay + jj) * nx + bi * ax + ii;
+          xv[b8] = R[((size_t)s * d + a) * kv + c];
+        }
+      }
+#pragma unroll
+      for (int b8 = 0; b8 < 8; ++b8) {
+        const int e = e0 + b8;
+        if (e < m) {
+          const T *Pr = PI + (size_t)e * DC;
 #pragma unroll
           for (int q = 0; q < QG; ++q) {
             T pq = conj(Pr[q]);
 #pragma unroll
-            for (int u = 0; u < VEC; ++u) acc[q][u] = acc[q][u] + pq * xv.v[u];
+            for (int u = 0; u < VEC; ++u) acc[q][u] = acc[q][u] + pq * xv[b8].v[u];
           }
         }
       }
+    }
 #pragma unroll
     for (int q = 0; q < QG; ++q) {
       V o;
