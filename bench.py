@@ -46,6 +46,14 @@ WORKLOADS = {
                            smooth_pre=1, smooth_post=1, kcycle_its=2, restart=8, inner_its=8, block=64,
                            coarse_block=128, noise="rademacher", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8,
                            seed=0, learned=False),
+    # the paper's Fig. 5 setting: N = 127, bilinear hierarchy to N_L = 15 (L = 4), blocks of 8
+    # samples so that large eps are not held at a 64-sample minimum (the paper's minimum is 5)
+    "laplace127bil": dict(name="laplace2d-127x127-bilinear-L4-k8", kind="laplace", transfer="bilinear",
+                          form="hat", nx=127, ny=127, levels=4, n_tv=1, spin_split=0, setup="smooth",
+                          setup_sweeps=0, coarse_sweeps=0, omega=2.0 / 3.0, bootstrap=0, boot_iters=0,
+                          smooth_pre=1, smooth_post=1, kcycle_its=2, restart=8, inner_its=8, block=8,
+                          coarse_block=8, noise="rademacher", eps=1e-3, tol_fp64=1e-10, tol_mixed=1e-8,
+                          seed=0, learned=False),
     # 2-spin Wilson operator 128^2, theta ~ N(0, 0.3^2), m0 tuned to sigma_min / sigma_max = 1e-3
     "wilson128": dict(name="wilson2d-128x128-L3-8dof-k32", kind="wilson", nx=128, ny=128, levels=3, n_tv=4,
                       spin_split=1, setup="inverse", setup_sweeps=20, coarse_sweeps=10, omega=1.0, bootstrap=4,
@@ -246,7 +254,8 @@ def cpu_baseline(result, w):
 REFERENCE = {"laplace1024": {"n_samples": [64, 128, 1024], "iters": [2.0, 2.0, 3.0]},
              "wilson128": {"n_samples": [128, 896], "iters": [3.0, 3.0]},
              "wilson256": {"n_samples": [32, 96], "iters": [3.0, 4.0]},
-             "laplace1023bil": {"n_samples": [64, 128, 128, 128, 128, 256], "iters": [2.0, 3.0, 2.0, 2.0, 2.0, 2.0]}}
+             "laplace1023bil": {"n_samples": [64, 128, 128, 128, 128, 256], "iters": [2.0, 3.0, 2.0, 2.0, 2.0, 2.0]},
+             "laplace127bil": {"n_samples": [40, 80, 160], "iters": [2.0, 2.0, 2.0]}}
 
 
 def run_reference(args):
