@@ -98,6 +98,9 @@ def parse():
     ap.add_argument("--profile-kernel", default="", choices=["", "multidot", "multiaxpy", "rbgs", "rbgs2", "stencil", "dense"],
                     help="with --profile-sample: instead of sample blocks, the one kernel launch the bench's "
                          "roofline measures (3 warm launches, then 1), inside cudaProfilerStart/Stop")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="for ncu launch lists only: setup, --warmup estimates, then one estimate inside "
+                         "cudaProfilerStart/Stop; prints no bench line")
     ap.add_argument("--profile-nx", type=int, default=0,
                     help="with --profile-sample: lattice side for a smaller capture (default: the workload's)")
     ap.add_argument("--workload", default="laplace1024", choices=sorted(WORKLOADS) + ["batch48"],
@@ -325,6 +328,29 @@ def profile_sample(args):
     h.close()
 
 
+def profile_step(args):
+    """One estimate of the workload inside cudaProfilerStart/Stop, after setup and --warmup
+    estimates (the launch list of exactly what one timed bench step runs)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2108_11281_gb300 import mlmc
+    w = WORKLOADS[args.workload]
+    nz = mlmc.NOISE_Z4 if w["noise"] == "z4" else mlmc.NOISE_RADEMACHER
+    form = mlmc.FORM_HAT if w.get("form") == "hat" else mlmc.FORM_SIMPLIFIED
+    h = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, torch.cuda.current_stream().cuda_stream)
+    for _ in range(args.warmup):
+        h.trace_estimate(eps=w["eps"], noise=nz, seed=w["seed"], tol=w["tol_mixed"], form=form,
+                         allocation=mlmc.ALLOC_OPTIMAL)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    h.trace_estimate(eps=w["eps"], noise=nz, seed=w["seed"], tol=w["tol_mixed"], form=form,
+                     allocation=mlmc.ALLOC_OPTIMAL)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    h.close()
+
+
 def eps_sweep(args):
     """Time-to-trace and arithmetic cost of MLMC (simplified form, Sec. 2 optimal allocation) and
     of plain Hutchinson on the fine operator, for eps = 10^-1, 10^-1.5, ..., 10^-3 (the study of
@@ -469,6 +495,9 @@ def main():
         return
     if args.eps_sweep:
         eps_sweep(args)
+        return
+    if args.profile_step:
+        profile_step(args)
         return
     import torch
     rank = int(os.environ.get("RANK", "0"))
