@@ -328,6 +328,28 @@ def profile_sample(args):
     h.close()
 
 
+def replica_seed(base_seed, rank):
+    """Replicas draw disjoint noise: replica r uses seed base + 1000 r (Philox key)."""
+    return base_seed + 1000 * rank
+
+
+def max_over_ranks(t, device="cuda"):
+    """The job's time per step is the slowest replica's: all-reduce MAX over the process
+    group (the identity for one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(t_step_max, world):
+    """Whole-job metric: seconds per trace when `world` replicas estimate concurrently."""
+    return t_step_max / world
+
+
 def profile_step(args):
     """One estimate of the workload inside cudaProfilerStart/Stop, after setup and --warmup
     estimates (the launch list of exactly what one timed bench step runs)."""
@@ -529,7 +551,7 @@ def main():
         _, rep = h.learned_train(n_pairs=w["train_pairs"], epochs=w["train_epochs"], lr=w["train_lr"],
                                  tol=w["tol_mixed"], seed=7, enable=1)
         learned = dict(rep, seconds_total=time.time() - t)
-    seed = w["seed"] + 1000 * rank          # replicas draw disjoint noise
+    seed = replica_seed(w["seed"], rank)    # replicas draw disjoint noise
     for _ in range(args.warmup):
         res = step(h, w["tol_mixed"], seed)
 
@@ -557,12 +579,8 @@ def main():
         torch.cuda.profiler.stop()
     ms = ev0.elapsed_time(ev1)
     launches = (h.launch_count() - l0) // max(args.steps, 1)
-    t_step = ms / 1e3 / args.steps
-    if world > 1:
-        tt = torch.tensor([t_step], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
-    value = t_step / world                 # seconds per trace over all replicas
+    t_step = max_over_ranks(ms / 1e3 / args.steps, "cuda")
+    value = job_value(t_step, world)       # seconds per trace over all replicas
     res = results[-1]
 
     # dominant kernels, timed alone with CUDA events on the hierarchy's stream
