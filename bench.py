@@ -605,7 +605,7 @@ def main():
         kms, kbytes = h.profile_kernel(5, w["levels"], kc, 20)
         flops = (8.0 if w["kind"] == "wilson" else 2.0) * nL * nL * kc
         kern[name] = {"ms": kms, "bytes": kbytes, "flops": flops, "tflops": flops / kms / 1e9, "n": nL, "k": kc}
-    h.set_dense_kernel(mlmc.DENSE_TC)
+    h.set_dense_kernel(mlmc.DENSE_AUTO)
     # dominant kernel of the timed step (largest share of the step's ncu launch list): the
     # coarse-level block Gauss-Seidel k_rbgs_half on level 2; one sweep = two launches
     dom_name = "rbgs_sweep_fp32_level2" if w["levels"] > 2 else "multidot_fp32"

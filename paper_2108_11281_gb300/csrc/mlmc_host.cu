@@ -118,7 +118,7 @@ struct mlmc_hierarchy {
   std::vector<std::unique_ptr<Krylov>> outer;     // FP64 outer FGMRES per level
   std::vector<std::unique_ptr<Krylov>> inner[2];  // fixed-length inner FGMRES per level, [0] FP64 [1] FP32
   int const_laplace = 0, periodic = 0;
-  int dense_tc = 1;    // coarsest apply of the FP32 cycle on the tensor cores (else the SIMT kernel)
+  int dense_kernel = MLMC_DENSE_AUTO;   // coarsest apply of the FP32 cycle: tensor cores, CUDA cores, or by size
   int bilinear = 0;    // the Example 5.1 hierarchy of Sec. 5: bilinear P, Galerkin 9-point levels
   double coarse_term_hat = 0.0;   // bilinear: tr(A_L^{-1} R^_L P^_L) (Remark 4.2), computed at setup
   double laplace_diag = 4.0;
@@ -242,7 +242,9 @@ void residual_op(H_t &h, int l, int lo, const void *x, const void *b, void *r, i
 
 void dense_apply(H_t &h, int lo, const void *b, void *x, int k) {
   const Level &C = h.lv[h.L - 1];
-  if (lo && h.dense_tc && dense_apply_tc_ok(h.t32, (int)C.n, k)) {
+  const int kdim = (int)C.n * (h.complex_op ? 2 : 1);
+  const bool tc = h.dense_kernel == MLMC_DENSE_TC || (h.dense_kernel == MLMC_DENSE_AUTO && kdim >= 512);
+  if (lo && tc && dense_apply_tc_ok(h.t32, (int)C.n, k)) {
     launch_dense_apply_tc(h.t32, C.Ainv32.p, b, x, (int)C.n, k, C.dense_part.p, C.dense_part.bytes, h.err.as<int>(),
                           h.stream);
     h.launches += dense_apply_tc_part_bytes(h.t32, (int)C.n, k) ? 2 : 1;
@@ -1340,8 +1342,9 @@ int mlmc_dense_apply(int complex_data, const void *A, const void *B, void *Y, in
 int mlmc_set_dense_kernel(mlmc_hierarchy *h, int which) {
   return translate([&] {
     need(h);
-    if (which != MLMC_DENSE_SIMT && which != MLMC_DENSE_TC) fail(MLMC_ERR_INVALID_ARG, "unknown dense kernel");
-    h->dense_tc = which == MLMC_DENSE_TC ? 1 : 0;
+    if (which != MLMC_DENSE_SIMT && which != MLMC_DENSE_TC && which != MLMC_DENSE_AUTO)
+      fail(MLMC_ERR_INVALID_ARG, "unknown dense kernel");
+    h->dense_kernel = which;
   });
 }
 

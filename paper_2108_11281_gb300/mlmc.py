@@ -23,7 +23,7 @@ PREC_FP64, PREC_MIXED_FP32 = 0, 1
 FORM_SIMPLIFIED, FORM_HAT, FORM_PLAIN = 0, 1, 2
 CYCLE_V, CYCLE_K = 0, 1
 ALLOC_RHO, ALLOC_OPTIMAL, ALLOC_FIXED = 0, 1, 2
-DENSE_SIMT, DENSE_TC, DENSE_TC_WITHHOLD = 0, 1, 2
+DENSE_SIMT, DENSE_TC, DENSE_TC_WITHHOLD, DENSE_AUTO = 0, 1, 2, 3
 TRANSFER_AGGREGATION, TRANSFER_BILINEAR = 0, 1
 
 
