@@ -35,7 +35,7 @@ WORKLOADS = {
     "laplace1024": dict(name="laplace2d-1024x1024-L4-4tv-k64", kind="laplace", nx=1024, ny=1024, levels=4, n_tv=4,
                         spin_split=0, setup="smooth", setup_sweeps=160, coarse_sweeps=20, omega=2.0 / 3.0,
                         bootstrap=2, boot_iters=5, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=8,
-                        inner_its=12, block=64, coarse_block=128, noise="rademacher", eps=1e-3, tol_fp64=1e-10,
+                        inner_its=8, block=64, coarse_block=128, noise="rademacher", eps=1e-3, tol_fp64=1e-10,
                         tol_mixed=1e-8,
                         seed=0, learned=False),
     # the paper's own hierarchy for Example 5.1 (Sec. 5, Table 1): bilinear P, N_{l+1} = (N_l - 1)/2,
@@ -254,7 +254,7 @@ def cpu_baseline(result, w):
 # per-level sample counts and mean outer iterations of each workload's estimate
 # (same estimator and noise on both sides, optimal allocation); used only by
 # the reference arm's extrapolation, which runs before any GPU number exists.
-REFERENCE = {"laplace1024": {"n_samples": [64, 128, 1024], "iters": [2.0, 2.0, 3.0]},
+REFERENCE = {"laplace1024": {"n_samples": [64, 128, 1024], "iters": [2.0, 3.0, 5.0]},
              "wilson128": {"n_samples": [128, 896], "iters": [3.0, 3.0]},
              "wilson256": {"n_samples": [32, 96], "iters": [3.0, 4.0]},
              "laplace1023bil": {"n_samples": [64, 128, 128, 128, 128, 256], "iters": [2.0, 3.0, 2.0, 2.0, 2.0, 2.0]},

@@ -173,23 +173,50 @@ void launch_sample_combine(int hc, const void *a, const void *b, void *out, int 
   MLMC_LAUNCH_CHECK("k_sample_combine");
 }
 
-// Welford's update in sample order: N += 1; d = s - mean; mean += d / N; M2 += |d| |s - mean|.
-// For complex samples M2 accumulates Re(conj(d) (s - mean_new)), which sums to sum |s - mean|^2.
-__global__ void k_accumulate(const cdouble *smp, int k, double *acc) {
-  if (threadIdx.x || blockIdx.x) return;
-  double n = acc[0], mr = acc[1], mi = acc[2], m2 = acc[3];
-  for (int c = 0; c < k; ++c) {
-    n += 1.0;
-    double dr = smp[c].re - mr, di = smp[c].im - mi;
-    mr += dr / n;
-    mi += di / n;
-    m2 += dr * (smp[c].re - mr) + di * (smp[c].im - mi);
+// Running (N, mean, M2) of the level's samples, updated with one block of k <= 256
+// samples: the block's own mean and M2 = sum |s - mean_b|^2 by a fixed-order tree
+// (deterministic), then the pairwise merge of Chan, Golub and LeVeque:
+//   N = Na + Nb,  d = mean_b - mean_a,  mean = mean_a + d Nb / N,
+//   M2 = M2_a + M2_b + |d|^2 Na Nb / N.
+// M2 / (N - 1) is the unbiased complex variance E|s - E s|^2.
+__device__ inline void block_tree_sum(double *a, double *b) {
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      a[threadIdx.x] += a[threadIdx.x + o];
+      b[threadIdx.x] += b[threadIdx.x + o];
+    }
+    __syncthreads();
   }
-  acc[0] = n; acc[1] = mr; acc[2] = mi; acc[3] = m2;
+}
+
+__global__ void __launch_bounds__(256) k_accumulate(const cdouble *smp, int k, double *acc) {
+  __shared__ double sr[256], si[256];
+  const int t = threadIdx.x;
+  const double re = t < k ? smp[t].re : 0.0, im = t < k ? smp[t].im : 0.0;
+  sr[t] = re;
+  si[t] = im;
+  __syncthreads();
+  block_tree_sum(sr, si);
+  const double mbr = sr[0] / k, mbi = si[0] / k;
+  __syncthreads();
+  const double dr = re - mbr, di = im - mbi;
+  sr[t] = t < k ? dr * dr + di * di : 0.0;
+  si[t] = 0.0;
+  __syncthreads();
+  block_tree_sum(sr, si);
+  if (t == 0) {
+    const double na = acc[0], nb = (double)k, n = na + nb;
+    const double er = mbr - acc[1], ei = mbi - acc[2];
+    acc[1] += er * nb / n;
+    acc[2] += ei * nb / n;
+    acc[3] += sr[0] + (er * er + ei * ei) * na * nb / n;
+    acc[0] = n;
+  }
 }
 
 void launch_accumulate(const void *samples, int k, double *acc, cudaStream_t s) {
-  k_accumulate<<<1, 32, 0, s>>>((const cdouble *)samples, k, acc);
+  if (k < 1 || k > 256) throw cuda_error{cudaErrorInvalidValue, "k_accumulate: 1 <= k <= 256"};
+  k_accumulate<<<1, 256, 0, s>>>((const cdouble *)samples, k, acc);
   MLMC_LAUNCH_CHECK("k_accumulate");
 }
 
