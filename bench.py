@@ -679,6 +679,11 @@ def main():
                            "coarse_term": res["coarse_term"].real, "n_samples": res["n_samples"],
                            "iters": res["iters"], "seconds_per_level": res["seconds"]},
                 "fp64_form": fp64, "learned": learned}
+        if fp64 is not None:
+            # the mixed form's trace against the plain FP64 form's on the same samples
+            line["result"]["rel_diff_vs_fp64_form"] = abs(res["trace"].real - fp64["trace"]) / abs(fp64["trace"])
+        if closed_form(w) is not None:
+            line["result"]["rel_err_vs_closed_form"] = abs(res["trace"].real - closed_form(w)) / closed_form(w)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
