@@ -447,6 +447,8 @@ def run_batch(args):
     insts = batch_instances()
     base = WORKLOADS["laplace1024"]
     wb = WORKLOADS["wilson128"]
+    tuned = {}                 # (kind, side) -> block width chosen by the autotuner
+    tuned_lock = threading.Lock()
 
     def one(inst):
         t0 = time.time()
@@ -463,7 +465,17 @@ def run_batch(args):
             h = mlmc.Hierarchy(mlmc.OP_WILSON2D, inst["side"], inst["side"], prm, mass=-0.10, links=U)
             nz = mlmc.NOISE_Z4
         t_setup = time.time() - t0
-        k, _ = h.autotune_block(1, nz, 1e-8)
+        # the autotuner runs once per (operator kind, lattice side); the other instances of
+        # that class reuse its choice
+        key = (inst["kind"], inst["side"])
+        with tuned_lock:
+            k = tuned.get(key)
+        if k is None:
+            k, _ = h.autotune_block(1, nz, 1e-8)
+            with tuned_lock:
+                tuned[key] = k
+        else:
+            h.set_block_width(k)
         t1 = time.time()
         r = mlmc.result_dict(h.trace_estimate(noise=nz, seed=inst["index"], tol=1e-8, allocation=mlmc.ALLOC_FIXED,
                                               n_fixed=inst["n_fixed"]))

@@ -167,8 +167,12 @@ typedef struct {
 
 /* Build the hierarchy on the GPU (Sec. 4.1; Example 5.3): fine operator,
  * test vectors, per-aggregate orthonormalisation, Galerkin coarse operators,
- * smoother blocks, dense inverse of A_L.  `stream` is a cudaStream_t or NULL.
- * On success *out owns the device memory until mlmc_destroy_hierarchy.      */
+ * smoother blocks, dense inverse of A_L.  `stream` is a cudaStream_t or NULL
+ * (NULL: the handle creates and owns a private stream).  On success *out owns
+ * the device memory until mlmc_destroy_hierarchy.  Device buffers are
+ * stream-ordered on that stream (no device-wide synchronisation when a handle
+ * allocates or frees, so handles on different streams run concurrently); a
+ * caller's stream must stay valid until mlmc_destroy_hierarchy returns.     */
 int mlmc_setup_hierarchy(const mlmc_operator_desc *op, const mlmc_hierarchy_params *params,
                          void *stream, mlmc_hierarchy **out);
 void mlmc_destroy_hierarchy(mlmc_hierarchy *h);

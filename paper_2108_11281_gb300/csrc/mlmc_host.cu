@@ -32,33 +32,41 @@ struct mlmc_fail {
 
 [[noreturn]] void fail(int code, const std::string &msg) { throw mlmc_fail{code, msg}; }
 
+// Stream of the current entry point's device allocations (set by need() /
+// need_level() to the hierarchy's stream, or to the call's stream).  Buffers are
+// stream-ordered (cudaMallocAsync / cudaFreeAsync): a hierarchy that allocates or
+// frees does not synchronise the device, so instances on other streams keep running.
+thread_local cudaStream_t g_alloc_stream = nullptr;
+
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
+  cudaStream_t s = nullptr;   // the stream it was allocated on, and is freed on
   DevBuf() = default;
   DevBuf(const DevBuf &) = delete;
   DevBuf &operator=(const DevBuf &) = delete;
-  DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes), s(o.s) { o.p = nullptr; o.bytes = 0; }
   DevBuf &operator=(DevBuf &&o) noexcept {
-    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; s = o.s; o.p = nullptr; o.bytes = 0; }
     return *this;
   }
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
     bytes = 0;
   }
   void alloc(size_t nbytes) {
     release();
     if (nbytes == 0) nbytes = 16;
-    cudaError_t e = cudaMalloc(&p, nbytes);
+    s = g_alloc_stream;
+    cudaError_t e = cudaMallocAsync(&p, nbytes, s);
     if (e == cudaErrorMemoryAllocation) {
       cudaGetLastError();
       p = nullptr;
       fail(MLMC_ERR_OOM, "device allocation of " + std::to_string(nbytes) + " bytes failed");
     }
-    check_cuda(e, "cudaMalloc");
+    check_cuda(e, "cudaMallocAsync");
     bytes = nbytes;
   }
   template <class T> T *as() const { return (T *)p; }
@@ -82,10 +90,7 @@ struct Krylov {
   size_t n = 0;
   int k = 0, m = 0;
   DevBuf V, Z, partials, H, cs, sn, g, y, h2, bnorm, invnrm, resid, active, jdone, nactive;
-  int *h_nactive = nullptr;
-  ~Krylov() {
-    if (h_nactive) cudaFreeHost(h_nactive);
-  }
+  int h_nactive = 0;         // host copy of the active-column count (pageable: the copy waits for it)
 };
 
 struct CycleBufs {
@@ -104,7 +109,17 @@ struct GraphEntry {
 
 }  // namespace
 
+// A private stream, destroyed after every member buffer was freed on it (it is
+// the first member, so the last one destroyed).
+struct OwnedStream {
+  cudaStream_t s = nullptr;
+  ~OwnedStream() {
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
 struct mlmc_hierarchy {
+  OwnedStream own;     // set when the caller passes the legacy stream
   cudaStream_t stream = nullptr;
   int complex_op = 0;
   DType t64 = F64, t32 = F32;
@@ -128,13 +143,11 @@ struct mlmc_hierarchy {
   DevBuf capture;
   size_t capture_blocks = 0, capture_n = 0;
   int capturing = 0;
-  // CUDA graphs of the inner solves; a private stream when the caller passes the legacy stream
+  // CUDA graphs of the inner solves
   std::vector<GraphEntry> graphs;
-  cudaStream_t own_stream = nullptr;
   ~mlmc_hierarchy() {
     for (auto &g : graphs)
       if (g.exec) cudaGraphExecDestroy(g.exec);
-    if (own_stream) cudaStreamDestroy(own_stream);
   }
   std::vector<DevBuf> xs, ys;                     // sample blocks per level (FP64)
   DevBuf dots, dots_part, samples, acc, err, trace;
@@ -203,13 +216,12 @@ void alloc_krylov(H_t &h, Krylov &K, DType t, size_t n, int k, int m) {
   K.active.alloc(k * sizeof(int));
   K.jdone.alloc(k * sizeof(int));
   K.nactive.alloc(sizeof(int));
-  check_cuda(cudaMallocHost(&K.h_nactive, sizeof(int)), "cudaMallocHost");
 }
 
 int read_nactive(H_t &h, Krylov &K) {
-  check_cuda(cudaMemcpyAsync(K.h_nactive, K.nactive.p, sizeof(int), cudaMemcpyDeviceToHost, h.stream), "D2H nactive");
+  check_cuda(cudaMemcpyAsync(&K.h_nactive, K.nactive.p, sizeof(int), cudaMemcpyDeviceToHost, h.stream), "D2H nactive");
   check_cuda(cudaStreamSynchronize(h.stream), "sync");
-  return *K.h_nactive;
+  return K.h_nactive;
 }
 
 // nnz of A_l: Example 5.1 (5n - 2nx - 2ny with Dirichlet), Example 5.3 (9 per row),
@@ -908,10 +920,11 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   if (!stream) {
     // stream capture is not allowed on the legacy default stream: use a private
     // blocking stream (ordered with the legacy stream; every call synchronises it)
-    check_cuda(cudaStreamCreate(&h.own_stream), "stream create");
-    stream = h.own_stream;
+    check_cuda(cudaStreamCreate(&h.own.s), "stream create");
+    stream = h.own.s;
   }
   h.stream = stream;
+  g_alloc_stream = stream;
   h.prm = *p;
   h.complex_op = op->kind == MLMC_OP_WILSON2D;
   h.const_laplace = op->kind == MLMC_OP_LAPLACE2D;
@@ -1123,6 +1136,10 @@ void copy_samples_out(H_t &h, int k, mlmc_c64 *out) {
 }
 
 int translate(const std::function<void()> &fn) {
+  struct AllocReset {
+    AllocReset() { g_alloc_stream = nullptr; }
+    ~AllocReset() { g_alloc_stream = nullptr; }
+  } reset;
   try {
     fn();
     return MLMC_OK;
@@ -1144,10 +1161,12 @@ int translate(const std::function<void()> &fn) {
 
 void need(H_t *h) {
   if (!h) fail(MLMC_ERR_INVALID_ARG, "null hierarchy");
+  g_alloc_stream = h->stream;
 }
 
 void need_level(const H_t *h, int level, int lo, int hi) {
   if (!h) fail(MLMC_ERR_INVALID_ARG, "null hierarchy");
+  g_alloc_stream = h->stream;
   if (level < lo || level > hi) fail(MLMC_ERR_INVALID_ARG, "level out of range");
 }
 
@@ -1168,8 +1187,11 @@ int mlmc_setup_hierarchy(const mlmc_operator_desc *op, const mlmc_hierarchy_para
 
 void mlmc_destroy_hierarchy(mlmc_hierarchy *h) {
   if (!h) return;
-  cudaStreamSynchronize(h->stream);
-  delete h;
+  cudaStream_t s = h->stream;
+  const bool own = h->own.s != nullptr;
+  cudaStreamSynchronize(s);
+  delete h;                              // queues the frees of its buffers on s
+  if (!own) cudaStreamSynchronize(s);    // a caller's stream: the frees are done on return
 }
 
 int mlmc_level_info(const mlmc_hierarchy *h, int level, int *nx, int *ny, int *d) {
@@ -1276,6 +1298,7 @@ int mlmc_column_dots(int complex_data, const void *x, const void *y, int n, int 
   return translate([&] {
     if (!x || !y || !out || n < 1 || k < 1 || k > 256) fail(MLMC_ERR_INVALID_ARG, "bad column-dot arguments (k must be in 1..256)");
     cudaStream_t s = (cudaStream_t)stream;
+    g_alloc_stream = s;
     DType t = complex_data ? C64 : F64;
     int parts = multidot_parts((size_t)n, k);
     DevBuf part;
@@ -1322,6 +1345,7 @@ int mlmc_dense_apply(int complex_data, const void *A, const void *B, void *Y, in
       fail(MLMC_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
     const DType t = complex_data ? C32 : F32;
     cudaStream_t s = (cudaStream_t)stream;
+    g_alloc_stream = s;
     DevBuf part, err;
     err.alloc(sizeof(int));
     check_cuda(cudaMemsetAsync(err.p, 0, sizeof(int), s), "memset err");
