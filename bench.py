@@ -35,7 +35,8 @@ WORKLOADS = {
     "laplace1024": dict(name="laplace2d-1024x1024-L4-4tv-k64", kind="laplace", nx=1024, ny=1024, levels=4, n_tv=4,
                         spin_split=0, setup="smooth", setup_sweeps=160, coarse_sweeps=20, omega=2.0 / 3.0,
                         bootstrap=2, boot_iters=5, smooth_pre=2, smooth_post=2, kcycle_its=2, restart=8,
-                        inner_its=8, block=64, coarse_block=128, noise="rademacher", eps=1e-3, tol_fp64=1e-10,
+                        inner_its=8, block=64, coarse_block=128, coarse_growth=1, noise="rademacher", eps=1e-3,
+                        tol_fp64=1e-10,
                         tol_mixed=1e-8,
                         seed=0, learned=False),
     # the paper's own hierarchy for Example 5.1 (Sec. 5, Table 1): bilinear P, N_{l+1} = (N_l - 1)/2,
@@ -122,7 +123,7 @@ def hierarchy_params(mlmc, precision, w=None):
                                smooth_pre=w["smooth_pre"], smooth_post=w["smooth_post"], cycle=mlmc.CYCLE_K,
                                kcycle_its=w["kcycle_its"], fgmres_restart=w["restart"], max_iter=5000,
                                precision=precision, block=w["block"], reorth=1, inner_its=w["inner_its"],
-                               coarse_block=w.get("coarse_block", 0),
+                               coarse_block=w.get("coarse_block", 0), coarse_growth=w.get("coarse_growth", 0),
                                transfer=(mlmc.TRANSFER_BILINEAR if w.get("transfer") == "bilinear"
                                          else mlmc.TRANSFER_AGGREGATION))
 

@@ -120,6 +120,11 @@ typedef struct {
                           smoothed by 4-colour Gauss-Seidel.  R P != I, so samples and
                           estimates need MLMC_FORM_HAT (or MLMC_FORM_PLAIN); agg_*, n_tv,
                           spin_split, setup_*, bootstrap and user_P are ignored.           */
+  int coarse_growth;   /* > 0: the block width doubles per level difference beyond the second
+                          (coarse_block on difference 2, then 2x, 4x, ... up to 256): coarser
+                          levels are cheaper per column and draw more samples, so wider
+                          blocks amortise their latency-bound launches.  0 = coarse_block
+                          on every difference >= 2.  Samples do not depend on widths.       */
 } mlmc_hierarchy_params;
 
 typedef struct mlmc_hierarchy mlmc_hierarchy;
@@ -207,7 +212,8 @@ int mlmc_noise(int noise, uint64_t seed, int level, int purpose, uint64_t first,
  *   s_j = x_j^* A_l^{-1} x_j - (P_l^* x_j)^* A_{l+1}^{-1} (P_l^* x_j),  x_j = noise(seed, l, j),
  * for 1 <= level < L; level == L gives x^* A_L^{-1} x.  out_samples is host
  * memory of n_samples entries.  out_iters (host, optional) receives the
- * outer iteration count of each block's two solves. */
+ * outer iteration count of each block's two solves (one entry per block of
+ * the level's block width: at most n_samples entries). */
 int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, uint64_t first,
                       int n_samples, double tol, mlmc_c64 *out_samples, int *out_iters);
 

@@ -126,8 +126,17 @@ struct mlmc_hierarchy {
   mlmc_hierarchy_params prm{};
   int L = 0, kmax = 0;
   int kact = 0;        // active vector-block width of estimates and sample calls (<= kmax)
-  int kwide = 0;       // vector-block width of samples drawn on level differences >= 2 (coarse levels)
-  int kbig = 0;        // max(kmax, kwide): sizes of the per-column scratch
+  int kwide = 0;       // vector-block width of samples drawn on level difference 2 (coarse levels)
+  int kgrow = 0;       // > 0: the width doubles per further level difference (up to 256)
+  int kbig = 0;        // the largest block width of any level difference: sizes the per-column scratch
+  std::vector<int> wl; // per level: the widest block its buffers serve
+  // block width of level difference l0 (0-based; l0 = 0 is the fine difference)
+  int kdiff(int l0) const {
+    if (l0 == 0) return kact;
+    long k = kwide;
+    for (int i = 1; i < l0 && kgrow; ++i) k = std::min(2 * k, 256L);
+    return (int)k;
+  }
   std::vector<Level> lv;
   std::vector<CycleBufs> cyc[2];                  // [0] FP64 cycle, [1] FP32 cycle
   std::vector<std::unique_ptr<Krylov>> outer;     // FP64 outer FGMRES per level
@@ -874,7 +883,7 @@ void validate(const mlmc_operator_desc *op, const mlmc_hierarchy_params *p) {
     if (p->inner_its < 0 || p->inner_its > 32) fail(MLMC_ERR_INVALID_ARG, "inner_its must be in 0..32");
     if (p->precision != MLMC_PREC_FP64 && p->precision != MLMC_PREC_MIXED_FP32)
       fail(MLMC_ERR_INVALID_ARG, "unknown precision");
-    if ((double)op->nx * op->ny * std::max(p->block, p->coarse_block) >= 2147483648.0)
+    if ((double)op->nx * op->ny * (p->coarse_growth > 0 ? 256 : std::max(p->block, p->coarse_block)) >= 2147483648.0)
       fail(MLMC_ERR_UNSUPPORTED, "n * block must stay below 2^31 (32-bit kernel indexing)");
     long nx = op->nx, ny = op->ny;
     for (int l = 0; l + 1 < p->levels; ++l) {
@@ -899,7 +908,8 @@ void validate(const mlmc_operator_desc *op, const mlmc_hierarchy_params *p) {
   if (p->inner_its < 0 || p->inner_its > 32) fail(MLMC_ERR_INVALID_ARG, "inner_its must be in 0..32");
   if (p->precision != MLMC_PREC_FP64 && p->precision != MLMC_PREC_MIXED_FP32)
     fail(MLMC_ERR_INVALID_ARG, "unknown precision");
-  if ((double)op->nx * op->ny * (op->kind == MLMC_OP_WILSON2D ? 2 : 1) * std::max(p->block, p->coarse_block) >=
+  if ((double)op->nx * op->ny * (op->kind == MLMC_OP_WILSON2D ? 2 : 1) *
+          (p->coarse_growth > 0 ? 256 : std::max(p->block, p->coarse_block)) >=
       2147483648.0)
     fail(MLMC_ERR_UNSUPPORTED, "n * block must stay below 2^31 (32-bit kernel indexing)");
   long nx = op->nx, ny = op->ny;
@@ -937,7 +947,17 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   h.kmax = p->block;
   h.kact = p->block;
   h.kwide = p->coarse_block > 0 ? p->coarse_block : p->block;
-  h.kbig = std::max(h.kmax, h.kwide);
+  h.kgrow = p->coarse_growth > 0 ? 1 : 0;
+  h.kbig = h.kmax;
+  for (int l0 = 1; l0 + 1 < h.L; ++l0) h.kbig = std::max(h.kbig, h.kdiff(l0));
+  // level l serves the solves of differences l (its fine side) and l - 1 (its coarse side)
+  h.wl.assign(h.L, 0);
+  for (int l = 0; l < h.L; ++l) {
+    int w = l == 0 ? h.kmax : 0;
+    if (l >= 1 && l + 1 < h.L) w = std::max(w, h.kdiff(l));
+    if (l >= 1) w = std::max(w, l - 1 == 0 ? h.kmax : h.kdiff(l - 1));
+    h.wl[l] = w;
+  }
   const bool mixed = p->precision == MLMC_PREC_MIXED_FP32;
   const int dc = p->n_tv * (p->spin_split ? 2 : 1);
   const size_t es = dtype_size(h.t64), es32 = dtype_size(h.t32);
@@ -971,11 +991,11 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
     } else {
       Lv.Ainv64.alloc(Lv.n * Lv.n * es);
       size_t most = 0;     // the split count depends on the column count of a call
-      for (int kk = 1; kk <= std::max(std::max(p->block, p->coarse_block), p->n_tv); ++kk)
+      for (int kk = 1; kk <= std::max(h.kbig, p->n_tv); ++kk)
         most = std::max(most, (size_t)dense_apply_splits((int)Lv.n, kk) * kk);
       size_t part_bytes = most * Lv.n * es;
       if (mixed)
-        for (int kk = 1; kk <= std::max(std::max(p->block, p->coarse_block), p->n_tv); ++kk)
+        for (int kk = 1; kk <= std::max(h.kbig, p->n_tv); ++kk)
           part_bytes = std::max(part_bytes, dense_apply_tc_part_bytes(dtype_lower(h.t64), (int)Lv.n, kk));
       Lv.dense_part.alloc(part_bytes);
       if (mixed) Lv.Ainv32.alloc(Lv.n * Lv.n * es32);
@@ -987,7 +1007,7 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   // Level 0 holds blocks of `block` columns; levels >= 1 also serve the wider
   // coarse-level samples (`coarse_block` columns).
   const int k = h.kmax;
-  auto width = [&](int l) { return l == 0 ? h.kmax : h.kbig; };
+  auto width = [&](int l) { return h.wl[l]; };
   for (int lo = 0; lo < (mixed ? 2 : 1); ++lo) {
     DType t = lo ? h.t32 : h.t64;
     h.cyc[lo].resize(h.L);
@@ -1279,7 +1299,7 @@ int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, ui
     if (h->bilinear && level < h->L)
       fail(MLMC_ERR_INVALID_ARG, "the simplified form needs R P = I; use the hat form with a bilinear hierarchy");
     bool all_conv = true;
-    const int kl = level == 1 ? h->kact : h->kwide;
+    const int kl = h->kdiff(std::min(level - 1, h->L - 2));   // level L: the coarsest buffers' width
     for (int done = 0, b = 0; done < n_samples; ++b) {
       int k = std::min(kl, n_samples - done);
       bool conv = true;
@@ -1321,7 +1341,7 @@ int mlmc_sample_level_form(mlmc_hierarchy *h, int level, int form, int noise, ui
     if (noise == MLMC_NOISE_Z4 && !h->complex_op) fail(MLMC_ERR_INVALID_ARG, "Z4 noise needs a complex operator");
     if (!(tol > 0.0)) fail(MLMC_ERR_INVALID_ARG, "tol must be positive");
     bool all_conv = true;
-    const int kl = level == 1 ? h->kact : h->kwide;
+    const int kl = h->kdiff(std::min(level - 1, h->L - 2));   // level L: the coarsest buffers' width
     for (int done = 0; done < n_samples;) {
       int k = std::min(kl, n_samples - done);
       bool conv = true;
@@ -1440,7 +1460,7 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
     std::vector<mlmc_c64> tmp(std::max(5, H.kbig));
     double warm[5];
     for (int i = 0; i < 5; ++i) warm[i] = TL.re;
-    auto width = [&](int l) { return l == 0 ? H.kact : H.kwide; };
+    auto width = [&](int l) { return H.kdiff(l); };
     // one block of samples on level difference l; samples 0..4 also enter the five
     // full estimates that define tau
     auto draw = [&](int l) {
@@ -1560,7 +1580,7 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
   return translate([&] {
     need_level(h, level, 1, h ? h->L : 0);
     // level 1 holds blocks of `block` columns, the coarser levels also the coarse-level blocks
-    if (k < 1 || k > (level > 1 ? h->kbig : h->kmax) || reps < 1) fail(MLMC_ERR_INVALID_ARG, "bad k or reps");
+    if (k < 1 || k > h->wl[level - 1] || reps < 1) fail(MLMC_ERR_INVALID_ARG, "bad k or reps");
     H_t &H = *h;
     int l = level - 1;
     int lo = which == 0 ? 0 : (H.prm.precision == MLMC_PREC_MIXED_FP32 ? 1 : 0);

@@ -47,7 +47,8 @@ class HierarchyParams(ctypes.Structure):
                 ("kcycle_its", ctypes.c_int), ("fgmres_restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("block", ctypes.c_int), ("reorth", ctypes.c_int),
                 ("inner_its", ctypes.c_int), ("graphs", ctypes.c_int), ("coarse_smooth", ctypes.c_int),
-                ("coarse_block", ctypes.c_int), ("user_P", ctypes.c_void_p), ("transfer", ctypes.c_int)]
+                ("coarse_block", ctypes.c_int), ("user_P", ctypes.c_void_p), ("transfer", ctypes.c_int),
+                ("coarse_growth", ctypes.c_int)]
 
 
 class EstimateParams(ctypes.Structure):
@@ -148,7 +149,7 @@ def default_params(**kw):
                         bootstrap=1, boot_iters=2, smooth_pre=1, smooth_post=1, cycle=CYCLE_K,
                         kcycle_its=2, fgmres_restart=30, max_iter=2000, precision=PREC_FP64, block=64,
                         reorth=1, inner_its=0, graphs=1, coarse_smooth=0, coarse_block=0, user_P=None,
-                        transfer=TRANSFER_AGGREGATION)
+                        transfer=TRANSFER_AGGREGATION, coarse_growth=0)
     for k, v in kw.items():
         if not hasattr(p, k):
             raise KeyError(k)
@@ -235,12 +236,12 @@ class Hierarchy:
 
     def sample_level(self, level, noise, seed, first, n_samples, tol):
         out = (C64 * max(n_samples, 1))()
-        width = self.params.block if level == 1 or self.params.coarse_block <= 0 else self.params.coarse_block
-        nblk = (n_samples + width - 1) // width
-        its = (ctypes.c_int * max(nblk, 1))()
+        # one iteration count per block; a block holds at least one sample, and the
+        # library's block width (block, coarse_block, the active width, growth) decides
+        its = (ctypes.c_int * max(n_samples, 1))(*([-1] * max(n_samples, 1)))
         check(lib.mlmc_sample_level(self.handle, level, noise, seed, first, n_samples, tol, out, its))
         vals = np.array([complex(out[i].re, out[i].im) for i in range(n_samples)])
-        return vals, list(its)[:nblk]
+        return vals, [v for v in its if v >= 0]
 
     def sample_level_form(self, level, form, noise, seed, first, n_samples, tol):
         out = (C64 * max(n_samples, 1))()

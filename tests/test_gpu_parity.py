@@ -355,3 +355,27 @@ def test_hat_and_plain_forms(mlmc):
         assert r["n_samples"] == ref.n_samples, name
         assert abs(r["trace"] - ref.trace) <= 1e-9 * abs(ref.trace), name
     h.close()
+
+
+def test_block_width_growth_keeps_samples(mlmc):
+    """Wider blocks on the coarse level differences (coarse_growth) change only the
+    batching: samples are indexed (seed, level, j), so the same samples come back, the
+    per-block iteration list has one entry per block, and an estimate with a fixed budget
+    has the same mean."""
+    N = 64
+    kw = dict(n_tv=4, setup_sweeps=20, coarse_sweeps=10, block=4, coarse_block=8, bootstrap=0)
+    h0 = laplace_h(mlmc, N, 4, **kw)
+    h1 = laplace_h(mlmc, N, 4, coarse_growth=1, **kw)
+    for level, width in ((2, 8), (3, 16)):
+        s0, it0 = h0.sample_level(level, mlmc.NOISE_RADEMACHER, 1, 0, 40, 1e-12)
+        s1, it1 = h1.sample_level(level, mlmc.NOISE_RADEMACHER, 1, 0, 40, 1e-12)
+        assert np.abs(s0 - s1).max() <= 1e-9 * np.abs(s0).max()
+        assert len(it0) == 5 and len(it1) == (40 + width - 1) // width
+    r0 = mlmc.result_dict(h0.trace_estimate(noise=mlmc.NOISE_RADEMACHER, seed=2, tol=1e-12,
+                                            allocation=mlmc.ALLOC_FIXED, n_fixed=[16, 16, 32]))
+    r1 = mlmc.result_dict(h1.trace_estimate(noise=mlmc.NOISE_RADEMACHER, seed=2, tol=1e-12,
+                                            allocation=mlmc.ALLOC_FIXED, n_fixed=[16, 16, 32]))
+    assert r0["n_samples"] == r1["n_samples"] == [16, 16, 32]
+    assert abs(r0["trace"] - r1["trace"]) <= 1e-9 * abs(r0["trace"])
+    h0.close()
+    h1.close()
