@@ -20,9 +20,11 @@ template <> __device__ inline cdouble hdiv<cdouble>(cdouble a, cdouble b) {
 }
 template <class H> __device__ inline H hreal(double v) { return make<H>(v, 0.0); }
 
+// sc (optional): norms s_i of the unnormalised basis vectors of the fixed-length
+// variant (see k_lazy_coef); s_0 = |b|.
 template <class H>
 __global__ void k_arnoldi_init(H *g, double *bnorm, double *invnrm, int *active, int *jdone, int k,
-                               double tol, int first, int *nactive) {
+                               double tol, int first, int *nactive, double *sc) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= k) return;
   double beta = sqrt(fmax(creal_(g[c]), 0.0));
@@ -32,25 +34,57 @@ __global__ void k_arnoldi_init(H *g, double *bnorm, double *invnrm, int *active,
   int a = beta > 0.0 && beta > tol * bnorm[c];
   active[c] = a;
   invnrm[c] = a ? 1.0 / beta : 0.0;
+  if (sc) sc[c] = beta > 0.0 ? beta : 1.0;
   if (a) atomicAdd(nactive, 1);
+}
+
+// Fixed-length FGMRES with unnormalised basis vectors u_i = s_i v_i (the scaling pass
+// over each new basis vector is skipped; the cycle and the operator are linear, so
+// z_j and w scale along).  With d_i = u_i^* w for w = A z_j (z_j from u_j):
+//   Gram-Schmidt coefficient of u_i:  d_i / s_i^2,   Hessenberg entry:  d_i / (s_i s_j).
+template <class H>
+__global__ void k_lazy_coef(H *hcol, const double *sc, H *coef, int j, int k) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (j + 1) * k) return;
+  const int i = t / k, c = t - (t / k) * k;
+  const double si = sc[(size_t)i * k + c], sj = sc[(size_t)j * k + c];
+  const H d = hcol[t];
+  coef[t] = d * hreal<H>(1.0 / (si * si));
+  hcol[t] = d * hreal<H>(1.0 / (si * sj));
+}
+
+// y_i /= s_i for the computed rows: x = sum_i z_i y_i with z_i built from u_i.
+template <class H>
+__global__ void k_lazy_y(H *y, const double *sc, const int *jdone, int m, int k) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * k) return;
+  const int i = t / k, c = t - (t / k) * k;
+  if (i < jdone[c]) y[t] = y[t] * hreal<H>(1.0 / sc[t]);
 }
 
 // Hessenberg column j of column c lives at H[(j*(m+1) + i)*k + c], i = 0..j+1.
 // On entry H[j][j+1] holds |w|^2 from a column dot.
+// sc (optional, the unnormalised variant): the new basis vector keeps its norm,
+// s_{j+1} = |u_{j+1}|, and the Hessenberg entry is |u_{j+1}| / s_j.
 template <class H>
 __global__ void k_arnoldi_step(H *Hm, H *cs, H *sn, H *g, int j, int m, int k, int *active, int *jdone,
                                const double *bnorm, double tol, double *invnrm, double *resid, int *nactive,
-                               int fixed) {
+                               int fixed, double *sc) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= k) return;
   H *h = Hm + (size_t)j * (m + 1) * k + c;
   if (!active[c]) {
     invnrm[c] = 0.0;
+    if (sc) sc[(size_t)(j + 1) * k + c] = 1.0;   // its vectors are zero: any finite scale
     return;
   }
   double nrm = sqrt(fmax(creal_(h[(size_t)(j + 1) * k]), 0.0));
-  h[(size_t)(j + 1) * k] = hreal<H>(nrm);
   invnrm[c] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  if (sc) {
+    sc[(size_t)(j + 1) * k + c] = nrm > 0.0 ? nrm : 1.0;
+    nrm = nrm / sc[(size_t)j * k + c];
+  }
+  h[(size_t)(j + 1) * k] = hreal<H>(nrm);
   for (int i = 0; i < j; ++i) {
     H a = h[(size_t)i * k], b = h[(size_t)(i + 1) * k];
     H ci = cs[(size_t)i * k + c], si = sn[(size_t)i * k + c];
@@ -110,21 +144,36 @@ __global__ void k_add_acc(H *dst, const H *src, int count) {
 }
 
 void launch_arnoldi_init(int hc, void *g, double *bnorm, double *invnrm, int *active, int *jdone, int k,
-                         double tol, int first, int *nactive, cudaStream_t s) {
+                         double tol, int first, int *nactive, cudaStream_t s, double *sc) {
   unsigned gr = (k + 63) / 64;
-  if (hc) k_arnoldi_init<cdouble><<<gr, 64, 0, s>>>((cdouble *)g, bnorm, invnrm, active, jdone, k, tol, first, nactive);
-  else k_arnoldi_init<double><<<gr, 64, 0, s>>>((double *)g, bnorm, invnrm, active, jdone, k, tol, first, nactive);
+  if (hc) k_arnoldi_init<cdouble><<<gr, 64, 0, s>>>((cdouble *)g, bnorm, invnrm, active, jdone, k, tol, first, nactive,
+                                                     sc);
+  else k_arnoldi_init<double><<<gr, 64, 0, s>>>((double *)g, bnorm, invnrm, active, jdone, k, tol, first, nactive, sc);
   MLMC_LAUNCH_CHECK("k_arnoldi_init");
+}
+
+void launch_lazy_coef(int hc, void *hcol, const double *sc, void *coef, int j, int k, cudaStream_t s) {
+  unsigned gr = ((j + 1) * k + 127) / 128;
+  if (hc) k_lazy_coef<cdouble><<<gr, 128, 0, s>>>((cdouble *)hcol, sc, (cdouble *)coef, j, k);
+  else k_lazy_coef<double><<<gr, 128, 0, s>>>((double *)hcol, sc, (double *)coef, j, k);
+  MLMC_LAUNCH_CHECK("k_lazy_coef");
+}
+
+void launch_lazy_y(int hc, void *y, const double *sc, const int *jdone, int m, int k, cudaStream_t s) {
+  unsigned gr = (m * k + 127) / 128;
+  if (hc) k_lazy_y<cdouble><<<gr, 128, 0, s>>>((cdouble *)y, sc, jdone, m, k);
+  else k_lazy_y<double><<<gr, 128, 0, s>>>((double *)y, sc, jdone, m, k);
+  MLMC_LAUNCH_CHECK("k_lazy_y");
 }
 
 void launch_arnoldi_step(int hc, void *H, void *cs, void *sn, void *g, int j, int m, int k, int *active,
                          int *jdone, const double *bnorm, double tol, double *invnrm, double *resid,
-                         int *nactive, int fixed, cudaStream_t s) {
+                         int *nactive, int fixed, cudaStream_t s, double *sc) {
   unsigned gr = (k + 63) / 64;
   if (hc) k_arnoldi_step<cdouble><<<gr, 64, 0, s>>>((cdouble *)H, (cdouble *)cs, (cdouble *)sn, (cdouble *)g, j, m, k,
-                                                     active, jdone, bnorm, tol, invnrm, resid, nactive, fixed);
+                                                     active, jdone, bnorm, tol, invnrm, resid, nactive, fixed, sc);
   else k_arnoldi_step<double><<<gr, 64, 0, s>>>((double *)H, (double *)cs, (double *)sn, (double *)g, j, m, k,
-                                                 active, jdone, bnorm, tol, invnrm, resid, nactive, fixed);
+                                                 active, jdone, bnorm, tol, invnrm, resid, nactive, fixed, sc);
   MLMC_LAUNCH_CHECK("k_arnoldi_step");
 }
 

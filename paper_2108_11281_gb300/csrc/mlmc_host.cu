@@ -90,6 +90,7 @@ struct Krylov {
   size_t n = 0;
   int k = 0, m = 0;
   DevBuf V, Z, partials, H, cs, sn, g, y, h2, bnorm, invnrm, resid, active, jdone, nactive;
+  DevBuf sc, hco;           // fixed-length variant: basis-vector norms, Gram-Schmidt coefficients
   int h_nactive = 0;         // host copy of the active-column count (pageable: the copy waits for it)
 };
 
@@ -225,6 +226,8 @@ void alloc_krylov(H_t &h, Krylov &K, DType t, size_t n, int k, int m) {
   K.active.alloc(k * sizeof(int));
   K.jdone.alloc(k * sizeof(int));
   K.nactive.alloc(sizeof(int));
+  K.sc.alloc((size_t)(m + 1) * k * sizeof(double));
+  K.hco.alloc((size_t)(m + 1) * k * as);
 }
 
 int read_nactive(H_t &h, Krylov &K) {
@@ -299,27 +302,38 @@ int fgmres(H_t &h, Krylov &K, int l, int lo, const void *b, void *x, int k, doub
   auto Zj = [&](int j) { return (char *)K.Z.p + (size_t)j * blk * es; };
   auto Hcol = [&](int j) { return (char *)K.H.p + (size_t)j * (m + 1) * k * as; };
   const bool fixed = fixed_its > 0;
+  // fixed length (inner solves, K-cycle): the basis vectors stay unnormalised (no
+  // scaling pass over each new vector; see k_lazy_coef)
+  const bool lazy = fixed && !reorth;
+  double *sc = lazy ? K.sc.as<double>() : nullptr;
   cudaStream_t s = h.stream;
 
   check_cuda(cudaMemcpyAsync(Vj(0), b, blk * es, cudaMemcpyDeviceToDevice, s), "copy b");
   multidot(h, K, Vj(0), 1, Vj(0), k, K.g.p);
   check_cuda(cudaMemsetAsync(K.nactive.p, 0, sizeof(int), s), "memset");
   launch_arnoldi_init(K.hc, K.g.p, K.bnorm.as<double>(), K.invnrm.as<double>(), K.active.as<int>(),
-                      K.jdone.as<int>(), k, fixed ? 0.0 : tol, 1, K.nactive.as<int>(), s);
+                      K.jdone.as<int>(), k, fixed ? 0.0 : tol, 1, K.nactive.as<int>(), s, sc);
   h.launches++;
   check_cuda(cudaMemsetAsync(x, 0, blk * es, s), "memset x");
   if (converged) *converged = true;
   if (!fixed && read_nactive(h, K) == 0) return 0;
   int its = 0;
   for (;;) {
-    launch_scale_cols(K.t, Vj(0), Vj(0), K.invnrm.p, 0, K.n, k, s);
-    h.launches++;
+    if (!lazy) {
+      launch_scale_cols(K.t, Vj(0), Vj(0), K.invnrm.p, 0, K.n, k, s);
+      h.launches++;
+    }
     int jlast = 0;
     for (int j = 0; j < m; ++j) {
       M(Vj(j), Zj(j));
       apply_op(h, l, lo, Zj(j), Vj(j + 1), k);
       multidot(h, K, K.V.p, j + 1, Vj(j + 1), k, Hcol(j));
-      launch_multiaxpy(K.t, Vj(j + 1), K.V.p, blk, j + 1, Hcol(j), K.hc ? C64 : F64, k, -1.0, K.n, k, s);
+      if (lazy) {
+        launch_lazy_coef(K.hc, Hcol(j), sc, K.hco.p, j, k, s);
+        h.launches++;
+      }
+      launch_multiaxpy(K.t, Vj(j + 1), K.V.p, blk, j + 1, lazy ? K.hco.p : Hcol(j), K.hc ? C64 : F64, k, -1.0, K.n,
+                       k, s);
       h.launches++;
       if (reorth) {
         multidot(h, K, K.V.p, j + 1, Vj(j + 1), k, K.h2.p);
@@ -331,9 +345,12 @@ int fgmres(H_t &h, Krylov &K, int l, int lo, const void *b, void *x, int k, doub
       check_cuda(cudaMemsetAsync(K.nactive.p, 0, sizeof(int), s), "memset");
       launch_arnoldi_step(K.hc, K.H.p, K.cs.p, K.sn.p, K.g.p, j, m, k, K.active.as<int>(), K.jdone.as<int>(),
                           K.bnorm.as<double>(), tol, K.invnrm.as<double>(), K.resid.as<double>(),
-                          K.nactive.as<int>(), fixed ? 1 : 0, s);
-      launch_scale_cols(K.t, Vj(j + 1), Vj(j + 1), K.invnrm.p, 0, K.n, k, s);
-      h.launches += 2;
+                          K.nactive.as<int>(), fixed ? 1 : 0, s, sc);
+      h.launches++;
+      if (!lazy) {
+        launch_scale_cols(K.t, Vj(j + 1), Vj(j + 1), K.invnrm.p, 0, K.n, k, s);
+        h.launches++;
+      }
       ++its;
       jlast = j + 1;
       if (fixed) {
@@ -343,6 +360,10 @@ int fgmres(H_t &h, Krylov &K, int l, int lo, const void *b, void *x, int k, doub
       if (read_nactive(h, K) == 0 || its >= maxit) break;
     }
     launch_trisolve(K.hc, K.H.p, K.g.p, K.y.p, K.jdone.as<int>(), m, k, s);
+    if (lazy) {
+      launch_lazy_y(K.hc, K.y.p, sc, K.jdone.as<int>(), m, k, s);
+      h.launches++;
+    }
     launch_multiaxpy(K.t, x, K.Z.p, blk, jlast, K.y.p, K.hc ? C64 : F64, k, 1.0, K.n, k, s);
     h.launches += 2;
     if (fixed) return its;

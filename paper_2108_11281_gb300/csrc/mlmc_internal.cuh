@@ -212,11 +212,17 @@ void launch_dense_apply_tc(DType t, const void *Ainv, const void *B, void *Y, in
 namespace mlmc {
 // per-column Krylov kernels (kernels_krylov.cu).  `hc` = 1 for complex Hessenberg data.
 // g0[c] holds |r|^2 on entry (from a column dot); sets beta, active, invnrm.
+// sc (optional): per-column norms of the unnormalised basis vectors of the
+// fixed-length FGMRES (s_0 = |b| here; s_{j+1} set by the step)
 void launch_arnoldi_init(int hc, void *g, double *bnorm, double *invnrm, int *active, int *jdone,
-                         int k, double tol, int first, int *nactive, cudaStream_t s);
+                         int k, double tol, int first, int *nactive, cudaStream_t s, double *sc = nullptr);
+// unnormalised basis: Gram-Schmidt coefficients d_i / s_i^2 into coef, Hessenberg
+// entries d_i / (s_i s_j) in place; and y_i /= s_i before the solution update
+void launch_lazy_coef(int hc, void *hcol, const double *sc, void *coef, int j, int k, cudaStream_t s);
+void launch_lazy_y(int hc, void *y, const double *sc, const int *jdone, int m, int k, cudaStream_t s);
 void launch_arnoldi_step(int hc, void *H, void *cs, void *sn, void *g, int j, int m, int k, int *active,
                          int *jdone, const double *bnorm, double tol, double *invnrm, double *resid,
-                         int *nactive, int fixed, cudaStream_t s);
+                         int *nactive, int fixed, cudaStream_t s, double *sc = nullptr);
 void launch_trisolve(int hc, const void *H, const void *g, void *y, const int *jdone, int m, int k,
                      cudaStream_t s);
 void launch_add_acc(int hc, void *dst, const void *src, int count, cudaStream_t s);
