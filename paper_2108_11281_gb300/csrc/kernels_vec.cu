@@ -283,11 +283,26 @@ void launch_multidot(DType t, const void *V, size_t vstride, int nvec, const voi
 // the coefficients in registers and 8-byte packs.)
 static const int AXPY_SMEM = 32 * 1024;
 
+__device__ inline float norm2_l(float a) { return a * a; }
+__device__ inline double norm2_l(double a) { return a * a; }
+__device__ inline float norm2_l(cfloat a) { return a.re * a.re + a.im * a.im; }
+__device__ inline double norm2_l(cdouble a) { return a.re * a.re + a.im * a.im; }
+
+// norm_part (optional): per block and column, sum over its rows of |w_new|^2 (the
+// column norms of the result, for the Arnoldi step), summed per thread in row order
+// and over the block's threads in thread order (deterministic), stored as the FP64
+// accumulation type; k_multidot_reduce adds the blocks up.
 template <class T, class H, int VEC>
 __global__ void __launch_bounds__(256) k_multiaxpy(T *__restrict__ w, const T *__restrict__ V, size_t vstride, int nvec,
                                                    const H *__restrict__ h, size_t hstride, double sign, size_t total, int k,
-                                                   int group) {
+                                                   int group, typename acc_of<T>::type *__restrict__ norm_part) {
   typedef DPack<T, VEC> P;
+  typedef typename real_of<T>::type R;
+  typedef typename acc_of<T>::type A;
+  __shared__ double red[256 * VEC];
+  R sq[VEC];
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) sq[u] = R(0);
   extern __shared__ __align__(16) unsigned char axpy_smem[];
   T *hs = (T *)axpy_smem;
   const size_t stride = (size_t)gridDim.x * blockDim.x;       // in packs; a multiple of k / VEC
@@ -304,6 +319,7 @@ __global__ void __launch_bounds__(256) k_multiaxpy(T *__restrict__ w, const T *_
     for (int e = threadIdx.x; e < nv * k; e += blockDim.x)
       hs[e] = cvt<T, H>(rmul(sign, h[(size_t)(v0 + e / k) * hstride + e % k]));
     __syncthreads();
+    const bool last = v0 + nv >= nvec;
     for (size_t i = t0; i < totv; i += stride) {
       P acc = W[i];
       for (int v = 0; v < nv; ++v) {
@@ -313,6 +329,27 @@ __global__ void __launch_bounds__(256) k_multiaxpy(T *__restrict__ w, const T *_
         for (int u = 0; u < VEC; ++u) acc.v[u] = acc.v[u] + x.v[u] * hh.v[u];
       }
       W[i] = acc;
+      if (norm_part && last) {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) sq[u] += norm2_l(acc.v[u]);
+      }
+    }
+  }
+  if (norm_part) {
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) red[threadIdx.x * VEC + u] = (double)sq[u];
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+      const int cvv = c / VEC, u = c - (c / VEC) * VEC;
+      double sum = 0.0;
+      if ((int)blockDim.x % kv == 0) {
+        // the block starts on a column-group boundary: its threads of group cvv are cvv + j kv
+        for (int t = cvv; t < (int)blockDim.x; t += kv) sum += red[t * VEC + u];
+      } else {
+        for (int t = 0; t < (int)blockDim.x; ++t)
+          if ((int)((blockIdx.x * blockDim.x + t) % kv) == cvv) sum += red[t * VEC + u];
+      }
+      norm_part[(size_t)blockIdx.x * k + c] = make<A>(sum, 0.0);
     }
   }
 }
@@ -330,8 +367,9 @@ static unsigned column_grid(size_t total, int k) {
 }
 
 template <class T, class H>
-static void multiaxpy_go(void *w, const void *V, size_t vstride, int nvec, const void *h, size_t hstride, double sign,
-                         size_t total, int k, cudaStream_t s) {
+static unsigned multiaxpy_go(void *w, const void *V, size_t vstride, int nvec, const void *h, size_t hstride,
+                             double sign, size_t total, int k, void *norm_part, cudaStream_t s) {
+  typedef typename acc_of<T>::type A;
   constexpr int VW = 16 / (int)sizeof(T) > 0 ? 16 / (int)sizeof(T) : 1;      // 16-byte packs
   int group = AXPY_SMEM / (k * (int)sizeof(T));
   if (group < 1) group = 1;
@@ -340,26 +378,47 @@ static void multiaxpy_go(void *w, const void *V, size_t vstride, int nvec, const
   if (VW > 1 && k % VW == 0 && vstride % VW == 0) {
     unsigned g = column_grid(total / VW, k / VW);
     k_multiaxpy<T, H, VW><<<g, 256, smem, s>>>((T *)w, (const T *)V, vstride, nvec, (const H *)h, hstride, sign, total,
-                                               k, group);
-  } else {
-    unsigned g = column_grid(total, k);
-    k_multiaxpy<T, H, 1><<<g, 256, smem, s>>>((T *)w, (const T *)V, vstride, nvec, (const H *)h, hstride, sign, total,
-                                              k, group);
+                                               k, group, (A *)norm_part);
+    return g;
   }
+  unsigned g = column_grid(total, k);
+  k_multiaxpy<T, H, 1><<<g, 256, smem, s>>>((T *)w, (const T *)V, vstride, nvec, (const H *)h, hstride, sign, total,
+                                            k, group, (A *)norm_part);
+  return g;
 }
 
-void launch_multiaxpy(DType t, void *w, const void *V, size_t vstride, int nvec, const void *h,
-                      DType h_t, size_t hstride, double sign, size_t rows, int k, cudaStream_t s) {
+int launch_multiaxpy(DType t, void *w, const void *V, size_t vstride, int nvec, const void *h,
+                     DType h_t, size_t hstride, double sign, size_t rows, int k, cudaStream_t s, void *norm_part) {
   size_t total = rows * (size_t)k;
   (void)h_t;
-  if (nvec <= 0) return;
+  if (nvec <= 0) return 0;
+  unsigned g = 0;
   switch (t) {
-    case F64: multiaxpy_go<double, double>(w, V, vstride, nvec, h, hstride, sign, total, k, s); break;
-    case F32: multiaxpy_go<float, double>(w, V, vstride, nvec, h, hstride, sign, total, k, s); break;
-    case C64: multiaxpy_go<cdouble, cdouble>(w, V, vstride, nvec, h, hstride, sign, total, k, s); break;
-    case C32: multiaxpy_go<cfloat, cdouble>(w, V, vstride, nvec, h, hstride, sign, total, k, s); break;
+    case F64: g = multiaxpy_go<double, double>(w, V, vstride, nvec, h, hstride, sign, total, k, norm_part, s); break;
+    case F32: g = multiaxpy_go<float, double>(w, V, vstride, nvec, h, hstride, sign, total, k, norm_part, s); break;
+    case C64: g = multiaxpy_go<cdouble, cdouble>(w, V, vstride, nvec, h, hstride, sign, total, k, norm_part, s); break;
+    case C32: g = multiaxpy_go<cfloat, cdouble>(w, V, vstride, nvec, h, hstride, sign, total, k, norm_part, s); break;
   }
   MLMC_LAUNCH_CHECK("k_multiaxpy");
+  return (int)g;
+}
+
+int multiaxpy_norm_parts(size_t rows, int k) {
+  // the largest grid multiaxpy_go can choose: column_grid caps at 152 * 8 blocks, then
+  // rounds up to a multiple of k / gcd(k, 256)
+  (void)rows;
+  return 152 * 8 + k;
+}
+
+void launch_column_reduce(DType out_t, const void *partial, int nparts, int k, void *out, cudaStream_t s) {
+  const int tot = k;
+  if (out_t == C64)
+    k_multidot_reduce<cdouble><<<(tot * 32 + 255) / 256, 256, 0, s>>>((const cdouble *)partial, nparts, 1, k,
+                                                                        (cdouble *)out);
+  else
+    k_multidot_reduce<double><<<(tot * 32 + 255) / 256, 256, 0, s>>>((const double *)partial, nparts, 1, k,
+                                                                       (double *)out);
+  MLMC_LAUNCH_CHECK("k_multidot_reduce");
 }
 
 // ------------------------------------------------------------------ column scaling

@@ -213,7 +213,8 @@ void alloc_krylov(H_t &h, Krylov &K, DType t, size_t n, int k, int m) {
   size_t as = acc_size(h);
   K.V.alloc(blk * (m + 1));
   K.Z.alloc(blk * m);
-  K.partials.alloc((size_t)multidot_parts(n, k) * (m + 1) * k * as);
+  // multi-dot partials of up to m + 1 vectors, or the multi-AXPY's fused column norms
+  K.partials.alloc(std::max((size_t)multidot_parts(n, k) * (m + 1), (size_t)multiaxpy_norm_parts(n, k)) * k * as);
   K.H.alloc((size_t)m * (m + 1) * k * as);
   K.cs.alloc((size_t)m * k * as);
   K.sn.alloc((size_t)m * k * as);
@@ -332,8 +333,9 @@ int fgmres(H_t &h, Krylov &K, int l, int lo, const void *b, void *x, int k, doub
         launch_lazy_coef(K.hc, Hcol(j), sc, K.hco.p, j, k, s);
         h.launches++;
       }
-      launch_multiaxpy(K.t, Vj(j + 1), K.V.p, blk, j + 1, lazy ? K.hco.p : Hcol(j), K.hc ? C64 : F64, k, -1.0, K.n,
-                       k, s);
+      // fixed length: the multi-AXPY also sums |u_{j+1}|^2 per column (no separate norm pass)
+      const int nparts = launch_multiaxpy(K.t, Vj(j + 1), K.V.p, blk, j + 1, lazy ? K.hco.p : Hcol(j),
+                                          K.hc ? C64 : F64, k, -1.0, K.n, k, s, lazy ? K.partials.p : nullptr);
       h.launches++;
       if (reorth) {
         multidot(h, K, K.V.p, j + 1, Vj(j + 1), k, K.h2.p);
@@ -341,7 +343,12 @@ int fgmres(H_t &h, Krylov &K, int l, int lo, const void *b, void *x, int k, doub
         launch_add_acc(K.hc, Hcol(j), K.h2.p, (j + 1) * k, s);
         h.launches += 2;
       }
-      multidot(h, K, Vj(j + 1), 1, Vj(j + 1), k, (char *)Hcol(j) + (size_t)(j + 1) * k * as);
+      if (lazy) {
+        launch_column_reduce(K.hc ? C64 : F64, K.partials.p, nparts, k, (char *)Hcol(j) + (size_t)(j + 1) * k * as, s);
+        h.launches++;
+      } else {
+        multidot(h, K, Vj(j + 1), 1, Vj(j + 1), k, (char *)Hcol(j) + (size_t)(j + 1) * k * as);
+      }
       check_cuda(cudaMemsetAsync(K.nactive.p, 0, sizeof(int), s), "memset");
       launch_arnoldi_step(K.hc, K.H.p, K.cs.p, K.sn.p, K.g.p, j, m, k, K.active.as<int>(), K.jdone.as<int>(),
                           K.bnorm.as<double>(), tol, K.invnrm.as<double>(), K.resid.as<double>(),

@@ -152,8 +152,15 @@ void launch_scale_cols(DType t, void *y, const void *x, const void *alpha, int a
 void launch_multidot(DType t, const void *V, size_t vstride, int nvec, const void *w, size_t rows,
                      int k, void *partials, int nparts, void *out, DType out_t, cudaStream_t s);
 // w[i][c] -= sum_v V_v[i][c] * h[v][c]  (h in out precision), optional column mask
-void launch_multiaxpy(DType t, void *w, const void *V, size_t vstride, int nvec, const void *h,
-                      DType h_t, size_t hstride, double sign, size_t rows, int k, cudaStream_t s);
+// norm_part (optional): per-block column sums of |w_new|^2 in the FP64 accumulation
+// type (multiaxpy_norm_parts(rows, k) x k entries at most); returns the block count
+// to pass to launch_column_reduce.
+int launch_multiaxpy(DType t, void *w, const void *V, size_t vstride, int nvec, const void *h,
+                     DType h_t, size_t hstride, double sign, size_t rows, int k, cudaStream_t s,
+                     void *norm_part = nullptr);
+int multiaxpy_norm_parts(size_t rows, int k);
+// out[c] = sum_p partial[p][c] (fixed order), FP64 or complex FP64
+void launch_column_reduce(DType out_t, const void *partial, int nparts, int k, void *out, cudaStream_t s);
 int multidot_parts(size_t rows, int k);
 
 }  // namespace mlmc
