@@ -124,6 +124,7 @@ def hierarchy_params(mlmc, precision, w=None):
                                kcycle_its=w["kcycle_its"], fgmres_restart=w["restart"], max_iter=5000,
                                precision=precision, block=w["block"], reorth=1, inner_its=w["inner_its"],
                                coarse_block=w.get("coarse_block", 0), coarse_growth=w.get("coarse_growth", 0),
+                               coarse_smooth=w.get("coarse_smooth", 0),
                                transfer=(mlmc.TRANSFER_BILINEAR if w.get("transfer") == "bilinear"
                                          else mlmc.TRANSFER_AGGREGATION))
 

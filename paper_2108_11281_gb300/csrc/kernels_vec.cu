@@ -245,8 +245,11 @@ __global__ void k_multidot_reduce(const A *partial, int nparts, int nvec, int k,
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= nvec * k) return;
+  // each lane adds its parts in order; loads are independent, so four are in flight
   A s = zero<A>();
-  for (int p = lane; p < nparts; p += 32) s = addd(s, partial[(size_t)p * nvec * k + warp]);
+  const size_t stride = (size_t)nvec * k;
+#pragma unroll 4
+  for (int p = lane; p < nparts; p += 32) s = addd(s, partial[(size_t)p * stride + warp]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s = shfl_add(s, o);
   if (lane == 0) out[warp] = s;
