@@ -21,6 +21,7 @@ import argparse
 import json
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -578,8 +579,7 @@ def main():
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
-                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv")
+    sampler = ClockSampler(os.environ.get("MLMC_CLOCKS_CSV", os.path.join(tempfile.gettempdir(), "clocks_bench.csv")))
     results = []
     with sampler:
         torch.cuda.profiler.start()      # no-op unless a profiler is attached (launch lists)

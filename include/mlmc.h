@@ -48,7 +48,7 @@ typedef struct { double re, im; } mlmc_c64;
 typedef enum {
   MLMC_OK = 0,
   MLMC_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range */
-  MLMC_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+  MLMC_ERR_UNSUPPORTED = 2,   /* a valid request the library does not implement */
   MLMC_ERR_CUDA = 3,          /* a CUDA call failed; see mlmc_last_error() */
   MLMC_ERR_OOM = 4,           /* device allocation failed */
   MLMC_ERR_NOT_CONVERGED = 5, /* a solve hit max_iter before reaching tol */
