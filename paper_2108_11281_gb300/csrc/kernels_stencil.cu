@@ -335,9 +335,63 @@ __global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, c
   }
 }
 
+// Row-split variant for large site blocks (d >= 8, the coarse levels of the
+// Wilson hierarchy, which are small lattices): one thread per (row r of a site,
+// column c), so a site's block solve is spread over d x 32 threads instead of one
+// thread per column.  Phase 1: res_r = b_r - sum over the 4 neighbour blocks of
+// row r times their x (the 8 row threads of a column share the x loads in L1);
+// phase 2, after the block barrier: x_r = sum_q Dinv[r][q] res_q from shared memory.
+// Block = 32 columns x D rows of one site; grid = (column chunks, sites of the colour).
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_rbgs_half_rows(const T *__restrict__ coef, const T *__restrict__ dinv,
+                                                        T *__restrict__ x, const T *__restrict__ b, int nx, int ny,
+                                                        int k, int colour, int other_zero) {
+  __shared__ T res[D][32];
+  const int hx = nx / 2;
+  const int idx = blockIdx.y;                       // site of this colour: row j, position m
+  const int j = idx / hx, m = idx - (idx / hx) * hx;
+  const int i = 2 * m + ((j + colour) & 1);
+  const int s = j * nx + i;
+  const int cl = threadIdx.x, r = threadIdx.y;
+  const int c = blockIdx.x * 32 + cl;
+  const bool live = c < k;
+  if (live) {
+    T acc = b[((size_t)s * D + r) * k + c];
+    if (!other_zero) {
+      int nb[4];
+      nb[0] = j * nx + (i + 1 == nx ? 0 : i + 1);
+      nb[1] = j * nx + (i == 0 ? nx - 1 : i - 1);
+      nb[2] = (j + 1 == ny ? 0 : j + 1) * nx + i;
+      nb[3] = (j == 0 ? ny - 1 : j - 1) * nx + i;
+#pragma unroll
+      for (int dir = 0; dir < 4; ++dir) {
+        const T *B = coef + (((size_t)s * 5 + dir + 1) * D + r) * D;
+        const T *xs = x + (size_t)nb[dir] * D * k + c;
+#pragma unroll
+        for (int q = 0; q < D; ++q) acc = acc - B[q] * xs[(size_t)q * k];
+      }
+    }
+    res[r][cl] = acc;
+  }
+  __syncthreads();
+  if (live) {
+    const T *Di = dinv + ((size_t)s * D + r) * D;
+    T out = zero<T>();
+#pragma unroll
+    for (int q = 0; q < D; ++q) out = out + Di[q] * res[q][cl];
+    x[((size_t)s * D + r) * k + c] = out;
+  }
+}
+
 template <class T, int D>
 static void rbgs_go(const StencilView &A, void *x, const void *b, int k, int colour, int other_zero,
                     cudaStream_t s) {
+  if (D >= 8 && (A.nx / 2) * A.ny <= 65535) {
+    dim3 g((k + 31) / 32, (A.nx / 2) * A.ny);
+    k_rbgs_half_rows<T, D><<<g, dim3(32, D), 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b,
+                                                     A.nx, A.ny, k, colour, other_zero);
+    return;
+  }
   constexpr int VW = rbgs_vec<T, D>::v;
   if (VW > 1 && k % VW == 0) {
     int kv = k / VW;

@@ -81,6 +81,73 @@ __global__ void __launch_bounds__(128) k_restrict(const T *__restrict__ P, const
   }
 }
 
+// Split variant for small coarse levels: the S threads of an item (aggregate I,
+// coarse-dof group g, columns c) each sum a contiguous S-th of the aggregate's
+// m fine entries, and thread split 0 adds the S partials in split order
+// (deterministic).  Block = S x W threads, W = 256 / S items.
+template <class T, int DC, int VEC, int QG, int S>
+__global__ void __launch_bounds__(256) k_restrict_split(const T *__restrict__ P, const T *__restrict__ r,
+                                                        T *__restrict__ rc, int nx, int ny, int d, int ax, int ay,
+                                                        int kv) {
+  typedef TPack<T, VEC> V;
+  constexpr int NG = DC / QG, W = 256 / S;
+  __shared__ T red[S][W][QG][VEC];
+  const int split = threadIdx.x / W, w = threadIdx.x - (threadIdx.x / W) * W;
+  const int ncx = nx / ax, ncy = ny / ay;
+  const unsigned total = (unsigned)ncx * ncy * NG * kv;
+  const unsigned t = blockIdx.x * W + w;
+  const int m = ax * ay * d;
+  const V *R = (const V *)r;
+  T acc[QG][VEC];
+#pragma unroll
+  for (int q = 0; q < QG; ++q)
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) acc[q][u] = zero<T>();
+  int c = 0, g = 0, I = 0;
+  if (t < total) {
+    c = (int)(t % (unsigned)kv);
+    const unsigned ig = t / (unsigned)kv;
+    g = (int)(ig % NG);
+    I = (int)(ig / NG);
+    const int bi = I % ncx, bj = I / ncx;
+    const T *PI = P + (size_t)I * m * DC + g * QG;
+    const int per = (m + S - 1) / S;
+    const int e0 = split * per, e1 = min(m, e0 + per);
+    for (int e = e0; e < e1; ++e) {
+      const int loc = e / d, a = e - (e / d) * d;
+      const int jj = loc / ax, ii = loc - (loc / ax) * ax;
+      const int s = (bj * ay + jj) * nx + bi * ax + ii;
+      const V xv = R[((size_t)s * d + a) * kv + c];
+      const T *Pr = PI + (size_t)e * DC;
+#pragma unroll
+      for (int q = 0; q < QG; ++q) {
+        const T pq = conj(Pr[q]);
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) acc[q][u] = acc[q][u] + pq * xv.v[u];
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < QG; ++q)
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) red[split][w][q][u] = acc[q][u];
+  __syncthreads();
+  if (split == 0 && t < total) {
+    V *RC = (V *)rc;
+#pragma unroll
+    for (int q = 0; q < QG; ++q) {
+      V o;
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) {
+        T sum = red[0][w][q][u];
+        for (int sp = 1; sp < S; ++sp) sum = sum + red[sp][w][q][u];
+        o.v[u] = sum;
+      }
+      RC[((size_t)I * DC + g * QG + q) * kv + c] = o;
+    }
+  }
+}
+
 // x[s][a][c] += sum_q P[I(s)][loc(s)*d + a][q] ec[I][q][c]
 template <class T, int DC, int VEC>
 __global__ void __launch_bounds__(256) k_prolong_add(const T *__restrict__ P, const T *__restrict__ ec, T *__restrict__ x,
@@ -127,7 +194,21 @@ static void restrict_go(const ProlongView &P, const void *r, void *rc, int k, cu
   constexpr int QG = DC <= 4 ? DC : 2;
   const int vec = (VW > 1 && k % VW == 0) ? VW : 1;
   const int kv = k / vec;
-  unsigned g = grid_for((size_t)(P.nx / P.ax) * (P.ny / P.ay) * (DC / QG) * kv, 128, (size_t)1 << 20);
+  const size_t items = (size_t)(P.nx / P.ax) * (P.ny / P.ay) * (DC / QG) * kv;
+  const int m = P.ax * P.ay * P.d;
+  if (items < 32768 && m >= 32) {
+    // few items: spread each aggregate's sum over 8 threads
+    constexpr int S = 8;
+    unsigned gs = (unsigned)((items + 256 / S - 1) / (256 / S));
+    if (vec == VW && VW > 1)
+      k_restrict_split<T, DC, VW, QG, S><<<gs, 256, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d,
+                                                             P.ax, P.ay, kv);
+    else
+      k_restrict_split<T, DC, 1, QG, S><<<gs, 256, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d,
+                                                            P.ax, P.ay, kv);
+    return;
+  }
+  unsigned g = grid_for(items, 128, (size_t)1 << 20);
   if (vec == VW && VW > 1)
     k_restrict<T, DC, VW, QG><<<g, 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d, P.ax, P.ay, kv);
   else
