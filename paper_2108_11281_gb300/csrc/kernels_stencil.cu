@@ -105,8 +105,46 @@ template <int D> struct gen_vec<cfloat, D> { static const int v = D <= 2 ? 2 : 1
     default: throw cuda_error{cudaErrorInvalidValue, "unsupported dofs per site"}; \
   }
 
+// Row-split variant for large site blocks (d >= 8, the small coarse lattices of the
+// Wilson hierarchy): one thread per (row r of a site, column c) accumulates that
+// row over the 5 blocks; block = 32 columns x D rows of one site.
+template <class T, int D>
+__global__ void __launch_bounds__(256) k_stencil_rows(const T *__restrict__ coef, const T *__restrict__ x,
+                                                      const T *__restrict__ b, T *__restrict__ y, int nx, int ny,
+                                                      int k, int mode) {
+  const int s = blockIdx.y;
+  const int i = s % nx, j = s / nx;
+  const int r = threadIdx.y;
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  if (c >= k) return;
+  int nb[5];
+  nb[0] = s;
+  nb[1] = j * nx + (i + 1 == nx ? 0 : i + 1);
+  nb[2] = j * nx + (i == 0 ? nx - 1 : i - 1);
+  nb[3] = (j + 1 == ny ? 0 : j + 1) * nx + i;
+  nb[4] = (j == 0 ? ny - 1 : j - 1) * nx + i;
+  T acc = zero<T>();
+#pragma unroll
+  for (int dir = 0; dir < 5; ++dir) {
+    const T *B = coef + (((size_t)s * 5 + dir) * D + r) * D;
+    const T *xs = x + (size_t)nb[dir] * D * k + c;
+#pragma unroll
+    for (int q = 0; q < D; ++q) acc = acc + B[q] * xs[(size_t)q * k];
+  }
+  const size_t o = ((size_t)s * D + r) * k + c;
+  y[o] = mode ? b[o] - acc : acc;
+}
+
 template <class T, int D>
 static void stencil_go(const StencilView &A, const void *x, const void *b, void *y, int k, int mode, cudaStream_t s) {
+  if constexpr (D >= 8) {
+    if (A.nx * A.ny <= 65535) {
+      dim3 g((k + 31) / 32, A.nx * A.ny);
+      k_stencil_rows<T, D><<<g, dim3(32, D), 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx,
+                                                     A.ny, k, mode);
+      return;
+    }
+  }
   constexpr int VW = gen_vec<T, D>::v;
   if (VW > 1 && k % VW == 0) {
     int kv = k / VW;
@@ -386,11 +424,13 @@ __global__ void __launch_bounds__(256) k_rbgs_half_rows(const T *__restrict__ co
 template <class T, int D>
 static void rbgs_go(const StencilView &A, void *x, const void *b, int k, int colour, int other_zero,
                     cudaStream_t s) {
-  if (D >= 8 && (A.nx / 2) * A.ny <= 65535) {
-    dim3 g((k + 31) / 32, (A.nx / 2) * A.ny);
-    k_rbgs_half_rows<T, D><<<g, dim3(32, D), 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b,
-                                                     A.nx, A.ny, k, colour, other_zero);
-    return;
+  if constexpr (D >= 8) {
+    if ((A.nx / 2) * A.ny <= 65535) {
+      dim3 g((k + 31) / 32, (A.nx / 2) * A.ny);
+      k_rbgs_half_rows<T, D><<<g, dim3(32, D), 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b,
+                                                       A.nx, A.ny, k, colour, other_zero);
+      return;
+    }
   }
   constexpr int VW = rbgs_vec<T, D>::v;
   if (VW > 1 && k % VW == 0) {
