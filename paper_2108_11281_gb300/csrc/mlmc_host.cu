@@ -1411,11 +1411,20 @@ int mlmc_dense_apply(int complex_data, const void *A, const void *B, void *Y, in
   });
 }
 
+// Captured inner solves bake in the kernel choices: drop them when a choice changes.
+static void drop_graphs(mlmc_hierarchy &h) {
+  check_cuda(cudaStreamSynchronize(h.stream), "sync");
+  for (auto &g : h.graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h.graphs.clear();
+}
+
 int mlmc_set_dense_kernel(mlmc_hierarchy *h, int which) {
   return translate([&] {
     need(h);
     if (which != MLMC_DENSE_SIMT && which != MLMC_DENSE_TC && which != MLMC_DENSE_AUTO)
       fail(MLMC_ERR_INVALID_ARG, "unknown dense kernel");
+    if (h->dense_kernel != which) drop_graphs(*h);
     h->dense_kernel = which;
   });
 }

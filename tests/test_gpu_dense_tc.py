@@ -90,13 +90,18 @@ def test_hierarchy_dense_kernels_agree(mlmc):
                               coarse_sweeps=5, setup_omega=1.0, precision=mlmc.PREC_MIXED_FP32, block=16,
                               bootstrap=0)
     h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.1, links=gauge_links(N, N, 0.3, 7))
-    got = {}
+    got, launches, iters = {}, {}, {}
     for which in (mlmc.DENSE_TC, mlmc.DENSE_SIMT):
         h.set_dense_kernel(which)
+        n0 = h.launch_count()
         s, its = h.sample_level(2, mlmc.NOISE_Z4, 3, 0, 16, 1e-12)
-        got[which] = s
+        launches[which], iters[which], got[which] = h.launch_count() - n0, list(its), s
     a, b = got[mlmc.DENSE_TC], got[mlmc.DENSE_SIMT]
     assert np.abs(a - b).max() <= 1e-8 * np.abs(b).max()
+    # the switch reaches the captured inner solves: the tensor-core apply is two
+    # launches (products, slice sum), the CUDA-core one a single launch
+    if iters[mlmc.DENSE_TC] == iters[mlmc.DENSE_SIMT]:
+        assert launches[mlmc.DENSE_TC] > launches[mlmc.DENSE_SIMT]
     ms = {}
     for which in (mlmc.DENSE_TC, mlmc.DENSE_SIMT):
         h.set_dense_kernel(which)
