@@ -76,9 +76,9 @@ WORKLOAD = WORKLOADS["laplace1024"]
 # ncu DRAM traffic (read + write bytes) per launch unit of the roofline kernel, keyed by
 # (workload, kernel row); only for the kernel version the capture was taken on
 TRAFFIC = {
-    # k_rbgs_half<float,4,4>, level 2 (256^2 x 4, k = 128), both halves of one sweep:
-    # dram__bytes_read 149.44 + 149.43 MB, dram__bytes_write 40.31 + 37.25 MB (1 pass each)
-    ("laplace2d-1024x1024-L4-4tv-k64", "rbgs_sweep_fp32_level2"): 376.43e6,
+    # k_rbgs_half_p<float,4,4>, level 2 (256^2 x 4, k = 128), both halves of one sweep:
+    # dram__bytes_read 149.44 + 149.43 MB, dram__bytes_write 39.54 + 36.90 MB (1 pass each)
+    ("laplace2d-1024x1024-L4-4tv-k64", "rbgs_sweep_fp32_level2"): 375.32e6,
 }
 METRIC = "Seconds to tr(A^-1) at 1e-3 rel. error, mixed+learned vs plain FP64; HBM %"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -626,7 +626,7 @@ def main():
     dom = kern[dom_name]
     # DRAM bytes per sweep of this kernel version from an ncu capture (None until taken)
     traffic = TRAFFIC.get((w["name"], dom_name))
-    label = ("k_rbgs_half (coarse-level red-black block GS, level 2, one sweep = 2 launches, k=%d)" % kcb
+    label = ("k_rbgs_half_p (coarse-level red-black block GS, level 2, one sweep = 2 launches, k=%d)" % kcb
              if dom_name != "multidot_fp32" else
              "k_multidot_partial<float> (inner Arnoldi: 4 basis blocks + w, level 1, k=%d)" % w["block"])
     roofline = {"bound": "hbm", "kernel": label,

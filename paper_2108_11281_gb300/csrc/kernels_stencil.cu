@@ -311,9 +311,9 @@ template <int D> struct rbgs_vec<cdouble, D> { static const int v = 1; };
 
 // grid.y = lattice row j; threads of a row cover (site m of the colour, VEC columns).
 template <class T, int D, int VEC>
-__global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, const T *__restrict__ dinv,
-                                                   T *__restrict__ x, const T *__restrict__ b, int nx, int ny, int kv,
-                                                   int colour, int other_zero) {
+__device__ __forceinline__ void rbgs_half_body(const T *__restrict__ coef, const T *__restrict__ dinv,
+                                               T *__restrict__ x, const T *__restrict__ b, int nx, int ny, int kv,
+                                               int colour, int other_zero) {
   typedef Pack<T, VEC> V;
   const int j = blockIdx.y;
   const int hx = nx / 2;
@@ -371,6 +371,27 @@ __global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, c
       X[o + (size_t)r * kv] = out;
     }
   }
+}
+
+template <class T, int D, int VEC>
+__global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, const T *__restrict__ dinv,
+                                                   T *__restrict__ x, const T *__restrict__ b, int nx, int ny, int kv,
+                                                   int colour, int other_zero) {
+  rbgs_half_body<T, D, VEC>(coef, dinv, x, b, nx, ny, kv, colour, other_zero);
+}
+
+// The same half-sweep in blocks of 128 threads with residency pinned at 8 blocks
+// per SM (<= 64 registers), for FP32 blocks with d = 4 (the aggregation levels of
+// the Laplace hierarchy).  The kernel is load-latency bound; measured on the
+// 256^2 x 4 level, k = 128, per sweep: 88.3 us here, 90.6 us with 256 threads x 4
+// blocks, 93.7 us unpinned (256 threads), 96-99 us with two or four neighbour
+// blocks' loads issued together (80-128 registers, 2-3 blocks of 256 per SM) and
+// 100-104 us with 5-8 blocks of 256 per SM (8-byte packs or spills).
+template <class T, int D, int VEC>
+__global__ void __launch_bounds__(128, 8) k_rbgs_half_p(const T *__restrict__ coef, const T *__restrict__ dinv,
+                                                        T *__restrict__ x, const T *__restrict__ b, int nx, int ny,
+                                                        int kv, int colour, int other_zero) {
+  rbgs_half_body<T, D, VEC>(coef, dinv, x, b, nx, ny, kv, colour, other_zero);
 }
 
 // Row-split variant for large site blocks (d >= 8, the coarse levels of the
@@ -436,8 +457,12 @@ static void rbgs_go(const StencilView &A, void *x, const void *b, int k, int col
   if (VW > 1 && k % VW == 0) {
     int kv = k / VW;
     dim3 g(((A.nx / 2) * kv + 255) / 256, A.ny);
-    k_rbgs_half<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny,
-                                            kv, colour, other_zero);
+    if constexpr (std::is_same<T, float>::value && D == 4)
+      k_rbgs_half_p<T, D, VW><<<dim3(((A.nx / 2) * kv + 127) / 128, A.ny), 128, 0, s>>>(
+          (const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny, kv, colour, other_zero);
+    else
+      k_rbgs_half<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny,
+                                              kv, colour, other_zero);
   } else {
     dim3 g(((A.nx / 2) * k + 255) / 256, A.ny);
     k_rbgs_half<T, D, 1><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny,
