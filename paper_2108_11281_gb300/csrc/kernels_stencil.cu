@@ -36,9 +36,9 @@ __device__ inline void load_row(const T *__restrict__ p, T out[D]) {
 }
 
 template <class T, int D, int VEC>
-__global__ void __launch_bounds__(256) k_stencil(const T *__restrict__ coef, const T *__restrict__ x,
-                                                 const T *__restrict__ b, T *__restrict__ y, int nx, int ny, int kv,
-                                                 int mode) {
+__device__ __forceinline__ void stencil_body(const T *__restrict__ coef, const T *__restrict__ x,
+                                             const T *__restrict__ b, T *__restrict__ y, int nx, int ny, int kv,
+                                             int mode) {
   typedef Pack<T, VEC> V;
   const int j = blockIdx.y;                 // grid.y = lattice row
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -88,6 +88,23 @@ __global__ void __launch_bounds__(256) k_stencil(const T *__restrict__ coef, con
       ((V *)y)[o + (size_t)r * kv] = out;
     }
   }
+}
+
+template <class T, int D, int VEC>
+__global__ void __launch_bounds__(256) k_stencil(const T *__restrict__ coef, const T *__restrict__ x,
+                                                 const T *__restrict__ b, T *__restrict__ y, int nx, int ny, int kv,
+                                                 int mode) {
+  stencil_body<T, D, VEC>(coef, x, b, y, nx, ny, kv, mode);
+}
+
+// The same in blocks of 128 threads pinned at 8 per SM (<= 64 registers), for FP32
+// blocks with d = 4 (the aggregation levels of the Laplace hierarchy), like the
+// block smoother: both are load-latency bound.
+template <class T, int D, int VEC>
+__global__ void __launch_bounds__(128, 8) k_stencil_p(const T *__restrict__ coef, const T *__restrict__ x,
+                                                      const T *__restrict__ b, T *__restrict__ y, int nx, int ny,
+                                                      int kv, int mode) {
+  stencil_body<T, D, VEC>(coef, x, b, y, nx, ny, kv, mode);
 }
 
 // columns per thread for the generic kernels: 16-byte packs for FP32 data on
@@ -149,7 +166,12 @@ static void stencil_go(const StencilView &A, const void *x, const void *b, void 
   if (VW > 1 && k % VW == 0) {
     int kv = k / VW;
     dim3 g((A.nx * kv + 255) / 256, A.ny);
-    k_stencil<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, mode);
+    if constexpr (std::is_same<T, float>::value && D == 4)
+      k_stencil_p<T, D, VW><<<dim3((A.nx * kv + 127) / 128, A.ny), 128, 0, s>>>(
+          (const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, mode);
+    else
+      k_stencil<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv,
+                                            mode);
   } else {
     dim3 g((A.nx * k + 255) / 256, A.ny);
     k_stencil<T, D, 1><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, k, mode);
