@@ -29,7 +29,7 @@ def pure_gauge_links(nx, ny, seed):
     return np.stack([ux, uy]), g
 
 
-# Workloads (sizes follow the paper's classes; see the design doc for the recipe).
+# Workloads: synthetic operators with the sizes and classes of the paper's examples (Sec. 5).
 LAPLACE_SMALL = dict(name="laplace2d-64x64-L2-const", kind="laplace", nx=64, ny=64, shift=0.0,
                      levels=2, n_tv=1, setup="constant", noise="rademacher", block=64,
                      tol=1e-10, samples=1000)
