@@ -227,7 +227,7 @@ def cpu_baseline(result, w):
             kcycle_its=w["kcycle_its"]))
     setup_s = time.time() - t0
     per_it = []
-    its_probe = 3
+    its_probe = 8
     for l in range(len(lv) - 1):
         M = Cycle(lv, l, w["smooth_pre"], w["smooth_post"], "K", w["kcycle_its"])
         b = noise(lv[l].n, w["noise"], 1, l + 1, 0)
