@@ -143,10 +143,11 @@ __global__ void __launch_bounds__(256) k_stencil_rows(const T *__restrict__ coef
   T acc = zero<T>();
 #pragma unroll
   for (int dir = 0; dir < 5; ++dir) {
-    const T *B = coef + (((size_t)s * 5 + dir) * D + r) * D;
+    T row[D];                                      // row r of the block: 16-byte loads, warp-uniform
+    load_row<T, D>(coef + (((size_t)s * 5 + dir) * D + r) * D, row);
     const T *xs = x + (size_t)nb[dir] * D * k + c;
 #pragma unroll
-    for (int q = 0; q < D; ++q) acc = acc + B[q] * xs[(size_t)q * k];
+    for (int q = 0; q < D; ++q) acc = acc + row[q] * xs[(size_t)q * k];
   }
   const size_t o = ((size_t)s * D + r) * k + c;
   y[o] = mode ? b[o] - acc : acc;
@@ -446,20 +447,22 @@ __global__ void __launch_bounds__(256) k_rbgs_half_rows(const T *__restrict__ co
       nb[3] = (j == 0 ? ny - 1 : j - 1) * nx + i;
 #pragma unroll
       for (int dir = 0; dir < 4; ++dir) {
-        const T *B = coef + (((size_t)s * 5 + dir + 1) * D + r) * D;
+        T row[D];                                    // row r of the block: 16-byte loads, warp-uniform
+        load_row<T, D>(coef + (((size_t)s * 5 + dir + 1) * D + r) * D, row);
         const T *xs = x + (size_t)nb[dir] * D * k + c;
 #pragma unroll
-        for (int q = 0; q < D; ++q) acc = acc - B[q] * xs[(size_t)q * k];
+        for (int q = 0; q < D; ++q) acc = acc - row[q] * xs[(size_t)q * k];
       }
     }
     res[r][cl] = acc;
   }
   __syncthreads();
   if (live) {
-    const T *Di = dinv + ((size_t)s * D + r) * D;
+    T di[D];
+    load_row<T, D>(dinv + ((size_t)s * D + r) * D, di);
     T out = zero<T>();
 #pragma unroll
-    for (int q = 0; q < D; ++q) out = out + Di[q] * res[q][cl];
+    for (int q = 0; q < D; ++q) out = out + di[q] * res[q][cl];
     x[((size_t)s * D + r) * k + c] = out;
   }
 }

@@ -228,6 +228,36 @@ def test_wilson_samples_imported_P(mlmc):
     h.close()
 
 
+@pytest.mark.parametrize("precision,rtol", [(0, 1e-9), (1, 1e-8)])
+def test_wilson_d8_level_apply_and_samples(mlmc, precision, rtol):
+    """Coarse level with 8 dofs per site (4 test vectors x 2 spin halves), where the block
+    apply and the block smoother take one thread per block row: the level-2 operator apply
+    against its stencil matrix, and level-1 / level-2 samples against the oracle."""
+    N = 32
+    U = gauge_links(N, N, 0.3, 13)
+    S = wilson2d(N, N, 0.05, U)
+    lv = build_hierarchy(S, N, N, 2, SetupParams(levels=3, n_tv=4, spin_split=True, kind="inverse", sweeps=6,
+                                                 coarse_sweeps=4, omega=1.0, noise_kind="z4"))
+    prm = mlmc.default_params(levels=3, n_tv=4, spin_split=1, block=8, smooth_pre=2, smooth_post=2,
+                              precision=precision)
+    h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.05, links=U,
+                       user_P=[lv[0].P_blocks, lv[1].P_blocks])
+    nx, ny, d = h.level_info(2)
+    assert (nx, ny, d) == (8, 8, 8)
+    A2 = block_from_stencil(h.operator(2), nx, ny)
+    assert abs(A2 - lv[1].A).max() <= 1e-12 * abs(lv[1].A).max()
+    x = torch.randn(nx * ny * d, 5, dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    h.apply(2, x.data_ptr(), y.data_ptr(), 5)
+    assert np.abs(y.cpu().numpy() - A2 @ x.cpu().numpy()).max() <= 1e-12 * abs(A2).max()
+    solv = E.LevelSolvers(lv)
+    for level in (1, 2):
+        got, _ = h.sample_level(level, mlmc.NOISE_Z4, 5, 0, 6, 1e-12 if precision == 0 else 1e-10)
+        ref = E.level_samples(lv, solv, level, "z4", 5, 0, 6)
+        compare_samples(got, ref, rtol)
+    h.close()
+
+
 def test_trace_estimate_matches_oracle(mlmc):
     """Sec. 5 procedure on a 32x32 Laplacian, 2 levels: same tau, same N_l, same estimate."""
     N = 32
