@@ -238,22 +238,24 @@ def test_wilson_d8_level_apply_and_samples(mlmc, precision, rtol):
     S = wilson2d(N, N, 0.05, U)
     lv = build_hierarchy(S, N, N, 2, SetupParams(levels=3, n_tv=4, spin_split=True, kind="inverse", sweeps=6,
                                                  coarse_sweeps=4, omega=1.0, noise_kind="z4"))
-    prm = mlmc.default_params(levels=3, n_tv=4, spin_split=1, block=8, smooth_pre=2, smooth_post=2,
-                              precision=precision)
+    prm = mlmc.default_params(levels=3, n_tv=4, spin_split=1, block=8, coarse_block=64, smooth_pre=2,
+                              smooth_post=2, precision=precision)
     h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.05, links=U,
                        user_P=[lv[0].P_blocks, lv[1].P_blocks])
     nx, ny, d = h.level_info(2)
     assert (nx, ny, d) == (8, 8, 8)
     A2 = block_from_stencil(h.operator(2), nx, ny)
     assert abs(A2 - lv[1].A).max() <= 1e-12 * abs(lv[1].A).max()
-    x = torch.randn(nx * ny * d, 5, dtype=torch.complex128, device="cuda")
-    y = torch.empty_like(x)
-    h.apply(2, x.data_ptr(), y.data_ptr(), 5)
-    assert np.abs(y.cpu().numpy() - A2 @ x.cpu().numpy()).max() <= 1e-12 * abs(A2).max()
+    for k in (5, 64, 66):          # one column per thread; two (k even, >= 64), with a ragged chunk
+        x = torch.randn(nx * ny * d, k, dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        h.apply(2, x.data_ptr(), y.data_ptr(), k)
+        assert np.abs(y.cpu().numpy() - A2 @ x.cpu().numpy()).max() <= 1e-12 * abs(A2).max()
     solv = E.LevelSolvers(lv)
-    for level in (1, 2):
-        got, _ = h.sample_level(level, mlmc.NOISE_Z4, 5, 0, 6, 1e-12 if precision == 0 else 1e-10)
-        ref = E.level_samples(lv, solv, level, "z4", 5, 0, 6)
+    # level 1 in blocks of 8; level 2 in one block of 64 columns (two columns per thread)
+    for level, count in ((1, 6), (2, 64)):
+        got, _ = h.sample_level(level, mlmc.NOISE_Z4, 5, 0, count, 1e-12 if precision == 0 else 1e-10)
+        ref = E.level_samples(lv, solv, level, "z4", 5, 0, count)
         compare_samples(got, ref, rtol)
     h.close()
 
