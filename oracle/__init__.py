@@ -13,7 +13,7 @@ Modules:
   solver      exact level solves; FGMRES + multigrid cycle (Remark 4.1, Ex. 5.3)
   estimator   difference samples, exact coarse trace, estimate and stopping rule (Secs. 2, 4, 5)
 
-Parity pins live in tests/test_oracle_pins.py.  Functions with no pin other
-than construction ("parity unpinned"): the stopping rule's tau / rho split
-(Sec. 5 prints no values).
+Parity pins live in tests/test_oracle_pins.py.  The stopping rule's tau / rho
+split (Sec. 5 prints no values) is pinned against a hand-derived closed form on
+synthetic sample streams (test_stopping_rule_closed_form).
 """

@@ -269,6 +269,42 @@ def test_small_laplace_estimate_against_closed_form():
     assert all(n >= 5 for n in res.n_samples)
 
 
+def test_stopping_rule_closed_form(monkeypatch):
+    """Sec. 5 stopping rule on synthetic samples with a closed form.  Level l draws
+    s_i = mu_l + sigma_l (-1)^i (sample index i), the coarse term is T_L.  Then the five
+    full estimates are m + S (-1)^i with m = T_L + sum mu_l, S = sum sigma_l, so
+    tau = m + S/5 - sqrt(0.96) S (population deviation of +,-,+,-,+).  For an even count n
+    the unbiased variance is n sigma^2 / (n - 1), so level l stops at the first multiple of
+    the block (and >= 5) with sigma_l^2 / (n - 1) <= rho_l^2, rho_l = sqrt(w_l) eps tau, and
+    the estimate is exactly m."""
+    mu, sigma, TL = [10.0, 5.0], [3.0, 1.0], 100.0
+
+    def fake_samples(levels, solvers, l, kind, seed, first, count, form="simplified", purpose=0, hats=None):
+        i = np.arange(first, first + count)
+        return mu[l - 1] + sigma[l - 1] * (-1.0) ** i + 0j
+
+    monkeypatch.setattr(E, "level_samples", fake_samples)
+    monkeypatch.setattr(E, "exact_coarse_trace", lambda levels, form="simplified": TL)
+    eps, block = 0.01, 8
+    for weights in (None, [0.8, 0.2]):
+        r = E.trace_estimate([None, None, None], "rademacher", eps=eps, weights=weights, block=block,
+                             solvers=object())
+        m, S = TL + sum(mu), sum(sigma)
+        tau = m + S / 5 - np.sqrt(0.96) * S
+        assert abs(r.tau - tau) <= 1e-12 * tau
+        w = [0.5, 0.5] if weights is None else weights
+        for l in range(2):
+            rho2 = w[l] * (eps * tau) ** 2
+            n = block
+            while not (n >= 5 and sigma[l] ** 2 / (n - 1) <= rho2):
+                n += block
+            assert r.n_samples[l] == n
+            assert abs(r.variances[l] - n * sigma[l] ** 2 / (n - 1)) <= 1e-12 * sigma[l] ** 2
+        assert abs(r.trace - m) <= 1e-12 * m
+        se = np.sqrt(sum(sigma[l] ** 2 / (r.n_samples[l] - 1) for l in range(2)))
+        assert abs(r.std_err - se) <= 1e-12 * se
+
+
 # ---------------------------------------------------------------- learned correction (no paper basis)
 @pytest.mark.parametrize("case", ["wilson", "laplace"])
 def test_learned_gradient_matches_finite_differences(case):
