@@ -11,7 +11,8 @@ Modules:
   operators   2-D Laplacian (Example 5.1) and 2-spin Wilson/Schwinger operator (Example 5.3)
   hierarchy   aggregation hierarchy with orthonormal P and Galerkin coarsening (Sec. 4.1, Ex. 5.3)
   solver      exact level solves; FGMRES + multigrid cycle (Remark 4.1, Ex. 5.3)
-  estimator   difference samples, exact coarse trace, estimate and stopping rule (Secs. 2, 4, 5)
+  estimator   difference samples, exact coarse trace, estimate, stopping rule and the
+              Sec. 2 optimal allocation (Secs. 2, 4, 5)
 
 Parity pins live in tests/test_oracle_pins.py.  The stopping rule's tau / rho
 split (Sec. 5 prints no values) is pinned against a hand-derived closed form on

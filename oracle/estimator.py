@@ -122,6 +122,27 @@ class EstimateResult:
     warmup: List[complex]
 
 
+def optimal_allocation(variances, costs, target, min_samples=5):
+    """Sec. 2: the sample counts minimising sum_l N_l C_l subject to
+    sum_l V_l / N_l = target^2.  Stationarity of the Lagrangian gives
+    N_l = mu sqrt(V_l / C_l); the constraint then fixes
+    mu = target^-2 sum_j sqrt(V_j C_j).  (The multiplier printed in Sec. 2 has
+    sqrt(V_j / C_j) in the sum, which does not satisfy the constraint; the
+    minimal cost printed there, target^-2 (sum_j sqrt(V_j C_j))^2, agrees with
+    this reading.)
+    Returns the real optimum N_l, the whole counts max(min_samples, ceil(N_l))
+    and the weights w_l = sqrt(V_l C_l) / sum_j sqrt(V_j C_j), with which the
+    optimum is the split rho_l^2 = w_l target^2 of the Sec. 5 stopping rule."""
+    V = np.asarray(variances, dtype=float)
+    C = np.asarray(costs, dtype=float)
+    S = 0.0
+    for v, c in zip(V, C):
+        S += np.sqrt(v * c)
+    N = np.sqrt(V / C) * S / (target * target)
+    counts = [max(min_samples, int(np.ceil(n))) for n in N]
+    return N, counts, np.sqrt(V * C) / S
+
+
 def trace_estimate(levels, kind, seed=0, eps=1e-3, weights=None, block=64, min_samples=5,
                    max_samples=1 << 20, form="simplified", solvers=None):
     """Sec. 5 procedure; returns an EstimateResult."""

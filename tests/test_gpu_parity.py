@@ -274,6 +274,19 @@ def test_trace_estimate_matches_oracle(mlmc):
     h.close()
 
 
+def check_optimal_counts(r, eps, min_samples=5):
+    """The estimate stops with every level at or above the oracle's Sec. 2 count for the
+    variances and per-sample costs it ended with, and with the same weights."""
+    nd = len(r["n_samples"])
+    n = np.array(r["n_samples"], dtype=float)
+    V = np.array(r["variance"], dtype=float)
+    C = np.array(r["cost_nnz"][:nd], dtype=float) / n
+    Nopt, _, w = E.optimal_allocation(V, C, eps * abs(r["tau"]), min_samples)
+    for got, want in zip(n, Nopt):
+        assert got >= max(min_samples, np.ceil(want * (1 - 1e-9)))
+    assert np.allclose(r["weights_used"], w, rtol=1e-9, atol=0)
+
+
 def test_optimal_allocation_estimate(mlmc):
     """Sec. 2 optimal allocation: the total variance meets (eps tau)^2 and the
     estimate equals the oracle's mean of the same samples (same N_l, same noise)."""
@@ -285,6 +298,7 @@ def test_optimal_allocation_estimate(mlmc):
     assert r["std_err"] <= target * (1 + 1e-12)
     assert all(n >= 5 for n in r["n_samples"])
     assert abs(sum(r["weights_used"]) - 1.0) < 1e-12
+    check_optimal_counts(r, 1e-2)
     # the same samples, drawn by the GPU itself one level at a time, give the same means
     for l, n in enumerate(r["n_samples"], start=1):
         s, _ = h.sample_level(l, mlmc.NOISE_RADEMACHER, 2, 0, n, 1e-12)

@@ -269,6 +269,34 @@ def test_small_laplace_estimate_against_closed_form():
     assert all(n >= 5 for n in res.n_samples)
 
 
+def test_optimal_allocation_minimises_cost():
+    """Sec. 2: the counts minimise sum N_l C_l subject to sum V_l / N_l = eps^2, checked
+    against a numerical constrained minimisation (scipy SLSQP, from several starts), the
+    constraint itself, and the minimal cost eps^-2 (sum sqrt(V_l C_l))^2 printed there."""
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        L = int(rng.integers(2, 5))
+        V = rng.uniform(0.1, 50.0, L)
+        C = rng.uniform(1.0, 100.0, L)
+        eps = rng.uniform(0.05, 0.5)
+        N, counts, w = E.optimal_allocation(V, C, eps, min_samples=1)
+        assert abs(np.sum(V / N) - eps ** 2) <= 1e-12 * eps ** 2
+        assert abs(np.dot(N, C) - np.sum(np.sqrt(V * C)) ** 2 / eps ** 2) <= 1e-10 * np.dot(N, C)
+        assert abs(w.sum() - 1.0) <= 1e-14 and np.allclose(V / N, w * eps ** 2, rtol=1e-12)
+        assert counts == [max(1, int(np.ceil(n))) for n in N]
+        best = None
+        for start in (np.full(L, 10.0), rng.uniform(1.0, 1e3, L)):
+            res = minimize(lambda n: np.dot(n, C) / np.dot(N, C), start * N.mean() / start.mean(),
+                           constraints=[{"type": "eq", "fun": lambda n: np.sum(V / n) / eps ** 2 - 1.0}],
+                           bounds=[(1e-6, None)] * L, method="SLSQP", options={"ftol": 1e-14, "maxiter": 500})
+            if res.success and (best is None or res.fun < best.fun):
+                best = res
+        assert best is not None
+        assert np.allclose(best.x, N, rtol=1e-4)
+        assert best.fun >= 1.0 - 1e-9          # nothing feasible is cheaper than the closed form
+
+
 def test_stopping_rule_closed_form(monkeypatch):
     """Sec. 5 stopping rule on synthetic samples with a closed form.  Level l draws
     s_i = mu_l + sigma_l (-1)^i (sample index i), the coarse term is T_L.  Then the five
