@@ -1,6 +1,8 @@
-// Nearest-neighbour block-stencil kernels: operator apply / residual, red-black
-// block Gauss-Seidel half-sweeps, aggregation restriction and prolongation,
-// and the damped-Jacobi update used by the setup filter.
+// Nearest-neighbour block-stencil kernels: operator apply / residual (the generic
+// d x d block stencil, its row-split form for d = 8 and the constant-coefficient
+// Example 5.1 operator) and red-black block Gauss-Seidel half-sweeps.  Transfers
+// and the setup filter are in kernels_transfer.cu, the 9-point levels of the
+// bilinear hierarchy in kernels_bilinear.cu.
 //
 // Layout: the operator of a level is coef[site][dir][r][c] (dir 0 self, 1 +x,
 // 2 -x, 3 +y, 4 -y; periodic indexing, Dirichlet boundaries are zero blocks);
