@@ -1,7 +1,8 @@
 // Per-column kernels of the batched flexible GMRES (Saad, Alg. 9.6): every
 // column of a vector block is an independent system, and its small Hessenberg
 // least-squares problem (Givens rotations, triangular solve) is handled by one
-// thread in FP64.  Also: sample combination and accumulation (Secs. 2-3), the
+// thread in FP64, as are the coefficient rescalings of the fixed-length FGMRES that
+// keeps its basis unnormalised.  Also: sample combination and accumulation (Secs. 2-3), the
 // fine-operator builders (Examples 5.1 and 5.3) and a dense scatter of the
 // coarsest operator.
 #include "mlmc_internal.cuh"

@@ -1,5 +1,6 @@
 // Vector-block kernels: noise generation, precision conversion, column-wise
-// dot products (two-stage, fixed order), multi-AXPY and column scaling.
+// dot products (two-stage, fixed order), multi-AXPY (optionally summing the
+// result's column norms) and column scaling.
 // Vector blocks are [row][k] with the k columns (independent right-hand
 // sides / samples) innermost, so a warp touches consecutive columns of one row.
 #include <algorithm>
