@@ -268,7 +268,9 @@ int mlmc_dense_apply(int complex_data, const void *A, const void *B, void *Y, in
  * 512, else the CUDA cores (measured: n_L = 1024 real 20.6 vs 55.4 us,
  * 512 complex 24.3 vs 30.8 us, 225 real 20.7 vs 14.5 us at k = 128).  The
  * FP64 cycle always uses the CUDA-core kernel, GB300's FP64 tensor rate being
- * far below its FP32 one. */
+ * far below its FP32 one.  A change of kernel synchronises the handle's stream
+ * and drops the CUDA graphs captured for the inner solves (they are captured
+ * again on next use). */
 int mlmc_set_dense_kernel(mlmc_hierarchy *h, int which);
 
 /* The exact coarsest term of the estimator (Remark 4.2), tr(A_L^{-1} R^_L P^_L)
