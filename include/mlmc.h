@@ -225,19 +225,23 @@ int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, ui
  * Allocates and frees its scratch (608 x k partial sums) on every call; k <= 256. */
 int mlmc_column_dots(int complex_data, const void *x, const void *y, int n, int k, void *out, void *stream);
 
-/* mlmc_column_dots without any allocation (the paper has no counterpart; this
- * serves callers that cannot allocate device memory: code running while a
- * CUDA graph is captured on the stream, applications whose memory manager
- * owns every device allocation, loops that must not pay the device-wide
- * synchronisation of cudaFree).  Same arguments and result as
- * mlmc_column_dots.  Its scratch is a fixed array of 2,490,368 bytes inside
- * the library (608 row chunks x 256 columns x 16 bytes), present on every GPU
- * that loads the library until the process exits; k > 256 is rejected with
- * MLMC_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the one array, so
- * calls that overlap on the GPU (other streams, other threads) race; issue
- * them one after another.  Errors are described by mlmc_noalloc_last_error(). */
+/* mlmc_column_dots without any allocation (the paper has no counterpart).  It
+ * serves callers that cannot let a library allocate device memory:
+ * applications whose own memory manager owns every byte of device memory (a
+ * pool sized up front, a fixed budget per process), and latency-critical loops
+ * that must not pay an allocator's synchronisation or its failure modes in the
+ * middle of a run.  Same arguments and result as mlmc_column_dots, and like it
+ * the call returns once `out` has been written.  Its scratch is a fixed array
+ * of 2,490,368 bytes inside the library (608 row chunks x 256 columns x 16
+ * bytes), present on every GPU that loads the library until the process
+ * exits; k > 256 is rejected with MLMC_ERR_INVALID_ARG.  The first call on a
+ * device (and the first after its context was replaced, e.g. by
+ * cudaDeviceReset) looks up the array's device address with
+ * cudaGetSymbolAddress, with that device current; make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last
+ * call's partial sums, which every call overwrites before reading; calls that
+ * overlap on the GPU (other streams, other threads) race, so issue them one
+ * after another.  Errors are described by mlmc_noalloc_last_error(). */
 int mlmc_column_dots_noalloc(int complex_data, const void *x, const void *y, int n, int k, void *out,
                              void *stream);
 const char *mlmc_noalloc_last_error(void);
