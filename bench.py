@@ -115,6 +115,9 @@ def parse():
                          "workload: seconds, device-counted cost (Sec. 5 model) and N per method; one JSON line")
     ap.add_argument("--alloc", default="optimal", choices=["optimal", "rho"],
                     help="Sec. 2 optimal allocation (default) or the Sec. 5 equal rho split")
+    ap.add_argument("--cost-model", default="counted", choices=["counted", "nominal"],
+                    help="per-sample cost C_l of the optimal allocation: products the solves performed "
+                         "(counted) or one product per operator solved with (nominal, solver-independent)")
     return ap.parse_args()
 
 
@@ -561,9 +564,11 @@ def main():
 
     form = mlmc.FORM_HAT if w.get("form") == "hat" else mlmc.FORM_SIMPLIFIED
 
+    cost_model = mlmc.COST_NOMINAL if args.cost_model == "nominal" else mlmc.COST_COUNTED
+
     def step(hh, tol, seed):
         return mlmc.result_dict(hh.trace_estimate(eps=w["eps"], noise=nz, seed=seed, tol=tol,
-                                                  allocation=alloc, form=form))
+                                                  allocation=alloc, form=form, cost_model=cost_model))
 
     learned = None
     if w.get("learned"):
@@ -684,7 +689,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
-                "config": dict(config_dict("mixed: FP32 K-cycle under FP64 FGMRES", w), allocation=args.alloc),
+                "config": dict(config_dict("mixed: FP32 K-cycle under FP64 FGMRES", w), allocation=args.alloc,
+                               cost_model=args.cost_model),
                 "clocks": sampler.summary(local), "gpu_launches": int(launches), "wall_s_timed": wall,
                 "e2e": {"value": e2e, "unit": "s",
                         "h2d_bytes_per_step": 0 if w["kind"] == "laplace" else 2 * w["nx"] * w["ny"] * 16,

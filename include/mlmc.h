@@ -65,6 +65,7 @@ enum { MLMC_PREC_FP64 = 0, MLMC_PREC_MIXED_FP32 = 1 };
 enum { MLMC_FORM_SIMPLIFIED = 0, MLMC_FORM_HAT = 1, MLMC_FORM_PLAIN = 2 };
 enum { MLMC_CYCLE_V = 0, MLMC_CYCLE_K = 1 };
 enum { MLMC_ALLOC_RHO = 0, MLMC_ALLOC_OPTIMAL = 1, MLMC_ALLOC_FIXED = 2 };
+enum { MLMC_COST_COUNTED = 0, MLMC_COST_NOMINAL = 1 };
 enum { MLMC_TRANSFER_AGGREGATION = 0, MLMC_TRANSFER_BILINEAR = 1 };
 
 /* Fine operator A = A_1 (Examples 5.1 and 5.3).  Sites s = j*nx + i. */
@@ -150,6 +151,14 @@ typedef struct {
                           MLMC_ALLOC_FIXED: exactly n_fixed[l] samples on level difference l
                           (serving requests with a fixed sample budget; eps unused)            */
   int n_fixed[16];
+  int cost_model;      /* per-sample cost C_l of MLMC_ALLOC_OPTIMAL (Sec. 5 cost model, nnz(B)
+                          per product B x): MLMC_COST_COUNTED (0) = the products the samples'
+                          solves actually performed (iteration counts included), averaged
+                          over the samples drawn; MLMC_COST_NOMINAL (1) = a fixed figure per
+                          level difference that does not depend on the solver: the
+                          restrictions the noise needs (nnz(P_j) each) plus one product with
+                          each operator solved with (nnz(A_l), nnz(A_{l+1}); n_L^2 for the
+                          coarsest dense inverse).  N_l then depends on the samples alone.   */
 } mlmc_estimate_params;
 
 typedef struct {

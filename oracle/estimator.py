@@ -16,6 +16,13 @@ Estimate (Sec. 2): sum over levels of the sample means plus the exact term;
 variance sum_l V_l / N_l with V_l the unbiased sample variance of |s - mean|^2
 (complex variance convention of Sec. 3).
 
+Optimal allocation (Sec. 2), run adaptively (``optimal_trace_estimate``):
+after the first block of every level, repeatedly set
+N_l = max(5, ceil(sqrt(V_l / C_l) sum_j sqrt(V_j C_j) / (eps tau)^2)) from the
+current variance estimates V_l and per-sample costs C_l (the Sec. 5 cost
+model), draw a block on every level below its count, and stop when no level
+is below its count and sum_l V_l / N_l <= (eps tau)^2.
+
 Stopping rule (Sec. 5): five full estimates t_1..t_5 (one sample per level
 difference plus the exact term) give tau = mean(t) - rms(t - mean(t)) (real
 parts).  They are samples 0..4 of each level's noise stream, taken from the
@@ -120,6 +127,7 @@ class EstimateResult:
     means: List[complex]
     variances: List[float]
     warmup: List[complex]
+    weights: Optional[List[float]] = None     # optimal allocation: w_l = sqrt(V_l C_l) / sum_j sqrt(V_j C_j)
 
 
 def optimal_allocation(variances, costs, target, min_samples=5):
@@ -179,3 +187,122 @@ def trace_estimate(levels, kind, seed=0, eps=1e-3, weights=None, block=64, min_s
     se = np.sqrt(sum(a.var() / a.n for a in acc))
     return EstimateResult(est, se, tau, TL, [a.n for a in acc], [a.mean() for a in acc],
                           [a.var() for a in acc], list(warm))
+
+
+def nominal_sample_cost(levels, l, form="simplified"):
+    """Cost of one sample of level difference l (1-based) in the Sec. 5 cost
+    model, where a product B x costs nnz(B), counted without the solver's
+    iteration counts: the restrictions the sample's noise goes through (each
+    R_j = P_j^* costs nnz(P_j)), plus one product with each operator the sample
+    solves with; the coarsest level is solved with its dense inverse, n_L^2
+    entries.  An optimal multigrid solve costs a level-independent multiple of
+    one product with its operator, and a common factor cancels in the optimal
+    N_l of Sec. 2.
+
+    simplified form: R_l x, then solves on levels l and l+1;
+    hat form:        R^_l x and R^_{l+1} x = R_l ... R_1 x, i.e. P_1 .. P_l;
+    plain form:      one solve on level 1."""
+    L = len(levels)
+
+    def solve(i):                         # 0-based level
+        if i == L - 1:
+            return float(levels[i].n) ** 2
+        return float(levels[i].A.count_nonzero())
+
+    if form == "plain":
+        return solve(0)
+    i = l - 1
+    c = solve(i) + solve(i + 1)
+    for j in (range(i + 1) if form == "hat" else [i]):
+        c += float(levels[j].P.count_nonzero())
+    return c
+
+
+def optimal_trace_estimate(levels, kind, seed=0, eps=1e-3, widths=64, min_samples=5, max_samples=1 << 24,
+                           form="simplified", solvers=None, costs=None):
+    """Sec. 2's optimal sample allocation, with V_l and C_l estimated as the samples arrive.
+
+    widths: samples per block, one value for every level difference or a list (the
+    last value repeats).  costs: per-sample cost C_l of every level difference;
+    default ``nominal_sample_cost``.  Steps:
+      1. the exact coarsest term T_L (Remark 4.2);
+      2. every level difference draws blocks until it holds 5 samples; samples 0..4 of
+         each level plus T_L are the five full estimates that give tau (Sec. 5);
+      3. target T = eps |tau|;
+      4. repeat: with S = sum_j sqrt(V_j C_j) from the current unbiased variances,
+         go through the levels in order; level l wants
+         N_l* = max(min_samples, ceil(sqrt(V_l / C_l) S / T^2)) (Sec. 2, reading the
+         multiplier from the constraint, see ``optimal_allocation``) and draws one block
+         if it holds fewer (and fewer than max_samples).  When no level drew and
+         sum_l V_l / N_l <= T^2 (variances as they stood before the pass) the estimate
+         stops.  When no level drew but the sum is above T^2 (only possible when a level
+         is held at max_samples), one block goes to the level whose next block lowers
+         sum V/N most per unit of cost, and when no level can draw any more, it stops."""
+    L = len(levels)
+    solvers = solvers or LevelSolvers(levels)
+    hats = None
+    if form == "hat":
+        hats = [accumulated_prolongation(levels, l) for l in range(1, L + 1)]
+    if form == "plain":
+        nd, TL = 1, 0.0
+    else:
+        nd, TL = L - 1, exact_coarse_trace(levels, form)
+    if isinstance(widths, int):
+        widths = [widths]
+    width = [int(widths[min(i, len(widths) - 1)]) for i in range(nd)]
+    if costs is None:
+        costs = [nominal_sample_cost(levels, l, form) for l in range(1, nd + 1)]
+    C = [float(c) for c in costs]
+    acc = [Accumulator() for _ in range(nd)]
+
+    def draw(i):
+        k = min(width[i], max_samples - acc[i].n)
+        if k <= 0:
+            return False
+        acc[i].add(level_samples(levels, solvers, i + 1, kind, seed, acc[i].n, k, form, PURPOSE_NOISE, hats))
+        return True
+
+    for i in range(nd):
+        while acc[i].n < 5:
+            if not draw(i):
+                raise ValueError("max_samples allows fewer than five samples per level")
+    warm = np.zeros(5, dtype=np.complex128) + TL
+    for a in acc:
+        warm += np.asarray(a.values[:5])
+    tr = warm.real
+    tau = tr.mean() - np.sqrt(np.mean((tr - tr.mean()) ** 2))
+    T2 = (eps * abs(tau)) ** 2
+    w = [0.0] * nd
+    while True:
+        V = [a.var() for a in acc]
+        S = 0.0
+        for i in range(nd):
+            S += np.sqrt(V[i] * C[i])
+        drew, total = False, 0.0
+        for i in range(nd):
+            want = max(float(min_samples), np.ceil(np.sqrt(V[i] / C[i]) * S / T2))
+            w[i] = np.sqrt(V[i] * C[i]) / S
+            total += V[i] / acc[i].n
+            if acc[i].n < want and acc[i].n < max_samples:
+                drew = True
+                draw(i)
+        if drew:
+            continue
+        if total <= T2:
+            break
+        best, gain = -1, -1.0
+        for i in range(nd):
+            n, v = acc[i].n, acc[i].var()
+            k = min(width[i], max_samples - n)
+            if k <= 0:
+                continue
+            g = (v / n - v / (n + k)) / (C[i] * k)
+            if g > gain:
+                best, gain = i, g
+        if best < 0:
+            break
+        draw(best)
+    est = TL + sum(a.mean() for a in acc)
+    se = np.sqrt(sum(a.var() / a.n for a in acc))
+    return EstimateResult(est, se, tau, TL, [a.n for a in acc], [a.mean() for a in acc],
+                          [a.var() for a in acc], list(warm), list(w))

@@ -237,20 +237,54 @@ int read_nactive(H_t &h, Krylov &K) {
   return K.h_nactive;
 }
 
-// nnz of A_l: Example 5.1 (5n - 2nx - 2ny with Dirichlet), Example 5.3 (9 per row),
-// dense d x d blocks in 5 directions on coarse levels
-double nnz_of(const H_t &h, int l) {
-  const Level &L = h.lv[l];
-  if (l == 0 && h.const_laplace) return 5.0 * L.n - (h.periodic ? 0.0 : 2.0 * (L.nx + L.ny));
-  if (l == 0 && h.complex_op) return 9.0 * L.n;
-  if (L.taps == 9) return (3.0 * L.nx - 2.0) * (3.0 * L.ny - 2.0);      // Table 1: (3 N_l - 2)^2
-  return 5.0 * L.nsite * L.d * L.d;
+// Number of (site, coupled site) pairs of a nearest-neighbour stencil on an
+// nx x ny lattice: the site itself and its distinct +-x, +-y neighbours
+// (Dirichlet: neighbours off the lattice are absent; periodic: on sides of 1
+// or 2 sites the neighbours coincide with the site or with each other).
+double site_pairs(int nx, int ny, int periodic) {
+  auto axis = [&](int n) {               // distinct neighbours other than the site, summed over a line
+    if (!periodic) return 2.0 * n - 2.0;
+    return n >= 3 ? 2.0 * n : n == 2 ? 2.0 : 0.0;
+  };
+  return (double)nx * ny + axis(nx) * ny + axis(ny) * nx;
 }
 
-// nnz(P_l): the cost-model weight of one restriction or prolongation per column
+// nnz of A_l: Example 5.1 (5n - 2nx - 2ny with Dirichlet), Example 5.3 (9 per row:
+// a diagonal self block and four full 2 x 2 hopping blocks), Table 1's 9-point
+// levels, and full d x d blocks for every coupled site pair on coarse levels
+double nnz_of(const H_t &h, int l) {
+  const Level &L = h.lv[l];
+  if (l == 0 && h.const_laplace) return site_pairs(L.nx, L.ny, h.periodic);
+  if (l == 0 && h.complex_op) return 2.0 * L.nsite + 4.0 * (site_pairs(L.nx, L.ny, 1) - L.nsite);
+  if (L.taps == 9) return (3.0 * L.nx - 2.0) * (3.0 * L.ny - 2.0);      // Table 1: (3 N_l - 2)^2
+  return site_pairs(L.nx, L.ny, h.periodic) * L.d * L.d;
+}
+
+// nnz(P_l): the cost-model weight of one restriction or prolongation per column.
+// Aggregation: every fine dof row holds the dc columns of its aggregate, or
+// half of them with the spin split (each column lives on one spin half).
 double nnz_P(const H_t &h, int l) {
   if (h.bilinear) return 9.0 * (double)h.lv[l + 1].n;     // three 1-D weights per coarse point and direction
-  return (double)h.lv[l].n * h.lv[l].dc;
+  return (double)h.lv[l].n * h.lv[l].dc / (h.prm.spin_split ? 2.0 : 1.0);
+}
+
+// Nominal cost of one sample of level difference l (0-based) in the Sec. 5
+// cost model, independent of how many iterations the solves take: the
+// restrictions the sample's noise needs, then one product with each operator
+// it solves with (the multigrid solve costs a level-independent multiple of
+// that for an optimal solver), the dense inverse of the coarsest level
+// counting n_L^2.
+double nominal_sample_cost(const H_t &h, int l, int form) {
+  auto solve_cost = [&](int lev) {
+    return lev == h.L - 1 ? (double)h.lv[lev].n * h.lv[lev].n : nnz_of(h, lev);
+  };
+  if (form == MLMC_FORM_PLAIN) return solve_cost(0);
+  double c = solve_cost(l);
+  if (l + 1 < h.L) c += solve_cost(l + 1);
+  const int restrictions = form == MLMC_FORM_HAT ? l + 1 : 1;   // R^_l x, R^_{l+1} x  /  R_l x
+  for (int j = (form == MLMC_FORM_HAT ? 0 : l); j < (form == MLMC_FORM_HAT ? restrictions : l + 1); ++j)
+    if (j + 1 < h.L) c += nnz_P(h, j);
+  return c;
 }
 
 void apply_op(H_t &h, int l, int lo, const void *x, void *y, int k) {
@@ -1462,6 +1496,8 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
     if (p->allocation == MLMC_ALLOC_FIXED)
       for (int l = 0; l < h->L - 1; ++l)
         if (p->n_fixed[l] < 5) fail(MLMC_ERR_INVALID_ARG, "n_fixed must be >= 5 on every level difference");
+    if (p->cost_model != MLMC_COST_COUNTED && p->cost_model != MLMC_COST_NOMINAL)
+      fail(MLMC_ERR_INVALID_ARG, "unknown cost model");
     H_t &H = *h;
     const int L = H.L, nd = plain ? 1 : L - 1;
     std::memset(r, 0, sizeof(*r));
@@ -1493,7 +1529,9 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
     DevBuf accs;
     accs.alloc((size_t)nd * 4 * sizeof(double));
     check_cuda(cudaMemsetAsync(accs.p, 0, (size_t)nd * 4 * sizeof(double), H.stream), "memset acc");
-    std::vector<double> st((size_t)nd * 4, 0.0), cost(nd, 0.0), secs(nd, 0.0);
+    std::vector<double> st((size_t)nd * 4, 0.0), cost(nd, 0.0), secs(nd, 0.0), nominal(nd, 0.0);
+    for (int l = 0; l < nd; ++l) nominal[l] = nominal_sample_cost(H, l, p->form);
+    const bool nominal_cost = p->cost_model == MLMC_COST_NOMINAL;
     std::vector<mlmc_c64> tmp(std::max(5, H.kbig));
     double warm[5];
     for (int i = 0; i < 5; ++i) warm[i] = TL.re;
@@ -1518,7 +1556,7 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
       check_cuda(cudaMemcpyAsync(&st[4 * l], accs.as<double>() + 4 * l, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                                  H.stream), "D2H acc");
       check_cuda(cudaStreamSynchronize(H.stream), "sync");
-      cost[l] += H.cost - c0;
+      cost[l] += nominal_cost ? nominal[l] * k : H.cost - c0;
       secs[l] += std::chrono::duration<double>(std::chrono::steady_clock::now() - tl).count();
       return true;
     };

@@ -23,6 +23,7 @@ PREC_FP64, PREC_MIXED_FP32 = 0, 1
 FORM_SIMPLIFIED, FORM_HAT, FORM_PLAIN = 0, 1, 2
 CYCLE_V, CYCLE_K = 0, 1
 ALLOC_RHO, ALLOC_OPTIMAL, ALLOC_FIXED = 0, 1, 2
+COST_COUNTED, COST_NOMINAL = 0, 1
 DENSE_SIMT, DENSE_TC, DENSE_TC_WITHHOLD, DENSE_AUTO = 0, 1, 2, 3
 TRANSFER_AGGREGATION, TRANSFER_BILINEAR = 0, 1
 
@@ -55,7 +56,7 @@ class EstimateParams(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("weights", ctypes.c_double * 16), ("noise", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("tol", ctypes.c_double), ("min_samples", ctypes.c_int),
                 ("max_samples", ctypes.c_int), ("form", ctypes.c_int), ("allocation", ctypes.c_int),
-                ("n_fixed", ctypes.c_int * 16)]
+                ("n_fixed", ctypes.c_int * 16), ("cost_model", ctypes.c_int)]
 
 
 class EstimateResult(ctypes.Structure):
@@ -254,9 +255,10 @@ class Hierarchy:
         return complex(out.re, out.im)
 
     def trace_estimate(self, eps=1e-3, noise=NOISE_RADEMACHER, seed=0, tol=1e-10, weights=None, min_samples=5,
-                       max_samples=1 << 24, form=FORM_SIMPLIFIED, allocation=ALLOC_RHO, n_fixed=None):
+                       max_samples=1 << 24, form=FORM_SIMPLIFIED, allocation=ALLOC_RHO, n_fixed=None,
+                       cost_model=COST_COUNTED):
         p = EstimateParams(eps=eps, noise=noise, seed=seed, tol=tol, min_samples=min_samples,
-                           max_samples=max_samples, form=form, allocation=allocation)
+                           max_samples=max_samples, form=form, allocation=allocation, cost_model=cost_model)
         if n_fixed is not None:
             for i, n in enumerate(n_fixed):
                 p.n_fixed[i] = n
@@ -345,9 +347,9 @@ def trace_estimate_batch(hierarchies, params, workers=4):
 
 
 def estimate_params(eps=1e-3, noise=NOISE_RADEMACHER, seed=0, tol=1e-8, allocation=ALLOC_OPTIMAL, weights=None,
-                    min_samples=5, max_samples=1 << 24, n_fixed=None):
+                    min_samples=5, max_samples=1 << 24, n_fixed=None, cost_model=COST_COUNTED):
     p = EstimateParams(eps=eps, noise=noise, seed=seed, tol=tol, min_samples=min_samples, max_samples=max_samples,
-                       form=FORM_SIMPLIFIED, allocation=allocation)
+                       form=FORM_SIMPLIFIED, allocation=allocation, cost_model=cost_model)
     if n_fixed is not None:
         for i, n in enumerate(n_fixed):
             p.n_fixed[i] = n

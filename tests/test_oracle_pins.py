@@ -333,6 +333,101 @@ def test_stopping_rule_closed_form(monkeypatch):
         assert abs(r.std_err - se) <= 1e-12 * se
 
 
+def test_nominal_sample_cost_hand_counts():
+    """Sec. 5 cost model (a product B x costs nnz(B)) of one sample, counted by hand.
+    64^2 Dirichlet Laplacian, 2 levels, piecewise-constant P: nnz(A_1) = 5*4096 - 4*64
+    (Example 5.1), n_2 = 256 so the coarsest dense inverse has 256^2 entries, and P_1
+    has one entry per fine row.  32^2 with 4 test vectors and 3 levels: level 2 is 8^2
+    sites of 4 dofs with full 4 x 4 blocks for each of the 5*64 - 4*8 coupled site
+    pairs, P_1 has 4 entries per fine row, P_2 4 per level-2 row, n_3 = 2*2*4 = 16."""
+    lv = build_hierarchy(laplace2d(64, 64), 64, 64, 1, SetupParams(levels=2, n_tv=1, kind="constant"))
+    assert E.nominal_sample_cost(lv, 1) == 20224 + 65536 + 4096
+    assert E.nominal_sample_cost(lv, 1, "plain") == 20224
+    lv = build_hierarchy(laplace2d(32, 32), 32, 32, 1, SetupParams(levels=3, n_tv=4, sweeps=5, coarse_sweeps=3,
+                                                                     bootstrap=0))
+    a1, a2, p1, p2 = 5 * 1024 - 4 * 32, 16 * (5 * 64 - 4 * 8), 1024 * 4, 256 * 4
+    assert E.nominal_sample_cost(lv, 1) == a1 + a2 + p1
+    assert E.nominal_sample_cost(lv, 2) == a2 + 16 ** 2 + p2
+    assert E.nominal_sample_cost(lv, 2, "hat") == a2 + 16 ** 2 + p1 + p2
+
+
+def _constant_variance_stream(mu, V, width):
+    """Samples of one level difference whose unbiased variance is exactly V after every
+    whole block of `width` (even) samples and whose mean is exactly mu: within block m
+    the values are mu + a_m (-1)^j, a_0 = sqrt(V (width - 1) / width), a_m = sqrt(V) after
+    (each block has mean mu, so the sums of squared deviations add: V (width - 1) for
+    the first block, V width for every further one)."""
+    a0 = np.sqrt(V * (width - 1) / width)
+
+    def values(first, count):
+        i = np.arange(first, first + count)
+        a = np.where(i < width, a0, np.sqrt(V))
+        return mu + a * (-1.0) ** (i % width) + 0j
+    return values, a0
+
+
+def test_optimal_allocation_loop_closed_form(monkeypatch):
+    """Sec. 2 optimal allocation, run adaptively, on sample streams with constant variances
+    V_l and fixed per-sample costs C_l.  The five full estimates are m + A (-1)^i with
+    m = T_L + sum mu_l and A = sum a_0,l, so tau = m + A/5 - sqrt(0.96) A (Sec. 5).  The
+    optimum of Sec. 2 for the target T = eps tau is N_l* = sqrt(V_l / C_l) S / T^2 with
+    S = sum_j sqrt(V_j C_j); whole blocks are drawn until N_l >= max(5, ceil(N_l*)), at
+    which point sum V_l / N_l <= T^2 holds, so each level ends at the first block multiple
+    at or above that count; the estimate is exactly m and the weights are
+    sqrt(V_l C_l) / S.  A multiplier read as printed (sqrt(V_j / C_j) in S), V and C
+    swapped, or a wrong tau changes the counts."""
+    TL = 50.0
+    for mu, V, C, widths, eps in [([10.0, 5.0], [400.0, 90.0], [1000.0, 30.0], [8, 16], 0.02),
+                                  ([3.0, 2.0, 1.0], [90.0, 60.0, 40.0], [5000.0, 400.0, 20.0], [6, 8, 16], 0.03)]:
+        streams = [_constant_variance_stream(m_, v, w) for m_, v, w in zip(mu, V, widths)]
+
+        def fake_samples(levels, solvers, l, kind, seed, first, count, form="simplified", purpose=0, hats=None):
+            return streams[l - 1][0](first, count)
+
+        monkeypatch.setattr(E, "level_samples", fake_samples)
+        monkeypatch.setattr(E, "exact_coarse_trace", lambda levels, form="simplified": TL)
+        r = E.optimal_trace_estimate([None] * (len(mu) + 1), "rademacher", eps=eps, widths=widths, costs=C,
+                                     solvers=object())
+        m, A = TL + sum(mu), sum(a0 for _, a0 in streams)
+        tau = m + A / 5 - np.sqrt(0.96) * A
+        assert abs(r.tau - tau) <= 1e-12 * tau
+        T2 = (eps * tau) ** 2
+        S = sum(np.sqrt(v * c) for v, c in zip(V, C))
+        for l in range(len(mu)):
+            need = max(5, int(np.ceil(np.sqrt(V[l] / C[l]) * S / T2)))
+            want = widths[l] * max(1, -(-need // widths[l]))
+            assert r.n_samples[l] == want
+            assert abs(r.variances[l] - V[l]) <= 1e-9 * V[l]
+            assert abs(r.weights[l] - np.sqrt(V[l] * C[l]) / S) <= 1e-12
+        assert abs(r.trace - m) <= 1e-12 * m
+        assert r.std_err ** 2 <= T2 * (1 + 1e-12)
+        assert any(n > w for n, w in zip(r.n_samples, widths))      # the loop did draw beyond the pilot
+
+
+def test_optimal_allocation_loop_one_level_reestimates(monkeypatch):
+    """One level difference with s_i = mu + sigma (-1)^i: after an even count N the unbiased
+    variance is N sigma^2 / (N - 1), so V changes as samples arrive.  With one level Sec. 2
+    gives N* = V / T^2 (S = sqrt(V C)), independent of C; the loop stops at the first
+    block multiple N with N >= ceil(N sigma^2 / ((N - 1) T^2))."""
+    mu, sigma, TL, block, eps = 4.0, 2.0, 30.0, 8, 0.01
+
+    def fake_samples(levels, solvers, l, kind, seed, first, count, form="simplified", purpose=0, hats=None):
+        i = np.arange(first, first + count)
+        return mu + sigma * (-1.0) ** i + 0j
+
+    monkeypatch.setattr(E, "level_samples", fake_samples)
+    monkeypatch.setattr(E, "exact_coarse_trace", lambda levels, form="simplified": TL)
+    for C in (1.0, 1e6):
+        r = E.optimal_trace_estimate([None, None], "rademacher", eps=eps, widths=block, costs=[C], solvers=object())
+        tau = (TL + mu) + sigma / 5 - np.sqrt(0.96) * sigma
+        T2 = (eps * tau) ** 2
+        n = block
+        while n < np.ceil(n * sigma ** 2 / ((n - 1) * T2)):
+            n += block
+        assert r.n_samples == [n]
+        assert abs(r.trace - (TL + mu)) <= 1e-12 * (TL + mu)
+
+
 # ---------------------------------------------------------------- learned correction (no paper basis)
 @pytest.mark.parametrize("case", ["wilson", "laplace"])
 def test_learned_gradient_matches_finite_differences(case):
