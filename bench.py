@@ -97,6 +97,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the config-4 leg (Wilson 256^2 with and without the learned correction)")
     ap.add_argument("--profile-sample", action="store_true",
                     help="for ncu only: after setup, one warm block and one profiled 64-sample block per level "
                          "difference inside cudaProfilerStart/Stop; prints no bench line")
@@ -115,7 +117,7 @@ def parse():
                          "workload: seconds, device-counted cost (Sec. 5 model) and N per method; one JSON line")
     ap.add_argument("--alloc", default="optimal", choices=["optimal", "rho"],
                     help="Sec. 2 optimal allocation (default) or the Sec. 5 equal rho split")
-    ap.add_argument("--cost-model", default="counted", choices=["counted", "nominal"],
+    ap.add_argument("--cost-model", default="nominal", choices=["counted", "nominal"],
                     help="per-sample cost C_l of the optimal allocation: products the solves performed "
                          "(counted) or one product per operator solved with (nominal, solver-independent)")
     return ap.parse_args()
@@ -203,92 +205,210 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(result, w):
-    """Oracle (FP64 CPU, as it stands) on a bounded sample of the workload.
+def host_info():
+    """Host cores and CPU model of the machine the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
-    The sample: the oracle's own hierarchy for the workload, then per level l
-    a few FGMRES iterations (preconditioned by the oracle's K-cycle), timed,
-    and ten products with the dense coarsest inverse.  Extrapolation:
-    seconds per cycle x cycles per solve x (N_l + 5), with N_l and the cycles
-    per solve of the same estimator on the same inputs (taken from the GPU
-    result, which matches the oracle sample by sample)."""
+
+def oracle_levels(w):
+    """The oracle's FP64 hierarchy of workload w, built on the host."""
     from oracle.hierarchy import SetupParams, build_hierarchy
     from oracle.operators import laplace2d, wilson2d
-    from oracle.philox import noise
-    from oracle.solver import Cycle, dense_inverse, fgmres
-    t0 = time.time()
+    if w.get("transfer") == "bilinear":
+        from oracle.bilinear import build_bilinear_hierarchy
+        return build_bilinear_hierarchy(w["nx"], w["levels"])
     if w["kind"] == "laplace":
-        A, d = laplace2d(w["nx"], w["ny"]), 1
+        A, d = laplace2d(w["nx"], w["ny"], w.get("shift", 0.0)), 1
     else:
         from paper_2108_11281_gb300.workloads import gauge_links
         A, d = wilson2d(w["nx"], w["ny"], w["mass"], gauge_links(w["nx"], w["ny"], w["link_sd"], w["link_seed"])), 2
-    if w.get("transfer") == "bilinear":
-        from oracle.bilinear import build_bilinear_hierarchy
-        lv = build_bilinear_hierarchy(w["nx"], w["levels"])
-    else:
-        lv = build_hierarchy(A, w["nx"], w["ny"], d, SetupParams(
-            levels=w["levels"], n_tv=w["n_tv"], spin_split=bool(w["spin_split"]), kind=w["setup"],
-            sweeps=w["setup_sweeps"], coarse_sweeps=w["coarse_sweeps"], omega=w["omega"],
-            noise_kind="z4" if w["kind"] == "wilson" else "rademacher", bootstrap=w["bootstrap"],
-            boot_iters=w["boot_iters"], smooth_pre=w["smooth_pre"], smooth_post=w["smooth_post"],
-            kcycle_its=w["kcycle_its"]))
-    setup_s = time.time() - t0
-    per_it = []
-    its_probe = 8
-    for l in range(len(lv) - 1):
-        M = Cycle(lv, l, w["smooth_pre"], w["smooth_post"], "K", w["kcycle_its"])
-        b = noise(lv[l].n, w["noise"], 1, l + 1, 0)
-        t = time.time()
-        fgmres(lv[l].A, b, M, tol=0.0, m=its_probe, maxit=its_probe)
-        per_it.append((time.time() - t) / its_probe)
+    if w["setup"] == "constant":
+        return build_hierarchy(A, w["nx"], w["ny"], d, SetupParams(levels=w["levels"], n_tv=1, kind="constant"))
+    return build_hierarchy(A, w["nx"], w["ny"], d, SetupParams(
+        levels=w["levels"], n_tv=w["n_tv"], spin_split=bool(w["spin_split"]), kind=w["setup"],
+        sweeps=w["setup_sweeps"], coarse_sweeps=w["coarse_sweeps"], omega=w["omega"],
+        noise_kind="z4" if w["kind"] == "wilson" else "rademacher", bootstrap=w["bootstrap"],
+        boot_iters=w["boot_iters"], smooth_pre=w["smooth_pre"], smooth_post=w["smooth_post"],
+        kcycle_its=w["kcycle_its"]))
+
+
+# per worker process of the oracle pool (spawned: the parent may already hold a CUDA context)
+_POOL = {}
+
+
+def _pool_init(levels, w, tol):
+    _POOL.clear()
+    _POOL.update(levels=levels, w=w, tol=tol, cycles={})
+
+
+def _oracle_sample(task):
+    """One level-difference sample (simplified form, Remark 4.3) with the oracle's own solver:
+    FGMRES(30) preconditioned by one K-cycle (oracle/solver.py) to the workload's tolerance on
+    level l, the same on level l+1 or the dense inverse on the coarsest level.  Returns
+    (level, sample index, value, seconds); the cycle's set-up is not timed."""
+    from oracle.philox import noise
+    from oracle.solver import Cycle, dense_inverse, fgmres
+    import numpy as np
+    l, j, seed = task
+    lv, w, tol, cyc = _POOL["levels"], _POOL["w"], _POOL["tol"], _POOL["cycles"]
     L = len(lv)
-    Ainv = dense_inverse(lv[-1].A)
-    xL = noise(lv[-1].n, w["noise"], 1, L, 0)
+    for i in (l - 1, l):
+        if i not in cyc:
+            cyc[i] = dense_inverse(lv[i].A) if i == L - 1 else \
+                Cycle(lv, i, w["smooth_pre"], w["smooth_post"], "K", w["kcycle_its"])
     t = time.time()
-    for _ in range(10):
-        Ainv @ xL
-    per_it.append((time.time() - t) / 10)
-    # the GPU reports outer iterations; each preconditions with inner_its cycles
-    cyc = [it * max(1, w["inner_its"]) for it in result["iters"]]
-    total = 0.0
-    for l in range(L - 1):
-        n_l = result["n_samples"][l] + 5          # + the five warm-up estimates
-        it_next = cyc[l + 1] if l + 1 < L - 1 else 1.0
-        total += n_l * (cyc[l] * per_it[l] + it_next * per_it[l + 1])
-    return {"value": total, "unit": "s (extrapolated)", "cores": 1, "kind": "oracle",
-            "sample": "oracle FGMRES+K-cycle: %d cycle iterations timed per level (%.1f s of CPU, setup %.1f s "
-                      "excluded); seconds/cycle x cycles/solve x (N_l + 5) of the same estimate" %
-                      (its_probe, sum(per_it) * its_probe, setup_s)}
+    x = noise(lv[l - 1].n, w["noise"], seed, l, j)
+    y = fgmres(lv[l - 1].A, x, cyc[l - 1], tol=tol, m=30, maxit=5000)[0]
+    z = lv[l - 1].P.conj().T @ x
+    if l == L - 1:
+        v = cyc[l] @ z
+    else:
+        v = fgmres(lv[l].A, z, cyc[l], tol=tol, m=30, maxit=5000)[0]
+    s = np.vdot(x, y) - np.vdot(z, v)
+    return l, j, complex(s), time.time() - t
 
 
-# per-level sample counts and mean outer iterations of each workload's estimate
-# (same estimator and noise on both sides, optimal allocation); used only by
-# the reference arm's extrapolation, which runs before any GPU number exists.
-REFERENCE = {"laplace1024": {"n_samples": [64, 128, 1024], "iters": [2.0, 3.0, 5.0]},
-             "wilson128": {"n_samples": [128, 896], "iters": [3.0, 3.0]},
-             "wilson256": {"n_samples": [32, 96], "iters": [3.0, 4.0]},
-             "laplace1023bil": {"n_samples": [64, 128, 128, 128, 128, 256], "iters": [2.0, 3.0, 2.0, 2.0, 2.0, 2.0]},
-             "laplace127bil": {"n_samples": [40, 80, 160], "iters": [2.0, 2.0, 2.0]}}
+def oracle_pool(levels, w, tol, procs):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(procs, initializer=_pool_init, initargs=(levels, w, tol))
+
+
+def oracle_plan(w, levels, pool, procs, seed):
+    """The oracle's own pilot (Sec. 5 and Sec. 2): samples 0..4 of every level difference,
+    computed concurrently on `procs` single-threaded processes, give tau, V_l and the seconds
+    per sample; N_l follows from the Sec. 2 optimal allocation with the nominal cost model.
+    Nothing here comes from the GPU."""
+    import numpy as np
+    from oracle import estimator as E
+    nd = len(levels) - 1
+    t0 = time.time()
+    res = pool.map(_oracle_sample, [(l, j, seed) for j in range(5) for l in range(1, nd + 1)], chunksize=1)
+    wall = time.time() - t0
+    TL = E.exact_coarse_trace(levels).real
+    vals = {l: [r[2] for r in res if r[0] == l] for l in range(1, nd + 1)}
+    secs = {l: [r[3] for r in res if r[0] == l] for l in range(1, nd + 1)}
+    t_est = np.array([TL + sum(vals[l][i] for l in vals).real for i in range(5)])
+    tau = t_est.mean() - np.sqrt(np.mean((t_est - t_est.mean()) ** 2))
+    V = [float(np.var(np.array(vals[l]), ddof=1)) for l in range(1, nd + 1)]
+    C = [E.nominal_sample_cost(levels, l) for l in range(1, nd + 1)]
+    _, counts, _ = E.optimal_allocation(V, C, w["eps"] * abs(tau))
+    return {"tau": float(tau), "variance": V, "n_samples": counts,
+            "sec_per_sample": [float(np.mean(secs[l])) for l in range(1, nd + 1)],
+            "pilot_wall_s": wall, "pilot_samples": 5 * nd, "procs": procs}
+
+
+def trace_seconds(plan):
+    """Seconds to trace: sum_l N_l x seconds per sample; the samples are independent, so
+    `procs` processes share them (per-sample times were measured with all of them busy)."""
+    one = sum(n * t for n, t in zip(plan["n_samples"], plan["sec_per_sample"]))
+    return one, one / plan["procs"]
+
+
+def config1_oracle(procs):
+    """Config 1 end to end with the oracle (measured, not extrapolated): 64^2 Dirichlet
+    Laplacian, 2 levels, piecewise-constant P, 1000 Rademacher samples (seed 0) at level 1,
+    tol 1e-10, plus the exact coarse term; once on one process, once on `procs`."""
+    import numpy as np
+    from oracle import estimator as E
+    w1 = dict(WORKLOADS["laplace1024"], nx=64, ny=64, levels=2, setup="constant", smooth_pre=1, smooth_post=1)
+    t0 = time.time()
+    lv = oracle_levels(w1)
+    tasks = [(1, j, 0) for j in range(1000)]
+    _pool_init(lv, w1, 1e-10)
+    vals = [_oracle_sample(tk)[2] for tk in tasks]
+    one = time.time() - t0
+    pool = oracle_pool(lv, w1, 1e-10, procs)
+    try:
+        pool.map(_oracle_sample, tasks[:procs], chunksize=1)          # workers up and warm
+        t0 = time.time()
+        par = pool.map(_oracle_sample, tasks, chunksize=8)
+        allc = time.time() - t0
+    finally:
+        pool.close()
+        pool.join()
+    trace = E.exact_coarse_trace(lv).real + float(np.mean(np.array(vals).real))
+    assert all(a[2] == b for a, b in zip(par, vals))      # the same samples on one and on many processes
+    return {"workload": "laplace2d-64x64-L2-constP-1000samples", "seconds_1core": one, "seconds_all_cores": allc,
+            "procs": procs, "trace": trace, "closed_form": closed_form(w1), "measured": True}
+
+
+def cpu_baseline(w):
+    """The FP64 oracle (as it stands) on the host cores, with nothing taken from the GPU run:
+    its own hierarchy, its own pilot (five samples per level difference, concurrently on all
+    cores), N_l from its own variances (Sec. 2 allocation, nominal costs), seconds to trace
+    extrapolated as sum N_l x seconds per sample; and config 1 measured end to end."""
+    procs = max(1, min(os.cpu_count() or 1, 16))
+    t0 = time.time()
+    lv = oracle_levels(w)
+    setup_s = time.time() - t0
+    pool = oracle_pool(lv, w, w["tol_mixed"], procs)
+    try:
+        plan = oracle_plan(w, lv, pool, procs, w["seed"])
+    finally:
+        pool.close()
+        pool.join()
+    one, allc = trace_seconds(plan)
+    cfg1 = config1_oracle(procs)
+    return {"value": allc, "unit": "s (extrapolated)", "cores": procs, "kind": "oracle",
+            "single_core_s": one, "setup_s": setup_s, "plan": plan, "host": host_info(),
+            "config1_end_to_end": cfg1,
+            "sample": "oracle FP64 FGMRES(30)+K-cycle at tol %g: its own hierarchy (setup %.1f s, excluded), "
+                      "samples 0..4 of each level difference on %d processes (%.1f s wall); N_l %s from its "
+                      "own pilot (Sec. 2, nominal costs); value = sum N_l x s/sample / %d processes" %
+                      (w["tol_mixed"], setup_s, procs, plan["pilot_wall_s"], plan["n_samples"], procs)}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on the machine's host cores.  Setup:
+    the oracle's hierarchy and its own pilot (N_l, seconds per sample).  Each step is a bounded
+    sample of the workload: one level difference in rotation, one sample per process
+    concurrently; the step's value is the seconds to trace with that level's per-sample time
+    re-measured (the other levels' from their latest measurement)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w = WORKLOADS[args.workload]
+    procs = max(1, min(os.cpu_count() or 1, 16))
+    lv = oracle_levels(w)
+    pool = oracle_pool(lv, w, w["tol_mixed"], procs)
     steps = []
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(REFERENCE[args.workload], w)
-        if i >= args.warmup:
-            steps.append(cb["value"])
+    try:
+        plan = oracle_plan(w, lv, pool, procs, w["seed"])
+        nd = len(lv) - 1
+        nxt = 5
+        for i in range(args.warmup + args.steps):
+            l = 1 + i % nd
+            res = pool.map(_oracle_sample, [(l, nxt + q, w["seed"]) for q in range(procs)], chunksize=1)
+            nxt += procs
+            plan["sec_per_sample"][l - 1] = sum(r[3] for r in res) / len(res)
+            if i >= args.warmup:
+                steps.append(trace_seconds(plan)[1])
+    finally:
+        pool.close()
+        pool.join()
     v = statistics.mean(steps)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(config_dict("fp64-cpu-oracle", w), allocation=args.alloc),
-            "cpu_baseline": {"value": v, "unit": "s (extrapolated)", "kind": "oracle", "cores": 1,
-                             "sample": cb["sample"] + "; N_l and iterations per solve from "
-                                       "recorded values of this estimate"},
+            "cpu_baseline": {"value": v, "unit": "s (extrapolated)", "kind": "oracle", "cores": procs,
+                             "host": host_info(), "n_samples": plan["n_samples"],
+                             "sample": "oracle FP64 FGMRES(30)+K-cycle at tol %g; N_l %s from its own 5-sample "
+                                       "pilot (Sec. 2, nominal costs); each step re-times one level "
+                                       "difference (one sample on each of %d processes); value = sum N_l x "
+                                       "s/sample / %d" % (w["tol_mixed"], plan["n_samples"], procs, procs)},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -516,6 +636,81 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def learned_leg(mlmc, stream, warmup, steps, seed=0):
+    """Config 4: Wilson 256^2 (theta ~ N(0, 0.4^2)), mixed form, with the learned correction
+    trained on the GPU (10^4 residual/error pairs from plain solves; training is setup) and
+    without it (plain multigrid smoother), the same warm-up and number of estimates timed
+    between CUDA events for both."""
+    import torch
+    w = WORKLOADS["wilson256"]
+    nz = mlmc.NOISE_Z4
+    t0 = time.time()
+    h = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, stream)
+    setup_s = time.time() - t0
+    t0 = time.time()
+    _, rep = h.learned_train(n_pairs=w["train_pairs"], epochs=w["train_epochs"], lr=w["train_lr"],
+                             tol=w["tol_mixed"], seed=7, enable=1)
+    train_s = time.time() - t0
+
+    def timed():
+        for _ in range(warmup):
+            h.trace_estimate(eps=w["eps"], noise=nz, seed=seed, tol=w["tol_mixed"], allocation=mlmc.ALLOC_OPTIMAL,
+                             cost_model=mlmc.COST_NOMINAL)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            r = mlmc.result_dict(h.trace_estimate(eps=w["eps"], noise=nz, seed=seed, tol=w["tol_mixed"],
+                                                  allocation=mlmc.ALLOC_OPTIMAL, cost_model=mlmc.COST_NOMINAL))
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / steps, r
+
+    net_on = h.learned_stats()[0]
+    t_net, r_net = timed()
+    fallbacks = h.learned_stats()[1]
+    h.learned_set(None, enable=0)
+    t_plain, r_plain = timed()
+    h.close()
+    return {"workload": w["name"], "train": dict(rep, seconds_total=train_s), "setup_s": setup_s,
+            "net_enabled": net_on, "fallbacks": fallbacks,
+            "with_net_s": t_net, "plain_s": t_plain, "speedup_plain_over_net": t_plain / t_net,
+            "with_net_iters": r_net["iters"], "plain_iters": r_plain["iters"],
+            "with_net_n_samples": r_net["n_samples"], "plain_n_samples": r_plain["n_samples"],
+            "trace_with_net": r_net["trace"].real, "trace_plain": r_plain["trace"].real,
+            "std_err": r_plain["std_err"], "steps": steps, "warmup": warmup}
+
+
+def gpu_config1(mlmc, stream, warmup, steps=3):
+    """Config 1 on the GPU, FP64 form: 64^2 Dirichlet Laplacian, 2 levels, piecewise-constant
+    P, exactly 1000 Rademacher samples (seed 0) at level 1 in blocks of 200, tol 1e-10, plus
+    the exact coarse term; setup outside, estimates between CUDA events after warm-up."""
+    import torch
+    prm = mlmc.default_params(levels=2, n_tv=1, setup_kind=mlmc.SETUP_CONSTANT, bootstrap=0,
+                              precision=mlmc.PREC_FP64, block=200, smooth_pre=1, smooth_post=1)
+    t0 = time.time()
+    h = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, 64, 64, prm, stream=stream)
+    setup_s = time.time() - t0
+
+    def one():
+        return mlmc.result_dict(h.trace_estimate(noise=mlmc.NOISE_RADEMACHER, seed=0, tol=1e-10,
+                                                 allocation=mlmc.ALLOC_FIXED, n_fixed=[1000]))
+    for _ in range(max(1, warmup)):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        r = one()
+    e1.record()
+    torch.cuda.synchronize()
+    h.close()
+    cf = closed_form(dict(kind="laplace", nx=64, ny=64))
+    return {"workload": "laplace2d-64x64-L2-constP-1000samples", "form": "fp64", "seconds": e0.elapsed_time(e1) / 1e3 / steps,
+            "setup_s": setup_s, "trace": r["trace"].real, "std_err": r["std_err"], "closed_form": cf,
+            "n_samples": r["n_samples"], "within_4se": abs(r["trace"].real - cf) <= 4 * r["std_err"]}
+
+
 def closed_form(w):
     """Example 5.1: tr(A^{-1}) = sum over the eigenvalues 4 + shift - 2cos(i pi/(N+1)) - 2cos(j pi/(N+1))
     (Dirichlet Laplacian; None for other operators)."""
@@ -570,12 +765,9 @@ def main():
         return mlmc.result_dict(hh.trace_estimate(eps=w["eps"], noise=nz, seed=seed, tol=tol,
                                                   allocation=alloc, form=form, cost_model=cost_model))
 
-    learned = None
     if w.get("learned"):
-        t = time.time()
-        _, rep = h.learned_train(n_pairs=w["train_pairs"], epochs=w["train_epochs"], lr=w["train_lr"],
-                                 tol=w["tol_mixed"], seed=7, enable=1)
-        learned = dict(rep, seconds_total=time.time() - t)
+        h.learned_train(n_pairs=w["train_pairs"], epochs=w["train_epochs"], lr=w["train_lr"],
+                        tol=w["tol_mixed"], seed=7, enable=1)
     seed = replica_seed(w["seed"], rank)    # replicas draw disjoint noise
     for _ in range(args.warmup):
         res = step(h, w["tol_mixed"], seed)
@@ -643,26 +835,24 @@ def main():
                 "achieved": dom["gbs"], "peak": peak, "unit": "GB/s", "frac": dom["gbs"] / peak,
                 "peak_source": peak_kind, "traffic": traffic, "algorithmic_bytes": dom["bytes"], "kernels": kern}
 
-    if learned is not None and rank == 0:
-        # the same mixed estimate without the network (plain multigrid smoother)
-        h.learned_set(None, enable=0)
-        torch.cuda.synchronize()
-        t = time.time()
-        rp = step(h, w["tol_mixed"], seed)
-        torch.cuda.synchronize()
-        learned["plain_mixed_seconds"] = time.time() - t
-        learned["plain_mixed_iters"] = rp["iters"]
-        learned["with_net_iters"] = res["iters"]
-        learned["with_net_seconds"] = t_step
     fp64 = None
     if not args.no_fp64_form and rank == 0:
+        # the plain FP64 form (FP64 cycle, FP64 tolerance), timed like the mixed form: the same
+        # warm-up estimates, then the same number of steps between CUDA events
         h.close()
         h64 = make_hierarchy(mlmc, mlmc.PREC_FP64, w, stream)
-        torch.cuda.synchronize()
-        t = time.time()
-        r64 = step(h64, w["tol_fp64"], seed)
-        torch.cuda.synchronize()
-        fp64 = {"seconds": time.time() - t, "unit": "s (one estimate, same allocation and noise)",
+        for _ in range(args.warmup):
+            step(h64, w["tol_fp64"], seed)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            r64 = step(h64, w["tol_fp64"], seed)
+        e1.record()
+        barrier()
+        fp64 = {"seconds": e0.elapsed_time(e1) / 1e3 / args.steps,
+                "unit": "s per estimate (%d warm-up, %d timed; same allocation and noise)" % (args.warmup, args.steps),
                 "trace": r64["trace"].real, "std_err": r64["std_err"],
                 "n_samples": r64["n_samples"], "iters": r64["iters"]}
         h64.close()
@@ -681,9 +871,14 @@ def main():
     torch.cuda.synchronize()
     e2e = time.time() - t
 
+    cfg1 = gpu_config1(mlmc, stream, args.warmup) if rank == 0 else None
+    # config 4 (Wilson 256^2): the learned correction against the plain smoother
+    learned = None
+    if rank == 0 and not args.no_learned:
+        learned = learned_leg(mlmc, stream, args.warmup, args.steps, seed)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(res, w)
+        cpu = cpu_baseline(w)
     if rank == 0:
         import ctypes
         line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -703,7 +898,7 @@ def main():
                            "closed_form": closed_form(w),
                            "coarse_term": res["coarse_term"].real, "n_samples": res["n_samples"],
                            "iters": res["iters"], "seconds_per_level": res["seconds"]},
-                "fp64_form": fp64, "learned": learned}
+                "fp64_form": fp64, "learned": learned, "config1": cfg1}
         if fp64 is not None:
             # the mixed form's trace against the plain FP64 form's on the same samples
             line["result"]["rel_diff_vs_fp64_form"] = abs(res["trace"].real - fp64["trace"]) / abs(fp64["trace"])

@@ -353,6 +353,12 @@ typedef struct {
   double seconds_capture, seconds_train;
 } mlmc_train_report;
 
+/* State of the learned correction: *enabled (1 when the network acts in the
+ * FP32 cycle) and *fallbacks (level solves that did not converge with it and
+ * were repeated without it, since the handle was created).  Either pointer may
+ * be NULL. */
+int mlmc_learned_stats(const mlmc_hierarchy *h, int *enabled, int *fallbacks);
+
 /* Capture residual/error pairs from plain multigrid solves (the error enters
  * through A e = r), train the network on the GPU (forward, backward, Adam),
  * validate, and install it.  weights_out (host, optional) receives n_weights floats. */

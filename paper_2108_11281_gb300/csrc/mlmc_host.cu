@@ -257,7 +257,7 @@ double nnz_of(const H_t &h, int l) {
   if (l == 0 && h.const_laplace) return site_pairs(L.nx, L.ny, h.periodic);
   if (l == 0 && h.complex_op) return 2.0 * L.nsite + 4.0 * (site_pairs(L.nx, L.ny, 1) - L.nsite);
   if (L.taps == 9) return (3.0 * L.nx - 2.0) * (3.0 * L.ny - 2.0);      // Table 1: (3 N_l - 2)^2
-  return site_pairs(L.nx, L.ny, h.periodic) * L.d * L.d;
+  return site_pairs(L.nx, L.ny, h.periodic || h.complex_op) * L.d * L.d;   // Wilson lattices are periodic
 }
 
 // nnz(P_l): the cost-model weight of one restriction or prolongation per column.
@@ -1744,6 +1744,14 @@ int mlmc_learned_set(mlmc_hierarchy *h, const float *weights, int enable) {
       check_cuda(cudaMemcpyAsync(h->netW.p, weights, h->net_nw * sizeof(float), cudaMemcpyHostToDevice, h->stream), "H2D W");
     check_cuda(cudaStreamSynchronize(h->stream), "sync");
     h->net_on = enable ? 1 : 0;
+  });
+}
+
+int mlmc_learned_stats(const mlmc_hierarchy *h, int *enabled, int *fallbacks) {
+  return translate([&] {
+    if (!h) fail(MLMC_ERR_INVALID_ARG, "null handle");
+    if (enabled) *enabled = h->net_on;
+    if (fallbacks) *fallbacks = h->net_fallbacks;
   });
 }
 

@@ -117,6 +117,7 @@ def _load():
         "mlmc_dense_apply": [i, vp, vp, vp, i, i, i, vp],
         "mlmc_level_taps": [vp, i, ctypes.POINTER(i)],
         "mlmc_set_dense_kernel": [vp, i],
+        "mlmc_learned_stats": [vp, ctypes.POINTER(i), ctypes.POINTER(i)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -136,7 +137,7 @@ EXPORTED = ["mlmc_setup_hierarchy", "mlmc_destroy_hierarchy", "mlmc_level_info",
             "mlmc_last_error", "mlmc_learned_train", "mlmc_learned_set", "mlmc_learned_apply", "mlmc_learned_grad",
             "mlmc_column_dots", "mlmc_column_dots_noalloc", "mlmc_noalloc_last_error", "mlmc_set_block_width",
             "mlmc_autotune_block", "mlmc_trace_estimate_batch", "mlmc_sample_level_form", "mlmc_dense_apply",
-            "mlmc_set_dense_kernel", "mlmc_level_taps"]
+            "mlmc_set_dense_kernel", "mlmc_level_taps", "mlmc_learned_stats"]
 
 
 def check(status):
@@ -292,6 +293,13 @@ class Hierarchy:
     def learned_set(self, weights, enable=1):
         w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
         check(lib.mlmc_learned_set(self.handle, None if w is None else w.ctypes.data, enable))
+
+    def learned_stats(self):
+        """(enabled, fallbacks): whether the network acts in the cycle, and how many level
+        solves were repeated without it because they did not converge with it."""
+        en, fb = ctypes.c_int(), ctypes.c_int()
+        check(lib.mlmc_learned_stats(self.handle, ctypes.byref(en), ctypes.byref(fb)))
+        return en.value, fb.value
 
     def learned_apply(self, r_ptr, e_ptr, k):
         check(lib.mlmc_learned_apply(self.handle, ctypes.c_void_p(r_ptr), ctypes.c_void_p(e_ptr), k))

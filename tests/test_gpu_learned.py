@@ -70,27 +70,62 @@ def test_forward_and_gradient_match_oracle(mlmc, case):
     h.close()
 
 
-def test_training_on_gpu_and_gain(mlmc):
-    """Train on residuals captured from plain solves of a 32x32 Wilson operator; the
-    network must lower its training loss, solves with it must still meet the FP64
-    tolerance, and the iteration counts with and without it are reported."""
+def wilson32(mlmc, max_iter=2000):
     N, k = 32, 16
     U = gauge_links(N, N, 0.3, 4)
     prm = mlmc.default_params(levels=3, n_tv=2, spin_split=1, setup_kind=mlmc.SETUP_INVERSE, setup_sweeps=8,
                               coarse_sweeps=4, setup_omega=1.0, precision=mlmc.PREC_MIXED_FP32, block=k,
-                              smooth_pre=1, smooth_post=1, inner_its=6, fgmres_restart=10)
-    h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.02, links=U)
+                              smooth_pre=1, smooth_post=1, inner_its=6, fgmres_restart=10, max_iter=max_iter)
+    return mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.02, links=U), wilson2d(N, N, 0.02, U), N, k
+
+
+def solve_checked(h, A, N, k, tol=1e-10, seed=0):
+    """Solve a seeded complex block on level 1 and check the FP64 true residual."""
+    n = N * N * 2
+    g = torch.Generator().manual_seed(seed)
+    b = torch.complex(torch.randn(n, k, generator=g, dtype=torch.float64),
+                      torch.randn(n, k, generator=g, dtype=torch.float64)).cuda()
+    x = torch.zeros_like(b)
+    its = h.solve(1, b.data_ptr(), x.data_ptr(), k, tol)
+    bn, xn = b.cpu().numpy(), x.cpu().numpy()
+    assert (np.linalg.norm(bn - A @ xn, axis=0) / np.linalg.norm(bn, axis=0)).max() <= tol
+    return its
+
+
+def test_training_on_gpu_and_gain(mlmc):
+    """Train on residuals captured from plain solves of a 32x32 Wilson operator
+    (m = 0.02, one pre- and one post-sweep, inner FGMRES(6)); the network must lower
+    its training loss, solves with it must still meet the FP64 tolerance, and on this
+    operator it must save outer iterations: fewer with it than without it."""
+    h, A, N, k = wilson32(mlmc)
     W, rep = h.learned_train(n_pairs=32 * k, epochs=4, lr=2e-3, tol=1e-6, seed=1, enable=1)
     assert rep["loss_last"] < rep["loss_first"]
     assert np.isfinite(W).all() and rep["n_weights"] == W.size
-    n = N * N * 2
-    b = torch.complex(torch.randn(n, k, dtype=torch.float64), torch.randn(n, k, dtype=torch.float64)).cuda()
-    x = torch.zeros_like(b)
-    its_net = h.solve(1, b.data_ptr(), x.data_ptr(), k, 1e-10)
-    A = wilson2d(N, N, 0.02, U)
-    bn, xn = b.cpu().numpy(), x.cpu().numpy()
-    assert (np.linalg.norm(bn - A @ xn, axis=0) / np.linalg.norm(bn, axis=0)).max() <= 1e-10
+    assert rep["enabled"] == 1 and h.learned_stats()[0] == 1
+    its_net = solve_checked(h, A, N, k)
     h.learned_set(None, enable=0)
-    its_plain = h.solve(1, b.data_ptr(), x.data_ptr(), k, 1e-10)
+    its_plain = solve_checked(h, A, N, k)
     print("learned: val_loss %.3f, outer iterations with net %d, without %d" % (rep["val_loss"], its_net, its_plain))
+    assert its_net < its_plain
+    assert h.learned_stats() == (0, 0)
+    h.close()
+
+
+def test_learned_fallback_to_plain_smoother(mlmc):
+    """The plain smoother is the fallback and the FP64 true residual the judge.  Weights
+    scaled up 100-fold make the correction useless: the solve with it does not converge
+    within max_iter, is repeated without it (the fallback count rises) and still meets
+    the tolerance.  All-zero weights add nothing: the same iterations as the plain cycle."""
+    h, A, N, k = wilson32(mlmc, max_iter=40)
+    its_plain = solve_checked(h, A, N, k)
+    assert its_plain < 40
+    nw = h.net_weights()
+    rng = np.random.default_rng(3)
+    h.learned_set(np.zeros(nw, dtype=np.float32), enable=1)
+    assert solve_checked(h, A, N, k) == its_plain
+    assert h.learned_stats() == (1, 0)
+    h.learned_set((100.0 * rng.standard_normal(nw)).astype(np.float32), enable=1)
+    solve_checked(h, A, N, k)
+    enabled, fallbacks = h.learned_stats()
+    assert enabled == 1 and fallbacks >= 1
     h.close()
