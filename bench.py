@@ -822,6 +822,22 @@ def main():
         flops = (8.0 if w["kind"] == "wilson" else 2.0) * nL * nL * kc
         kern[name] = {"ms": kms, "bytes": kbytes, "flops": flops, "tflops": flops / kms / 1e9, "n": nL, "k": kc}
     h.set_dense_kernel(mlmc.DENSE_AUTO)
+    # the transfers (Sec. 4.1 aggregation P_l and R_l = P_l^*) on every level pair, k = that
+    # level difference's block (the fine pair at the fine block width)
+    for lvl in range(1, w["levels"]):
+        kt = w["block"] if lvl == 1 else kcb
+        for name, which in (("restrict", 6), ("prolong", 7)):
+            kms, kbytes = h.profile_kernel(which, lvl, kt, 20)
+            kern["%s_fp32_level%d" % (name, lvl)] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6, "k": kt}
+    # the arithmetic ceilings the FP64 kernels meet: measured FMA rates
+    fma64 = mlmc.measure_fma_rate(True, stream)
+    fma32 = mlmc.measure_fma_rate(False, stream)
+    kern["fma_rate"] = {"fp64_tfma_s": fma64 / 1e12, "fp32_tfma_s": fma32 / 1e12}
+    # the FP64 fine-level apply: 4 FP64 operations per element (3 additions, 1 FMA)
+    st = kern["stencil_fp64"]
+    ops = 4.0 * w["nx"] * w["ny"] * w["block"] * (1 if w["kind"] == "laplace" else 36)
+    st["fp64_ops_per_s"] = ops / (st["ms"] * 1e-3)
+    st["alu_frac_of_measured_fma_rate"] = st["fp64_ops_per_s"] / fma64
     # dominant kernel of the timed step (largest share of the step's ncu launch list): the
     # coarse-level block Gauss-Seidel k_rbgs_half on level 2; one sweep = two launches
     dom_name = "rbgs_sweep_fp32_level2" if w["levels"] > 2 else "multidot_fp32"

@@ -286,6 +286,18 @@ int mlmc_dense_apply(int complex_data, const void *A, const void *B, void *Y, in
  * again on next use). */
 int mlmc_set_dense_kernel(mlmc_hierarchy *h, int which);
 
+/* Kernels of the learned correction's 3x3 convolutions (forward, backward-data,
+ * weight gradient) for this handle: MLMC_CONV_AUTO (the default) runs them on
+ * the tensor cores (tcgen05 implicit GEMMs, three TF32 products per term for
+ * FP32 accuracy, accumulators in tensor memory, every wait bounded) whenever
+ * the block width k is 8, 16, 32, 64 or 128 and the fine lattice's rows hold
+ * whole tiles of 128 / k sites (weight gradient: k a multiple of 8, at most
+ * 32 or a multiple of 32), else on the CUDA cores; MLMC_CONV_SIMT always on
+ * the CUDA cores.  A change drops the CUDA graphs captured for the inner
+ * solves. */
+enum { MLMC_CONV_SIMT = 0, MLMC_CONV_AUTO = 1 };
+int mlmc_set_conv_kernel(mlmc_hierarchy *h, int which);
+
 /* The exact coarsest term of the estimator (Remark 4.2), tr(A_L^{-1} R^_L P^_L)
  * from the FP64 dense inverse: tr(A_L^{-1}) when R^_L P^_L = I (aggregation). */
 int mlmc_coarse_trace_exact(mlmc_hierarchy *h, mlmc_c64 *out);
@@ -314,13 +326,22 @@ int mlmc_autotune_block(mlmc_hierarchy *h, int level, int noise, double tol, int
 int mlmc_trace_estimate_batch(mlmc_hierarchy *const *hs, int count, const mlmc_estimate_params *params, int workers,
                               mlmc_estimate_result *results, int *status);
 
+/* Measured arithmetic ceiling (the paper has no counterpart; a roofline
+ * denominator): fused multiply-adds per second of the whole GPU in FP64
+ * (fp64 = 1) or FP32 (fp64 = 0), from 8 independent FMA chains per thread on
+ * 8 blocks of 256 threads per SM, timed with CUDA events on `stream`.
+ * Allocates a small output buffer; synchronous on return. */
+int mlmc_measure_fma_rate(int fp64, void *stream, double *fma_per_s);
+
 /* Time one kernel family on level l with CUDA events on the hierarchy's
  * stream: which = 0 operator apply (FP64), 1 operator apply (FP32),
  * 2 red-black GS sweep, 3 column multi-dot of 4 basis blocks against w,
  * 4 multi-AXPY of 4 basis blocks into w, 5 coarsest dense apply
- * Y = A_L^-1 B (level = L; the kernel chosen by mlmc_set_dense_kernel)
- * (2-5 in the cycle precision).  k <= block on level 1, k <= max(block,
- * coarse_block) on the coarser levels.
+ * Y = A_L^-1 B (level = L; the kernel chosen by mlmc_set_dense_kernel),
+ * 6 restriction R_l = P_l^* from level l to l+1, 7 prolongation x += P_l e
+ * from level l+1 (2-7 in the cycle precision).  k <= block on level 1,
+ * k <= max(block, coarse_block) on the coarser levels (6, 7: also within
+ * level l+1's buffers).
  * Reports the average launch time and the algorithmic bytes one launch must
  * move (for 5: the dense inverse once plus B and Y; its FLOPs are
  * 2 n_L^2 k real, 8 n_L^2 k complex). */

@@ -28,15 +28,18 @@ __global__ void k_arnoldi_init(H *g, double *bnorm, double *invnrm, int *active,
                                double tol, int first, int *nactive, double *sc) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= k) return;
-  double beta = sqrt(fmax(creal_(g[c]), 0.0));
+  const double g0 = creal_(g[c]);
+  const bool finite = isfinite(g0);
+  double beta = finite ? sqrt(fmax(g0, 0.0)) : 0.0;
   if (first) bnorm[c] = beta;
   g[c] = hreal<H>(beta);
   jdone[c] = 0;
-  int a = beta > 0.0 && beta > tol * bnorm[c];
+  int a = finite && beta > 0.0 && beta > tol * bnorm[c];
   active[c] = a;
   invnrm[c] = a ? 1.0 / beta : 0.0;
   if (sc) sc[c] = beta > 0.0 ? beta : 1.0;
   if (a) atomicAdd(nactive, 1);
+  else if (!finite) atomicAdd(nactive, NONFINITE_COLUMN);    // a residual that is NaN or infinite
 }
 
 // Fixed-length FGMRES with unnormalised basis vectors u_i = s_i v_i (the scaling pass

@@ -314,6 +314,11 @@ void launch_conv_bwd_weight(int ci, int co, const float *in, const float *gout, 
   throw cuda_error{cudaErrorInvalidValue, "conv: unsupported channel counts"};
 }
 
+void launch_weight_reduce(const float *partial, int nblocks, int nw, float *grad, float scale, cudaStream_t s) {
+  k_weight_reduce<<<(nw + 127) / 128, 128, 0, s>>>(partial, nblocks, nw, grad, scale);
+  MLMC_LAUNCH_CHECK("k_weight_reduce");
+}
+
 void launch_adam(float *W, const float *g, float *m, float *v, int n, float lr, int step, cudaStream_t s) {
   const float b1 = 0.9f, b2 = 0.999f;
   float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);

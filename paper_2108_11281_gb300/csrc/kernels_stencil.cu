@@ -219,9 +219,51 @@ static void stencil_go(const StencilView &A, const void *x, const void *b, void 
 }
 
 // ------------------------------------------------------------------ Example 5.1, constant coefficients
-// y = diag x - (sum of the in-grid neighbours), VEC columns per thread with
-// 16-byte loads; grid.y = lattice row, so the +-y neighbours of a block are
-// the rows just touched by the blocks before it (L2 hits).
+// The four neighbours of site (i, j), each with a flag: present, or outside a
+// Dirichlet lattice (periodic lattices wrap).  Straight-line code: no array
+// indexed at run time, so nothing goes through local memory.
+struct Nbrs {
+  int s[4];
+  bool on[4];
+};
+
+__device__ __forceinline__ Nbrs laplace_nbrs(int i, int j, int nx, int ny, int periodic) {
+  Nbrs n;
+  const int s = j * nx + i;
+  n.on[0] = i + 1 < nx || periodic;
+  n.s[0] = i + 1 < nx ? s + 1 : j * nx;
+  n.on[1] = i > 0 || periodic;
+  n.s[1] = i > 0 ? s - 1 : j * nx + nx - 1;
+  n.on[2] = j + 1 < ny || periodic;
+  n.s[2] = j + 1 < ny ? s + nx : i;
+  n.on[3] = j > 0 || periodic;
+  n.s[3] = j > 0 ? s - nx : (ny - 1) * nx + i;
+  return n;
+}
+
+// Sum of the present neighbours' packs: (x_+x + x_-x) + (x_+y + x_-y), absent ones zero.
+template <class T, int VEC>
+__device__ __forceinline__ void laplace_nbr_sum(const Pack<T, VEC> *__restrict__ X, const Nbrs &n, int kv, int c,
+                                                T sum[VEC]) {
+  Pack<T, VEC> v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (n.on[q]) {
+      v[q] = X[(size_t)n.s[q] * kv + c];
+    } else {
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) v[q].v[u] = zero<T>();
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) sum[u] = (v[0].v[u] + v[1].v[u]) + (v[2].v[u] + v[3].v[u]);
+}
+
+// y = diag x - (sum of the in-grid neighbours) (mode 0) or r = b - that (mode 1),
+// VEC columns per thread with 16-byte loads; grid.y = lattice row, so the +-y
+// neighbours of a block are the rows just touched by the blocks before it (L2
+// hits).  Per element: three additions and one fused multiply-add (FP64 lanes
+// are the limit of the FP64 form on GB300).
 template <class T, int VEC>
 __global__ void __launch_bounds__(256) k_laplace(const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ y,
                                                  int nx, int ny, int kv, T diag, int periodic, int mode) {
@@ -232,29 +274,18 @@ __global__ void __launch_bounds__(256) k_laplace(const T *__restrict__ x, const 
   const int i = t / kv, c = t - (t / kv) * kv;
   const V *X = (const V *)x;
   const int s = j * nx + i;
+  const Nbrs n = laplace_nbrs(i, j, nx, ny, periodic);
   V xc = X[(size_t)s * kv + c];
-  T acc[VEC];
-#pragma unroll
-  for (int u = 0; u < VEC; ++u) acc[u] = diag * xc.v[u];
-  int nbs[4];
-  int cnt = 0;
-  if (i + 1 < nx) nbs[cnt++] = s + 1; else if (periodic) nbs[cnt++] = j * nx;
-  if (i > 0) nbs[cnt++] = s - 1; else if (periodic) nbs[cnt++] = j * nx + nx - 1;
-  if (j + 1 < ny) nbs[cnt++] = s + nx; else if (periodic) nbs[cnt++] = i;
-  if (j > 0) nbs[cnt++] = s - nx; else if (periodic) nbs[cnt++] = (ny - 1) * nx + i;
-  for (int q = 0; q < cnt; ++q) {
-    V xn = X[(size_t)nbs[q] * kv + c];
-#pragma unroll
-    for (int u = 0; u < VEC; ++u) acc[u] = acc[u] - xn.v[u];
-  }
+  T sum[VEC];
+  laplace_nbr_sum<T, VEC>(X, n, kv, c, sum);
   V out;
   if (mode) {
     V bb = ((const V *)b)[(size_t)s * kv + c];
 #pragma unroll
-    for (int u = 0; u < VEC; ++u) out.v[u] = bb.v[u] - acc[u];
+    for (int u = 0; u < VEC; ++u) out.v[u] = (bb.v[u] + sum[u]) - diag * xc.v[u];
   } else {
 #pragma unroll
-    for (int u = 0; u < VEC; ++u) out.v[u] = acc[u];
+    for (int u = 0; u < VEC; ++u) out.v[u] = diag * xc.v[u] - sum[u];
   }
   ((V *)y)[(size_t)s * kv + c] = out;
 }
@@ -276,17 +307,11 @@ __global__ void __launch_bounds__(256) k_laplace_rbgs(T *__restrict__ x, const T
   V *X = (V *)x;
   V acc = ((const V *)b)[(size_t)s * kv + c];
   if (!other_zero) {
-    int nbs[4];
-    int cnt = 0;
-    if (i + 1 < nx) nbs[cnt++] = s + 1; else if (periodic) nbs[cnt++] = j * nx;
-    if (i > 0) nbs[cnt++] = s - 1; else if (periodic) nbs[cnt++] = j * nx + nx - 1;
-    if (j + 1 < ny) nbs[cnt++] = s + nx; else if (periodic) nbs[cnt++] = i;
-    if (j > 0) nbs[cnt++] = s - nx; else if (periodic) nbs[cnt++] = (ny - 1) * nx + i;
-    for (int q = 0; q < cnt; ++q) {
-      V xn = X[(size_t)nbs[q] * kv + c];
+    const Nbrs n = laplace_nbrs(i, j, nx, ny, periodic);
+    T sum[VEC];
+    laplace_nbr_sum<T, VEC>(X, n, kv, c, sum);
 #pragma unroll
-      for (int u = 0; u < VEC; ++u) acc.v[u] = acc.v[u] + xn.v[u];
-    }
+    for (int u = 0; u < VEC; ++u) acc.v[u] = acc.v[u] + sum[u];
   }
 #pragma unroll
   for (int u = 0; u < VEC; ++u) acc.v[u] = acc.v[u] * dinv;

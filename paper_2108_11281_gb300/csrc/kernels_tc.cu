@@ -34,6 +34,7 @@
 
 #include "mlmc.h"
 #include "mlmc_internal.cuh"
+#include "tcgen05.cuh"
 
 namespace mlmc {
 
@@ -50,75 +51,15 @@ constexpr int A_BYTES = TC_M * TC_BK * 4;            // one A half (hi or lo), 1
 __host__ __device__ constexpr int b_bytes(int ntile) { return ntile * TC_BK * 4; }
 constexpr size_t stage_smem(int ntile) { return (size_t)2 * (2 * A_BYTES + 2 * b_bytes(ntile)); }
 
-__device__ inline uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using tc::mbar_init;
+using tc::mbar_wait_bounded;
+using tc::mma_commit;
+using tc::mma_tf32;
+using tc::smem_desc;
+using tc::smem_u32;
+using tc::split_store;
 
-// Shared-memory matrix descriptor for tcgen05: start address, leading byte
-// offset (between core matrices adjacent along K), stride byte offset
-// (between 8-row groups), fixed version field 1, no swizzle.
-__device__ inline uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// Instruction descriptor of kind::tf32: D in F32, A and B TF32, both K-major.
-__device__ inline uint32_t tf32_idesc(int n) {
-  uint32_t d = 0;
-  d |= 1u << 4;                        // D format: F32
-  d |= 2u << 7;                        // A format: TF32
-  d |= 2u << 10;                       // B format: TF32
-  d |= (uint32_t)(n >> 3) << 17;       // N / 8
-  d |= (uint32_t)(TC_M >> 4) << 24;    // M / 16
-  return d;
-}
-
-__device__ inline float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-__device__ inline void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-// Non-blocking test of phase `parity`, polled for at most `limit` SM cycles.
-__device__ inline bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
-  const long long t0 = clock64();
-  for (uint32_t it = 0;; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > limit) return false;
-    if (it > 64) __nanosleep(64);
-  }
-}
-
-__device__ inline void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ inline void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ inline void split_store(unsigned char *hi, unsigned char *lo, uint32_t off, float4 v) {
-  float4 h = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
-  *(float4 *)(hi + off) = h;
-  *(float4 *)(lo + off) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-}
+__device__ inline uint32_t tf32_idesc(int n) { return tc::tf32_idesc(TC_M, n); }
 
 }  // namespace
 

@@ -144,6 +144,7 @@ struct mlmc_hierarchy {
   std::vector<std::unique_ptr<Krylov>> inner[2];  // fixed-length inner FGMRES per level, [0] FP64 [1] FP32
   int const_laplace = 0, periodic = 0;
   int dense_kernel = MLMC_DENSE_AUTO;   // coarsest apply of the FP32 cycle: tensor cores, CUDA cores, or by size
+  int conv_kernel = MLMC_CONV_AUTO;     // learned correction's convolutions: tensor cores where the shape allows
   int bilinear = 0;    // the Example 5.1 hierarchy of Sec. 5: bilinear P, Galerkin 9-point levels
   double coarse_term_hat = 0.0;   // bilinear: tr(A_L^{-1} R^_L P^_L) (Remark 4.2), computed at setup
   double laplace_diag = 4.0;
@@ -351,7 +352,14 @@ int fgmres(H_t &h, Krylov &K, int l, int lo, const void *b, void *x, int k, doub
   h.launches++;
   check_cuda(cudaMemsetAsync(x, 0, blk * es, s), "memset x");
   if (converged) *converged = true;
-  if (!fixed && read_nactive(h, K) == 0) return 0;
+  if (!fixed) {
+    const int na = read_nactive(h, K);
+    if (na >= NONFINITE_COLUMN) {            // b is not finite: no iteration can help
+      if (converged) *converged = false;
+      return 0;
+    }
+    if (na == 0) return 0;
+  }
   int its = 0;
   for (;;) {
     if (!lazy) {
@@ -415,7 +423,12 @@ int fgmres(H_t &h, Krylov &K, int l, int lo, const void *b, void *x, int k, doub
     launch_arnoldi_init(K.hc, K.g.p, K.bnorm.as<double>(), K.invnrm.as<double>(), K.active.as<int>(),
                         K.jdone.as<int>(), k, tol, 0, K.nactive.as<int>(), s);
     h.launches++;
-    if (read_nactive(h, K) == 0) return its;
+    const int na = read_nactive(h, K);
+    if (na >= NONFINITE_COLUMN) {            // the iterate went NaN / infinite: stop, not converged
+      if (converged) *converged = false;
+      return its;
+    }
+    if (na == 0) return its;
     if (its >= maxit) {
       if (converged) *converged = false;
       return its;
@@ -611,16 +624,56 @@ const float *netW1(H_t &h) { return h.netW.as<float>(); }
 const float *netW2(H_t &h) { return h.netW.as<float>() + 9 * NET_CH * h.net_c0; }
 const float *netW3(H_t &h) { return h.netW.as<float>() + 9 * (NET_CH * h.net_c0 + NET_CH * NET_CH); }
 
+// One convolution layer: the tensor-core implicit GEMM (kernels_conv_tc.cu) when the
+// handle allows it and the shape fits (k in {8, 16, 32, 64, 128}, whole tiles of 128 / k
+// sites per lattice row), else the CUDA-core kernel (kernels_learned.cu).
+bool conv_on_tc(const H_t &h, int nx, int k, int cin, int cout) {
+  return h.conv_kernel != MLMC_CONV_SIMT && conv_tc_ok(nx, k, cin, cout);
+}
+
+void conv_forward(H_t &h, int ci, int co, bool relu, const float *in, const float *W, float *out, int k) {
+  const Level &F = h.lv[0];
+  const int per = h.periodic || h.complex_op;
+  if (conv_on_tc(h, F.nx, k, ci, co))
+    launch_conv_tc(in, W, nullptr, out, F.nx, F.ny, k, ci, co, per, 0, relu ? 1 : 0, h.err.as<int>(), h.stream);
+  else
+    launch_conv_fwd(ci, co, relu, in, W, out, F.nx, F.ny, k, per, h.stream);
+  h.launches++;
+}
+
+// gradient wrt the input of a layer ci -> co, masked by act > 0 (the ReLU below it)
+void conv_backward_data(H_t &h, int ci, int co, const float *gout, const float *W, const float *act, float *gin,
+                        int k) {
+  const Level &F = h.lv[0];
+  const int per = h.periodic || h.complex_op;
+  if (conv_on_tc(h, F.nx, k, co, ci))
+    launch_conv_tc(gout, W, act, gin, F.nx, F.ny, k, co, ci, per, 1, 0, h.err.as<int>(), h.stream);
+  else
+    launch_conv_bwd_data(ci, co, gout, W, act, gin, F.nx, F.ny, k, per, h.stream);
+  h.launches++;
+}
+
+void conv_backward_weight(H_t &h, int ci, int co, const float *in, const float *gout, float *G, int k) {
+  const Level &F = h.lv[0];
+  const int per = h.periodic || h.complex_op;
+  if (h.conv_kernel != MLMC_CONV_SIMT && conv_wgrad_tc_ok(k, ci, co)) {
+    launch_conv_wgrad_tc(in, gout, h.netPart.as<float>(), F.nx, F.ny, k, ci, co, per, h.err.as<int>(), h.stream);
+    launch_weight_reduce(h.netPart.as<float>(), conv_wgrad_tc_blocks(), ci * co * 9, G, 1.f, h.stream);
+  } else {
+    launch_conv_bwd_weight(ci, co, in, gout, h.netPart.as<float>(), G, 1.f, F.nx, F.ny, k, per, h.stream);
+  }
+  h.launches += 2;
+}
+
 // act3 = net(r) in channel layout; act0..act2 keep the activations
 void net_forward(H_t &h, const void *r, int k) {
   const Level &F = h.lv[0];
   cudaStream_t s = h.stream;
-  int per = h.periodic || h.complex_op;
   launch_to_channels(h.t32, r, h.act0.as<float>(), (int)F.nsite, F.d, k, s);
-  launch_conv_fwd(h.net_c0, NET_CH, true, h.act0.as<float>(), netW1(h), h.act1.as<float>(), F.nx, F.ny, k, per, s);
-  launch_conv_fwd(NET_CH, NET_CH, true, h.act1.as<float>(), netW2(h), h.act2.as<float>(), F.nx, F.ny, k, per, s);
-  launch_conv_fwd(NET_CH, h.net_c0, false, h.act2.as<float>(), netW3(h), h.act3.as<float>(), F.nx, F.ny, k, per, s);
-  h.launches += 4;
+  h.launches++;
+  conv_forward(h, h.net_c0, NET_CH, true, h.act0.as<float>(), netW1(h), h.act1.as<float>(), k);
+  conv_forward(h, NET_CH, NET_CH, true, h.act1.as<float>(), netW2(h), h.act2.as<float>(), k);
+  conv_forward(h, NET_CH, h.net_c0, false, h.act2.as<float>(), netW3(h), h.act3.as<float>(), k);
 }
 
 // Loss mean_c ||A net(r_c) - r_c||^2 / ||r_c||^2 over the block and (grad = 1)
@@ -628,7 +681,6 @@ void net_forward(H_t &h, const void *r, int k) {
 double net_loss_grad(H_t &h, const void *r, int k, bool grad, bool read_loss) {
   const Level &F = h.lv[0];
   cudaStream_t s = h.stream;
-  int per = h.periodic || h.complex_op;
   size_t cnt = F.n * (size_t)k;
   void *E = h.cyc[1][0].x.p, *Tt = h.cyc[1][0].b.p;
   net_forward(h, r, k);
@@ -662,12 +714,12 @@ double net_loss_grad(H_t &h, const void *r, int k, bool grad, bool read_loss) {
   launch_to_channels(h.t32, E, g3, (int)F.nsite, F.d, k, s);
   float *G = h.netG.as<float>();
   float *G1 = G, *G2 = G + 9 * NET_CH * h.net_c0, *G3 = G2 + 9 * NET_CH * NET_CH;
-  launch_conv_bwd_weight(NET_CH, h.net_c0, h.act2.as<float>(), g3, h.netPart.as<float>(), G3, 1.f, F.nx, F.ny, k, per, s);
-  launch_conv_bwd_data(NET_CH, h.net_c0, g3, netW3(h), h.act2.as<float>(), h.g2.as<float>(), F.nx, F.ny, k, per, s);
-  launch_conv_bwd_weight(NET_CH, NET_CH, h.act1.as<float>(), h.g2.as<float>(), h.netPart.as<float>(), G2, 1.f, F.nx, F.ny, k, per, s);
-  launch_conv_bwd_data(NET_CH, NET_CH, h.g2.as<float>(), netW2(h), h.act1.as<float>(), h.g1.as<float>(), F.nx, F.ny, k, per, s);
-  launch_conv_bwd_weight(h.net_c0, NET_CH, h.act0.as<float>(), h.g1.as<float>(), h.netPart.as<float>(), G1, 1.f, F.nx, F.ny, k, per, s);
-  h.launches += 16;
+  conv_backward_weight(h, NET_CH, h.net_c0, h.act2.as<float>(), g3, G3, k);
+  conv_backward_data(h, NET_CH, h.net_c0, g3, netW3(h), h.act2.as<float>(), h.g2.as<float>(), k);
+  conv_backward_weight(h, NET_CH, NET_CH, h.act1.as<float>(), h.g2.as<float>(), G2, k);
+  conv_backward_data(h, NET_CH, NET_CH, h.g2.as<float>(), netW2(h), h.act1.as<float>(), h.g1.as<float>(), k);
+  conv_backward_weight(h, h.net_c0, NET_CH, h.act0.as<float>(), h.g1.as<float>(), G1, k);
+  h.launches += h.complex_op ? 5 : 3;   // spin flips, column factors, scaling, channel layout
   return loss;
 }
 
@@ -1463,6 +1515,15 @@ int mlmc_set_dense_kernel(mlmc_hierarchy *h, int which) {
   });
 }
 
+int mlmc_set_conv_kernel(mlmc_hierarchy *h, int which) {
+  return translate([&] {
+    need(h);
+    if (which != MLMC_CONV_SIMT && which != MLMC_CONV_AUTO) fail(MLMC_ERR_INVALID_ARG, "unknown conv kernel");
+    if (h->conv_kernel != which) drop_graphs(*h);
+    h->conv_kernel = which;
+  });
+}
+
 int mlmc_coarse_trace_exact(mlmc_hierarchy *h, mlmc_c64 *out) {
   return translate([&] {
     need(h);
@@ -1660,8 +1721,10 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
     int l = level - 1;
     int lo = which == 0 ? 0 : (H.prm.precision == MLMC_PREC_MIXED_FP32 ? 1 : 0);
     if (which == 1 && !lo) fail(MLMC_ERR_INVALID_ARG, "FP32 kernels need the mixed form");
-    if (which < 0 || which > 5) fail(MLMC_ERR_INVALID_ARG, "unknown kernel family");
+    if (which < 0 || which > 7) fail(MLMC_ERR_INVALID_ARG, "unknown kernel family");
     if (which == 5 && l != H.L - 1) fail(MLMC_ERR_INVALID_ARG, "the dense apply lives on the coarsest level");
+    if ((which == 6 || which == 7) && (l == H.L - 1 || k > H.wl[l + 1]))
+      fail(MLMC_ERR_INVALID_ARG, "transfers run from a level above the coarsest, k within the coarse buffers");
     if (which == 2 && l == H.L - 1) fail(MLMC_ERR_INVALID_ARG, "no smoother on the coarsest level");
     const Level &Lv = H.lv[l];
     DType t = lo ? H.t32 : H.t64;
@@ -1694,6 +1757,10 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
       } else if (which == 4) {
         launch_multiaxpy(t, y, Vb.p, Lv.n * (size_t)k, nvec, outb.p, H.complex_op ? C64 : F64, k, -1e-30, Lv.n, k,
                          H.stream);
+      } else if (which == 6) {
+        launch_restrict(pview(H, l, lo), x, H.cyc[lo][l + 1].b.p, k, H.stream);
+      } else if (which == 7) {
+        launch_prolong_add(pview(H, l, lo), H.cyc[lo][l + 1].b.p, y, k, H.stream);
       } else {
         launch_stencil(view(H, l, lo), x, nullptr, y, k, 0, H.stream);
       }
@@ -1711,7 +1778,15 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
     bool const_coef = l == 0 && !H.complex_op;      // Example 5.1 stencil has no matrix to read
     double coefb = const_coef ? 0.0 : (double)Lv.nsite * Lv.taps * Lv.d * Lv.d * es;
     double bytes;
-    if (which == 5) {
+    if (which == 6 || which == 7) {
+      // restriction: the fine block in, the coarse block out; prolongation: the coarse block
+      // in, the fine block read and written; both read the P blocks once (none for bilinear P)
+      const Level &C = H.lv[l + 1];
+      double cvec = (double)C.n * k * es;
+      double pb = H.bilinear ? 0.0 : (double)Lv.n * Lv.dc * es;
+      bytes = (which == 6 ? vec : 2.0 * vec) + cvec + pb;
+      if (ms_per_launch) *ms_per_launch = ms / reps;
+    } else if (which == 5) {
       // the dense inverse once, the block in, the block out
       bytes = (double)Lv.n * Lv.n * es + 2.0 * vec;
       if (ms_per_launch) *ms_per_launch = ms / reps;
@@ -1732,6 +1807,35 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
       if (ms_per_launch) *ms_per_launch = ms / reps;
     }
     if (bytes_per_launch) *bytes_per_launch = bytes;
+  });
+}
+
+int mlmc_measure_fma_rate(int fp64, void *stream, double *fma_per_s) {
+  return translate([&] {
+    if (!fma_per_s) fail(MLMC_ERR_INVALID_ARG, "null output");
+    cudaStream_t s = (cudaStream_t)stream;
+    g_alloc_stream = s;
+    int dev = 0, sms = 0;
+    check_cuda(cudaGetDevice(&dev), "device");
+    check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attribute");
+    const int blocks = sms * 8, iters = fp64 ? 4096 : 65536;
+    DevBuf out;
+    out.alloc((size_t)blocks * 256 * 8);
+    DType t = fp64 ? F64 : F32;
+    cudaEvent_t e0, e1;
+    check_cuda(cudaEventCreate(&e0), "event");
+    check_cuda(cudaEventCreate(&e1), "event");
+    launch_fma_rate(t, out.p, blocks, iters, s);                 // warm-up
+    check_cuda(cudaEventRecord(e0, s), "record");
+    const int reps = 5;
+    for (int i = 0; i < reps; ++i) launch_fma_rate(t, out.p, blocks, iters, s);
+    check_cuda(cudaEventRecord(e1, s), "record");
+    check_cuda(cudaEventSynchronize(e1), "sync");
+    float ms = 0.f;
+    check_cuda(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *fma_per_s = (double)reps * blocks * 256.0 * iters * 8.0 / (ms * 1e-3);
   });
 }
 

@@ -143,6 +143,9 @@ void launch_noise(int kind, uint64_t seed, uint64_t key_hi, uint64_t first_sampl
                   DType t, void *out, cudaStream_t s);
 void launch_convert(DType to, void *dst, DType from, const void *src, size_t count, cudaStream_t s);
 void launch_fill_zero(DType t, void *dst, size_t count, cudaStream_t s);
+// blocks x 256 threads, each running 8 FMA chains of `iters` steps (F64 or F32): 2048 blocks' worth of
+// out entries are written only by a condition that never holds
+void launch_fma_rate(DType t, void *out, int blocks, int iters, cudaStream_t s);
 void launch_fill_one(DType t, void *dst, size_t count, cudaStream_t s);
 void launch_sub(DType t, void *out, const void *a, const void *b, size_t count, cudaStream_t s);
 // y[i][c] = alpha[c] * x[i][c] (+ y if accumulate)
@@ -221,6 +224,9 @@ namespace mlmc {
 // g0[c] holds |r|^2 on entry (from a column dot); sets beta, active, invnrm.
 // sc (optional): per-column norms of the unnormalised basis vectors of the
 // fixed-length FGMRES (s_0 = |b| here; s_{j+1} set by the step)
+// Added to the active-column count by launch_arnoldi_init for every column whose
+// residual norm is not finite (such a column can never converge).
+constexpr int NONFINITE_COLUMN = 1 << 20;
 void launch_arnoldi_init(int hc, void *g, double *bnorm, double *invnrm, int *active, int *jdone,
                          int k, double tol, int first, int *nactive, cudaStream_t s, double *sc = nullptr);
 // unnormalised basis: Gram-Schmidt coefficients d_i / s_i^2 into coef, Hessenberg
@@ -255,6 +261,18 @@ void launch_conv_bwd_data(int ci, int co, const float *gout, const float *W, con
 int conv_weight_blocks();
 void launch_conv_bwd_weight(int ci, int co, const float *in, const float *gout, float *partial, float *grad,
                             float scale, int nx, int ny, int k, int periodic, cudaStream_t s);
+// tensor-core convolutions (kernels_conv_tc.cu): forward (mirror = 0; W [cout][cin][9]) or
+// backward-data (mirror = 1; W [cin][cout][9]), output masked by act > 0 when act is given
+bool conv_tc_ok(int nx, int k, int cin, int cout);
+void launch_conv_tc(const float *in, const float *W, const float *act, float *out, int nx, int ny, int k, int cin,
+                    int cout, int periodic, int mirror, int relu, int *err, cudaStream_t s);
+// per-CTA partial weight gradients [conv_wgrad_tc_blocks()][cout][cin][9]; k_weight_reduce adds them
+bool conv_wgrad_tc_ok(int k, int cin, int cout);
+int conv_wgrad_tc_blocks();
+void launch_conv_wgrad_tc(const float *in, const float *gout, float *partial, int nx, int ny, int k, int cin,
+                          int cout, int periodic, int *err, cudaStream_t s);
+// grad[w] = scale * sum over blocks of partial[block][w], blocks in order
+void launch_weight_reduce(const float *partial, int nblocks, int nw, float *grad, float scale, cudaStream_t s);
 void launch_adam(float *W, const float *g, float *m, float *v, int n, float lr, int step, cudaStream_t s);
 void launch_spin_flip(DType t, void *x, int nsite, int d, int k, cudaStream_t s);
 // alpha[c] = scale / |dot[c]| (real part), FP64 per-column factors from a column dot

@@ -25,6 +25,7 @@ CYCLE_V, CYCLE_K = 0, 1
 ALLOC_RHO, ALLOC_OPTIMAL, ALLOC_FIXED = 0, 1, 2
 COST_COUNTED, COST_NOMINAL = 0, 1
 DENSE_SIMT, DENSE_TC, DENSE_TC_WITHHOLD, DENSE_AUTO = 0, 1, 2, 3
+CONV_SIMT, CONV_AUTO = 0, 1
 TRANSFER_AGGREGATION, TRANSFER_BILINEAR = 0, 1
 
 
@@ -118,6 +119,8 @@ def _load():
         "mlmc_level_taps": [vp, i, ctypes.POINTER(i)],
         "mlmc_set_dense_kernel": [vp, i],
         "mlmc_learned_stats": [vp, ctypes.POINTER(i), ctypes.POINTER(i)],
+        "mlmc_measure_fma_rate": [i, vp, ctypes.POINTER(d)],
+        "mlmc_set_conv_kernel": [vp, i],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -137,7 +140,8 @@ EXPORTED = ["mlmc_setup_hierarchy", "mlmc_destroy_hierarchy", "mlmc_level_info",
             "mlmc_last_error", "mlmc_learned_train", "mlmc_learned_set", "mlmc_learned_apply", "mlmc_learned_grad",
             "mlmc_column_dots", "mlmc_column_dots_noalloc", "mlmc_noalloc_last_error", "mlmc_set_block_width",
             "mlmc_autotune_block", "mlmc_trace_estimate_batch", "mlmc_sample_level_form", "mlmc_dense_apply",
-            "mlmc_set_dense_kernel", "mlmc_level_taps", "mlmc_learned_stats"]
+            "mlmc_set_dense_kernel", "mlmc_level_taps", "mlmc_learned_stats",
+            "mlmc_measure_fma_rate", "mlmc_set_conv_kernel"]
 
 
 def check(status):
@@ -316,6 +320,9 @@ class Hierarchy:
     def set_dense_kernel(self, which):
         check(lib.mlmc_set_dense_kernel(self.handle, which))
 
+    def set_conv_kernel(self, which):
+        check(lib.mlmc_set_conv_kernel(self.handle, which))
+
     def autotune_block(self, level=1, noise=NOISE_RADEMACHER, tol=1e-8):
         k, t = ctypes.c_int(), ctypes.c_double()
         check(lib.mlmc_autotune_block(self.handle, level, noise, tol, ctypes.byref(k), ctypes.byref(t)))
@@ -352,6 +359,13 @@ def trace_estimate_batch(hierarchies, params, workers=4):
     st = (ctypes.c_int * n)()
     check(lib.mlmc_trace_estimate_batch(hs, n, ps, workers, rs, st))
     return [result_dict(rs[i]) for i in range(n)], list(st)
+
+
+def measure_fma_rate(fp64=True, stream=0):
+    """Fused multiply-adds per second of the whole GPU (FP64 or FP32), measured."""
+    r = ctypes.c_double()
+    check(lib.mlmc_measure_fma_rate(int(bool(fp64)), ctypes.c_void_p(stream or None), ctypes.byref(r)))
+    return r.value
 
 
 def estimate_params(eps=1e-3, noise=NOISE_RADEMACHER, seed=0, tol=1e-8, allocation=ALLOC_OPTIMAL, weights=None,

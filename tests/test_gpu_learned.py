@@ -42,9 +42,11 @@ def flat(Ws):
     return np.concatenate([W.astype(np.float32).ravel() for W in Ws])
 
 
+@pytest.mark.parametrize("k", [3, 16])
 @pytest.mark.parametrize("case", ["wilson", "laplace"])
-def test_forward_and_gradient_match_oracle(mlmc, case):
-    N, k = 8, 3
+def test_forward_and_gradient_match_oracle(mlmc, case, k):
+    """k = 3: the CUDA-core convolutions; k = 16: the tensor-core ones (tiles of 8 sites)."""
+    N = 8
     h, A, d, cplx, per = make(mlmc, case, N, k)
     c0 = NN.channels_of(d, cplx)
     Ws = [W.astype(np.float32).astype(np.float64) for W in NN.init_weights(c0, 9)]
@@ -68,6 +70,37 @@ def test_forward_and_gradient_match_oracle(mlmc, case):
     assert abs(loss - ref_loss) <= 1e-4 * abs(ref_loss)
     assert np.abs(grad - ref_flat).max() <= 1e-3 * np.abs(ref_flat).max()
     h.close()
+
+
+def test_tensor_core_convolutions_match_cuda_cores(mlmc):
+    """The tcgen05 implicit-GEMM convolutions (three TF32 products per term) against the
+    FP32 CUDA-core kernels on a 32x32 Wilson lattice (periodic) and a 32x32 Dirichlet
+    Laplacian, k = 32: the network output to 1e-5 and the loss gradient to 1e-4 of their
+    scales (both FP32, summed in different orders)."""
+    for case in ("wilson", "laplace"):
+        N, k = 32, 32
+        h, A, d, cplx, per = make(mlmc, case, N, k)
+        c0 = NN.channels_of(d, cplx)
+        Ws = [W.astype(np.float32).astype(np.float64) for W in NN.init_weights(c0, 4)]
+        h.learned_set(flat(Ws), enable=0)
+        n = N * N * d
+        g = torch.Generator().manual_seed(1)
+        if cplx:
+            R = torch.complex(torch.randn(n, k, generator=g), torch.randn(n, k, generator=g)).to(torch.complex64).cuda()
+        else:
+            R = torch.randn(n, k, generator=g, dtype=torch.float32).cuda()
+        out = {}
+        for which in (mlmc.CONV_AUTO, mlmc.CONV_SIMT):
+            h.set_conv_kernel(which)
+            E = torch.zeros_like(R)
+            h.learned_apply(R.data_ptr(), E.data_ptr(), k)
+            loss, grad = h.learned_grad(R.data_ptr(), k)
+            out[which] = (E.cpu().numpy(), loss, grad)
+        (Et, lt, gt), (Es, ls, gs) = out[mlmc.CONV_AUTO], out[mlmc.CONV_SIMT]
+        assert np.abs(Et - Es).max() <= 1e-5 * np.abs(Es).max()
+        assert abs(lt - ls) <= 1e-5 * abs(ls)
+        assert np.abs(gt - gs).max() <= 1e-4 * np.abs(gs).max()
+        h.close()
 
 
 def wilson32(mlmc, max_iter=2000):
