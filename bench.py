@@ -18,6 +18,7 @@ for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 import argparse
+import ctypes
 import json
 import statistics
 import subprocess
@@ -626,14 +627,82 @@ def run_batch(args):
         res = list(ex.map(one, insts))
     torch.cuda.synchronize()
     wall = time.time() - t0
+    # roofline: the level-2 block Gauss-Seidel sweep (the headline's dominant kernel family) on a
+    # 1024^2 Laplace instance of the batch, timed alone with CUDA events
+    peak, peak_kind = measured_peaks()
+    w = dict(base, nx=1024, ny=1024, levels=4, block=128)
+    hp = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, 1024, 1024, hierarchy_params(mlmc, mlmc.PREC_MIXED_FP32, w), shift=1e-2)
+    kern = {}
+    for name, which, lvl in (("rbgs_sweep_fp32_level1", 2, 1), ("rbgs_sweep_fp32_level2", 2, 2),
+                             ("stencil_fp32_level2", 1, 2), ("restrict_fp32_level1", 6, 1)):
+        kms, kbytes = hp.profile_kernel(which, lvl, 128, 20)
+        kern[name] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6, "k": 128}
+    hp.close()
+    dom = kern["rbgs_sweep_fp32_level2"]
+    roofline = {"bound": "hbm", "kernel": "k_rbgs_half_p (level-2 block GS of a 1024^2 instance, k=128, one sweep)",
+                "achieved": dom["gbs"], "peak": peak, "unit": "GB/s", "frac": dom["gbs"] / peak,
+                "peak_source": peak_kind, "traffic": None, "algorithmic_bytes": dom["bytes"], "kernels": kern}
+    cpu = None if args.no_cpu_baseline else batch_cpu_baseline(insts)
+    h2d = sum(2 * r["side"] * r["side"] * 16 for r in res if r["kind"] == "wilson")
     line = {"metric": METRIC, "value": wall, "unit": "s (48-instance batch)", "n_gpus": 1, "steps": 1,
             "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
             "config": {"workload": "batch48-uneven", "workers": workers, "instances": len(insts),
                        "allocation": "fixed budget per level ~ U{16..128}", "form": "mixed"},
+            "e2e": {"value": wall, "unit": "s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": len(insts) * ctypes.sizeof(mlmc.EstimateResult),
+                    "includes": "every instance's setup from its host descriptor (links copied in), block-width "
+                                "autotuning, the estimate and the result read-back"},
+            "roofline": roofline, "cpu_baseline": cpu,
             "instances_per_s": len(insts) / wall, "gpu_launches": int(sum(r["launches"] for r in res)),
             "sum_instance_seconds": sum(r["total_s"] for r in res), "instances": res}
     print(json.dumps(line), flush=True)
+
+
+def batch_cpu_baseline(insts):
+    """The oracle on a bounded sample of the batch: per (kind, side) class up to 512^2 sites it
+    builds the class's oracle hierarchy and times samples 0..4 of every level difference on all
+    host cores (single-threaded processes); larger classes are scaled from the largest timed
+    class of their kind by the number of unknowns.  Seconds for the batch = sum over instances
+    and levels of n_fixed x seconds per sample, shared by the processes (extrapolated)."""
+    procs = max(1, min(os.cpu_count() or 1, 16))
+    per_class = {}
+    t0 = time.time()
+    for kind in ("wilson", "laplace"):
+        sides = sorted({i["side"] for i in insts if i["kind"] == kind})
+        timed = [sd for sd in sides if sd <= 512][:2]
+        for sd in timed:
+            inst = next(i for i in insts if i["kind"] == kind and i["side"] == sd)
+            if kind == "laplace":
+                w = dict(WORKLOADS["laplace1024"], nx=sd, ny=sd, levels=inst["levels"], shift=inst["shift"])
+            else:
+                w = dict(WORKLOADS["wilson128"], nx=sd, ny=sd, levels=inst["levels"], mass=-0.10,
+                         link_seed=inst["link_seed"])
+            lv = oracle_levels(w)
+            pool = oracle_pool(lv, w, 1e-8, procs)
+            try:
+                plan = oracle_plan(w, lv, pool, procs, 0)
+            finally:
+                pool.close()
+                pool.join()
+            per_class[(kind, sd)] = plan["sec_per_sample"]
+    total = 0.0
+    for inst in insts:
+        key = (inst["kind"], inst["side"])
+        if key in per_class:
+            sec = per_class[key]
+        else:
+            ref = max(sd for (kd, sd) in per_class if kd == inst["kind"])
+            scale = (inst["side"] / ref) ** 2
+            sec = [v * scale for v in per_class[(inst["kind"], ref)]]
+            sec += [sec[-1]] * (len(inst["n_fixed"]) - len(sec))
+        total += sum(n * t for n, t in zip(inst["n_fixed"], sec))
+    return {"value": total / procs, "unit": "s (extrapolated)", "cores": procs, "kind": "oracle",
+            "single_core_s": total, "host": host_info(), "timed_classes": sorted("%s%d" % k for k in per_class),
+            "seconds_measuring": time.time() - t0,
+            "sample": "oracle FP64 FGMRES(30)+K-cycle at tol 1e-8, samples 0..4 per level difference of one "
+                      "instance per class up to 512^2 sites on %d processes; larger classes scaled by unknowns; "
+                      "value = sum n_fixed x s/sample / %d" % (procs, procs)}
 
 
 def learned_leg(mlmc, stream, warmup, steps, seed=0):
@@ -666,6 +735,15 @@ def learned_leg(mlmc, stream, warmup, steps, seed=0):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3 / steps, r
 
+    # the network alone on a fine-level block: tensor-core vs CUDA-core convolutions
+    kern = {}
+    c0 = 4
+    flops = 2.0 * 9 * (16 * c0 + 256 + 16 * c0) * w["nx"] * w["ny"] * w["block"]
+    for name, which in (("net_forward_tc", mlmc.CONV_AUTO), ("net_forward_simt", mlmc.CONV_SIMT)):
+        h.set_conv_kernel(which)
+        kms, kbytes = h.profile_kernel(8, 1, w["block"], 20)
+        kern[name] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6, "tflops": flops / kms / 1e9}
+    h.set_conv_kernel(mlmc.CONV_AUTO)
     net_on = h.learned_stats()[0]
     t_net, r_net = timed()
     fallbacks = h.learned_stats()[1]
@@ -678,7 +756,7 @@ def learned_leg(mlmc, stream, warmup, steps, seed=0):
             "with_net_iters": r_net["iters"], "plain_iters": r_plain["iters"],
             "with_net_n_samples": r_net["n_samples"], "plain_n_samples": r_plain["n_samples"],
             "trace_with_net": r_net["trace"].real, "trace_plain": r_plain["trace"].real,
-            "std_err": r_plain["std_err"], "steps": steps, "warmup": warmup}
+            "std_err": r_plain["std_err"], "steps": steps, "warmup": warmup, "kernels": kern}
 
 
 def gpu_config1(mlmc, stream, warmup, steps=3):

@@ -339,7 +339,10 @@ int mlmc_measure_fma_rate(int fp64, void *stream, double *fma_per_s);
  * 4 multi-AXPY of 4 basis blocks into w, 5 coarsest dense apply
  * Y = A_L^-1 B (level = L; the kernel chosen by mlmc_set_dense_kernel),
  * 6 restriction R_l = P_l^* from level l to l+1, 7 prolongation x += P_l e
- * from level l+1 (2-7 in the cycle precision).  k <= block on level 1,
+ * from level l+1, 8 the learned correction's network on a level-1 block (mixed
+ * form; the convolutions chosen by mlmc_set_conv_kernel; its FLOPs are
+ * 2 x 9 x (16 c0 + 256 + 16 c0) per site and column, c0 its input channels)
+ * (2-8 in the cycle precision).  k <= block on level 1,
  * k <= max(block, coarse_block) on the coarser levels (6, 7: also within
  * level l+1's buffers).
  * Reports the average launch time and the algorithmic bytes one launch must

@@ -31,6 +31,7 @@
 // Every mbarrier wait is bounded (about a second): a CTA whose wait gives up
 // records MLMC_ERR_TIMEOUT in *err, waits (bounded) for its own MMAs, frees its
 // tensor memory and returns without writing.
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -76,10 +77,15 @@ size_t wgrad_tc_smem(int cin, int kc) {
 
 }  // namespace
 
-// out[s][n][c] for the CTA's 128 pairs (see the file comment).  mirror = 0: forward,
-// B[n][tap][c] = W[n][c][tap] (W is [cout][cin][9]); mirror = 1: backward-data,
-// B[n][tap][c] = W[c][n][tap] (W is [cin][cout][9]) with tap (tx, ty) reading the site at
-// offset (1 - tx, 1 - ty).  act (mask, optional): out = acc where act[s][n][c] > 0, else 0.
+// Loads of one staging pass are issued in batches of STAGE_BATCH 16-byte elements per
+// thread (all loads of a batch in flight before the first shared store).
+constexpr int STAGE_BATCH = 8;
+
+// out[s][n][c] for tiles of 128 pairs (see the file comment), CTAs persistent over
+// the tiles.  mirror = 0: forward, B[n][tap][c] = W[n][c][tap] (W is [cout][cin][9]);
+// mirror = 1: backward-data, B[n][tap][c] = W[c][n][tap] (W is [cin][cout][9]) with tap
+// (tx, ty) reading the site at offset (1 - tx, 1 - ty).  act (mask, optional): out =
+// acc where act[s][n][c] > 0, else 0.
 __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict__ in, const float *__restrict__ W,
                                                         const float *__restrict__ act, float *__restrict__ out,
                                                         int nx, int ny, int k, int cin, int cout, int periodic,
@@ -91,8 +97,7 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ts = CT_M / k, kg = k >> 3, hw = ts + 2;
   const int cip = pad8(cin), c4n = cip / 4;
-  const int tiles_x = nx / ts;
-  const int j = blockIdx.x / tiles_x, i0 = (blockIdx.x - j * tiles_x) * ts;
+  const int tiles_x = nx / ts, tiles = tiles_x * ny;
   const uint32_t LBO = 128u, SBO = (uint32_t)c4n * 128u;
   const uint32_t halo_bytes = (uint32_t)(3 * hw * kg) * SBO;
   const uint32_t BSBO = (uint32_t)(9 * c4n) * 128u, wbytes = (uint32_t)(CT_N / 8) * BSBO;
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
     failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  // weights: (n, tap, channel quad), zero outside cout x cin
+  // weights, once per CTA: (n, tap, channel quad), zero outside cout x cin
   for (int e = tid; e < CT_N * 9 * c4n; e += CT_THREADS) {
     const int n = e / (9 * c4n), rem = e - n * (9 * c4n), tap = rem / c4n, q = rem - tap * c4n;
     float v[4];
@@ -119,50 +124,72 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
     const uint32_t off = (uint32_t)(n >> 3) * BSBO + (uint32_t)(tap * c4n + q) * LBO + (uint32_t)(n & 7) * 16u;
     tc::split_store(Bhi, Blo, off, make_float4(v[0], v[1], v[2], v[3]));
   }
-  // halo: (halo site, channel quad, column), columns fastest (coalesced loads)
-  const int nel = 3 * hw * c4n * k;
-  for (int e = tid; e < nel; e += CT_THREADS) {
-    const int c = e % k, rest = e / k, q = rest % c4n, h = rest / c4n;
-    const int hy = h / hw, hx = h - hy * hw;
-    const int site = conv_site(i0 - 1 + hx, j - 1 + hy, nx, ny, periodic);
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    if (site >= 0) {
-      const float *src = in + (size_t)site * cin * k + c;
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (4 * q + u < cin) v[u] = __ldg(src + (size_t)(4 * q + u) * k);
-    }
-    const uint32_t off = (uint32_t)(h * kg + (c >> 3)) * SBO + (uint32_t)q * LBO + (uint32_t)(c & 7) * 16u;
-    tc::split_store(Hhi, Hlo, off, make_float4(v[0], v[1], v[2], v[3]));
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  if (tid == 0) {
-    const uint32_t idesc = tc::tf32_idesc(CT_M, CT_N);
-    const uint32_t hh = tc::smem_u32(Hhi), hl = tc::smem_u32(Hlo), bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
-    for (int tap = 0; tap < 9; ++tap) {
-      const int tx = tap % 3, ty = tap / 3;
-      const int dx = mirror ? 2 - tx : tx, dy = mirror ? 2 - ty : ty;
-      const uint32_t hofs = (uint32_t)((dy * hw + dx) * kg) * SBO;
-      for (int ks = 0; ks < cip / 8; ++ks) {
-        const uint32_t a = hofs + (uint32_t)ks * 2u * LBO, b = (uint32_t)(tap * c4n + 2 * ks) * LBO;
-        tc::mma_tf32x3(tmem, tc::smem_desc(hh + a, LBO, SBO), tc::smem_desc(hl + a, LBO, SBO),
-                       tc::smem_desc(bh + b, LBO, BSBO), tc::smem_desc(bl + b, LBO, BSBO), idesc,
-                       (tap > 0 || ks > 0) ? 1u : 0u);
+  const uint32_t idesc = tc::tf32_idesc(CT_M, CT_N);
+  const int nel = 3 * hw * c4n * k;            // 16-byte halo elements per tile
+
+  uint32_t phase = 0;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, phase ^= 1u) {
+    const int j = tile / tiles_x, i0 = (tile - j * tiles_x) * ts;
+    // halo: (halo site, channel quad, column), columns fastest (coalesced loads)
+    for (int base = 0; base < nel; base += STAGE_BATCH * CT_THREADS) {
+      float4 v[STAGE_BATCH];
+#pragma unroll
+      for (int b = 0; b < STAGE_BATCH; ++b) {
+        const int e = base + b * CT_THREADS + tid;
+        v[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < nel) {
+          const int c = e % k, rest = e / k, q = rest % c4n, h = rest / c4n;
+          const int hy = h / hw, hx = h - hy * hw;
+          const int site = conv_site(i0 - 1 + hx, j - 1 + hy, nx, ny, periodic);
+          if (site >= 0) {
+            const float *src = in + ((size_t)site * cin + 4 * q) * k + c;
+            if (4 * q + 0 < cin) v[b].x = __ldg(src);
+            if (4 * q + 1 < cin) v[b].y = __ldg(src + k);
+            if (4 * q + 2 < cin) v[b].z = __ldg(src + 2 * k);
+            if (4 * q + 3 < cin) v[b].w = __ldg(src + 3 * k);
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < STAGE_BATCH; ++b) {
+        const int e = base + b * CT_THREADS + tid;
+        if (e < nel) {
+          const int c = e % k, rest = e / k, q = rest % c4n, h = rest / c4n;
+          const uint32_t off = (uint32_t)(h * kg + (c >> 3)) * SBO + (uint32_t)q * LBO + (uint32_t)(c & 7) * 16u;
+          tc::split_store(Hhi, Hlo, off, v[b]);
+        }
       }
     }
-    tc::mma_commit(&bar);
-  }
-  if (!tc::mbar_wait_bounded(&bar, 0u, wait_cycles)) failed = 1;
-  __syncthreads();
-  if (failed) {
-    // give the MMAs in flight one more bounded chance before the memory goes
-    tc::mbar_wait_bounded(&bar, 0u, wait_cycles);
-    if (tid == 0) atomicExch(err, (int)MLMC_ERR_TIMEOUT);
-  } else {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      const uint32_t hh = tc::smem_u32(Hhi), hl = tc::smem_u32(Hlo), bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
+      for (int tap = 0; tap < 9; ++tap) {
+        const int tx = tap % 3, ty = tap / 3;
+        const int dx = mirror ? 2 - tx : tx, dy = mirror ? 2 - ty : ty;
+        const uint32_t hofs = (uint32_t)((dy * hw + dx) * kg) * SBO;
+        for (int ks = 0; ks < cip / 8; ++ks) {
+          const uint32_t a = hofs + (uint32_t)ks * 2u * LBO, b = (uint32_t)(tap * c4n + 2 * ks) * LBO;
+          tc::mma_tf32x3(tmem, tc::smem_desc(hh + a, LBO, SBO), tc::smem_desc(hl + a, LBO, SBO),
+                         tc::smem_desc(bh + b, LBO, BSBO), tc::smem_desc(bl + b, LBO, BSBO), idesc,
+                         (tap > 0 || ks > 0) ? 1u : 0u);
+        }
+      }
+      tc::mma_commit(&bar);
+    }
+    if (!tc::mbar_wait_bounded(&bar, phase, wait_cycles)) failed = 1;
+    __syncthreads();
+    if (failed) {
+      // give the MMAs in flight one more bounded chance before the memory goes
+      tc::mbar_wait_bounded(&bar, phase, wait_cycles);
+      break;
+    }
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int m = 32 * (warp & 3) + lane, n0 = (warp >> 2) * 8;
     float acc[8];
@@ -180,7 +207,13 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
         out[o] = v;
       }
     }
+    // every accumulator read and every halo read of this tile is done before the next
+    // tile's shared stores and MMAs
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
   }
+  if (failed && tid == 0) atomicExch(err, (int)MLMC_ERR_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) {
@@ -234,17 +267,29 @@ __global__ void __launch_bounds__(CT_THREADS, 1)
     const int u = u0 + t, s = u / chunks, cc0 = (u - s * chunks) * kc;
     const int si = s % nx, sj = s / nx;
     // A: rows (tap, ci) of the unit, 16-byte column quads; padded rows and channels zero
-    for (int e = tid; e < mt * CT_M * kq; e += CT_THREADS) {
-      const int r = e / kq, q = e - r * kq;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r < rows) {
-        const int tap = r / cip, ci = r - tap * cip;
-        if (ci < cin) {
-          const int nb = conv_site(si + tap % 3 - 1, sj + tap / 3 - 1, nx, ny, periodic);
-          if (nb >= 0) v = __ldg((const float4 *)(in + ((size_t)nb * cin + ci) * k + cc0) + q);
+    const int nela = mt * CT_M * kq;
+    for (int base = 0; base < nela; base += STAGE_BATCH * CT_THREADS) {
+      float4 v[STAGE_BATCH];
+#pragma unroll
+      for (int b = 0; b < STAGE_BATCH; ++b) {
+        const int e = base + b * CT_THREADS + tid;
+        v[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int r = e / kq, q = e - r * kq;
+        if (e < nela && r < rows) {
+          const int tap = r / cip, ci = r - tap * cip;
+          if (ci < cin) {
+            const int nb = conv_site(si + tap % 3 - 1, sj + tap / 3 - 1, nx, ny, periodic);
+            if (nb >= 0) v[b] = __ldg((const float4 *)(in + ((size_t)nb * cin + ci) * k + cc0) + q);
+          }
         }
       }
-      tc::split_store(Ahi, Alo, (uint32_t)(r >> 3) * KSBO + (uint32_t)q * LBO + (uint32_t)(r & 7) * 16u, v);
+#pragma unroll
+      for (int b = 0; b < STAGE_BATCH; ++b) {
+        const int e = base + b * CT_THREADS + tid;
+        const int r = e / kq, q = e - r * kq;
+        if (e < nela)
+          tc::split_store(Ahi, Alo, (uint32_t)(r >> 3) * KSBO + (uint32_t)q * LBO + (uint32_t)(r & 7) * 16u, v[b]);
+      }
     }
     // B: rows co of the unit's output gradient
     for (int e = tid; e < CT_N * kq; e += CT_THREADS) {
@@ -358,8 +403,15 @@ void launch_conv_tc(const float *in, const float *W, const float *act, float *ou
   if (!conv_tc_ok(nx, k, cin, cout)) throw cuda_error{cudaErrorInvalidValue, "k_conv_tc: unsupported shape"};
   conv_attrs();
   const int tiles = nx / (CT_M / k) * ny;
-  k_conv_tc<<<tiles, CT_THREADS, conv_tc_smem(k, cin), s>>>(in, W, act, out, nx, ny, k, cin, cout, periodic, mirror,
-                                                            relu, CT_WAIT_CYCLES, err);
+  // persistent CTAs: as many as fit on the GPU at once (shared memory bounds them)
+  int dev = 0, sms = 0;
+  MLMC_CUDA(cudaGetDevice(&dev));
+  MLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t smem = conv_tc_smem(k, cin);
+  const int per_sm = (int)((227u * 1024u) / (smem + 2048u));
+  const int grid = std::min(tiles, sms * std::max(1, std::min(per_sm, 4)));
+  k_conv_tc<<<grid, CT_THREADS, smem, s>>>(in, W, act, out, nx, ny, k, cin, cout, periodic, mirror, relu,
+                                           CT_WAIT_CYCLES, err);
   MLMC_LAUNCH_CHECK("k_conv_tc");
 }
 

@@ -1721,7 +1721,10 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
     int l = level - 1;
     int lo = which == 0 ? 0 : (H.prm.precision == MLMC_PREC_MIXED_FP32 ? 1 : 0);
     if (which == 1 && !lo) fail(MLMC_ERR_INVALID_ARG, "FP32 kernels need the mixed form");
-    if (which < 0 || which > 7) fail(MLMC_ERR_INVALID_ARG, "unknown kernel family");
+    if (which < 0 || which > 8) fail(MLMC_ERR_INVALID_ARG, "unknown kernel family");
+    if (which == 8 && (l != 0 || H.prm.precision != MLMC_PREC_MIXED_FP32))
+      fail(MLMC_ERR_INVALID_ARG, "the learned correction acts on level 1 in the mixed form");
+    if (which == 8) net_alloc(H);
     if (which == 5 && l != H.L - 1) fail(MLMC_ERR_INVALID_ARG, "the dense apply lives on the coarsest level");
     if ((which == 6 || which == 7) && (l == H.L - 1 || k > H.wl[l + 1]))
       fail(MLMC_ERR_INVALID_ARG, "transfers run from a level above the coarsest, k within the coarse buffers");
@@ -1757,6 +1760,8 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
       } else if (which == 4) {
         launch_multiaxpy(t, y, Vb.p, Lv.n * (size_t)k, nvec, outb.p, H.complex_op ? C64 : F64, k, -1e-30, Lv.n, k,
                          H.stream);
+      } else if (which == 8) {
+        net_forward(H, x, k);
       } else if (which == 6) {
         launch_restrict(pview(H, l, lo), x, H.cyc[lo][l + 1].b.p, k, H.stream);
       } else if (which == 7) {
@@ -1778,7 +1783,13 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
     bool const_coef = l == 0 && !H.complex_op;      // Example 5.1 stencil has no matrix to read
     double coefb = const_coef ? 0.0 : (double)Lv.nsite * Lv.taps * Lv.d * Lv.d * es;
     double bytes;
-    if (which == 6 || which == 7) {
+    if (which == 8) {
+      // the network's activations: the block in (to channels), then per layer its input
+      // channels read and output channels written (c0 -> 16 -> 16 -> c0), FP32
+      const double pairs = (double)Lv.nsite * k, c0 = H.net_c0;
+      bytes = vec + pairs * 4.0 * (c0 + (c0 + 16) + 32 + (16 + c0));
+      if (ms_per_launch) *ms_per_launch = ms / reps;
+    } else if (which == 6 || which == 7) {
       // restriction: the fine block in, the coarse block out; prolongation: the coarse block
       // in, the fine block read and written; both read the P blocks once (none for bilinear P)
       const Level &C = H.lv[l + 1];
