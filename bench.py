@@ -103,7 +103,9 @@ def parse():
     ap.add_argument("--profile-sample", action="store_true",
                     help="for ncu only: after setup, one warm block and one profiled 64-sample block per level "
                          "difference inside cudaProfilerStart/Stop; prints no bench line")
-    ap.add_argument("--profile-kernel", default="", choices=["", "multidot", "multiaxpy", "rbgs", "rbgs2", "stencil", "dense"],
+    ap.add_argument("--profile-kernel", default="",
+                    choices=["", "multidot", "multiaxpy", "rbgs", "rbgs2", "stencil", "stencil64", "dense", "restrict",
+                             "prolong", "restrict2", "prolong2", "net", "net_simt"],
                     help="with --profile-sample: instead of sample blocks, the one kernel launch the bench's "
                          "roofline measures (3 warm launches, then 1), inside cudaProfilerStart/Stop")
     ap.add_argument("--profile-step", action="store_true",
@@ -435,12 +437,16 @@ def profile_sample(args):
     nz = mlmc.NOISE_Z4 if w["noise"] == "z4" else mlmc.NOISE_RADEMACHER
     h = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, torch.cuda.current_stream().cuda_stream)
     if args.profile_kernel:
-        which = {"stencil": 1, "rbgs": 2, "rbgs2": 2, "multidot": 3, "multiaxpy": 4, "dense": 5}[args.profile_kernel]
+        which = {"stencil": 1, "stencil64": 0, "rbgs": 2, "rbgs2": 2, "multidot": 3, "multiaxpy": 4, "dense": 5,
+                 "restrict": 6, "restrict2": 6, "prolong": 7, "prolong2": 7, "net": 8,
+                 "net_simt": 8}[args.profile_kernel]
         level, kk = 1, w["block"]
         if which == 5:
             level, kk = w["levels"], w.get("coarse_block") or w["block"]
-        elif args.profile_kernel == "rbgs2":
+        elif args.profile_kernel in ("rbgs2", "restrict2", "prolong2"):
             level, kk = 2, w.get("coarse_block") or w["block"]
+        if which == 8:
+            h.set_conv_kernel(mlmc.CONV_SIMT if args.profile_kernel == "net_simt" else mlmc.CONV_AUTO)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
         h.profile_kernel(which, level, kk, 1)
@@ -910,13 +916,18 @@ def main():
     # the arithmetic ceilings the FP64 kernels meet: measured FMA rates
     fma64 = mlmc.measure_fma_rate(True, stream)
     fma32 = mlmc.measure_fma_rate(False, stream)
-    kern["fma_rate"] = {"fp64_tfma_s": fma64 / 1e12, "fp32_tfma_s": fma32 / 1e12}
+    add64 = mlmc.measure_fma_rate(True, stream, add=True)
+    kern["fma_rate"] = {"fp64_tfma_s": fma64 / 1e12, "fp32_tfma_s": fma32 / 1e12, "fp64_tadd_s": add64 / 1e12}
     # the FP64 fine-level apply: 4 FP64 operations per element (3 additions, 1 FMA)
     if w["kind"] == "laplace" and w.get("transfer") != "bilinear":
         st = kern["stencil_fp64"]
         ops = 4.0 * w["nx"] * w["ny"] * w["block"]
         st["fp64_ops_per_s"] = ops / (st["ms"] * 1e-3)
         st["alu_frac_of_measured_fma_rate"] = st["fp64_ops_per_s"] / fma64
+        # 3 additions and 1 FMA per element at the measured rates: the FP64 ALU time floor
+        floor_s = w["nx"] * w["ny"] * w["block"] * (3.0 / add64 + 1.0 / fma64)
+        st["alu_floor_ms"] = floor_s * 1e3
+        st["alu_frac"] = floor_s * 1e3 / st["ms"]
     # dominant kernel of the timed step (largest share of the step's ncu launch list): the
     # coarse-level block Gauss-Seidel k_rbgs_half on level 2; one sweep = two launches
     dom_name = "rbgs_sweep_fp32_level2" if w["levels"] > 2 else "multidot_fp32"

@@ -445,18 +445,18 @@ void launch_scale_cols(DType t, void *y, const void *x, const void *alpha, int, 
 }
 
 // ------------------------------------------------------------------ arithmetic rate probe
-// Eight independent FMA chains per thread (x <- x a + b), enough to keep the FP64
-// or FP32 pipes busy; the result is stored only under a condition that never
+// Eight independent FMA chains per thread (x <- x a + b; or additions x <- x + b),
+// enough to keep the FP64 or FP32 pipes busy; the result is stored only under a condition that never
 // holds, so the chains are not removed.  Measures the ALU ceiling that FP64
 // kernels (apply, Arnoldi) meet on this GPU.
-template <class T>
+template <class T, bool ADD>
 __global__ void __launch_bounds__(256) k_fma_rate(T *out, int iters, T a, T b) {
   T x[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) x[q] = (T)(threadIdx.x + q) * (T)1e-3;
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = fma(x[q], a, b);
+    for (int q = 0; q < 8; ++q) x[q] = ADD ? x[q] + b : fma(x[q], a, b);
   }
   T sum = 0;
 #pragma unroll
@@ -464,11 +464,13 @@ __global__ void __launch_bounds__(256) k_fma_rate(T *out, int iters, T a, T b) {
   if (sum == (T)-1.2345) out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
 }
 
-void launch_fma_rate(DType t, void *out, int blocks, int iters, cudaStream_t s) {
-  if (t == F64)
-    k_fma_rate<double><<<blocks, 256, 0, s>>>((double *)out, iters, 0.999999, 1e-7);
+void launch_fma_rate(DType t, int add, void *out, int blocks, int iters, cudaStream_t s) {
+  if (t == F64 && add)
+    k_fma_rate<double, true><<<blocks, 256, 0, s>>>((double *)out, iters, 0.999999, 1e-7);
+  else if (t == F64)
+    k_fma_rate<double, false><<<blocks, 256, 0, s>>>((double *)out, iters, 0.999999, 1e-7);
   else
-    k_fma_rate<float><<<blocks, 256, 0, s>>>((float *)out, iters, 0.999999f, 1e-7f);
+    k_fma_rate<float, false><<<blocks, 256, 0, s>>>((float *)out, iters, 0.999999f, 1e-7f);
   MLMC_LAUNCH_CHECK("k_fma_rate");
 }
 

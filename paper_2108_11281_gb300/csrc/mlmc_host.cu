@@ -1829,17 +1829,19 @@ int mlmc_measure_fma_rate(int fp64, void *stream, double *fma_per_s) {
     int dev = 0, sms = 0;
     check_cuda(cudaGetDevice(&dev), "device");
     check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attribute");
+    if (fp64 < 0 || fp64 > 2) fail(MLMC_ERR_INVALID_ARG, "unknown operation");
     const int blocks = sms * 8, iters = fp64 ? 4096 : 65536;
     DevBuf out;
     out.alloc((size_t)blocks * 256 * 8);
     DType t = fp64 ? F64 : F32;
+    const int add = fp64 == 2;
     cudaEvent_t e0, e1;
     check_cuda(cudaEventCreate(&e0), "event");
     check_cuda(cudaEventCreate(&e1), "event");
-    launch_fma_rate(t, out.p, blocks, iters, s);                 // warm-up
+    launch_fma_rate(t, add, out.p, blocks, iters, s);            // warm-up
     check_cuda(cudaEventRecord(e0, s), "record");
     const int reps = 5;
-    for (int i = 0; i < reps; ++i) launch_fma_rate(t, out.p, blocks, iters, s);
+    for (int i = 0; i < reps; ++i) launch_fma_rate(t, add, out.p, blocks, iters, s);
     check_cuda(cudaEventRecord(e1, s), "record");
     check_cuda(cudaEventSynchronize(e1), "sync");
     float ms = 0.f;

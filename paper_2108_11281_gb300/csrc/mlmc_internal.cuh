@@ -143,9 +143,9 @@ void launch_noise(int kind, uint64_t seed, uint64_t key_hi, uint64_t first_sampl
                   DType t, void *out, cudaStream_t s);
 void launch_convert(DType to, void *dst, DType from, const void *src, size_t count, cudaStream_t s);
 void launch_fill_zero(DType t, void *dst, size_t count, cudaStream_t s);
-// blocks x 256 threads, each running 8 FMA chains of `iters` steps (F64 or F32): 2048 blocks' worth of
-// out entries are written only by a condition that never holds
-void launch_fma_rate(DType t, void *out, int blocks, int iters, cudaStream_t s);
+// blocks x 256 threads, each running 8 FMA (add = 1: addition) chains of `iters` steps (F64 or F32);
+// out (blocks x 256 entries) is written only under a condition that never holds
+void launch_fma_rate(DType t, int add, void *out, int blocks, int iters, cudaStream_t s);
 void launch_fill_one(DType t, void *dst, size_t count, cudaStream_t s);
 void launch_sub(DType t, void *out, const void *a, const void *b, size_t count, cudaStream_t s);
 // y[i][c] = alpha[c] * x[i][c] (+ y if accumulate)

@@ -361,10 +361,11 @@ def trace_estimate_batch(hierarchies, params, workers=4):
     return [result_dict(rs[i]) for i in range(n)], list(st)
 
 
-def measure_fma_rate(fp64=True, stream=0):
-    """Fused multiply-adds per second of the whole GPU (FP64 or FP32), measured."""
+def measure_fma_rate(fp64=True, stream=0, add=False):
+    """Fused multiply-adds (add=True: FP64 additions) per second of the whole GPU, measured."""
     r = ctypes.c_double()
-    check(lib.mlmc_measure_fma_rate(int(bool(fp64)), ctypes.c_void_p(stream or None), ctypes.byref(r)))
+    op = 2 if add else int(bool(fp64))
+    check(lib.mlmc_measure_fma_rate(op, ctypes.c_void_p(stream or None), ctypes.byref(r)))
     return r.value
 
 
