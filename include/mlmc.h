@@ -159,6 +159,12 @@ typedef struct {
                           restrictions the noise needs (nnz(P_j) each) plus one product with
                           each operator solved with (nnz(A_l), nnz(A_{l+1}); n_L^2 for the
                           coarsest dense inverse).  N_l then depends on the samples alone.   */
+  int tau_separate;    /* 0 (default): tau's five full estimates (Sec. 5) are samples 0..4 of
+                          every level's noise stream, which also count in the level means (so
+                          rho_l and N_l correlate with the means they control); 1: they come
+                          from five separate samples per level (Philox purpose
+                          MLMC_PURPOSE_WARMUP) that do not enter the means (their solves are
+                          not in cost_nnz)                                                     */
 } mlmc_estimate_params;
 
 typedef struct {

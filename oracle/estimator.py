@@ -26,7 +26,8 @@ is below its count and sum_l V_l / N_l <= (eps tau)^2.
 Stopping rule (Sec. 5): five full estimates t_1..t_5 (one sample per level
 difference plus the exact term) give tau = mean(t) - rms(t - mean(t)) (real
 parts).  They are samples 0..4 of each level's noise stream, taken from the
-first block every level draws, and they also count in the level means.
+first block every level draws, and they also count in the level means (or,
+with tau_separate, samples 0..4 of the warm-up stream, which do not).
 rho_l = sqrt(w_l) eps |tau| with sum w_l = 1 (default w_l = 1/(L-1)); level l
 then draws further blocks of `block` samples until N_l >= 5 and the standard
 error sqrt(V_l / N_l) <= rho_l.
@@ -151,8 +152,21 @@ def optimal_allocation(variances, costs, target, min_samples=5):
     return N, counts, np.sqrt(V * C) / S
 
 
+def five_estimates(levels, solvers, kind, seed, TL, form, hats, acc, separate):
+    """The five full estimates of Sec. 5 (one sample per level difference plus the exact
+    term): samples 0..4 of every level's noise stream (held in acc), or, separate, samples
+    0..4 of the warm-up stream (Philox purpose 1), which do not enter the level means."""
+    warm = np.zeros(5, dtype=np.complex128) + TL
+    for l, a in enumerate(acc, start=1):
+        if separate:
+            warm += level_samples(levels, solvers, l, kind, seed, 0, 5, form, PURPOSE_WARMUP, hats)
+        else:
+            warm += np.asarray(a.values[:5])
+    return warm
+
+
 def trace_estimate(levels, kind, seed=0, eps=1e-3, weights=None, block=64, min_samples=5,
-                   max_samples=1 << 20, form="simplified", solvers=None):
+                   max_samples=1 << 20, form="simplified", solvers=None, tau_separate=False):
     """Sec. 5 procedure; returns an EstimateResult."""
     L = len(levels)
     solvers = solvers or LevelSolvers(levels)
@@ -170,9 +184,7 @@ def trace_estimate(levels, kind, seed=0, eps=1e-3, weights=None, block=64, min_s
         while acc[l - 1].n < 5:
             a = acc[l - 1]
             a.add(level_samples(levels, solvers, l, kind, seed, a.n, block, form, PURPOSE_NOISE, hats))
-    warm = np.zeros(5, dtype=np.complex128) + TL
-    for a in acc:
-        warm += np.asarray(a.values[:5])
+    warm = five_estimates(levels, solvers, kind, seed, TL, form, hats, acc, tau_separate)
     tr = warm.real
     tau = tr.mean() - np.sqrt(np.mean((tr - tr.mean()) ** 2))
     w = np.full(L - 1, 1.0 / (L - 1)) if weights is None else np.asarray(weights, dtype=float)
@@ -219,7 +231,7 @@ def nominal_sample_cost(levels, l, form="simplified"):
 
 
 def optimal_trace_estimate(levels, kind, seed=0, eps=1e-3, widths=64, min_samples=5, max_samples=1 << 24,
-                           form="simplified", solvers=None, costs=None):
+                           form="simplified", solvers=None, costs=None, tau_separate=False):
     """Sec. 2's optimal sample allocation, with V_l and C_l estimated as the samples arrive.
 
     widths: samples per block, one value for every level difference or a list (the
@@ -266,9 +278,7 @@ def optimal_trace_estimate(levels, kind, seed=0, eps=1e-3, widths=64, min_sample
         while acc[i].n < 5:
             if not draw(i):
                 raise ValueError("max_samples allows fewer than five samples per level")
-    warm = np.zeros(5, dtype=np.complex128) + TL
-    for a in acc:
-        warm += np.asarray(a.values[:5])
+    warm = five_estimates(levels, solvers, kind, seed, TL, form, hats, acc, tau_separate)
     tr = warm.real
     tau = tr.mean() - np.sqrt(np.mean((tr - tr.mean()) ** 2))
     T2 = (eps * abs(tau)) ** 2

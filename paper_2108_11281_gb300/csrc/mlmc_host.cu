@@ -1608,7 +1608,7 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
       bool conv = true;
       sample_block(H, l, p->noise, p->seed, (uint64_t)N0, k, p->tol, MLMC_PURPOSE_NOISE, &conv, p->form);
       if (!conv) fail(MLMC_ERR_NOT_CONVERGED, "level solve did not converge");
-      if (N0 < 5) {
+      if (N0 < 5 && !p->tau_separate) {
         copy_samples_out(H, k, tmp.data());
         for (int i = N0; i < std::min(5, N0 + k); ++i) warm[i] += tmp[i - N0].re;
       }
@@ -1623,7 +1623,22 @@ int mlmc_trace_estimate(mlmc_hierarchy *h, const mlmc_estimate_params *p, mlmc_e
     };
     auto var = [&](int l) { double N = st[4 * l]; return N > 1 ? st[4 * l + 3] / (N - 1) : INFINITY; };
     // Sec. 5: five full estimates (one sample per level difference plus the exact term);
-    // they are samples 0..4 of every level's stream, drawn with each level's first block
+    // they are samples 0..4 of every level's stream, drawn with each level's first block,
+    // or (tau_separate) five samples of the warm-up stream that do not enter the means
+    if (p->tau_separate) {
+      for (int l = 0; l < nd; ++l)
+        for (int done = 0; done < 5;) {
+          const int k = std::min(5 - done, width(l));
+          bool conv = true;
+          const double c0 = H.cost;
+          sample_block(H, l, p->noise, p->seed, (uint64_t)done, k, p->tol, MLMC_PURPOSE_WARMUP, &conv, p->form);
+          H.cost = c0;
+          if (!conv) fail(MLMC_ERR_NOT_CONVERGED, "level solve did not converge");
+          copy_samples_out(H, k, tmp.data());
+          for (int i = 0; i < k; ++i) warm[done + i] += tmp[i].re;
+          done += k;
+        }
+    }
     for (int l = 0; l < nd; ++l)
       while (st[4 * l] < 5)
         if (!draw(l)) fail(MLMC_ERR_INVALID_ARG, "fewer than five samples allowed on a level");

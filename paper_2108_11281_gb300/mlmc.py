@@ -57,7 +57,7 @@ class EstimateParams(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("weights", ctypes.c_double * 16), ("noise", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("tol", ctypes.c_double), ("min_samples", ctypes.c_int),
                 ("max_samples", ctypes.c_int), ("form", ctypes.c_int), ("allocation", ctypes.c_int),
-                ("n_fixed", ctypes.c_int * 16), ("cost_model", ctypes.c_int)]
+                ("n_fixed", ctypes.c_int * 16), ("cost_model", ctypes.c_int), ("tau_separate", ctypes.c_int)]
 
 
 class EstimateResult(ctypes.Structure):
@@ -261,9 +261,10 @@ class Hierarchy:
 
     def trace_estimate(self, eps=1e-3, noise=NOISE_RADEMACHER, seed=0, tol=1e-10, weights=None, min_samples=5,
                        max_samples=1 << 24, form=FORM_SIMPLIFIED, allocation=ALLOC_RHO, n_fixed=None,
-                       cost_model=COST_COUNTED):
+                       cost_model=COST_COUNTED, tau_separate=0):
         p = EstimateParams(eps=eps, noise=noise, seed=seed, tol=tol, min_samples=min_samples,
-                           max_samples=max_samples, form=form, allocation=allocation, cost_model=cost_model)
+                           max_samples=max_samples, form=form, allocation=allocation, cost_model=cost_model,
+                           tau_separate=tau_separate)
         if n_fixed is not None:
             for i, n in enumerate(n_fixed):
                 p.n_fixed[i] = n

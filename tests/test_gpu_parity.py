@@ -260,13 +260,17 @@ def test_wilson_d8_level_apply_and_samples(mlmc, precision, rtol):
     h.close()
 
 
-def test_trace_estimate_matches_oracle(mlmc):
-    """Sec. 5 procedure on a 32x32 Laplacian, 2 levels: same tau, same N_l, same estimate."""
+@pytest.mark.parametrize("tau_separate", [0, 1])
+def test_trace_estimate_matches_oracle(mlmc, tau_separate):
+    """Sec. 5 procedure on a 32x32 Laplacian, 2 levels: same tau, same N_l, same estimate;
+    tau from samples 0..4 of the noise stream (counted in the means) or from five separate
+    warm-up samples."""
     N = 32
     h = laplace_h(mlmc, N, 2, block=16, n_tv=1, setup_kind=mlmc.SETUP_CONSTANT, bootstrap=0)
-    r = mlmc.result_dict(h.trace_estimate(eps=2e-2, noise=mlmc.NOISE_RADEMACHER, seed=4, tol=1e-12))
+    r = mlmc.result_dict(h.trace_estimate(eps=2e-2, noise=mlmc.NOISE_RADEMACHER, seed=4, tol=1e-12,
+                                          tau_separate=tau_separate))
     lv = build_hierarchy(laplace2d(N, N), N, N, 1, SetupParams(levels=2, n_tv=1, kind="constant"))
-    ref = E.trace_estimate(lv, "rademacher", seed=4, eps=2e-2, block=16)
+    ref = E.trace_estimate(lv, "rademacher", seed=4, eps=2e-2, block=16, tau_separate=bool(tau_separate))
     assert r["n_samples"] == ref.n_samples
     assert abs(r["tau"] - ref.tau) <= 1e-9 * abs(ref.tau)
     assert abs(r["trace"] - ref.trace) <= 1e-9 * abs(ref.trace)

@@ -333,6 +333,33 @@ def test_stopping_rule_closed_form(monkeypatch):
         assert abs(r.std_err - se) <= 1e-12 * se
 
 
+def test_tau_from_separate_warmup_samples(monkeypatch):
+    """Sec. 5 with tau from separate samples: the five full estimates use the warm-up
+    stream (level l: s_i = 2 mu_l + 3 sigma_l (-1)^i there), the level means only the noise
+    stream (s_i = mu_l + sigma_l (-1)^i), so tau = m' + S'/5 - sqrt(0.96) S' with
+    m' = T_L + 2 sum mu_l, S' = 3 sum sigma_l, and the estimate is still exactly m."""
+    from oracle.philox import PURPOSE_WARMUP
+    mu, sigma, TL = [10.0, 5.0], [3.0, 1.0], 100.0
+
+    def fake_samples(levels, solvers, l, kind, seed, first, count, form="simplified", purpose=0, hats=None):
+        i = np.arange(first, first + count)
+        if purpose == PURPOSE_WARMUP:
+            return 2 * mu[l - 1] + 3 * sigma[l - 1] * (-1.0) ** i + 0j
+        return mu[l - 1] + sigma[l - 1] * (-1.0) ** i + 0j
+
+    monkeypatch.setattr(E, "level_samples", fake_samples)
+    monkeypatch.setattr(E, "exact_coarse_trace", lambda levels, form="simplified": TL)
+    m2, S2 = TL + 2 * sum(mu), 3 * sum(sigma)
+    tau = m2 + S2 / 5 - np.sqrt(0.96) * S2
+    for run in (lambda: E.trace_estimate([None] * 3, "rademacher", eps=0.01, block=8, solvers=object(),
+                                         tau_separate=True),
+                lambda: E.optimal_trace_estimate([None] * 3, "rademacher", eps=0.01, widths=8, costs=[10.0, 1.0],
+                                                 solvers=object(), tau_separate=True)):
+        r = run()
+        assert abs(r.tau - tau) <= 1e-12 * tau
+        assert abs(r.trace - (TL + sum(mu))) <= 1e-12 * (TL + sum(mu))
+
+
 def test_nominal_sample_cost_hand_counts():
     """Sec. 5 cost model (a product B x costs nnz(B)) of one sample, counted by hand.
     64^2 Dirichlet Laplacian, 2 levels, piecewise-constant P: nnz(A_1) = 5*4096 - 4*64
