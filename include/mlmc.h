@@ -232,6 +232,23 @@ int mlmc_noise(int noise, uint64_t seed, int level, int purpose, uint64_t first,
 int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, uint64_t first,
                       int n_samples, double tol, mlmc_c64 *out_samples, int *out_iters);
 
+/* One block of level-difference samples for a caller-driven estimate, e.g. one
+ * estimate whose blocks are spread over several GPUs (Sec. 2 estimator; the
+ * per-level statistics of Sec. 5 are merged block by block): samples
+ * first .. first + k - 1 of level difference `level` (1 <= level < L) in the
+ * given form (as mlmc_sample_level_form), 1 <= k <= that level difference's
+ * block width.  out_samples (host, optional): the k samples.  out_stats (host,
+ * optional, 4 doubles): the block's N, mean (re, im) and sum of |s - mean|^2,
+ * from the device's fixed-order reduction.  out_cost (host, optional): the
+ * Sec. 5 cost model of the block's products.  Synchronous on return. */
+int mlmc_sample_block(mlmc_hierarchy *h, int level, int form, int noise, uint64_t seed, uint64_t first, int k,
+                      double tol, mlmc_c64 *out_samples, double *out_stats, double *out_cost);
+/* Samples per block on level difference `level` (1 <= level < L): the widths the
+ * estimate draws (block, coarse_block, coarse_growth, mlmc_set_block_width). */
+int mlmc_block_width(const mlmc_hierarchy *h, int level, int *k);
+/* The nominal per-sample cost of level difference `level` (MLMC_COST_NOMINAL). */
+int mlmc_nominal_sample_cost(const mlmc_hierarchy *h, int level, int form, double *out);
+
 /* Column dots out[c] = sum_i conj(x[i][c]) y[i][c] of two device blocks [n][k]
  * (the x_j^* y_j products of the difference samples, Remark 4.3), in FP64:
  * double (complex = 0) or interleaved complex double (complex = 1) inputs; out

@@ -1428,6 +1428,54 @@ int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, ui
   });
 }
 
+int mlmc_sample_block(mlmc_hierarchy *h, int level, int form, int noise, uint64_t seed, uint64_t first, int k,
+                      double tol, mlmc_c64 *out_samples, double *out_stats, double *out_cost) {
+  return translate([&] {
+    need_level(h, level, 1, h ? h->L - 1 : 0);
+    if (form != MLMC_FORM_SIMPLIFIED && form != MLMC_FORM_HAT && form != MLMC_FORM_PLAIN)
+      fail(MLMC_ERR_INVALID_ARG, "unknown form");
+    if (form == MLMC_FORM_PLAIN && level != 1) fail(MLMC_ERR_INVALID_ARG, "plain samples live on level 1");
+    if (form == MLMC_FORM_SIMPLIFIED && h->bilinear)
+      fail(MLMC_ERR_INVALID_ARG, "the simplified form needs R P = I; use the hat form with a bilinear hierarchy");
+    if (noise == MLMC_NOISE_Z4 && !h->complex_op) fail(MLMC_ERR_INVALID_ARG, "Z4 noise needs a complex operator");
+    if (!(tol > 0.0)) fail(MLMC_ERR_INVALID_ARG, "tol must be positive");
+    if (k < 1 || k > h->kdiff(level - 1)) fail(MLMC_ERR_INVALID_ARG, "k must be within the level's block width");
+    H_t &H = *h;
+    bool conv = true;
+    const double c0 = H.cost;
+    sample_block(H, level - 1, noise, seed, first, k, tol, MLMC_PURPOSE_NOISE, &conv, form);
+    if (out_cost) *out_cost = H.cost - c0;
+    if (out_stats) {
+      // the block's own (N, mean, M2) by the device's fixed-order reduction
+      check_cuda(cudaMemsetAsync(H.acc.p, 0, 4 * sizeof(double), H.stream), "memset acc");
+      launch_accumulate(H.samples.p, k, H.acc.as<double>(), H.stream);
+      H.launches++;
+      check_cuda(cudaMemcpyAsync(out_stats, H.acc.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, H.stream),
+                 "D2H stats");
+    }
+    if (out_samples) copy_samples_out(H, k, out_samples);
+    check_cuda(cudaStreamSynchronize(H.stream), "sync");
+    check_timeout(H);
+    if (!conv) fail(MLMC_ERR_NOT_CONVERGED, "a level solve did not reach tol within max_iter");
+  });
+}
+
+int mlmc_block_width(const mlmc_hierarchy *h, int level, int *k) {
+  return translate([&] {
+    need_level(h, level, 1, h ? h->L - 1 : 0);
+    if (!k) fail(MLMC_ERR_INVALID_ARG, "null output");
+    *k = h->kdiff(level - 1);
+  });
+}
+
+int mlmc_nominal_sample_cost(const mlmc_hierarchy *h, int level, int form, double *out) {
+  return translate([&] {
+    need_level(h, level, 1, h ? h->L - 1 : 0);
+    if (!out) fail(MLMC_ERR_INVALID_ARG, "null output");
+    *out = nominal_sample_cost(*h, level - 1, form);
+  });
+}
+
 int mlmc_column_dots(int complex_data, const void *x, const void *y, int n, int k, void *out, void *stream) {
   return translate([&] {
     if (!x || !y || !out || n < 1 || k < 1 || k > 256) fail(MLMC_ERR_INVALID_ARG, "bad column-dot arguments (k must be in 1..256)");

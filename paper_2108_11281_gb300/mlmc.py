@@ -121,6 +121,9 @@ def _load():
         "mlmc_learned_stats": [vp, ctypes.POINTER(i), ctypes.POINTER(i)],
         "mlmc_measure_fma_rate": [i, vp, ctypes.POINTER(d)],
         "mlmc_set_conv_kernel": [vp, i],
+        "mlmc_sample_block": [vp, i, i, i, u64, u64, i, d, ctypes.POINTER(C64), ctypes.POINTER(d), ctypes.POINTER(d)],
+        "mlmc_nominal_sample_cost": [vp, i, i, ctypes.POINTER(d)],
+        "mlmc_block_width": [vp, i, ctypes.POINTER(i)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -141,7 +144,8 @@ EXPORTED = ["mlmc_setup_hierarchy", "mlmc_destroy_hierarchy", "mlmc_level_info",
             "mlmc_column_dots", "mlmc_column_dots_noalloc", "mlmc_noalloc_last_error", "mlmc_set_block_width",
             "mlmc_autotune_block", "mlmc_trace_estimate_batch", "mlmc_sample_level_form", "mlmc_dense_apply",
             "mlmc_set_dense_kernel", "mlmc_level_taps", "mlmc_learned_stats",
-            "mlmc_measure_fma_rate", "mlmc_set_conv_kernel"]
+            "mlmc_measure_fma_rate", "mlmc_set_conv_kernel", "mlmc_sample_block", "mlmc_nominal_sample_cost",
+            "mlmc_block_width"]
 
 
 def check(status):
@@ -320,6 +324,27 @@ class Hierarchy:
 
     def set_dense_kernel(self, which):
         check(lib.mlmc_set_dense_kernel(self.handle, which))
+
+    def sample_block(self, level, form, noise, seed, first, k, tol):
+        """(samples, (N, mean, M2), cost) of one block of level-difference samples."""
+        out = (C64 * k)()
+        st = (ctypes.c_double * 4)()
+        cost = ctypes.c_double()
+        check(lib.mlmc_sample_block(self.handle, level, form, noise, seed, first, k, tol, out, st,
+                                    ctypes.byref(cost)))
+        samples = np.array([complex(v.re, v.im) for v in out])
+        return samples, (st[0], complex(st[1], st[2]), st[3]), cost.value
+
+    def nominal_sample_cost(self, level, form=FORM_SIMPLIFIED):
+        r = ctypes.c_double()
+        check(lib.mlmc_nominal_sample_cost(self.handle, level, form, ctypes.byref(r)))
+        return r.value
+
+    def block_width(self, level):
+        """Samples per block on level difference `level` (1-based)."""
+        r = ctypes.c_int()
+        check(lib.mlmc_block_width(self.handle, level, ctypes.byref(r)))
+        return r.value
 
     def set_conv_kernel(self, which):
         check(lib.mlmc_set_conv_kernel(self.handle, which))
