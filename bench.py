@@ -120,6 +120,9 @@ def parse():
                          "workload: seconds, device-counted cost (Sec. 5 model) and N per method; one JSON line")
     ap.add_argument("--alloc", default="optimal", choices=["optimal", "rho"],
                     help="Sec. 2 optimal allocation (default) or the Sec. 5 equal rho split")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several GPUs: independent estimates (disjoint seeds) instead of one estimate whose "
+                         "samples are spread over the GPUs")
     ap.add_argument("--cost-model", default="nominal", choices=["counted", "nominal"],
                     help="per-sample cost C_l of the optimal allocation: products the solves performed "
                          "(counted) or one product per operator solved with (nominal, solver-independent)")
@@ -849,10 +852,28 @@ def main():
         return mlmc.result_dict(hh.trace_estimate(eps=w["eps"], noise=nz, seed=seed, tol=tol,
                                                   allocation=alloc, form=form, cost_model=cost_model))
 
+    if world > 1 and not args.replicas:
+        # one estimate over all ranks: disjoint blocks of one sample stream per rank, block
+        # statistics all-gathered over NCCL after every round (sharded.py); nominal costs
+        from paper_2108_11281_gb300 import sharded
+        gather = sharded.torch_allgather("cuda")
+        serial_step = step
+
+        def step(hh, tol, seed):
+            if hh is not h:
+                return serial_step(hh, tol, seed)
+            smp = sharded.HierarchySampler(hh, nz, w["seed"], tol, form)
+            r = sharded.sharded_trace_estimate(smp, gather, rank, world, eps=w["eps"],
+                                               allocation="optimal" if args.alloc == "optimal" else "rho")
+            r.update(trace=complex(r["trace"]), coarse_term=complex(r["coarse_term"]),
+                     iters=None, seconds=None, cost_nnz=None)
+            return r
+
     if w.get("learned"):
         h.learned_train(n_pairs=w["train_pairs"], epochs=w["train_epochs"], lr=w["train_lr"],
                         tol=w["tol_mixed"], seed=7, enable=1)
-    seed = replica_seed(w["seed"], rank)    # replicas draw disjoint noise
+    # replicas (--replicas) draw disjoint noise; the sharded estimate shares one stream
+    seed = replica_seed(w["seed"], rank) if args.replicas else w["seed"]
     for _ in range(args.warmup):
         res = step(h, w["tol_mixed"], seed)
 
@@ -880,7 +901,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     launches = (h.launch_count() - l0) // max(args.steps, 1)
     t_step = max_over_ranks(ms / 1e3 / args.steps, "cuda")
-    value = job_value(t_step, world)       # seconds per trace over all replicas
+    # replicas: seconds per trace over all of them; sharded: the one estimate's seconds
+    value = job_value(t_step, world) if args.replicas else t_step
     res = results[-1]
 
     # dominant kernels, timed alone with CUDA events on the hierarchy's stream
@@ -989,7 +1011,8 @@ def main():
         import ctypes
         line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
+                "scaling": "weak" if (args.replicas or world == 1) else "strong", "vs_baseline": None,
+                "dtype": "f64/f32", "data": "synthetic",
                 "config": dict(config_dict("mixed: FP32 K-cycle under FP64 FGMRES", w), allocation=args.alloc,
                                cost_model=args.cost_model),
                 "clocks": sampler.summary(local), "gpu_launches": int(launches), "wall_s_timed": wall,

@@ -86,17 +86,19 @@ constexpr int STAGE_BATCH = 8;
 // mirror = 1: backward-data, B[n][tap][c] = W[c][n][tap] (W is [cin][cout][9]) with tap
 // (tx, ty) reading the site at offset (1 - tx, 1 - ty).  act (mask, optional): out =
 // acc where act[s][n][c] > 0, else 0.
+// K (columns) and CIP (input channels padded to 8 or 16) are compile-time, so the
+// staging index arithmetic is shifts and masks: the kernel was issue-bound on it.
+template <int K, int CIP>
 __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict__ in, const float *__restrict__ W,
                                                         const float *__restrict__ act, float *__restrict__ out,
-                                                        int nx, int ny, int k, int cin, int cout, int periodic,
+                                                        int nx, int ny, int cin, int cout, int periodic,
                                                         int mirror, int relu, long long wait_cycles, int *err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_base;
   __shared__ int failed;
+  constexpr int k = K, cip = CIP, c4n = CIP / 4, ts = CT_M / K, kg = K / 8, hw = ts + 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ts = CT_M / k, kg = k >> 3, hw = ts + 2;
-  const int cip = pad8(cin), c4n = cip / 4;
   const int tiles_x = nx / ts, tiles = tiles_x * ny;
   const uint32_t LBO = 128u, SBO = (uint32_t)c4n * 128u;
   const uint32_t halo_bytes = (uint32_t)(3 * hw * kg) * SBO;
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = tc::tf32_idesc(CT_M, CT_N);
-  const int nel = 3 * hw * c4n * k;            // 16-byte halo elements per tile
+  constexpr int nel = 3 * hw * c4n * k;        // 16-byte halo elements per tile
 
   uint32_t phase = 0;
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, phase ^= 1u) {
@@ -182,14 +184,15 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
         }
       }
       tc::mma_commit(&bar);
+      // one thread waits for the commit; the others sleep in the barrier below
+      if (!tc::mbar_wait_bounded(&bar, phase, wait_cycles)) {
+        failed = 1;
+        // give the MMAs in flight one more bounded chance before the memory goes
+        tc::mbar_wait_bounded(&bar, phase, wait_cycles);
+      }
     }
-    if (!tc::mbar_wait_bounded(&bar, phase, wait_cycles)) failed = 1;
     __syncthreads();
-    if (failed) {
-      // give the MMAs in flight one more bounded chance before the memory goes
-      tc::mbar_wait_bounded(&bar, phase, wait_cycles);
-      break;
-    }
+    if (failed) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int m = 32 * (warp & 3) + lane, n0 = (warp >> 2) * 8;
     float acc[8];
@@ -260,7 +263,8 @@ __global__ void __launch_bounds__(CT_THREADS, 1)
     const int buf = t & 1;
     unsigned char *Ahi = smem + buf * sbytes, *Alo = Ahi + abytes, *Bhi = Alo + abytes, *Blo = Bhi + bbytes;
     if (t >= 2) {
-      if (!tc::mbar_wait_bounded(&bars[buf], (uint32_t)(((t >> 1) - 1) & 1), wait_cycles)) failed = 1;
+      // one thread waits for the MMAs of unit t - 2 (they read this buffer); the rest sleep
+      if (tid == 0 && !tc::mbar_wait_bounded(&bars[buf], (uint32_t)(((t >> 1) - 1) & 1), wait_cycles)) failed = 1;
       __syncthreads();
       if (failed) break;
     }
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1)
     issued = t + 1;
   }
   // drain: the last commit of each stage that nobody waited for yet
-  if (issued > 0) {
+  if (issued > 0 && tid == 0) {
     const int tl = issued - 1;
     bool ok = true;
     if (!failed) {
@@ -390,8 +394,14 @@ static void conv_attrs() {
   MLMC_CUDA(cudaGetDevice(&dev));
   std::call_once(g_conv_attr_once[dev & 63], [] {
     const int a = (int)conv_tc_smem(128, 16), b = (int)wgrad_tc_smem(16, WG_KC);
-    check_cuda(cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, a),
-               "cudaFuncSetAttribute(k_conv_tc)");
+    const void *fs[] = {(const void *)k_conv_tc<8, 8>,   (const void *)k_conv_tc<8, 16>,
+                        (const void *)k_conv_tc<16, 8>,  (const void *)k_conv_tc<16, 16>,
+                        (const void *)k_conv_tc<32, 8>,  (const void *)k_conv_tc<32, 16>,
+                        (const void *)k_conv_tc<64, 8>,  (const void *)k_conv_tc<64, 16>,
+                        (const void *)k_conv_tc<128, 8>, (const void *)k_conv_tc<128, 16>};
+    for (const void *f : fs)
+      check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, a),
+                 "cudaFuncSetAttribute(k_conv_tc)");
     check_cuda(cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, b),
                "cudaFuncSetAttribute(k_conv_wgrad_tc)");
     g_conv_smem_max = a > b ? a : b;
@@ -403,6 +413,7 @@ void launch_conv_tc(const float *in, const float *W, const float *act, float *ou
   if (!conv_tc_ok(nx, k, cin, cout)) throw cuda_error{cudaErrorInvalidValue, "k_conv_tc: unsupported shape"};
   conv_attrs();
   const int tiles = nx / (CT_M / k) * ny;
+  const int cip = pad8(cin);
   // persistent CTAs: as many as fit on the GPU at once (shared memory bounds them)
   int dev = 0, sms = 0;
   MLMC_CUDA(cudaGetDevice(&dev));
@@ -410,8 +421,15 @@ void launch_conv_tc(const float *in, const float *W, const float *act, float *ou
   const size_t smem = conv_tc_smem(k, cin);
   const int per_sm = (int)((227u * 1024u) / (smem + 2048u));
   const int grid = std::min(tiles, sms * std::max(1, std::min(per_sm, 4)));
-  k_conv_tc<<<grid, CT_THREADS, smem, s>>>(in, W, act, out, nx, ny, k, cin, cout, periodic, mirror, relu,
-                                           CT_WAIT_CYCLES, err);
+#define MLMC_CONV_TC(KK, CC)                                                                                  \
+  if (k == KK && cip == CC) {                                                                                 \
+    k_conv_tc<KK, CC><<<grid, CT_THREADS, smem, s>>>(in, W, act, out, nx, ny, cin, cout, periodic, mirror, relu, \
+                                                     CT_WAIT_CYCLES, err);                                     \
+  } else
+  MLMC_CONV_TC(8, 8) MLMC_CONV_TC(8, 16) MLMC_CONV_TC(16, 8) MLMC_CONV_TC(16, 16) MLMC_CONV_TC(32, 8)
+  MLMC_CONV_TC(32, 16) MLMC_CONV_TC(64, 8) MLMC_CONV_TC(64, 16) MLMC_CONV_TC(128, 8) MLMC_CONV_TC(128, 16)
+  throw cuda_error{cudaErrorInvalidValue, "k_conv_tc: unsupported shape"};
+#undef MLMC_CONV_TC
   MLMC_LAUNCH_CHECK("k_conv_tc");
 }
 

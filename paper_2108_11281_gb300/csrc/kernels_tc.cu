@@ -174,8 +174,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char *Ahi = smem + buf * sbytes, *Alo = Ahi + A_BYTES;
     unsigned char *Bhi = Ahi + 2 * A_BYTES, *Blo = Bhi + bb;
     if (t >= 2) {
-      // the MMAs of step t-2 read this stage: wait for their commit
-      if (!mbar_wait_bounded(&bars[buf], (uint32_t)(((t >> 1) - 1) & 1), wait_cycles)) failed = 1;
+      // the MMAs of step t-2 read this stage: one thread waits for their commit, the
+      // others sleep in the barrier
+      if (tid == 0 && !mbar_wait_bounded(&bars[buf], (uint32_t)(((t >> 1) - 1) & 1), wait_cycles)) failed = 1;
       __syncthreads();
       if (failed) break;
     }
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 
   // drain: the last commit of each stage that nobody waited for yet
-  if (issued > 0) {
+  if (issued > 0 && tid == 0) {
     const int tl = issued - 1;
     bool ok = true;
     if (!failed) {

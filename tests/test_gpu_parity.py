@@ -468,3 +468,25 @@ def test_block_width_growth_keeps_samples(mlmc):
     assert abs(r0["trace"] - r1["trace"]) <= 1e-9 * abs(r0["trace"])
     h0.close()
     h1.close()
+
+
+def test_sharded_driver_one_rank_matches_library_estimate(mlmc):
+    """The multi-GPU driver (sharded.py) on one rank draws its blocks through
+    mlmc_sample_block and merges their device statistics on the host: the same N_l, tau
+    and trace (1e-12) as mlmc_trace_estimate's loop with nominal costs, and the sharded
+    blocks reproduce mlmc_sample_level's samples."""
+    from paper_2108_11281_gb300 import sharded
+    h, lv = imported_laplace(mlmc, N=32, levels=3, block=16, coarse_block=16)
+    r = mlmc.result_dict(h.trace_estimate(eps=1e-2, noise=mlmc.NOISE_RADEMACHER, seed=2, tol=1e-12,
+                                          allocation=mlmc.ALLOC_OPTIMAL, cost_model=mlmc.COST_NOMINAL))
+    smp = sharded.HierarchySampler(h, mlmc.NOISE_RADEMACHER, 2, 1e-12)
+    s = sharded.sharded_trace_estimate(smp, lambda v: [v], 0, 1, eps=1e-2)
+    assert s["n_samples"] == r["n_samples"]
+    assert abs(s["tau"] - r["tau"]) <= 1e-12 * abs(r["tau"])
+    assert abs(s["trace"] - r["trace"]) <= 1e-12 * abs(r["trace"])
+    blk, stats, cost = h.sample_block(2, mlmc.FORM_SIMPLIFIED, mlmc.NOISE_RADEMACHER, 2, 16, 16, 1e-12)
+    ref, _ = h.sample_level(2, mlmc.NOISE_RADEMACHER, 2, 16, 16, 1e-12)
+    assert np.abs(blk - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert stats[0] == 16 and abs(stats[1] - blk.mean()) <= 1e-12 * abs(blk.mean())
+    assert cost > 0 and h.block_width(1) == 16 and h.nominal_sample_cost(1) == E.nominal_sample_cost(lv, 1)
+    h.close()
