@@ -27,23 +27,36 @@ def levels():
 
 
 class OracleSampler:
-    """Blocks of exact-solve samples (oracle) with their (N, mean, M2)."""
+    """Blocks of exact-solve samples (oracle) with their (N, mean, M2).  The samples are
+    computed once (NS per level) and handed to every rank, so that all ranks and runs see
+    the same floating-point values whatever the BLAS threading of each process."""
+    NS = 256
 
-    def __init__(self, lv):
-        self.lv, self.sv = lv, E.LevelSolvers(lv)
-        self.n_differences = len(lv) - 1
+    def __init__(self, table):
+        self.table = table
+        self.n_differences = len(table["samples"])
+
+    @staticmethod
+    def make_table():
+        lv = levels()
+        sv = E.LevelSolvers(lv)
+        return {"samples": [E.level_samples(lv, sv, l, "rademacher", SEED, 0, OracleSampler.NS)
+                            for l in range(1, len(lv))],
+                "costs": [E.nominal_sample_cost(lv, l) for l in range(1, len(lv))],
+                "term": float(np.real(E.exact_coarse_trace(lv)))}
 
     def width(self, l):
         return WIDTHS[l - 1]
 
     def cost(self, l):
-        return E.nominal_sample_cost(self.lv, l)
+        return self.table["costs"][l - 1]
 
     def coarse_term(self):
-        return float(np.real(E.exact_coarse_trace(self.lv)))
+        return self.table["term"]
 
     def block(self, l, first, k):
-        s = E.level_samples(self.lv, self.sv, l, "rademacher", SEED, first, k)
+        assert first + k <= self.NS
+        s = self.table["samples"][l - 1][first:first + k]
         m = s.mean()
         return s, (k, complex(m), float(np.sum(np.abs(s - m) ** 2)))
 
@@ -56,17 +69,22 @@ def _free_port():
     return port
 
 
-def _rank_main(rank, world, port, out):
+def _rank_main(rank, world, port, table, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    r = S.sharded_trace_estimate(OracleSampler(levels()), S.torch_allgather("cpu"), rank, world, eps=EPS)
+    r = S.sharded_trace_estimate(OracleSampler(table), S.torch_allgather("cpu"), rank, world, eps=EPS)
     dist.barrier()
     out[rank] = r
     dist.destroy_process_group()
 
 
-def single(allocation="optimal", n_fixed=None):
-    return S.sharded_trace_estimate(OracleSampler(levels()), lambda v: [v], 0, 1, eps=EPS, allocation=allocation,
+@pytest.fixture(scope="module")
+def table():
+    return OracleSampler.make_table()
+
+
+def single(table, allocation="optimal", n_fixed=None):
+    return S.sharded_trace_estimate(OracleSampler(table), lambda v: [v], 0, 1, eps=EPS, allocation=allocation,
                                     n_fixed=n_fixed)
 
 
@@ -85,23 +103,23 @@ def test_merge_is_the_two_pass_statistics():
     assert abs(acc[2] - np.sum(np.abs(x - x.mean()) ** 2)) <= 1e-12 * acc[2]
 
 
-def test_one_rank_follows_the_oracle_allocation_loop():
+def test_one_rank_follows_the_oracle_allocation_loop(table):
     """One rank: the same N_l, tau and trace as the oracle's Sec. 2 loop on the same samples."""
-    r = single()
+    r = single(table)
     ref = E.optimal_trace_estimate(levels(), "rademacher", seed=SEED, eps=EPS, widths=WIDTHS)
     assert r["n_samples"] == ref.n_samples
     assert abs(r["tau"] - ref.tau) <= 1e-12 * abs(ref.tau)
     assert abs(r["trace"] - ref.trace) <= 1e-12 * abs(ref.trace)
 
 
-def test_two_ranks_equal_one_rank_over_the_same_samples():
+def test_two_ranks_equal_one_rank_over_the_same_samples(table):
     world, port = 2, _free_port()
     mgr = tmp.get_context("spawn").Manager()
     out = mgr.dict()
-    tmp.start_processes(_rank_main, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
+    tmp.start_processes(_rank_main, args=(world, port, table, out), nprocs=world, start_method="spawn", join=True)
     r0, r1 = out[0], out[1]
     assert r0 == r1                                          # every rank holds the same estimate
     assert all(n % (2 * w) == 0 for n, w in zip(r0["n_samples"], WIDTHS))   # whole rounds of two blocks
-    one = single("fixed", r0["n_samples"])                   # one rank, the same sample indices
+    one = single(table, "fixed", r0["n_samples"])            # one rank, the same sample indices
     for key in ("trace", "tau", "std_err", "coarse_term", "n_samples", "mean", "variance"):
         assert one[key] == r0[key], key
