@@ -15,8 +15,9 @@
 // sites further on: nine descriptors into one staging, no im2col copy.  B is
 // the layer's weights, [out channel (padded to 16)][tap][in channel].  One
 // elected thread issues tcgen05.mma.kind::tf32 (M = 128, N = 16, K = 8) three
-// times per K step (TF32 head and tail of both operands: FP32 accuracy), all
-// nine taps into one accumulator, and commits to an mbarrier.  The epilogue
+// times per K step (TF32 head and tail of both operands: FP32 accuracy) into six
+// accumulators (three products x even / odd taps: independent chains) and commits
+// to an mbarrier.  The epilogue
 // reads the accumulator with tcgen05.ld (warps 0-3 columns 0-7, warps 4-7
 // columns 8-15 of the same lanes), applies the ReLU (forward) or the ReLU mask
 // of the layer below (backward-data) and stores the output channels.
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
   unsigned char *Hhi = smem, *Hlo = smem + halo_bytes;
   unsigned char *Bhi = smem + 2 * halo_bytes, *Blo = Bhi + wbytes;
 
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 32);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 128);
   if (tid == 0) {
     tc::mbar_init(&bar, 1);
     failed = 0;
@@ -172,15 +173,21 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (tid == 0) {
       const uint32_t hh = tc::smem_u32(Hhi), hl = tc::smem_u32(Hlo), bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
+      // six independent accumulators (product hi.hi / hi.lo / lo.hi times even / odd tap),
+      // so that the MMAs do not form one dependent chain through a single accumulator
       for (int tap = 0; tap < 9; ++tap) {
         const int tx = tap % 3, ty = tap / 3;
         const int dx = mirror ? 2 - tx : tx, dy = mirror ? 2 - ty : ty;
         const uint32_t hofs = (uint32_t)((dy * hw + dx) * kg) * SBO;
+        const uint32_t d0 = tmem + (uint32_t)((tap & 1) * 3 * CT_N);
         for (int ks = 0; ks < cip / 8; ++ks) {
           const uint32_t a = hofs + (uint32_t)ks * 2u * LBO, b = (uint32_t)(tap * c4n + 2 * ks) * LBO;
-          tc::mma_tf32x3(tmem, tc::smem_desc(hh + a, LBO, SBO), tc::smem_desc(hl + a, LBO, SBO),
-                         tc::smem_desc(bh + b, LBO, BSBO), tc::smem_desc(bl + b, LBO, BSBO), idesc,
-                         (tap > 0 || ks > 0) ? 1u : 0u);
+          const uint32_t accf = (tap > 1 || ks > 0) ? 1u : 0u;
+          const uint64_t ah = tc::smem_desc(hh + a, LBO, SBO), al = tc::smem_desc(hl + a, LBO, SBO);
+          const uint64_t bhd = tc::smem_desc(bh + b, LBO, BSBO), bld = tc::smem_desc(bl + b, LBO, BSBO);
+          tc::mma_tf32(d0, ah, bhd, idesc, accf);
+          tc::mma_tf32(d0 + CT_N, ah, bld, idesc, accf);
+          tc::mma_tf32(d0 + 2 * CT_N, al, bhd, idesc, accf);
         }
       }
       tc::mma_commit(&bar);
@@ -195,8 +202,15 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
     if (failed) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int m = 32 * (warp & 3) + lane, n0 = (warp >> 2) * 8;
-    float acc[8];
-    tc::tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)n0, acc);
+    float acc[8], part[8];
+    const uint32_t lanes = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)n0;
+    tc::tmem_ld8(lanes, acc);
+#pragma unroll 1
+    for (int q = 1; q < 6; ++q) {               // the accumulators, added in a fixed order
+      tc::tmem_ld8(lanes + (uint32_t)(q * CT_N), part);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] += part[u];
+    }
     const int qs = m / k, c = m - qs * k;
     const size_t s = (size_t)j * nx + i0 + qs;
 #pragma unroll
@@ -221,7 +235,7 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    tc::tmem_dealloc(tmem, 32);
+    tc::tmem_dealloc(tmem, 128);
   }
 }
 
