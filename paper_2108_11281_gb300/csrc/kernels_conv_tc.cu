@@ -89,11 +89,12 @@ constexpr int STAGE_BATCH = 8;
 // acc where act[s][n][c] > 0, else 0.
 // K (columns) and CIP (input channels padded to 8 or 16) are compile-time, so the
 // staging index arithmetic is shifts and masks: the kernel was issue-bound on it.
-template <int K, int CIP>
-__global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict__ in, const float *__restrict__ W,
+template <int K, int CIP, int MIRROR>
+__global__ void __launch_bounds__(CT_THREADS, 2) k_conv_tc(const float *__restrict__ in, const float *__restrict__ W,
                                                         const float *__restrict__ act, float *__restrict__ out,
                                                         int nx, int ny, int cin, int cout, int periodic,
-                                                        int mirror, int relu, long long wait_cycles, int *err) {
+                                                        int relu, long long wait_cycles, int *err) {
+  constexpr int mirror = MIRROR;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_base;
@@ -101,9 +102,9 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
   constexpr int k = K, cip = CIP, c4n = CIP / 4, ts = CT_M / K, kg = K / 8, hw = ts + 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tiles_x = nx / ts, tiles = tiles_x * ny;
-  const uint32_t LBO = 128u, SBO = (uint32_t)c4n * 128u;
-  const uint32_t halo_bytes = (uint32_t)(3 * hw * kg) * SBO;
-  const uint32_t BSBO = (uint32_t)(9 * c4n) * 128u, wbytes = (uint32_t)(CT_N / 8) * BSBO;
+  constexpr uint32_t LBO = 128u, SBO = (uint32_t)c4n * 128u;
+  constexpr uint32_t halo_bytes = (uint32_t)(3 * hw * kg) * SBO;
+  constexpr uint32_t BSBO = (uint32_t)(9 * c4n) * 128u, wbytes = (uint32_t)(CT_N / 8) * BSBO;
   unsigned char *Hhi = smem, *Hlo = smem + halo_bytes;
   unsigned char *Bhi = smem + 2 * halo_bytes, *Blo = Bhi + wbytes;
 
@@ -133,6 +134,8 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = tc::tf32_idesc(CT_M, CT_N);
   constexpr int nel = 3 * hw * c4n * k;        // 16-byte halo elements per tile
+  const uint64_t dAh = tc::smem_desc(tc::smem_u32(Hhi), LBO, SBO), dAl = tc::smem_desc(tc::smem_u32(Hlo), LBO, SBO);
+  const uint64_t dBh = tc::smem_desc(tc::smem_u32(Bhi), LBO, BSBO), dBl = tc::smem_desc(tc::smem_u32(Blo), LBO, BSBO);
 
   uint32_t phase = 0;
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, phase ^= 1u) {
@@ -172,22 +175,23 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv_tc(const float *__restrict_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (tid == 0) {
-      const uint32_t hh = tc::smem_u32(Hhi), hl = tc::smem_u32(Hlo), bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
       // six independent accumulators (product hi.hi / hi.lo / lo.hi times even / odd tap),
-      // so that the MMAs do not form one dependent chain through a single accumulator
+      // so that the MMAs do not form one dependent chain through a single accumulator.
+      // Descriptors are the base descriptors plus compile-time offsets (start address / 16
+      // in the low bits): the single issuing thread spends little time per MMA.
+#pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
         const int tx = tap % 3, ty = tap / 3;
         const int dx = mirror ? 2 - tx : tx, dy = mirror ? 2 - ty : ty;
         const uint32_t hofs = (uint32_t)((dy * hw + dx) * kg) * SBO;
         const uint32_t d0 = tmem + (uint32_t)((tap & 1) * 3 * CT_N);
+#pragma unroll
         for (int ks = 0; ks < cip / 8; ++ks) {
-          const uint32_t a = hofs + (uint32_t)ks * 2u * LBO, b = (uint32_t)(tap * c4n + 2 * ks) * LBO;
+          const uint64_t a = (hofs + (uint32_t)ks * 2u * LBO) >> 4, b = ((uint32_t)(tap * c4n + 2 * ks) * LBO) >> 4;
           const uint32_t accf = (tap > 1 || ks > 0) ? 1u : 0u;
-          const uint64_t ah = tc::smem_desc(hh + a, LBO, SBO), al = tc::smem_desc(hl + a, LBO, SBO);
-          const uint64_t bhd = tc::smem_desc(bh + b, LBO, BSBO), bld = tc::smem_desc(bl + b, LBO, BSBO);
-          tc::mma_tf32(d0, ah, bhd, idesc, accf);
-          tc::mma_tf32(d0 + CT_N, ah, bld, idesc, accf);
-          tc::mma_tf32(d0 + 2 * CT_N, al, bhd, idesc, accf);
+          tc::mma_tf32(d0, dAh + a, dBh + b, idesc, accf);
+          tc::mma_tf32(d0 + CT_N, dAh + a, dBl + b, idesc, accf);
+          tc::mma_tf32(d0 + 2 * CT_N, dAl + a, dBh + b, idesc, accf);
         }
       }
       tc::mma_commit(&bar);
@@ -408,11 +412,13 @@ static void conv_attrs() {
   MLMC_CUDA(cudaGetDevice(&dev));
   std::call_once(g_conv_attr_once[dev & 63], [] {
     const int a = (int)conv_tc_smem(128, 16), b = (int)wgrad_tc_smem(16, WG_KC);
-    const void *fs[] = {(const void *)k_conv_tc<8, 8>,   (const void *)k_conv_tc<8, 16>,
-                        (const void *)k_conv_tc<16, 8>,  (const void *)k_conv_tc<16, 16>,
-                        (const void *)k_conv_tc<32, 8>,  (const void *)k_conv_tc<32, 16>,
-                        (const void *)k_conv_tc<64, 8>,  (const void *)k_conv_tc<64, 16>,
-                        (const void *)k_conv_tc<128, 8>, (const void *)k_conv_tc<128, 16>};
+#define MLMC_CONV_FNS(M)                                                                                      \
+  (const void *)k_conv_tc<8, 8, M>, (const void *)k_conv_tc<8, 16, M>, (const void *)k_conv_tc<16, 8, M>,        \
+      (const void *)k_conv_tc<16, 16, M>, (const void *)k_conv_tc<32, 8, M>, (const void *)k_conv_tc<32, 16, M>, \
+      (const void *)k_conv_tc<64, 8, M>, (const void *)k_conv_tc<64, 16, M>, (const void *)k_conv_tc<128, 8, M>,  \
+      (const void *)k_conv_tc<128, 16, M>
+    const void *fs[] = {MLMC_CONV_FNS(0), MLMC_CONV_FNS(1)};
+#undef MLMC_CONV_FNS
     for (const void *f : fs)
       check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, a),
                  "cudaFuncSetAttribute(k_conv_tc)");
@@ -437,8 +443,12 @@ void launch_conv_tc(const float *in, const float *W, const float *act, float *ou
   const int grid = std::min(tiles, sms * std::max(1, std::min(per_sm, 4)));
 #define MLMC_CONV_TC(KK, CC)                                                                                  \
   if (k == KK && cip == CC) {                                                                                 \
-    k_conv_tc<KK, CC><<<grid, CT_THREADS, smem, s>>>(in, W, act, out, nx, ny, cin, cout, periodic, mirror, relu, \
-                                                     CT_WAIT_CYCLES, err);                                     \
+    if (mirror)                                                                                               \
+      k_conv_tc<KK, CC, 1><<<grid, CT_THREADS, smem, s>>>(in, W, act, out, nx, ny, cin, cout, periodic, relu,   \
+                                                          CT_WAIT_CYCLES, err);                                \
+    else                                                                                                      \
+      k_conv_tc<KK, CC, 0><<<grid, CT_THREADS, smem, s>>>(in, W, act, out, nx, ny, cin, cout, periodic, relu,   \
+                                                          CT_WAIT_CYCLES, err);                                \
   } else
   MLMC_CONV_TC(8, 8) MLMC_CONV_TC(8, 16) MLMC_CONV_TC(16, 8) MLMC_CONV_TC(16, 16) MLMC_CONV_TC(32, 8)
   MLMC_CONV_TC(32, 16) MLMC_CONV_TC(64, 8) MLMC_CONV_TC(64, 16) MLMC_CONV_TC(128, 8) MLMC_CONV_TC(128, 16)
