@@ -449,7 +449,7 @@ def profile_sample(args):
         elif args.profile_kernel in ("rbgs2", "restrict2", "prolong2"):
             level, kk = 2, w.get("coarse_block") or w["block"]
         if which == 8:
-            h.set_conv_kernel(mlmc.CONV_SIMT if args.profile_kernel == "net_simt" else mlmc.CONV_AUTO)
+            h.set_conv_kernel(mlmc.CONV_SIMT if args.profile_kernel == "net_simt" else mlmc.CONV_TC)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
         h.profile_kernel(which, level, kk, 1)
@@ -748,7 +748,7 @@ def learned_leg(mlmc, stream, warmup, steps, seed=0):
     kern = {}
     c0 = 4
     flops = 2.0 * 9 * (16 * c0 + 256 + 16 * c0) * w["nx"] * w["ny"] * w["block"]
-    for name, which in (("net_forward_tc", mlmc.CONV_AUTO), ("net_forward_simt", mlmc.CONV_SIMT)):
+    for name, which in (("net_forward_tc", mlmc.CONV_TC), ("net_forward_simt", mlmc.CONV_SIMT)):
         h.set_conv_kernel(which)
         kms, kbytes = h.profile_kernel(8, 1, w["block"], 20)
         kern[name] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6, "tflops": flops / kms / 1e9}

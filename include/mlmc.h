@@ -310,15 +310,17 @@ int mlmc_dense_apply(int complex_data, const void *A, const void *B, void *Y, in
 int mlmc_set_dense_kernel(mlmc_hierarchy *h, int which);
 
 /* Kernels of the learned correction's 3x3 convolutions (forward, backward-data,
- * weight gradient) for this handle: MLMC_CONV_AUTO (the default) runs them on
- * the tensor cores (tcgen05 implicit GEMMs, three TF32 products per term for
- * FP32 accuracy, accumulators in tensor memory, every wait bounded) whenever
- * the block width k is 8, 16, 32, 64 or 128 and the fine lattice's rows hold
- * whole tiles of 128 / k sites (weight gradient: k a multiple of 8, at most
- * 32 or a multiple of 32), else on the CUDA cores; MLMC_CONV_SIMT always on
- * the CUDA cores.  A change drops the CUDA graphs captured for the inner
- * solves. */
-enum { MLMC_CONV_SIMT = 0, MLMC_CONV_AUTO = 1 };
+ * weight gradient) for this handle.  MLMC_CONV_TC: on the tensor cores
+ * (tcgen05 implicit GEMMs, three TF32 products per term for FP32 accuracy,
+ * accumulators in tensor memory, every wait bounded) whenever the block width
+ * k is 8, 16, 32, 64 or 128 and the fine lattice's rows hold whole tiles of
+ * 128 / k sites (weight gradient: k a multiple of 8, at most 32 or a multiple
+ * of 32), else on the CUDA cores; MLMC_CONV_SIMT: always on the CUDA cores;
+ * MLMC_CONV_AUTO (the default): whichever of the two ran the network faster
+ * on a fine-level block of the sample width, timed once when the network is
+ * first installed or trained (or when AUTO is set again).  A change drops the
+ * CUDA graphs captured for the inner solves. */
+enum { MLMC_CONV_SIMT = 0, MLMC_CONV_AUTO = 1, MLMC_CONV_TC = 2 };
 int mlmc_set_conv_kernel(mlmc_hierarchy *h, int which);
 
 /* The exact coarsest term of the estimator (Remark 4.2), tr(A_L^{-1} R^_L P^_L)

@@ -144,7 +144,10 @@ struct mlmc_hierarchy {
   std::vector<std::unique_ptr<Krylov>> inner[2];  // fixed-length inner FGMRES per level, [0] FP64 [1] FP32
   int const_laplace = 0, periodic = 0;
   int dense_kernel = MLMC_DENSE_AUTO;   // coarsest apply of the FP32 cycle: tensor cores, CUDA cores, or by size
-  int conv_kernel = MLMC_CONV_AUTO;     // learned correction's convolutions: tensor cores where the shape allows
+  int conv_kernel = MLMC_CONV_AUTO;     // learned correction's convolutions: CUDA cores, tensor cores, or by timing
+  int conv_auto_tc = 0;                 // MLMC_CONV_AUTO: 1 when the tensor-core kernels timed faster
+  double conv_tuned_ms[2] = {0.0, 0.0}; // that timing: network forward, CUDA cores / tensor cores
+  int conv_tuned = 0;
   int bilinear = 0;    // the Example 5.1 hierarchy of Sec. 5: bilinear P, Galerkin 9-point levels
   double coarse_term_hat = 0.0;   // bilinear: tr(A_L^{-1} R^_L P^_L) (Remark 4.2), computed at setup
   double laplace_diag = 4.0;
@@ -628,7 +631,8 @@ const float *netW3(H_t &h) { return h.netW.as<float>() + 9 * (NET_CH * h.net_c0 
 // handle allows it and the shape fits (k in {8, 16, 32, 64, 128}, whole tiles of 128 / k
 // sites per lattice row), else the CUDA-core kernel (kernels_learned.cu).
 bool conv_on_tc(const H_t &h, int nx, int k, int cin, int cout) {
-  return h.conv_kernel != MLMC_CONV_SIMT && conv_tc_ok(nx, k, cin, cout);
+  const bool want = h.conv_kernel == MLMC_CONV_TC || (h.conv_kernel == MLMC_CONV_AUTO && h.conv_auto_tc);
+  return want && conv_tc_ok(nx, k, cin, cout);
 }
 
 void conv_forward(H_t &h, int ci, int co, bool relu, const float *in, const float *W, float *out, int k) {
@@ -656,7 +660,8 @@ void conv_backward_data(H_t &h, int ci, int co, const float *gout, const float *
 void conv_backward_weight(H_t &h, int ci, int co, const float *in, const float *gout, float *G, int k) {
   const Level &F = h.lv[0];
   const int per = h.periodic || h.complex_op;
-  if (h.conv_kernel != MLMC_CONV_SIMT && conv_wgrad_tc_ok(k, ci, co)) {
+  const bool want = h.conv_kernel == MLMC_CONV_TC || (h.conv_kernel == MLMC_CONV_AUTO && h.conv_auto_tc);
+  if (want && conv_wgrad_tc_ok(k, ci, co)) {
     launch_conv_wgrad_tc(in, gout, h.netPart.as<float>(), F.nx, F.ny, k, ci, co, per, h.err.as<int>(), h.stream);
     launch_weight_reduce(h.netPart.as<float>(), conv_wgrad_tc_blocks(), ci * co * 9, G, 1.f, h.stream);
   } else {
@@ -674,6 +679,50 @@ void net_forward(H_t &h, const void *r, int k) {
   conv_forward(h, h.net_c0, NET_CH, true, h.act0.as<float>(), netW1(h), h.act1.as<float>(), k);
   conv_forward(h, NET_CH, NET_CH, true, h.act1.as<float>(), netW2(h), h.act2.as<float>(), k);
   conv_forward(h, NET_CH, h.net_c0, false, h.act2.as<float>(), netW3(h), h.act3.as<float>(), k);
+}
+
+// MLMC_CONV_AUTO: time the network on a fine-level block of the sample width with the
+// tensor-core and with the CUDA-core convolutions (CUDA events, after a warm-up) and keep
+// the faster; the captured inner solves are dropped, since they bake the choice in.
+// Runs outside any stream capture (when the network is installed or trained).
+// Captured inner solves bake in the kernel choices: drop them when a choice changes.
+void drop_graphs(mlmc_hierarchy &h) {
+  check_cuda(cudaStreamSynchronize(h.stream), "sync");
+  for (auto &g : h.graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h.graphs.clear();
+}
+
+void tune_conv(H_t &h) {
+  if (h.conv_kernel != MLMC_CONV_AUTO) return;
+  const Level &F = h.lv[0];
+  const int k = h.kdiff(0);
+  if (!conv_tc_ok(F.nx, k, h.net_c0, NET_CH)) {
+    h.conv_auto_tc = 0;
+    return;
+  }
+  void *x = h.cyc[1][0].b.p;
+  launch_noise(h.complex_op, 9, 0, 0, F.n, k, h.t32, x, h.stream);
+  cudaEvent_t e0, e1;
+  check_cuda(cudaEventCreate(&e0), "event");
+  check_cuda(cudaEventCreate(&e1), "event");
+  float ms[2] = {0.f, 0.f};
+  for (int tc = 0; tc < 2; ++tc) {
+    h.conv_auto_tc = tc;
+    net_forward(h, x, k);
+    check_cuda(cudaEventRecord(e0, h.stream), "record");
+    for (int r = 0; r < 3; ++r) net_forward(h, x, k);
+    check_cuda(cudaEventRecord(e1, h.stream), "record");
+    check_cuda(cudaEventSynchronize(e1), "sync");
+    check_cuda(cudaEventElapsedTime(&ms[tc], e0, e1), "elapsed");
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h.conv_auto_tc = ms[1] < ms[0] ? 1 : 0;
+  h.conv_tuned = 1;
+  h.conv_tuned_ms[0] = ms[0] / 3.0;
+  h.conv_tuned_ms[1] = ms[1] / 3.0;
+  drop_graphs(h);
 }
 
 // Loss mean_c ||A net(r_c) - r_c||^2 / ||r_c||^2 over the block and (grad = 1)
@@ -1545,14 +1594,6 @@ int mlmc_dense_apply(int complex_data, const void *A, const void *B, void *Y, in
   });
 }
 
-// Captured inner solves bake in the kernel choices: drop them when a choice changes.
-static void drop_graphs(mlmc_hierarchy &h) {
-  check_cuda(cudaStreamSynchronize(h.stream), "sync");
-  for (auto &g : h.graphs)
-    if (g.exec) cudaGraphExecDestroy(g.exec);
-  h.graphs.clear();
-}
-
 int mlmc_set_dense_kernel(mlmc_hierarchy *h, int which) {
   return translate([&] {
     need(h);
@@ -1566,9 +1607,11 @@ int mlmc_set_dense_kernel(mlmc_hierarchy *h, int which) {
 int mlmc_set_conv_kernel(mlmc_hierarchy *h, int which) {
   return translate([&] {
     need(h);
-    if (which != MLMC_CONV_SIMT && which != MLMC_CONV_AUTO) fail(MLMC_ERR_INVALID_ARG, "unknown conv kernel");
+    if (which != MLMC_CONV_SIMT && which != MLMC_CONV_AUTO && which != MLMC_CONV_TC)
+      fail(MLMC_ERR_INVALID_ARG, "unknown conv kernel");
     if (h->conv_kernel != which) drop_graphs(*h);
     h->conv_kernel = which;
+    if (which == MLMC_CONV_AUTO && h->net_c0) tune_conv(*h);
   });
 }
 
@@ -1923,6 +1966,7 @@ int mlmc_learned_set(mlmc_hierarchy *h, const float *weights, int enable) {
     if (weights)
       check_cuda(cudaMemcpyAsync(h->netW.p, weights, h->net_nw * sizeof(float), cudaMemcpyHostToDevice, h->stream), "H2D W");
     check_cuda(cudaStreamSynchronize(h->stream), "sync");
+    if (enable && !h->conv_tuned) tune_conv(*h);
     h->net_on = enable ? 1 : 0;
   });
 }
@@ -1971,6 +2015,7 @@ int mlmc_learned_train(mlmc_hierarchy *h, const mlmc_train_params *p, float *wei
     if (p->n_pairs < 2 || p->epochs < 1 || !(p->lr > 0.0) || !(p->tol > 0.0)) fail(MLMC_ERR_INVALID_ARG, "bad training parameters");
     H_t &H = *h;
     net_alloc(H);
+    if (!H.conv_tuned) tune_conv(H);
     const Level &F = H.lv[0];
     const int k = H.kmax;
     cudaStream_t s = H.stream;

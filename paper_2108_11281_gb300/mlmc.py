@@ -25,7 +25,7 @@ CYCLE_V, CYCLE_K = 0, 1
 ALLOC_RHO, ALLOC_OPTIMAL, ALLOC_FIXED = 0, 1, 2
 COST_COUNTED, COST_NOMINAL = 0, 1
 DENSE_SIMT, DENSE_TC, DENSE_TC_WITHHOLD, DENSE_AUTO = 0, 1, 2, 3
-CONV_SIMT, CONV_AUTO = 0, 1
+CONV_SIMT, CONV_AUTO, CONV_TC = 0, 1, 2
 TRANSFER_AGGREGATION, TRANSFER_BILINEAR = 0, 1
 
 

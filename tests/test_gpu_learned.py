@@ -48,6 +48,7 @@ def test_forward_and_gradient_match_oracle(mlmc, case, k):
     """k = 3: the CUDA-core convolutions; k = 16: the tensor-core ones (tiles of 8 sites)."""
     N = 8
     h, A, d, cplx, per = make(mlmc, case, N, k)
+    h.set_conv_kernel(mlmc.CONV_TC if k == 16 else mlmc.CONV_SIMT)
     c0 = NN.channels_of(d, cplx)
     Ws = [W.astype(np.float32).astype(np.float64) for W in NN.init_weights(c0, 9)]
     h.learned_set(flat(Ws), enable=0)
@@ -90,13 +91,13 @@ def test_tensor_core_convolutions_match_cuda_cores(mlmc):
         else:
             R = torch.randn(n, k, generator=g, dtype=torch.float32).cuda()
         out = {}
-        for which in (mlmc.CONV_AUTO, mlmc.CONV_SIMT):
+        for which in (mlmc.CONV_TC, mlmc.CONV_SIMT):
             h.set_conv_kernel(which)
             E = torch.zeros_like(R)
             h.learned_apply(R.data_ptr(), E.data_ptr(), k)
             loss, grad = h.learned_grad(R.data_ptr(), k)
             out[which] = (E.cpu().numpy(), loss, grad)
-        (Et, lt, gt), (Es, ls, gs) = out[mlmc.CONV_AUTO], out[mlmc.CONV_SIMT]
+        (Et, lt, gt), (Es, ls, gs) = out[mlmc.CONV_TC], out[mlmc.CONV_SIMT]
         assert np.abs(Et - Es).max() <= 1e-5 * np.abs(Es).max()
         assert abs(lt - ls) <= 1e-5 * abs(ls)
         assert np.abs(gt - gs).max() <= 1e-4 * np.abs(gs).max()
