@@ -120,6 +120,8 @@ def parse():
                          "workload: seconds, device-counted cost (Sec. 5 model) and N per method; one JSON line")
     ap.add_argument("--alloc", default="optimal", choices=["optimal", "rho"],
                     help="Sec. 2 optimal allocation (default) or the Sec. 5 equal rho split")
+    ap.add_argument("--coarse-growth", type=int, default=-1,
+                    help="override the workload's block-width growth exponent on coarse level differences")
     ap.add_argument("--replicas", action="store_true",
                     help="with several GPUs: independent estimates (disjoint seeds) instead of one estimate whose "
                          "samples are spread over the GPUs")
@@ -837,7 +839,9 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2108_11281_gb300 import mlmc
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.coarse_growth >= 0:
+        w["coarse_growth"] = args.coarse_growth
     nz = mlmc.NOISE_Z4 if w["noise"] == "z4" else mlmc.NOISE_RADEMACHER
     stream = torch.cuda.current_stream().cuda_stream
     h = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, stream)

@@ -121,8 +121,9 @@ typedef struct {
                           smoothed by 4-colour Gauss-Seidel.  R P != I, so samples and
                           estimates need MLMC_FORM_HAT (or MLMC_FORM_PLAIN); agg_*, n_tv,
                           spin_split, setup_*, bootstrap and user_P are ignored.           */
-  int coarse_growth;   /* > 0: the block width doubles per level difference beyond the second
-                          (coarse_block on difference 2, then 2x, 4x, ... up to 256): coarser
+  int coarse_growth;   /* g > 0: the block width grows by 2^g per level difference beyond the
+                          second (coarse_block on difference 2, then 2^g x, 4^g x, ... up to
+                          512 columns for real operators, 256 for complex ones): coarser
                           levels are cheaper per column and draw more samples, so wider
                           blocks amortise their latency-bound launches.  0 = coarse_block
                           on every difference >= 2.  Samples do not depend on widths.       */

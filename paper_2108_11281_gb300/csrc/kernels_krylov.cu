@@ -226,8 +226,7 @@ void launch_sample_combine(int hc, const void *a, const void *b, void *out, int 
   MLMC_LAUNCH_CHECK("k_sample_combine");
 }
 
-// Running (N, mean, M2) of the level's samples, updated with one block of k <= 256
-// samples: the block's own mean and M2 = sum |s - mean_b|^2 by a fixed-order tree
+// Running (N, mean, M2) of the level's samples, updated with one block of k samples: the block's own mean and M2 = sum |s - mean_b|^2 by a fixed-order tree
 // (deterministic), then the pairwise merge of Chan, Golub and LeVeque:
 //   N = Na + Nb,  d = mean_b - mean_a,  mean = mean_a + d Nb / N,
 //   M2 = M2_a + M2_b + |d|^2 Na Nb / N.
@@ -245,15 +244,24 @@ __device__ inline void block_tree_sum(double *a, double *b) {
 __global__ void __launch_bounds__(256) k_accumulate(const cdouble *smp, int k, double *acc) {
   __shared__ double sr[256], si[256];
   const int t = threadIdx.x;
-  const double re = t < k ? smp[t].re : 0.0, im = t < k ? smp[t].im : 0.0;
+  // thread t holds samples t, t + 256, ... (summed in that order), then a fixed tree
+  double re = 0.0, im = 0.0;
+  for (int i = t; i < k; i += 256) {
+    re += smp[i].re;
+    im += smp[i].im;
+  }
   sr[t] = re;
   si[t] = im;
   __syncthreads();
   block_tree_sum(sr, si);
   const double mbr = sr[0] / k, mbi = si[0] / k;
   __syncthreads();
-  const double dr = re - mbr, di = im - mbi;
-  sr[t] = t < k ? dr * dr + di * di : 0.0;
+  double q = 0.0;
+  for (int i = t; i < k; i += 256) {
+    const double dr = smp[i].re - mbr, di = smp[i].im - mbi;
+    q += dr * dr + di * di;
+  }
+  sr[t] = q;
   si[t] = 0.0;
   __syncthreads();
   block_tree_sum(sr, si);
@@ -268,7 +276,7 @@ __global__ void __launch_bounds__(256) k_accumulate(const cdouble *smp, int k, d
 }
 
 void launch_accumulate(const void *samples, int k, double *acc, cudaStream_t s) {
-  if (k < 1 || k > 256) throw cuda_error{cudaErrorInvalidValue, "k_accumulate: 1 <= k <= 256"};
+  if (k < 1 || k > 4096) throw cuda_error{cudaErrorInvalidValue, "k_accumulate: 1 <= k <= 4096"};
   k_accumulate<<<1, 256, 0, s>>>((const cdouble *)samples, k, acc);
   MLMC_LAUNCH_CHECK("k_accumulate");
 }

@@ -223,8 +223,8 @@ __global__ void __launch_bounds__(DOT_THREADS, 4) k_multidot_partial(const T *V,
       for (int u = 0; u < VEC; ++u) red[tid * VEC + u] = live ? widen(acc[v][u]) : zero<A>();
       __syncthreads();
       // column c = cv * VEC + u lives at red[(slot * kv + cv) * VEC + u]
-      if (tid < k) {
-        const int c = tid, cvv = c / VEC, u = c % VEC;
+      for (int c = tid; c < k; c += DOT_THREADS) {
+        const int cvv = c / VEC, u = c % VEC;
         A sum = red[cvv * VEC + u];
         for (int sl = 1; sl < slots; ++sl) sum = addd(sum, red[(sl * kv + cvv) * VEC + u]);
         partial[((size_t)part * nvec + v0 + v) * k + c] = sum;
@@ -258,12 +258,15 @@ __global__ void k_multidot_reduce(const A *partial, int nparts, int nvec, int k,
 
 void launch_multidot(DType t, const void *V, size_t vstride, int nvec, const void *w, size_t rows,
                      int k, void *partials, int nparts, void *out, DType out_t, cudaStream_t s) {
-  if (k > DOT_THREADS) throw cuda_error{cudaErrorInvalidValue, "multidot: k > 256"};
   (void)out_t;
   MLMC_DISPATCH(t, T, {
     typedef typename acc_of<T>::type A;
     constexpr int VW = sizeof(T) == 4 ? 2 : (16 / (int)sizeof(T) > 0 ? 16 / (int)sizeof(T) : 1);
-    if (VW > 1 && k % VW == 0 && vstride % VW == 0)
+    // one thread per column group of VW: at most DOT_THREADS groups (k <= 256, or 512 with packs)
+    const bool packed = VW > 1 && k % VW == 0 && vstride % VW == 0;
+    if ((packed ? k / VW : k) > DOT_THREADS)
+      throw cuda_error{cudaErrorInvalidValue, "multidot: more column groups than threads"};
+    if (packed)
       k_multidot_partial<T, VW><<<nparts, DOT_THREADS, 0, s>>>((const T *)V, vstride, nvec, (const T *)w, rows, k,
                                                                (A *)partials);
     else

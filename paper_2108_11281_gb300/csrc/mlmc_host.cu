@@ -128,14 +128,15 @@ struct mlmc_hierarchy {
   int L = 0, kmax = 0;
   int kact = 0;        // active vector-block width of estimates and sample calls (<= kmax)
   int kwide = 0;       // vector-block width of samples drawn on level difference 2 (coarse levels)
-  int kgrow = 0;       // > 0: the width doubles per further level difference (up to 256)
+  int kgrow = 0;       // g > 0: the width grows by 2^g per further level difference (up to 512; 256 complex)
   int kbig = 0;        // the largest block width of any level difference: sizes the per-column scratch
   std::vector<int> wl; // per level: the widest block its buffers serve
   // block width of level difference l0 (0-based; l0 = 0 is the fine difference)
   int kdiff(int l0) const {
     if (l0 == 0) return kact;
     long k = kwide;
-    for (int i = 1; i < l0 && kgrow; ++i) k = std::min(2 * k, 256L);
+    const long cap = complex_op ? 256L : 512L;     // column groups of the Arnoldi dot products
+    for (int i = 1; i < l0 && kgrow; ++i) k = std::min(k << std::min(kgrow, 4), cap);
     return (int)k;
   }
   std::vector<Level> lv;
@@ -1046,7 +1047,7 @@ void validate(const mlmc_operator_desc *op, const mlmc_hierarchy_params *p) {
     if (p->inner_its < 0 || p->inner_its > 32) fail(MLMC_ERR_INVALID_ARG, "inner_its must be in 0..32");
     if (p->precision != MLMC_PREC_FP64 && p->precision != MLMC_PREC_MIXED_FP32)
       fail(MLMC_ERR_INVALID_ARG, "unknown precision");
-    if ((double)op->nx * op->ny * (p->coarse_growth > 0 ? 256 : std::max(p->block, p->coarse_block)) >= 2147483648.0)
+    if ((double)op->nx * op->ny * (p->coarse_growth > 0 ? 512 : std::max(p->block, p->coarse_block)) >= 2147483648.0)
       fail(MLMC_ERR_UNSUPPORTED, "n * block must stay below 2^31 (32-bit kernel indexing)");
     long nx = op->nx, ny = op->ny;
     for (int l = 0; l + 1 < p->levels; ++l) {
@@ -1072,7 +1073,7 @@ void validate(const mlmc_operator_desc *op, const mlmc_hierarchy_params *p) {
   if (p->precision != MLMC_PREC_FP64 && p->precision != MLMC_PREC_MIXED_FP32)
     fail(MLMC_ERR_INVALID_ARG, "unknown precision");
   if ((double)op->nx * op->ny * (op->kind == MLMC_OP_WILSON2D ? 2 : 1) *
-          (p->coarse_growth > 0 ? 256 : std::max(p->block, p->coarse_block)) >=
+          (p->coarse_growth > 0 ? 512 : std::max(p->block, p->coarse_block)) >=
       2147483648.0)
     fail(MLMC_ERR_UNSUPPORTED, "n * block must stay below 2^31 (32-bit kernel indexing)");
   long nx = op->nx, ny = op->ny;
@@ -1110,7 +1111,7 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   h.kmax = p->block;
   h.kact = p->block;
   h.kwide = p->coarse_block > 0 ? p->coarse_block : p->block;
-  h.kgrow = p->coarse_growth > 0 ? 1 : 0;
+  h.kgrow = p->coarse_growth > 0 ? std::min(p->coarse_growth, 4) : 0;
   h.kbig = h.kmax;
   for (int l0 = 1; l0 + 1 < h.L; ++l0) h.kbig = std::max(h.kbig, h.kdiff(l0));
   // level l serves the solves of differences l (its fine side) and l - 1 (its coarse side)

@@ -470,6 +470,21 @@ def test_block_width_growth_keeps_samples(mlmc):
     h1.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_512_column_blocks_on_a_coarse_difference(mlmc, precision):
+    """coarse_growth = 2 widens the third level difference to 512 columns (real operators):
+    its samples (two blocks, 512 + 88) agree with the oracle's exact solves (FP64 form 1e-9
+    at tol 1e-12; mixed form 1e-8 at tol 1e-10), and the width is reported."""
+    h, lv = imported_laplace(mlmc, N=64, levels=4, block=8, coarse_block=128, coarse_growth=2, precision=precision)
+    assert [h.block_width(l) for l in (1, 2, 3)] == [8, 128, 512]
+    tol, rtol = (1e-12, 1e-9) if precision == 0 else (1e-10, 1e-8)
+    got, its = h.sample_level(3, mlmc.NOISE_RADEMACHER, 3, 0, 600, tol)
+    ref = E.level_samples(lv, E.LevelSolvers(lv), 3, "rademacher", 3, 0, 600)
+    assert len(its) == 2
+    compare_samples(got, ref, rtol)
+    h.close()
+
+
 def test_sharded_driver_one_rank_matches_library_estimate(mlmc):
     """The multi-GPU driver (sharded.py) on one rank draws its blocks through
     mlmc_sample_block and merges their device statistics on the host: the same N_l, tau
