@@ -166,6 +166,7 @@ struct mlmc_hierarchy {
   }
   std::vector<DevBuf> xs, ys;                     // sample blocks per level (FP64)
   DevBuf dots, dots_part, samples, acc, err, trace;
+  DevBuf coarse_r;     // FP64 residual of the mixed form's refined coarsest solve (n_L x widest block)
   uint64_t launches = 0;
   double iters_accum[16] = {0}, solves_accum[16] = {0};
   double cost = 0.0;   // Sec. 5 cost model: running sum of nnz(B) over products B x (per column)
@@ -565,11 +566,42 @@ Precond outer_precond(H_t &h, int l, int k) {
   };
 }
 
+// x = A_L^{-1} b on the coarsest level in FP64 accuracy.  FP64 form: the FP64 dense
+// inverse.  Mixed form: the FP32 inverse (tensor cores where the cycle uses them) with
+// two steps of iterative refinement against the FP64 operator, x <- x + A32^{-1}(b - A x):
+// each step multiplies the relative error by about cond(A_L) x 2^-24, so two steps leave
+// it far below the FP64 form's tolerances, at three FP32 products instead of one FP64
+// product (FP64 arithmetic is the GB300's slow path).
+void coarse_solve(H_t &h, const void *b, void *x, int k) {
+  const int Lc = h.L - 1;
+  if (h.prm.precision != MLMC_PREC_MIXED_FP32) {
+    dense_apply(h, 0, b, x, k);
+    return;
+  }
+  const Level &C = h.lv[Lc];
+  const size_t cnt = C.n * (size_t)k;
+  CycleBufs &cb = h.cyc[1][Lc];
+  void *r = h.coarse_r.p;
+  cudaStream_t s = h.stream;
+  launch_convert(h.t32, cb.b.p, h.t64, b, cnt, s);
+  dense_apply(h, 1, cb.b.p, cb.x.p, k);
+  launch_convert(h.t64, x, h.t32, cb.x.p, cnt, s);
+  h.launches += 2;
+  for (int it = 0; it < 2; ++it) {
+    residual_op(h, Lc, 0, x, b, r, k);
+    launch_convert(h.t32, cb.b.p, h.t64, r, cnt, s);
+    dense_apply(h, 1, cb.b.p, cb.x.p, k);
+    launch_convert(h.t64, r, h.t32, cb.x.p, cnt, s);
+    launch_add_acc(h.complex_op, x, r, (int)cnt, s);
+    h.launches += 3;
+  }
+}
+
 // x = A_l^{-1} b in FP64 (dense inverse on the coarsest level).
 int solve_level(H_t &h, int l, const void *b, void *x, int k, double tol, bool *conv) {
   if (conv) *conv = true;
   if (l == h.L - 1) {
-    dense_apply(h, 0, b, x, k);
+    coarse_solve(h, b, x, k);
     return 0;
   }
   int its = fgmres(h, *h.outer[l], l, 0, b, x, k, tol, 0, h.prm.max_iter, outer_precond(h, l, k),
@@ -1209,6 +1241,7 @@ void setup(H_t &h, const mlmc_operator_desc *op, const mlmc_hierarchy_params *p,
   }
   (void)k;
   h.dots.alloc(2 * (size_t)h.kbig * 16);
+  if (mixed) h.coarse_r.alloc(h.lv[h.L - 1].n * (size_t)std::max(h.kbig, h.wl[h.L - 1]) * dtype_size(h.t64));
   h.dots_part.alloc((size_t)multidot_parts(h.lv[0].n, h.kbig) * h.kbig * 16);   // sample-dot partial sums
   h.samples.alloc((size_t)h.kbig * 16);
   h.acc.alloc(4 * sizeof(double));
