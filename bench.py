@@ -951,7 +951,15 @@ def main():
     fma64 = mlmc.measure_fma_rate(True, stream)
     fma32 = mlmc.measure_fma_rate(False, stream)
     add64 = mlmc.measure_fma_rate(True, stream, add=True)
-    kern["fma_rate"] = {"fp64_tfma_s": fma64 / 1e12, "fp32_tfma_s": fma32 / 1e12, "fp64_tadd_s": add64 / 1e12}
+    l2bw = mlmc.measure_fma_rate(stream=stream, l2=True)
+    kern["fma_rate"] = {"fp64_tfma_s": fma64 / 1e12, "fp32_tfma_s": fma32 / 1e12, "fp64_tadd_s": add64 / 1e12,
+                        "l2_copy_gbs": l2bw / 1e9}
+    # kernels whose working set fits in L2 (< 100 MB per launch): their fraction of the measured
+    # L2 copy bandwidth, not of HBM
+    for name, v in kern.items():
+        if "bytes" in v and "gbs" in v and v["bytes"] < 100e6:
+            v["bound"] = "l2"
+            v["l2_frac"] = v["gbs"] * 1e9 / l2bw
     # the FP64 fine-level apply: 4 FP64 operations per element (3 additions, 1 FMA)
     if w["kind"] == "laplace" and w.get("transfer") != "bilinear":
         st = kern["stencil_fp64"]

@@ -355,9 +355,11 @@ int mlmc_trace_estimate_batch(mlmc_hierarchy *const *hs, int count, const mlmc_e
 /* Measured arithmetic ceiling (the paper has no counterpart; a roofline
  * denominator): operations per second of the whole GPU, fused multiply-adds
  * in FP64 (fp64 = 1) or FP32 (fp64 = 0), or FP64 additions (fp64 = 2), from 8
- * independent chains per thread on 8 blocks of 256 threads per SM, timed with
- * CUDA events on `stream`.  Allocates a small output buffer; synchronous on
- * return. */
+ * independent chains per thread on 8 blocks of 256 threads per SM; or
+ * (fp64 = 3) the L2 bandwidth in bytes per second, from a copy between two
+ * 16 MB buffers that stay in L2 (the ceiling of the small coarse-level
+ * kernels).  Timed with CUDA events on `stream`; allocates its buffers;
+ * synchronous on return. */
 int mlmc_measure_fma_rate(int fp64, void *stream, double *fma_per_s);
 
 /* Time one kernel family on level l with CUDA events on the hierarchy's

@@ -477,4 +477,16 @@ void launch_fma_rate(DType t, int add, void *out, int blocks, int iters, cudaStr
   MLMC_LAUNCH_CHECK("k_fma_rate");
 }
 
+// Bandwidth probe: dst = src in 16-byte packs, grid-stride (an L2-resident pair of
+// buffers gives the L2 ceiling that the small coarse-level kernels meet).
+__global__ void __launch_bounds__(256) k_copy16(uint4 *__restrict__ dst, const uint4 *__restrict__ src, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+void launch_copy16(void *dst, const void *src, size_t n16, int blocks, cudaStream_t s) {
+  k_copy16<<<blocks, 256, 0, s>>>((uint4 *)dst, (const uint4 *)src, n16);
+  MLMC_LAUNCH_CHECK("k_copy16");
+}
+
 }  // namespace mlmc

@@ -1969,7 +1969,30 @@ int mlmc_measure_fma_rate(int fp64, void *stream, double *fma_per_s) {
     int dev = 0, sms = 0;
     check_cuda(cudaGetDevice(&dev), "device");
     check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attribute");
-    if (fp64 < 0 || fp64 > 2) fail(MLMC_ERR_INVALID_ARG, "unknown operation");
+    if (fp64 < 0 || fp64 > 3) fail(MLMC_ERR_INVALID_ARG, "unknown operation");
+    if (fp64 == 3) {
+      // L2 bandwidth: a 16 MB to 16 MB copy (32 MB in L2), bytes read + written per second
+      const size_t bytes = (size_t)16 << 20;
+      DevBuf a, b;
+      a.alloc(bytes);
+      b.alloc(bytes);
+      check_cuda(cudaMemsetAsync(a.p, 0, bytes, s), "memset");
+      cudaEvent_t e0, e1;
+      check_cuda(cudaEventCreate(&e0), "event");
+      check_cuda(cudaEventCreate(&e1), "event");
+      for (int i = 0; i < 3; ++i) launch_copy16(b.p, a.p, bytes / 16, sms * 8, s);
+      check_cuda(cudaEventRecord(e0, s), "record");
+      const int reps = 50;
+      for (int i = 0; i < reps; ++i) launch_copy16(b.p, a.p, bytes / 16, sms * 8, s);
+      check_cuda(cudaEventRecord(e1, s), "record");
+      check_cuda(cudaEventSynchronize(e1), "sync");
+      float ms = 0.f;
+      check_cuda(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      *fma_per_s = (double)reps * 2.0 * bytes / (ms * 1e-3);
+      return;
+    }
     const int blocks = sms * 8, iters = fp64 ? 4096 : 65536;
     DevBuf out;
     out.alloc((size_t)blocks * 256 * 8);

@@ -387,10 +387,11 @@ def trace_estimate_batch(hierarchies, params, workers=4):
     return [result_dict(rs[i]) for i in range(n)], list(st)
 
 
-def measure_fma_rate(fp64=True, stream=0, add=False):
-    """Fused multiply-adds (add=True: FP64 additions) per second of the whole GPU, measured."""
+def measure_fma_rate(fp64=True, stream=0, add=False, l2=False):
+    """Fused multiply-adds (add=True: FP64 additions) per second of the whole GPU, measured;
+    l2=True: the L2 bandwidth in bytes per second."""
     r = ctypes.c_double()
-    op = 2 if add else int(bool(fp64))
+    op = 3 if l2 else (2 if add else int(bool(fp64)))
     check(lib.mlmc_measure_fma_rate(op, ctypes.c_void_p(stream or None), ctypes.byref(r)))
     return r.value
 
