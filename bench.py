@@ -957,7 +957,7 @@ def main():
     # kernels whose working set fits in L2 (< 100 MB per launch): their fraction of the measured
     # L2 copy bandwidth, not of HBM
     for name, v in kern.items():
-        if "bytes" in v and "gbs" in v and v["bytes"] < 100e6:
+        if "bytes" in v and "gbs" in v and "flops" not in v and v["bytes"] < 100e6:
             v["bound"] = "l2"
             v["l2_frac"] = v["gbs"] * 1e9 / l2bw
     # the FP64 fine-level apply: 4 FP64 operations per element (3 additions, 1 FMA)
