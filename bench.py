@@ -126,6 +126,9 @@ def parse():
                     help="Sec. 2 optimal allocation (default) or the Sec. 5 equal rho split")
     ap.add_argument("--coarse-growth", type=int, default=-1,
                     help="override the workload's block-width growth exponent on coarse level differences")
+    ap.add_argument("--set", action="append", default=[], metavar="KEY=INT",
+                    help="override an integer workload parameter (smooth_pre, smooth_post, coarse_smooth, "
+                         "inner_its, kcycle_its, restart, coarse_block, block)")
     ap.add_argument("--replicas", action="store_true",
                     help="with several GPUs: independent estimates (disjoint seeds) instead of one estimate whose "
                          "samples are spread over the GPUs")
@@ -848,6 +851,12 @@ def main():
     w = dict(WORKLOADS[args.workload])
     if args.coarse_growth >= 0:
         w["coarse_growth"] = args.coarse_growth
+    for kv in args.set:
+        key, val = kv.split("=")
+        if key not in ("smooth_pre", "smooth_post", "coarse_smooth", "inner_its", "kcycle_its", "restart",
+                       "coarse_block", "block"):
+            raise SystemExit("--set: unknown parameter " + key)
+        w[key] = int(val)
     nz = mlmc.NOISE_Z4 if w["noise"] == "z4" else mlmc.NOISE_RADEMACHER
     stream = torch.cuda.current_stream().cuda_stream
     h = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, stream)
