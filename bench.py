@@ -418,7 +418,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(config_dict("fp64-cpu-oracle", w), allocation=args.alloc),
+            "config": config_dict(w, args.alloc), "form": "FP64 CPU oracle (FGMRES + K-cycle)",
             "cpu_baseline": {"value": v, "unit": "s (extrapolated)", "kind": "oracle", "cores": procs,
                              "host": host_info(), "n_samples": plan["n_samples"],
                              "sample": "oracle FP64 FGMRES(30)+K-cycle at tol %g; N_l %s from its own 5-sample "
@@ -429,11 +429,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(form, w):
+def config_dict(w, alloc="optimal"):
+    """The workload, identical for both arms (the implementation is named in `form`)."""
     blk = w["nx"] * w["ny"] * (2 if w["kind"] == "wilson" else 1) * w["block"] * (16 if w["kind"] == "wilson" else 8)
-    return {"workload": w["name"], "form": form, "nx": w["nx"], "ny": w["ny"], "levels": w["levels"],
+    return {"workload": w["name"], "nx": w["nx"], "ny": w["ny"], "levels": w["levels"],
             "n_tv": w["n_tv"], "block": w["block"], "eps": w["eps"], "noise": w["noise"],
             "outer_gram_schmidt_passes": 2 if w.get("reorth", 1) else 1,
+            "allocation": alloc,
             "l2": ("inputs larger than L2 (a level-1 block is %d MiB in FP64)" % (blk >> 20)) if blk > 130e6 else
                   ("level-1 block %d MiB: L2-resident working set, no flush" % (blk >> 20))}
 
@@ -1046,8 +1048,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
                 "scaling": "weak" if (args.replicas or world == 1) else "strong", "vs_baseline": None,
                 "dtype": "f64/f32", "data": "synthetic",
-                "config": dict(config_dict("mixed: FP32 K-cycle under FP64 FGMRES", w), allocation=args.alloc,
-                               cost_model=args.cost_model),
+                "config": config_dict(w, args.alloc), "form": "mixed: FP32 K-cycle under FP64 FGMRES",
+                "cost_model": args.cost_model,
                 "clocks": sampler.summary(local), "gpu_launches": int(launches), "wall_s_timed": wall,
                 "e2e": {"value": e2e, "unit": "s",
                         "h2d_bytes_per_step": 0 if w["kind"] == "laplace" else 2 * w["nx"] * w["ny"] * 16,

@@ -140,6 +140,22 @@ def test_setup_matches_oracle(mlmc, case):
         assert max(np.abs(g.conj().T @ g - np.eye(g.shape[1])).max() for g in G) <= 1e-13
     tr = h.coarse_trace_exact()
     assert abs(tr - E.exact_coarse_trace(lv)) <= 1e-8 * abs(tr)
+    # samples of the GPU-built hierarchy itself: in the hat form a sample depends on each
+    # aggregate's range of P only (not on the basis inside it), so the GPU's and the oracle's
+    # hierarchies give the same samples up to the setup's rounding (checked against the
+    # size of the sample's first term, z^* A_l^{-1} z)
+    kind = "rademacher" if case.startswith("laplace") else "z4"
+    nz = mlmc.NOISE_RADEMACHER if kind == "rademacher" else mlmc.NOISE_Z4
+    hats = [accumulated_prolongation(lv, l) for l in range(1, 4)]
+    solv = E.LevelSolvers(lv)
+    for level in (1, 2):
+        got = h.sample_level_form(level, mlmc.FORM_HAT, nz, 5, 0, 6, 1e-12)
+        ref = E.level_samples(lv, solv, level, kind, 5, 0, 6, form="hat", hats=hats)
+        for j in range(6):
+            x = (rademacher if kind == "rademacher" else z4)(lv[0].n, 5, level, j)
+            z0 = hats[level - 1].conj().T @ x
+            t0 = abs(np.vdot(z0, solv.solve(level - 1, z0)))
+            assert abs(got[j] - ref[j]) <= 1e-7 * t0, (level, j, abs(got[j] - ref[j]) / t0)
     h.close()
 
 
