@@ -477,15 +477,21 @@ void launch_fma_rate(DType t, int add, void *out, int blocks, int iters, cudaStr
   MLMC_LAUNCH_CHECK("k_fma_rate");
 }
 
-// Bandwidth probe: dst = src in 16-byte packs, grid-stride (an L2-resident pair of
-// buffers gives the L2 ceiling that the small coarse-level kernels meet).
-__global__ void __launch_bounds__(256) k_copy16(uint4 *__restrict__ dst, const uint4 *__restrict__ src, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = src[i];
+// Bandwidth probe: `passes` copies of n 16-byte packs between two buffers, a -> b, then
+// b -> a, ... in one launch (every thread keeps its indices, so no pass reads what another
+// thread writes); an L2-resident pair gives the L2 ceiling of the small coarse-level kernels
+// without launch overhead in the measurement.
+__global__ void __launch_bounds__(256) k_copy16(uint4 *a, uint4 *b, size_t n, int passes) {
+  for (int p = 0; p < passes; ++p) {
+    const uint4 *src = (p & 1) ? b : a;
+    uint4 *dst = (p & 1) ? a : b;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+      dst[i] = src[i];
+  }
 }
 
-void launch_copy16(void *dst, const void *src, size_t n16, int blocks, cudaStream_t s) {
-  k_copy16<<<blocks, 256, 0, s>>>((uint4 *)dst, (const uint4 *)src, n16);
+void launch_copy16(void *a, void *b, size_t n16, int passes, int blocks, cudaStream_t s) {
+  k_copy16<<<blocks, 256, 0, s>>>((uint4 *)a, (uint4 *)b, n16, passes);
   MLMC_LAUNCH_CHECK("k_copy16");
 }
 

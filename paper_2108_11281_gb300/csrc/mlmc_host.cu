@@ -1980,17 +1980,18 @@ int mlmc_measure_fma_rate(int fp64, void *stream, double *fma_per_s) {
       cudaEvent_t e0, e1;
       check_cuda(cudaEventCreate(&e0), "event");
       check_cuda(cudaEventCreate(&e1), "event");
-      for (int i = 0; i < 3; ++i) launch_copy16(b.p, a.p, bytes / 16, sms * 8, s);
+      const int passes = 64;
+      launch_copy16(a.p, b.p, bytes / 16, 4, sms * 8, s);
       check_cuda(cudaEventRecord(e0, s), "record");
-      const int reps = 50;
-      for (int i = 0; i < reps; ++i) launch_copy16(b.p, a.p, bytes / 16, sms * 8, s);
+      const int reps = 4;
+      for (int i = 0; i < reps; ++i) launch_copy16(a.p, b.p, bytes / 16, passes, sms * 8, s);
       check_cuda(cudaEventRecord(e1, s), "record");
       check_cuda(cudaEventSynchronize(e1), "sync");
       float ms = 0.f;
       check_cuda(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      *fma_per_s = (double)reps * 2.0 * bytes / (ms * 1e-3);
+      *fma_per_s = (double)reps * passes * 2.0 * bytes / (ms * 1e-3);
       return;
     }
     const int blocks = sms * 8, iters = fp64 ? 4096 : 65536;

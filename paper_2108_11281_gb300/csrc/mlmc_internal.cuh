@@ -146,8 +146,8 @@ void launch_fill_zero(DType t, void *dst, size_t count, cudaStream_t s);
 // blocks x 256 threads, each running 8 FMA (add = 1: addition) chains of `iters` steps (F64 or F32);
 // out (blocks x 256 entries) is written only under a condition that never holds
 void launch_fma_rate(DType t, int add, void *out, int blocks, int iters, cudaStream_t s);
-// dst = src, n16 16-byte packs (bandwidth probe)
-void launch_copy16(void *dst, const void *src, size_t n16, int blocks, cudaStream_t s);
+// `passes` copies a -> b -> a ... of n16 16-byte packs in one launch (bandwidth probe)
+void launch_copy16(void *a, void *b, size_t n16, int passes, int blocks, cudaStream_t s);
 void launch_fill_one(DType t, void *dst, size_t count, cudaStream_t s);
 void launch_sub(DType t, void *out, const void *a, const void *b, size_t count, cudaStream_t s);
 // y[i][c] = alpha[c] * x[i][c] (+ y if accumulate)
