@@ -244,6 +244,14 @@ int mlmc_sample_level(mlmc_hierarchy *h, int level, int noise, uint64_t seed, ui
  * Sec. 5 cost model of the block's products.  Synchronous on return. */
 int mlmc_sample_block(mlmc_hierarchy *h, int level, int form, int noise, uint64_t seed, uint64_t first, int k,
                       double tol, mlmc_c64 *out_samples, double *out_stats, double *out_cost);
+/* The cycle's restricted residual (Remark 4.1) in one pass: rc = P_l^* m (b - A_l x)
+ * with m the indicator of the sites of `colour` ((i + j) mod 2): after a red-black
+ * Gauss-Seidel sweep the residual vanishes on the colour updated last, so the cycle
+ * passes the other one.  Device blocks x, b [n_l][k], rc [n_{l+1}][k] in FP64
+ * (precision MLMC_PREC_FP64) or FP32 (MLMC_PREC_MIXED_FP32, mixed form only);
+ * aggregation levels with at most 4 dofs per site and coarse site.  Synchronous. */
+int mlmc_residual_restrict(mlmc_hierarchy *h, int level, int precision, const void *x, const void *b, void *rc,
+                           int k, int colour);
 /* Samples per block on level difference `level` (1 <= level < L): the widths the
  * estimate draws (block, coarse_block, coarse_growth, mlmc_set_block_width). */
 int mlmc_block_width(const mlmc_hierarchy *h, int level, int *k);
@@ -370,8 +378,10 @@ int mlmc_measure_fma_rate(int fp64, void *stream, double *fma_per_s);
  * 6 restriction R_l = P_l^* from level l to l+1, 7 prolongation x += P_l e
  * from level l+1, 8 the learned correction's network on a level-1 block (mixed
  * form; the convolutions chosen by mlmc_set_conv_kernel; its FLOPs are
- * 2 x 9 x (16 c0 + 256 + 16 c0) per site and column, c0 its input channels)
- * (2-8 in the cycle precision).  k <= block on level 1,
+ * 2 x 9 x (16 c0 + 256 + 16 c0) per site and column, c0 its input channels),
+ * 9 the cycle's fused residual and restriction from level l to l+1 (after
+ * red-black pre-smoothing the residual lives on one colour)
+ * (2-9 in the cycle precision).  k <= block on level 1,
  * k <= max(block, coarse_block) on the coarser levels (6, 7: also within
  * level l+1's buffers).
  * Reports the average launch time and the algorithmic bytes one launch must

@@ -245,6 +245,218 @@ void launch_prolong_add(const ProlongView &P, const void *ec, void *x, int k, cu
   MLMC_LAUNCH_CHECK("k_prolong_add");
 }
 
+// ------------------------------------------------------------------ residual and restriction, fused
+// After a red-black (block) Gauss-Seidel sweep that updated colour 1 - `colour` last,
+// the residual b - A x vanishes on that colour: each of its site blocks was solved
+// exactly given its neighbours (up to rounding).  The restricted residual of the cycle
+// (Remark 4.1) therefore only needs the residual on the sites of `colour`, computed on
+// the fly: rc[I][q][c] = sum over the aggregate's sites s of that colour of
+// sum_a conj(P[I][loc*d + a][q]) (b - A x)_s[a][c].  Against a residual kernel and a
+// restriction kernel this saves writing and re-reading r and half of the residual work.
+// One thread per (aggregate, VEC columns), all DC coarse dofs.
+template <class T, int D, int DC, int VEC>
+__global__ void __launch_bounds__(128) k_residual_restrict(const T *__restrict__ coef, const T *__restrict__ x,
+                                                           const T *__restrict__ b, const T *__restrict__ P,
+                                                           T *__restrict__ rc, int nx, int ny, int ax, int ay,
+                                                           int kv, int colour) {
+  typedef TPack<T, VEC> V;
+  const int ncx = nx / ax, ncy = ny / ay;
+  const unsigned total = (unsigned)ncx * ncy * kv;
+  const int m = ax * ay * D;
+  const V *X = (const V *)x;
+  const V *B = (const V *)b;
+  V *RC = (V *)rc;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int c = (int)(t % (unsigned)kv);
+    const int I = (int)(t / (unsigned)kv);
+    const int bi = I % ncx, bj = I / ncx;
+    T acc[DC][VEC];
+#pragma unroll
+    for (int q = 0; q < DC; ++q)
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) acc[q][u] = zero<T>();
+    const T *PI = P + (size_t)I * m * DC;
+    for (int loc = 0; loc < ax * ay; ++loc) {
+      const int jj = loc / ax, ii = loc - jj * ax;
+      const int i = bi * ax + ii, j = bj * ay + jj;
+      if (((i + j) & 1) != colour) continue;          // the residual is zero there
+      const int s = j * nx + i;
+      int nb[5];
+      nb[0] = s;
+      nb[1] = j * nx + (i + 1 == nx ? 0 : i + 1);
+      nb[2] = j * nx + (i == 0 ? nx - 1 : i - 1);
+      nb[3] = (j + 1 == ny ? 0 : j + 1) * nx + i;
+      nb[4] = (j == 0 ? ny - 1 : j - 1) * nx + i;
+      T r[D][VEC];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const V bb = B[((size_t)s * D + a) * kv + c];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) r[a][u] = bb.v[u];
+      }
+#pragma unroll
+      for (int dir = 0; dir < 5; ++dir) {
+        const T *Bd = coef + ((size_t)s * 5 + dir) * D * D;
+        V xq[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) xq[q] = X[((size_t)nb[dir] * D + q) * kv + c];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int q = 0; q < D; ++q) {
+            const T w = Bd[a * D + q];
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) r[a][u] = r[a][u] - w * xq[q].v[u];
+          }
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const T *Pr = PI + (size_t)(loc * D + a) * DC;
+#pragma unroll
+        for (int q = 0; q < DC; ++q) {
+          const T pq = conj(Pr[q]);
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) acc[q][u] = acc[q][u] + pq * r[a][u];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < DC; ++q) {
+      V o;
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) o.v[u] = acc[q][u];
+      RC[((size_t)I * DC + q) * kv + c] = o;
+    }
+  }
+}
+
+// The same for the constant-coefficient Example 5.1 operator (d = 1, no matrix read):
+// r_s = b_s - (diag x_s - sum of the in-grid neighbours).
+template <class T, int DC, int VEC>
+__global__ void __launch_bounds__(128) k_laplace_residual_restrict(const T *__restrict__ x, const T *__restrict__ b,
+                                                                   const T *__restrict__ P, T *__restrict__ rc,
+                                                                   int nx, int ny, int ax, int ay, int kv, T diag,
+                                                                   int periodic, int colour) {
+  typedef TPack<T, VEC> V;
+  const int ncx = nx / ax, ncy = ny / ay;
+  const unsigned total = (unsigned)ncx * ncy * kv;
+  const int m = ax * ay;
+  const V *X = (const V *)x;
+  const V *B = (const V *)b;
+  V *RC = (V *)rc;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int c = (int)(t % (unsigned)kv);
+    const int I = (int)(t / (unsigned)kv);
+    const int bi = I % ncx, bj = I / ncx;
+    T acc[DC][VEC];
+#pragma unroll
+    for (int q = 0; q < DC; ++q)
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) acc[q][u] = zero<T>();
+    const T *PI = P + (size_t)I * m * DC;
+    for (int loc = 0; loc < m; ++loc) {
+      const int jj = loc / ax, ii = loc - jj * ax;
+      const int i = bi * ax + ii, j = bj * ay + jj;
+      if (((i + j) & 1) != colour) continue;
+      const int s = j * nx + i;
+      const bool on0 = i + 1 < nx || periodic, on1 = i > 0 || periodic;
+      const bool on2 = j + 1 < ny || periodic, on3 = j > 0 || periodic;
+      const int s0 = i + 1 < nx ? s + 1 : j * nx, s1 = i > 0 ? s - 1 : j * nx + nx - 1;
+      const int s2 = j + 1 < ny ? s + nx : i, s3 = j > 0 ? s - nx : (ny - 1) * nx + i;
+      V x0, x1, x2, x3;
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) x0.v[u] = x1.v[u] = x2.v[u] = x3.v[u] = zero<T>();
+      if (on0) x0 = X[(size_t)s0 * kv + c];
+      if (on1) x1 = X[(size_t)s1 * kv + c];
+      if (on2) x2 = X[(size_t)s2 * kv + c];
+      if (on3) x3 = X[(size_t)s3 * kv + c];
+      const V xs = X[(size_t)s * kv + c];
+      const V bb = B[(size_t)s * kv + c];
+      const T *Pr = PI + (size_t)loc * DC;
+      T r[VEC];
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) r[u] = (bb.v[u] + ((x0.v[u] + x1.v[u]) + (x2.v[u] + x3.v[u]))) - diag * xs.v[u];
+#pragma unroll
+      for (int q = 0; q < DC; ++q) {
+        const T pq = Pr[q];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) acc[q][u] = acc[q][u] + pq * r[u];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < DC; ++q) {
+      V o;
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) o.v[u] = acc[q][u];
+      RC[((size_t)I * DC + q) * kv + c] = o;
+    }
+  }
+}
+
+bool residual_restrict_ok(const StencilView &A, const ProlongView &P) {
+  if (P.bilinear || A.taps == 9 || A.nx % 2 || A.ny % 2) return false;
+  if (A.const_laplace) return A.t == F32 || A.t == F64;
+  return A.d <= 4 && P.dc <= 4 && A.d == P.d;
+}
+
+template <class T, int D, int DC>
+static void residual_restrict_go(const StencilView &A, const ProlongView &P, const void *x, const void *b, void *rc,
+                                 int k, int colour, cudaStream_t s) {
+  constexpr int VW = tr_vec<T>::v;
+  const int vec = (VW > 1 && k % VW == 0) ? VW : 1;
+  const int kv = k / vec;
+  const size_t items = (size_t)(P.nx / P.ax) * (P.ny / P.ay) * kv;
+  unsigned g = grid_for(items, 128, (size_t)1 << 20);
+  if (vec == VW && VW > 1)
+    k_residual_restrict<T, D, DC, VW><<<g, 128, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b,
+                                                        (const T *)P.P, (T *)rc, A.nx, A.ny, P.ax, P.ay, kv, colour);
+  else
+    k_residual_restrict<T, D, DC, 1><<<g, 128, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b,
+                                                       (const T *)P.P, (T *)rc, A.nx, A.ny, P.ax, P.ay, kv, colour);
+}
+
+template <class T, int DC>
+static void laplace_residual_restrict_go(const StencilView &A, const ProlongView &P, const void *x, const void *b,
+                                         void *rc, int k, int colour, cudaStream_t s) {
+  constexpr int VW = tr_vec<T>::v;
+  const int vec = (VW > 1 && k % VW == 0) ? VW : 1;
+  const int kv = k / vec;
+  const size_t items = (size_t)(P.nx / P.ax) * (P.ny / P.ay) * kv;
+  unsigned g = grid_for(items, 128, (size_t)1 << 20);
+  if (vec == VW && VW > 1)
+    k_laplace_residual_restrict<T, DC, VW><<<g, 128, 0, s>>>((const T *)x, (const T *)b, (const T *)P.P, (T *)rc,
+                                                             A.nx, A.ny, P.ax, P.ay, kv, (T)A.diag, A.periodic,
+                                                             colour);
+  else
+    k_laplace_residual_restrict<T, DC, 1><<<g, 128, 0, s>>>((const T *)x, (const T *)b, (const T *)P.P, (T *)rc,
+                                                            A.nx, A.ny, P.ax, P.ay, kv, (T)A.diag, A.periodic,
+                                                            colour);
+}
+
+void launch_residual_restrict(const StencilView &A, const ProlongView &P, const void *x, const void *b, void *rc,
+                              int k, int colour, cudaStream_t s) {
+  if (!residual_restrict_ok(A, P)) throw cuda_error{cudaErrorInvalidValue, "residual_restrict: unsupported level"};
+  if (A.const_laplace) {
+    if (A.t == F32) {
+      MLMC_DDISPATCH(P.dc, DC, laplace_residual_restrict_go<float, DC>(A, P, x, b, rc, k, colour, s));
+    } else {
+      MLMC_DDISPATCH(P.dc, DC, laplace_residual_restrict_go<double, DC>(A, P, x, b, rc, k, colour, s));
+    }
+  } else {
+    switch (A.d * 16 + P.dc) {
+#define MLMC_RR(DD, CC)                                                                                       \
+  case DD * 16 + CC:                                                                                          \
+    MLMC_DISPATCH(A.t, T, (residual_restrict_go<T, DD, CC>(A, P, x, b, rc, k, colour, s)));                  \
+    break;
+      MLMC_RR(1, 1) MLMC_RR(1, 2) MLMC_RR(1, 4) MLMC_RR(2, 2) MLMC_RR(2, 4) MLMC_RR(4, 4)
+#undef MLMC_RR
+      default:
+        throw cuda_error{cudaErrorInvalidValue, "residual_restrict: unsupported dofs"};
+    }
+  }
+  MLMC_LAUNCH_CHECK("k_residual_restrict");
+}
+
 // ------------------------------------------------------------------ damped Jacobi update
 // out = base + omega * D^{-1} (rhs - y); D = diagonal entries of the self block.
 template <class T>

@@ -471,9 +471,18 @@ void cycle(H_t &h, int lo, int l, const void *b, void *x, int k) {
     h.launches += 2;
     h.cost += nnz_of(h, l) * k;
   }
-  residual_op(h, l, lo, x, b, cb.r.p, k);
-  launch_restrict(pview(h, l, lo), cb.r.p, cn.b.p, k, s);
-  h.launches++;
+  const ProlongView Pv = pview(h, l, lo);
+  if (npre >= 1 && residual_restrict_ok(A, Pv)) {
+    // the pre-smoothing sweeps end on colour 1, so the residual lives on colour 0 only:
+    // residual and restriction in one pass, r never stored
+    launch_residual_restrict(A, Pv, x, b, cn.b.p, k, 0, s);
+    h.launches++;
+    h.cost += nnz_of(h, l) * k;                 // the residual's product, as counted before
+  } else {
+    residual_op(h, l, lo, x, b, cb.r.p, k);
+    launch_restrict(Pv, cb.r.p, cn.b.p, k, s);
+    h.launches++;
+  }
   h.cost += 2.0 * nnz_P(h, l) * k;              // restriction and the prolongation below: nnz(P) each
   if (l + 1 == last) {
     dense_apply(h, lo, cn.b.p, cn.x.p, k);
@@ -1543,6 +1552,22 @@ int mlmc_sample_block(mlmc_hierarchy *h, int level, int form, int noise, uint64_
   });
 }
 
+int mlmc_residual_restrict(mlmc_hierarchy *h, int level, int precision, const void *x, const void *b, void *rc,
+                           int k, int colour) {
+  return translate([&] {
+    need_level(h, level, 1, h ? h->L - 1 : 0);
+    const int lo = precision == MLMC_PREC_MIXED_FP32 ? 1 : 0;
+    if (lo && h->prm.precision != MLMC_PREC_MIXED_FP32) fail(MLMC_ERR_INVALID_ARG, "FP32 data needs the mixed form");
+    if (!x || !b || !rc || k < 1 || k > h->wl[level] || (colour != 0 && colour != 1))
+      fail(MLMC_ERR_INVALID_ARG, "bad arguments");
+    const StencilView A = view(*h, level - 1, lo);
+    const ProlongView P = pview(*h, level - 1, lo);
+    if (!residual_restrict_ok(A, P)) fail(MLMC_ERR_UNSUPPORTED, "not an aggregation level with d, dc <= 4");
+    launch_residual_restrict(A, P, x, b, rc, k, colour, h->stream);
+    check_cuda(cudaStreamSynchronize(h->stream), "sync");
+  });
+}
+
 int mlmc_block_width(const mlmc_hierarchy *h, int level, int *k) {
   return translate([&] {
     need_level(h, level, 1, h ? h->L - 1 : 0);
@@ -1861,7 +1886,9 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
     int l = level - 1;
     int lo = which == 0 ? 0 : (H.prm.precision == MLMC_PREC_MIXED_FP32 ? 1 : 0);
     if (which == 1 && !lo) fail(MLMC_ERR_INVALID_ARG, "FP32 kernels need the mixed form");
-    if (which < 0 || which > 8) fail(MLMC_ERR_INVALID_ARG, "unknown kernel family");
+    if (which < 0 || which > 9) fail(MLMC_ERR_INVALID_ARG, "unknown kernel family");
+    if (which == 9 && (l == H.L - 1 || k > H.wl[l + 1] || !residual_restrict_ok(view(H, l, lo), pview(H, l, lo))))
+      fail(MLMC_ERR_INVALID_ARG, "the fused residual restriction needs an aggregation level above the coarsest");
     if (which == 8 && (l != 0 || H.prm.precision != MLMC_PREC_MIXED_FP32))
       fail(MLMC_ERR_INVALID_ARG, "the learned correction acts on level 1 in the mixed form");
     if (which == 8) net_alloc(H);
@@ -1902,6 +1929,8 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
                          H.stream);
       } else if (which == 8) {
         net_forward(H, x, k);
+      } else if (which == 9) {
+        launch_residual_restrict(view(H, l, lo), pview(H, l, lo), y, x, H.cyc[lo][l + 1].b.p, k, 0, H.stream);
       } else if (which == 6) {
         launch_restrict(pview(H, l, lo), x, H.cyc[lo][l + 1].b.p, k, H.stream);
       } else if (which == 7) {
@@ -1923,7 +1952,13 @@ int mlmc_profile_kernel(mlmc_hierarchy *h, int which, int level, int k, int reps
     bool const_coef = l == 0 && !H.complex_op;      // Example 5.1 stencil has no matrix to read
     double coefb = const_coef ? 0.0 : (double)Lv.nsite * Lv.taps * Lv.d * Lv.d * es;
     double bytes;
-    if (which == 8) {
+    if (which == 9) {
+      // b on one colour, x everywhere (the colour's own and its neighbours), the colour's
+      // coefficient blocks, P, the coarse block out
+      const Level &C = H.lv[l + 1];
+      bytes = 0.5 * vec + vec + 0.5 * coefb + (double)Lv.n * Lv.dc * es + (double)C.n * k * es;
+      if (ms_per_launch) *ms_per_launch = ms / reps;
+    } else if (which == 8) {
       // the network's activations: the block in (to channels), then per layer its input
       // channels read and output channels written (c0 -> 16 -> 16 -> c0), FP32
       const double pairs = (double)Lv.nsite * k, c0 = H.net_c0;

@@ -185,6 +185,12 @@ void launch_rbgs_sweep(const StencilView &A, void *x, const void *b, int k, int 
 void launch_restrict(const ProlongView &P, const void *r, void *rc, int k, cudaStream_t s);
 // x += P ec
 void launch_prolong_add(const ProlongView &P, const void *ec, void *x, int k, cudaStream_t s);
+// rc = P^* (b - A x) with the residual taken on the sites of `colour` only (zero on the
+// other colour after a red-black Gauss-Seidel sweep that updated it last); aggregation
+// levels with d, dc <= 4 and the Example 5.1 fine level
+bool residual_restrict_ok(const StencilView &A, const ProlongView &P);
+void launch_residual_restrict(const StencilView &A, const ProlongView &P, const void *x, const void *b, void *rc,
+                              int k, int colour, cudaStream_t s);
 // out = base + omega * D^{-1} (rhs - y), D = diagonal entries of the self blocks; base/rhs may be null
 void launch_jacobi_update(const StencilView &A, void *out, const void *base, const void *rhs,
                           const void *y, double omega, int k, cudaStream_t s);

@@ -124,6 +124,7 @@ def _load():
         "mlmc_sample_block": [vp, i, i, i, u64, u64, i, d, ctypes.POINTER(C64), ctypes.POINTER(d), ctypes.POINTER(d)],
         "mlmc_nominal_sample_cost": [vp, i, i, ctypes.POINTER(d)],
         "mlmc_block_width": [vp, i, ctypes.POINTER(i)],
+        "mlmc_residual_restrict": [vp, i, i, vp, vp, vp, i, i],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -145,7 +146,7 @@ EXPORTED = ["mlmc_setup_hierarchy", "mlmc_destroy_hierarchy", "mlmc_level_info",
             "mlmc_autotune_block", "mlmc_trace_estimate_batch", "mlmc_sample_level_form", "mlmc_dense_apply",
             "mlmc_set_dense_kernel", "mlmc_level_taps", "mlmc_learned_stats",
             "mlmc_measure_fma_rate", "mlmc_set_conv_kernel", "mlmc_sample_block", "mlmc_nominal_sample_cost",
-            "mlmc_block_width"]
+            "mlmc_block_width", "mlmc_residual_restrict"]
 
 
 def check(status):
@@ -334,6 +335,11 @@ class Hierarchy:
                                     ctypes.byref(cost)))
         samples = np.array([complex(v.re, v.im) for v in out])
         return samples, (st[0], complex(st[1], st[2]), st[3]), cost.value
+
+    def residual_restrict(self, level, precision, x_ptr, b_ptr, rc_ptr, k, colour):
+        """rc = P_l^* m (b - A_l x), m the sites of `colour` (device pointers)."""
+        check(lib.mlmc_residual_restrict(self.handle, level, precision, ctypes.c_void_p(x_ptr), ctypes.c_void_p(b_ptr),
+                                         ctypes.c_void_p(rc_ptr), k, colour))
 
     def nominal_sample_cost(self, level, form=FORM_SIMPLIFIED):
         r = ctypes.c_double()

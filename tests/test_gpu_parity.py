@@ -486,6 +486,74 @@ def test_block_width_growth_keeps_samples(mlmc):
     h1.close()
 
 
+@pytest.mark.parametrize("case", ["laplace", "wilson"])
+def test_fused_residual_restriction(mlmc, case):
+    """The cycle's fused residual-and-restriction kernel against P^* m (b - A x) formed
+    with the level's own operator and prolongation (m = the sites of one colour), on
+    random blocks: the Example 5.1 fine level and a d = 4 aggregation level (Laplace),
+    and the complex d = 2 fine level of a Wilson operator with spin-split P; FP64 data
+    (1e-12 of scale) and, for the Laplacian, FP32 data in the mixed form (1e-5)."""
+    if case == "laplace":
+        N = 32
+        h = laplace_h(mlmc, N, 3, block=8, n_tv=4, setup_sweeps=10, coarse_sweeps=5, bootstrap=0,
+                      precision=mlmc.PREC_MIXED_FP32)
+        A1 = laplace2d(N, N)
+        levels = [(1, A1), (2, block_from_stencil(h.operator(2), *h.level_info(2)[:2]))]
+        cplx = False
+    else:
+        N = 16
+        U = gauge_links(N, N, 0.3, 5)
+        prm = mlmc.default_params(levels=3, n_tv=2, spin_split=1, setup_kind=mlmc.SETUP_INVERSE, setup_sweeps=4,
+                                  setup_omega=1.0, block=8, bootstrap=0)
+        h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.1, links=U)
+        levels = [(1, wilson2d(N, N, 0.1, U))]
+        cplx = True
+    k = 8
+    g = torch.Generator().manual_seed(3)
+    for level, A in levels:
+        nx, ny, d = h.level_info(level)
+        Pb = h.prolongation(level)                       # [agg][ax*ay*d][dc]
+        n, nc = A.shape[0], h.level_info(level + 1)[0] * h.level_info(level + 1)[1] * h.level_info(level + 1)[2]
+        dt = torch.complex128 if cplx else torch.float64
+        if cplx:
+            x = torch.complex(torch.randn(n, k, generator=g, dtype=torch.float64),
+                              torch.randn(n, k, generator=g, dtype=torch.float64))
+            b = torch.complex(torch.randn(n, k, generator=g, dtype=torch.float64),
+                              torch.randn(n, k, generator=g, dtype=torch.float64))
+        else:
+            x = torch.randn(n, k, generator=g, dtype=dt)
+            b = torch.randn(n, k, generator=g, dtype=dt)
+        r = b.numpy() - A @ x.numpy()
+        j, i = np.divmod(np.arange(nx * ny), nx)
+        ax = ay = 4
+        ncx = nx // ax
+        for colour in (0, 1):
+            mask = np.repeat(((i + j) % 2 == colour).astype(float), d)
+            rm = r * mask[:, None]
+            ref = np.zeros((nc, k), dtype=r.dtype)
+            dc = Pb.shape[2]
+            for I in range(Pb.shape[0]):
+                bi, bj = I % ncx, I // ncx
+                rows = []
+                for loc in range(ax * ay):
+                    jj, ii = divmod(loc, ax)
+                    site = (bj * ay + jj) * nx + bi * ax + ii
+                    rows.extend(site * d + a for a in range(d))
+                ref[I * dc:(I + 1) * dc] = Pb[I].conj().T @ rm[rows]
+            for prec in ((0, 1) if not cplx else (0,)):
+                if prec == 0:
+                    xs, bs, rc = x.cuda(), b.cuda(), torch.zeros(nc, k, dtype=dt, device="cuda")
+                else:
+                    xs, bs = x.to(torch.float32).cuda(), b.to(torch.float32).cuda()
+                    rc = torch.zeros(nc, k, dtype=torch.float32, device="cuda")
+                h.residual_restrict(level, mlmc.PREC_MIXED_FP32 if prec else mlmc.PREC_FP64, xs.data_ptr(),
+                                    bs.data_ptr(), rc.data_ptr(), k, colour)
+                tol = 1e-12 if prec == 0 else 1e-5
+                got = rc.cpu().numpy()
+                assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), (level, colour, prec)
+    h.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_512_column_blocks_on_a_coarse_difference(mlmc, precision):
     """coarse_growth = 2 widens the third level difference to 512 columns (real operators):
