@@ -148,19 +148,26 @@ __global__ void __launch_bounds__(256) k_restrict_split(const T *__restrict__ P,
   }
 }
 
-// x[s][a][c] += sum_q P[I(s)][loc(s)*d + a][q] ec[I][q][c]
+// x[s][a][c] += sum_q P[I(s)][loc(s)*d + a][q] ec[I][q][c], on every site (colour < 0)
+// or on the sites of one red-black colour only (the cycle's post-smoothing overwrites the
+// other colour first without reading it, so its prolongation would be dead work).
 template <class T, int DC, int VEC>
 __global__ void __launch_bounds__(256) k_prolong_add(const T *__restrict__ P, const T *__restrict__ ec, T *__restrict__ x,
-                                                     int nx, int ny, int d, int ax, int ay, int kv) {
+                                                     int nx, int ny, int d, int ax, int ay, int kv, int colour) {
   typedef TPack<T, VEC> V;
   int ncx = nx / ax;
-  const unsigned total = (unsigned)nx * ny * kv;
+  const unsigned total = (unsigned)(colour < 0 ? nx : nx / 2) * ny * kv;
   int m = ax * ay * d;
   const V *E = (const V *)ec;
   V *X = (V *)x;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int s = (int)(t / (unsigned)kv);
-    const int c = (int)(t - (unsigned)s * kv);
+    const int ts = (int)(t / (unsigned)kv);
+    const int c = (int)(t - (unsigned)ts * kv);
+    int s = ts;
+    if (colour >= 0) {
+      const int hj = ts / (nx / 2), hm = ts - hj * (nx / 2);
+      s = hj * nx + 2 * hm + ((hj + colour) & 1);
+    }
     int i = s % nx, j = s / nx;
     int I = (j / ay) * ncx + i / ax;
     int loc = (j % ay) * ax + (i % ax);
@@ -216,15 +223,18 @@ static void restrict_go(const ProlongView &P, const void *r, void *rc, int k, cu
 }
 
 template <class T, int DC>
-static void prolong_go(const ProlongView &P, const void *ec, void *x, int k, cudaStream_t s) {
+static void prolong_go(const ProlongView &P, const void *ec, void *x, int k, int colour, cudaStream_t s) {
   constexpr int VW = tr_vec<T>::v;
   const int vec = (VW > 1 && k % VW == 0) ? VW : 1;
   const int kv = k / vec;
-  unsigned g = grid_for((size_t)P.nx * P.ny * kv, 256, (size_t)1 << 20);
+  const size_t sites = colour < 0 ? (size_t)P.nx * P.ny : (size_t)(P.nx / 2) * P.ny;
+  unsigned g = grid_for(sites * kv, 256, (size_t)1 << 20);
   if (vec == VW && VW > 1)
-    k_prolong_add<T, DC, VW><<<g, 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx, P.ny, P.d, P.ax, P.ay, kv);
+    k_prolong_add<T, DC, VW><<<g, 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx, P.ny, P.d, P.ax, P.ay, kv,
+                                               colour);
   else
-    k_prolong_add<T, DC, 1><<<g, 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx, P.ny, P.d, P.ax, P.ay, kv);
+    k_prolong_add<T, DC, 1><<<g, 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx, P.ny, P.d, P.ax, P.ay, kv,
+                                              colour);
 }
 
 void launch_restrict(const ProlongView &P, const void *r, void *rc, int k, cudaStream_t s) {
@@ -241,7 +251,16 @@ void launch_prolong_add(const ProlongView &P, const void *ec, void *x, int k, cu
     launch_prolong_bilinear(P.t, ec, x, P.nx, P.ny, k, s);
     return;
   }
-  MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC, prolong_go<T, DC>(P, ec, x, k, s)));
+  MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC, prolong_go<T, DC>(P, ec, x, k, -1, s)));
+  MLMC_LAUNCH_CHECK("k_prolong_add");
+}
+
+void launch_prolong_add_colour(const ProlongView &P, const void *ec, void *x, int k, int colour, cudaStream_t s) {
+  if (P.bilinear || P.nx % 2) {
+    launch_prolong_add(P, ec, x, k, s);
+    return;
+  }
+  MLMC_DISPATCH(P.t, T, MLMC_DDISPATCH(P.dc, DC, prolong_go<T, DC>(P, ec, x, k, colour, s)));
   MLMC_LAUNCH_CHECK("k_prolong_add");
 }
 

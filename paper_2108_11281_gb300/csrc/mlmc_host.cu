@@ -492,7 +492,13 @@ void cycle(H_t &h, int lo, int l, const void *b, void *x, int k) {
     Precond M = [&h, lo, l, k](const void *v, void *z) { cycle(h, lo, l + 1, v, z, k); };
     fgmres(h, *cn.kcyc, l + 1, lo, cn.b.p, cn.x.p, k, 0.0, h.prm.kcycle_its, h.prm.kcycle_its, M, false, nullptr);
   }
-  launch_prolong_add(pview(h, l, lo), cn.x.p, x, k, s);
+  // the post-smoothing starts with colour 1 and does not read x there, so colour 1 needs no
+  // prolongation, unless the fine-level hooks (learned correction, capture) read all of x
+  const bool hooks = l == 0 && lo == 1 && (h.net_on || h.capturing);
+  if (npost >= 1 && !hooks && A.taps == 5)
+    launch_prolong_add_colour(Pv, cn.x.p, x, k, 0, s);
+  else
+    launch_prolong_add(Pv, cn.x.p, x, k, s);
   h.launches++;
   if (l == 0 && lo == 1) fine_hooks(h, x, b, k);
   for (int it = 0; it < npost; ++it) {

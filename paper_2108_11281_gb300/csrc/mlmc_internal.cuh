@@ -185,6 +185,8 @@ void launch_rbgs_sweep(const StencilView &A, void *x, const void *b, int k, int 
 void launch_restrict(const ProlongView &P, const void *r, void *rc, int k, cudaStream_t s);
 // x += P ec
 void launch_prolong_add(const ProlongView &P, const void *ec, void *x, int k, cudaStream_t s);
+// x += P ec on the sites of one red-black colour only (aggregation levels; all sites otherwise)
+void launch_prolong_add_colour(const ProlongView &P, const void *ec, void *x, int k, int colour, cudaStream_t s);
 // rc = P^* (b - A x) with the residual taken on the sites of `colour` only (zero on the
 // other colour after a red-black Gauss-Seidel sweep that updated it last); aggregation
 // levels with d, dc <= 4 and the Example 5.1 fine level

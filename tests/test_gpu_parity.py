@@ -554,6 +554,20 @@ def test_fused_residual_restriction(mlmc, case):
     h.close()
 
 
+def test_prolongation_of_one_colour_is_exact(mlmc):
+    """The cycle prolongates only colour 0: its post-smoothing starts with colour 1 and does
+    not read x there.  With a zero-weight learned correction switched on, the fine level
+    prolongates every site (the correction reads all of x) and adds exactly zero, so the
+    samples must come out equal to the last bit."""
+    h = laplace_h(mlmc, 32, 3, block=8, n_tv=4, setup_sweeps=10, coarse_sweeps=5, bootstrap=0,
+                  precision=mlmc.PREC_MIXED_FP32)
+    s0, _ = h.sample_level(1, mlmc.NOISE_RADEMACHER, 4, 0, 8, 1e-10)
+    h.learned_set(np.zeros(h.net_weights(), dtype=np.float32), enable=1)
+    s1, _ = h.sample_level(1, mlmc.NOISE_RADEMACHER, 4, 0, 8, 1e-10)
+    assert np.array_equal(s0, s1)
+    h.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_512_column_blocks_on_a_coarse_difference(mlmc, precision):
     """coarse_growth = 2 widens the third level difference to 512 columns (real operators):
