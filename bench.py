@@ -958,6 +958,12 @@ def main():
         for name, which in (("restrict", 6), ("prolong", 7)):
             kms, kbytes = h.profile_kernel(which, lvl, kt, 20)
             kern["%s_fp32_level%d" % (name, lvl)] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6, "k": kt}
+        # the cycle's fused residual and restriction (levels whose stencil and P it supports)
+        try:
+            kms, kbytes = h.profile_kernel(9, lvl, kt, 20)
+        except mlmc.MLMCError:
+            continue
+        kern["residual_restrict_fp32_level%d" % lvl] = {"ms": kms, "bytes": kbytes, "gbs": kbytes / kms / 1e6, "k": kt}
     # the arithmetic ceilings the FP64 kernels meet: measured FMA rates
     fma64 = mlmc.measure_fma_rate(True, stream)
     fma32 = mlmc.measure_fma_rate(False, stream)

@@ -40,10 +40,9 @@ __device__ inline void load_row(const T *__restrict__ p, T out[D]) {
 template <class T, int D, int VEC>
 __device__ __forceinline__ void stencil_body(const T *__restrict__ coef, const T *__restrict__ x,
                                              const T *__restrict__ b, T *__restrict__ y, int nx, int ny, int kv,
-                                             int mode) {
+                                             int mode, int j, int t) {
+  // j = lattice row; t = (site i of the row, pack c of VEC columns)
   typedef Pack<T, VEC> V;
-  const int j = blockIdx.y;                 // grid.y = lattice row
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < nx * kv) {
     const int i = t / kv, c = t - (t / kv) * kv;
     const int s = j * nx + i;
@@ -96,17 +95,23 @@ template <class T, int D, int VEC>
 __global__ void __launch_bounds__(256) k_stencil(const T *__restrict__ coef, const T *__restrict__ x,
                                                  const T *__restrict__ b, T *__restrict__ y, int nx, int ny, int kv,
                                                  int mode) {
-  stencil_body<T, D, VEC>(coef, x, b, y, nx, ny, kv, mode);
+  stencil_body<T, D, VEC>(coef, x, b, y, nx, ny, kv, mode, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // The same in blocks of 128 threads pinned at 8 per SM (<= 64 registers), for FP32
 // blocks with d = 4 (the aggregation levels of the Laplace hierarchy), like the
-// block smoother: both are load-latency bound.
+// block smoother: both are load-latency bound.  The grid is resident (8 blocks per
+// SM) and strides over the units (row j, chunk of 128 threads of the row), in
+// row order, so the rows in flight stay a narrow band (vertical neighbours from L2).
 template <class T, int D, int VEC>
 __global__ void __launch_bounds__(128, 8) k_stencil_p(const T *__restrict__ coef, const T *__restrict__ x,
                                                       const T *__restrict__ b, T *__restrict__ y, int nx, int ny,
-                                                      int kv, int mode) {
-  stencil_body<T, D, VEC>(coef, x, b, y, nx, ny, kv, mode);
+                                                      int kv, int mode, int bpr) {
+  const int units = bpr * ny;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int j = u / bpr;
+    stencil_body<T, D, VEC>(coef, x, b, y, nx, ny, kv, mode, j, (u - j * bpr) * 128 + threadIdx.x);
+  }
 }
 
 // columns per thread for the generic kernels: 16-byte packs for FP32 data on
@@ -207,8 +212,11 @@ static void stencil_go(const StencilView &A, const void *x, const void *b, void 
     int kv = k / VW;
     dim3 g((A.nx * kv + 255) / 256, A.ny);
     if constexpr (std::is_same<T, float>::value && D == 4)
-      k_stencil_p<T, D, VW><<<dim3((A.nx * kv + 127) / 128, A.ny), 128, 0, s>>>(
-          (const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, mode);
+    {
+      const int bpr = (A.nx * kv + 127) / 128;
+      k_stencil_p<T, D, VW><<<resident_grid(bpr * A.ny, 8), 128, 0, s>>>(
+          (const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, mode, bpr);
+    }
     else
       k_stencil<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv,
                                             mode);
@@ -400,11 +408,10 @@ template <int D> struct rbgs_vec<cdouble, D> { static const int v = 1; };
 template <class T, int D, int VEC>
 __device__ __forceinline__ void rbgs_half_body(const T *__restrict__ coef, const T *__restrict__ dinv,
                                                T *__restrict__ x, const T *__restrict__ b, int nx, int ny, int kv,
-                                               int colour, int other_zero) {
+                                               int colour, int other_zero, int j, int t) {
+  // j = lattice row; t = (site m of the colour in the row, pack c of VEC columns)
   typedef Pack<T, VEC> V;
-  const int j = blockIdx.y;
   const int hx = nx / 2;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < hx * kv) {
     const int m = t / kv, c = t - (t / kv) * kv;
     const int i = 2 * m + ((j + colour) & 1);
@@ -464,21 +471,28 @@ template <class T, int D, int VEC>
 __global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, const T *__restrict__ dinv,
                                                    T *__restrict__ x, const T *__restrict__ b, int nx, int ny, int kv,
                                                    int colour, int other_zero) {
-  rbgs_half_body<T, D, VEC>(coef, dinv, x, b, nx, ny, kv, colour, other_zero);
+  rbgs_half_body<T, D, VEC>(coef, dinv, x, b, nx, ny, kv, colour, other_zero, blockIdx.y,
+                            blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // The same half-sweep in blocks of 128 threads with residency pinned at 8 blocks
 // per SM (<= 64 registers), for FP32 blocks with d = 4 (the aggregation levels of
-// the Laplace hierarchy).  The kernel is load-latency bound; measured on the
-// 256^2 x 4 level, k = 128, per sweep: 88.3 us here, 90.6 us with 256 threads x 4
+// the Laplace hierarchy), on a resident grid striding over the units (row j, chunk of
+// 128 threads of the row) in row order.  The kernel is load-latency bound; measured
+// on the 256^2 x 4 level, k = 128, per sweep: 86.7-87.0 us here, 88.3 us with one
+// block per unit (a grid of 8192 blocks), 90.6 us with 256 threads x 4
 // blocks, 93.7 us unpinned (256 threads), 96-99 us with two or four neighbour
 // blocks' loads issued together (80-128 registers, 2-3 blocks of 256 per SM) and
 // 100-104 us with 5-8 blocks of 256 per SM (8-byte packs or spills).
 template <class T, int D, int VEC>
 __global__ void __launch_bounds__(128, 8) k_rbgs_half_p(const T *__restrict__ coef, const T *__restrict__ dinv,
                                                         T *__restrict__ x, const T *__restrict__ b, int nx, int ny,
-                                                        int kv, int colour, int other_zero) {
-  rbgs_half_body<T, D, VEC>(coef, dinv, x, b, nx, ny, kv, colour, other_zero);
+                                                        int kv, int colour, int other_zero, int bpr) {
+  const int units = bpr * ny;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int j = u / bpr;
+    rbgs_half_body<T, D, VEC>(coef, dinv, x, b, nx, ny, kv, colour, other_zero, j, (u - j * bpr) * 128 + threadIdx.x);
+  }
 }
 
 // Row-split variant for large site blocks (d >= 8, the coarse levels of the
@@ -565,8 +579,11 @@ static void rbgs_go(const StencilView &A, void *x, const void *b, int k, int col
     int kv = k / VW;
     dim3 g(((A.nx / 2) * kv + 255) / 256, A.ny);
     if constexpr (std::is_same<T, float>::value && D == 4)
-      k_rbgs_half_p<T, D, VW><<<dim3(((A.nx / 2) * kv + 127) / 128, A.ny), 128, 0, s>>>(
-          (const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny, kv, colour, other_zero);
+    {
+      const int bpr = ((A.nx / 2) * kv + 127) / 128;
+      k_rbgs_half_p<T, D, VW><<<resident_grid(bpr * A.ny, 8), 128, 0, s>>>(
+          (const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny, kv, colour, other_zero, bpr);
+    }
     else
       k_rbgs_half<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny,
                                               kv, colour, other_zero);

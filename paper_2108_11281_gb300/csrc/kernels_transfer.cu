@@ -215,11 +215,17 @@ static void restrict_go(const ProlongView &P, const void *r, void *rc, int k, cu
                                                             P.ax, P.ay, kv);
     return;
   }
-  unsigned g = grid_for(items, 128, (size_t)1 << 20);
-  if (vec == VW && VW > 1)
-    k_restrict<T, DC, VW, QG><<<g, 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d, P.ax, P.ay, kv);
-  else
-    k_restrict<T, DC, 1, QG><<<g, 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx, P.ny, P.d, P.ax, P.ay, kv);
+  // resident grid striding over the items (block scheduling costs more than the tail)
+  const size_t blocks = (items + 127) / 128;
+  if (vec == VW && VW > 1) {
+    static const int occ = blocks_per_sm(k_restrict<T, DC, VW, QG>, 128, 0);
+    k_restrict<T, DC, VW, QG><<<resident_grid(blocks, occ), 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx,
+                                                                         P.ny, P.d, P.ax, P.ay, kv);
+  } else {
+    static const int occ = blocks_per_sm(k_restrict<T, DC, 1, QG>, 128, 0);
+    k_restrict<T, DC, 1, QG><<<resident_grid(blocks, occ), 128, 0, s>>>((const T *)P.P, (const T *)r, (T *)rc, P.nx,
+                                                                        P.ny, P.d, P.ax, P.ay, kv);
+  }
 }
 
 template <class T, int DC>
@@ -228,13 +234,16 @@ static void prolong_go(const ProlongView &P, const void *ec, void *x, int k, int
   const int vec = (VW > 1 && k % VW == 0) ? VW : 1;
   const int kv = k / vec;
   const size_t sites = colour < 0 ? (size_t)P.nx * P.ny : (size_t)(P.nx / 2) * P.ny;
-  unsigned g = grid_for(sites * kv, 256, (size_t)1 << 20);
-  if (vec == VW && VW > 1)
-    k_prolong_add<T, DC, VW><<<g, 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx, P.ny, P.d, P.ax, P.ay, kv,
-                                               colour);
-  else
-    k_prolong_add<T, DC, 1><<<g, 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx, P.ny, P.d, P.ax, P.ay, kv,
-                                              colour);
+  const size_t blocks = (sites * kv + 255) / 256;
+  if (vec == VW && VW > 1) {
+    static const int occ = blocks_per_sm(k_prolong_add<T, DC, VW>, 256, 0);
+    k_prolong_add<T, DC, VW><<<resident_grid(blocks, occ), 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx,
+                                                                        P.ny, P.d, P.ax, P.ay, kv, colour);
+  } else {
+    static const int occ = blocks_per_sm(k_prolong_add<T, DC, 1>, 256, 0);
+    k_prolong_add<T, DC, 1><<<resident_grid(blocks, occ), 256, 0, s>>>((const T *)P.P, (const T *)ec, (T *)x, P.nx,
+                                                                       P.ny, P.d, P.ax, P.ay, kv, colour);
+  }
 }
 
 void launch_restrict(const ProlongView &P, const void *r, void *rc, int k, cudaStream_t s) {
@@ -436,7 +445,10 @@ static void residual_restrict_go(const StencilView &A, const ProlongView &P, con
   const int vec = (VW > 1 && k % VW == 0) ? VW : 1;
   const int kv = k / vec;
   const size_t items = (size_t)(P.nx / P.ax) * (P.ny / P.ay) * kv;
-  unsigned g = grid_for(items, 128, (size_t)1 << 20);
+  const size_t blocks = (items + 127) / 128;
+  static const int occ_v = blocks_per_sm(k_residual_restrict<T, D, DC, VW>, 128, 0);
+  static const int occ_1 = blocks_per_sm(k_residual_restrict<T, D, DC, 1>, 128, 0);
+  const unsigned g = resident_grid(blocks, vec == VW && VW > 1 ? occ_v : occ_1);
   if (vec == VW && VW > 1)
     k_residual_restrict<T, D, DC, VW><<<g, 128, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b,
                                                         (const T *)P.P, (T *)rc, A.nx, A.ny, P.ax, P.ay, kv, colour);
@@ -452,7 +464,10 @@ static void laplace_residual_restrict_go(const StencilView &A, const ProlongView
   const int vec = (VW > 1 && k % VW == 0) ? VW : 1;
   const int kv = k / vec;
   const size_t items = (size_t)(P.nx / P.ax) * (P.ny / P.ay) * kv;
-  unsigned g = grid_for(items, 128, (size_t)1 << 20);
+  const size_t blocks = (items + 127) / 128;
+  static const int occ_v = blocks_per_sm(k_laplace_residual_restrict<T, DC, VW>, 128, 0);
+  static const int occ_1 = blocks_per_sm(k_laplace_residual_restrict<T, DC, 1>, 128, 0);
+  const unsigned g = resident_grid(blocks, vec == VW && VW > 1 ? occ_v : occ_1);
   if (vec == VW && VW > 1)
     k_laplace_residual_restrict<T, DC, VW><<<g, 128, 0, s>>>((const T *)x, (const T *)b, (const T *)P.P, (T *)rc,
                                                              A.nx, A.ny, P.ax, P.ay, kv, (T)A.diag, A.periodic,

@@ -4,6 +4,7 @@
 // Vector blocks are [row][k] with the k columns (independent right-hand
 // sides / samples) innermost, so a warp touches consecutive columns of one row.
 #include <algorithm>
+#include <atomic>
 
 #include "mlmc_internal.cuh"
 
@@ -11,6 +12,19 @@ namespace mlmc {
 
 void check_cuda(cudaError_t e, const char *where) {
   if (e != cudaSuccess) throw cuda_error{e, where};
+}
+
+unsigned resident_grid(size_t units, int per_sm) {
+  static std::atomic<int> sms_of[64];              // SM count per device ordinal, 0 = not looked up
+  int dev = 0;
+  MLMC_CUDA(cudaGetDevice(&dev));
+  int sms = dev < 64 ? sms_of[dev].load(std::memory_order_relaxed) : 0;
+  if (sms == 0) {
+    MLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (dev < 64) sms_of[dev].store(sms, std::memory_order_relaxed);
+  }
+  const size_t g = std::min(units, (size_t)sms * (size_t)per_sm);
+  return (unsigned)std::max<size_t>(g, 1);
 }
 
 // ------------------------------------------------------------------ Philox

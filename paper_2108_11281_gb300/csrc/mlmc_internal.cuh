@@ -112,6 +112,20 @@ inline unsigned grid_for(size_t work, int block, size_t cap = 152 * 32) {
   return (unsigned)g;
 }
 
+// Grid of a kernel whose blocks stride over `units` work units: `per_sm` blocks per
+// SM of the current device (all resident at once when the kernel's resources allow),
+// at most `units`, at least 1.
+unsigned resident_grid(size_t units, int per_sm);
+
+// Blocks of `kernel` that fit on one SM at once (launch block size, dynamic shared
+// memory), at least 1.
+template <class F>
+int blocks_per_sm(F kernel, int block, size_t smem) {
+  int n = 0;
+  check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem), "occupancy");
+  return n > 0 ? n : 1;
+}
+
 // ----------------------------------------------------------------- views
 // Nearest-neighbour block stencil on an nx x ny periodic lattice with d dofs
 // per site: coef[site][dir][r][c], dir = 0 self, 1 +x, 2 -x, 3 +y, 4 -y.
