@@ -109,7 +109,7 @@ def parse():
                          "difference inside cudaProfilerStart/Stop; prints no bench line")
     ap.add_argument("--profile-kernel", default="",
                     choices=["", "multidot", "multiaxpy", "rbgs", "rbgs2", "stencil", "stencil64", "dense", "restrict",
-                             "prolong", "restrict2", "prolong2", "net", "net_simt"],
+                             "prolong", "restrict2", "prolong2", "rr", "rr2", "rr3", "net", "net_simt"],
                     help="with --profile-sample: instead of sample blocks, the one kernel launch the bench's "
                          "roofline measures (3 warm launches, then 1), inside cudaProfilerStart/Stop")
     ap.add_argument("--profile-step", action="store_true",
@@ -137,6 +137,20 @@ def parse():
                          "(counted) or one product per operator solved with (nominal, solver-independent); "
                          "default: the workload's (nominal for the Laplacians, counted for Wilson)")
     return ap.parse_args()
+
+
+def workload_of(args):
+    """The workload named by --workload with the --coarse-growth and --set overrides."""
+    w = dict(WORKLOADS[args.workload])
+    if args.coarse_growth >= 0:
+        w["coarse_growth"] = args.coarse_growth
+    for kv in args.set:
+        key, val = kv.split("=")
+        if key not in ("smooth_pre", "smooth_post", "coarse_smooth", "inner_its", "kcycle_its", "restart",
+                       "coarse_block", "block"):
+            raise SystemExit("--set: unknown parameter " + key)
+        w[key] = int(val)
+    return w
 
 
 def hierarchy_params(mlmc, precision, w=None):
@@ -446,7 +460,7 @@ def profile_sample(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2108_11281_gb300 import mlmc
-    w = dict(WORKLOADS[args.workload])
+    w = workload_of(args)
     if args.profile_nx:
         w["nx"] = w["ny"] = args.profile_nx
     nz = mlmc.NOISE_Z4 if w["noise"] == "z4" else mlmc.NOISE_RADEMACHER
@@ -454,12 +468,14 @@ def profile_sample(args):
     if args.profile_kernel:
         which = {"stencil": 1, "stencil64": 0, "rbgs": 2, "rbgs2": 2, "multidot": 3, "multiaxpy": 4, "dense": 5,
                  "restrict": 6, "restrict2": 6, "prolong": 7, "prolong2": 7, "net": 8,
-                 "net_simt": 8}[args.profile_kernel]
+                 "net_simt": 8, "rr": 9, "rr2": 9, "rr3": 9}[args.profile_kernel]
         level, kk = 1, w["block"]
         if which == 5:
             level, kk = w["levels"], w.get("coarse_block") or w["block"]
-        elif args.profile_kernel in ("rbgs2", "restrict2", "prolong2"):
+        elif args.profile_kernel in ("rbgs2", "restrict2", "prolong2", "rr2"):
             level, kk = 2, w.get("coarse_block") or w["block"]
+        elif args.profile_kernel == "rr3":
+            level, kk = 3, w.get("coarse_block") or w["block"]
         if which == 8:
             h.set_conv_kernel(mlmc.CONV_SIMT if args.profile_kernel == "net_simt" else mlmc.CONV_TC)
         torch.cuda.synchronize()
@@ -850,15 +866,7 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2108_11281_gb300 import mlmc
-    w = dict(WORKLOADS[args.workload])
-    if args.coarse_growth >= 0:
-        w["coarse_growth"] = args.coarse_growth
-    for kv in args.set:
-        key, val = kv.split("=")
-        if key not in ("smooth_pre", "smooth_post", "coarse_smooth", "inner_its", "kcycle_its", "restart",
-                       "coarse_block", "block"):
-            raise SystemExit("--set: unknown parameter " + key)
-        w[key] = int(val)
+    w = workload_of(args)
     nz = mlmc.NOISE_Z4 if w["noise"] == "z4" else mlmc.NOISE_RADEMACHER
     stream = torch.cuda.current_stream().cuda_stream
     h = make_hierarchy(mlmc, mlmc.PREC_MIXED_FP32, w, stream)

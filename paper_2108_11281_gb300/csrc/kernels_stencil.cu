@@ -103,12 +103,15 @@ __global__ void __launch_bounds__(256) k_stencil(const T *__restrict__ coef, con
 // block smoother: both are load-latency bound.  The grid is resident (8 blocks per
 // SM) and strides over the units (row j, chunk of 128 threads of the row), in
 // row order, so the rows in flight stay a narrow band (vertical neighbours from L2).
+// rev = 1 walks the rows from the last: the apply follows a smoothing half-sweep that
+// ended there, whose last writes are then still in L2 when they are read.
 template <class T, int D, int VEC>
 __global__ void __launch_bounds__(128, 8) k_stencil_p(const T *__restrict__ coef, const T *__restrict__ x,
                                                       const T *__restrict__ b, T *__restrict__ y, int nx, int ny,
-                                                      int kv, int mode, int bpr) {
+                                                      int kv, int mode, int bpr, int rev) {
   const int units = bpr * ny;
-  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+  for (int u0 = blockIdx.x; u0 < units; u0 += gridDim.x) {
+    const int u = rev ? units - 1 - u0 : u0;
     const int j = u / bpr;
     stencil_body<T, D, VEC>(coef, x, b, y, nx, ny, kv, mode, j, (u - j * bpr) * 128 + threadIdx.x);
   }
@@ -215,7 +218,7 @@ static void stencil_go(const StencilView &A, const void *x, const void *b, void 
     {
       const int bpr = (A.nx * kv + 127) / 128;
       k_stencil_p<T, D, VW><<<resident_grid(bpr * A.ny, 8), 128, 0, s>>>(
-          (const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, mode, bpr);
+          (const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, mode, bpr, 0);
     }
     else
       k_stencil<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv,
@@ -300,11 +303,13 @@ __global__ void __launch_bounds__(256) k_laplace(const T *__restrict__ x, const 
 
 // Red-black Gauss-Seidel half-sweep for Example 5.1: x_s = (b_s + sum of neighbours) / diag
 // on the sites of `colour`.  other_zero = 1: the other colour holds zeros (not read).
+// Colour 1 takes the rows from the last (grid.y reversed): consecutive half-sweeps
+// alternate direction, so each starts on the rows the previous one wrote last.
 template <class T, int VEC>
 __global__ void __launch_bounds__(256) k_laplace_rbgs(T *__restrict__ x, const T *__restrict__ b, int nx, int ny,
                                                       int kv, T dinv, int periodic, int colour, int other_zero) {
   typedef Pack<T, VEC> V;
-  const int j = blockIdx.y;
+  const int j = colour ? ny - 1 - (int)blockIdx.y : (int)blockIdx.y;
   const int i0 = (j + colour) & 1;
   const int hx = (nx - i0 + 1) >> 1;      // sites of this colour in row j (odd nx too)
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -488,8 +493,11 @@ template <class T, int D, int VEC>
 __global__ void __launch_bounds__(128, 8) k_rbgs_half_p(const T *__restrict__ coef, const T *__restrict__ dinv,
                                                         T *__restrict__ x, const T *__restrict__ b, int nx, int ny,
                                                         int kv, int colour, int other_zero, int bpr) {
+  // colour 1 walks the rows from the last: consecutive half-sweeps alternate direction,
+  // so each starts on the rows the previous one wrote last (still in L2)
   const int units = bpr * ny;
-  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+  for (int u0 = blockIdx.x; u0 < units; u0 += gridDim.x) {
+    const int u = colour ? units - 1 - u0 : u0;
     const int j = u / bpr;
     rbgs_half_body<T, D, VEC>(coef, dinv, x, b, nx, ny, kv, colour, other_zero, j, (u - j * bpr) * 128 + threadIdx.x);
   }

@@ -1,5 +1,7 @@
 // Aggregation transfers (restriction P^* r and prolongation x += P e, with
 // dense per-aggregate blocks) and the damped-Jacobi update of the setup filter.
+#include <type_traits>
+
 #include "mlmc_internal.cuh"
 
 namespace mlmc {
@@ -281,33 +283,54 @@ void launch_prolong_add_colour(const ProlongView &P, const void *ec, void *x, in
 // the fly: rc[I][q][c] = sum over the aggregate's sites s of that colour of
 // sum_a conj(P[I][loc*d + a][q]) (b - A x)_s[a][c].  Against a residual kernel and a
 // restriction kernel this saves writing and re-reading r and half of the residual work.
-// One thread per (aggregate, VEC columns), all DC coarse dofs.
-template <class T, int D, int DC, int VEC>
-__global__ void __launch_bounds__(128) k_residual_restrict(const T *__restrict__ coef, const T *__restrict__ x,
-                                                           const T *__restrict__ b, const T *__restrict__ P,
-                                                           T *__restrict__ rc, int nx, int ny, int ax, int ay,
-                                                           int kv, int colour) {
+// The colour sites of an aggregate are spread over RR_SLOTS threads (slot n takes the
+// colour sites n, n + RR_SLOTS, ... in site order; odd aggregate sides: the sites
+// n, n + RR_SLOTS, ... of either colour, the other colour skipped), each for VEC
+// columns; the block is
+// (KC column packs) x (RR_SLOTS slots) of one aggregate, and the slots' partial sums meet
+// in shared memory, added in slot order (deterministic).
+constexpr int RR_SLOTS = 8;
+
+template <class T, int D, int DC, int VEC, int KC>
+__global__ void __launch_bounds__(KC * RR_SLOTS, 256 / (KC * RR_SLOTS) * 4) k_residual_restrict(const T *__restrict__ coef,
+                                                                     const T *__restrict__ x,
+                                                                     const T *__restrict__ b,
+                                                                     const T *__restrict__ P, T *__restrict__ rc,
+                                                                     int nx, int ny, int ax, int ay, int kv,
+                                                                     int colour) {
   typedef TPack<T, VEC> V;
-  const int ncx = nx / ax, ncy = ny / ay;
-  const unsigned total = (unsigned)ncx * ncy * kv;
+  __shared__ V red[RR_SLOTS][DC][KC];
+  const int ncx = nx / ax;
+  const int I = blockIdx.x;
+  const int cc = threadIdx.x, slot = threadIdx.y;
+  const int c = blockIdx.y * KC + cc;
+  const int bi = I % ncx, bj = I / ncx;
   const int m = ax * ay * D;
   const V *X = (const V *)x;
   const V *B = (const V *)b;
-  V *RC = (V *)rc;
-  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int c = (int)(t % (unsigned)kv);
-    const int I = (int)(t / (unsigned)kv);
-    const int bi = I % ncx, bj = I / ncx;
-    T acc[DC][VEC];
+  T acc[DC][VEC];
 #pragma unroll
-    for (int q = 0; q < DC; ++q)
+  for (int q = 0; q < DC; ++q)
 #pragma unroll
-      for (int u = 0; u < VEC; ++u) acc[q][u] = zero<T>();
+    for (int u = 0; u < VEC; ++u) acc[q][u] = zero<T>();
+  if (c < kv) {
     const T *PI = P + (size_t)I * m * DC;
-    for (int loc = 0; loc < ax * ay; ++loc) {
-      const int jj = loc / ax, ii = loc - jj * ax;
+    // with ax and ay even every aggregate row holds ax / 2 sites of each colour: the n-th
+    // colour site is row n / (ax / 2), column 2 (n mod ax / 2) + ((colour + row) mod 2)
+    const bool even = ((ax | ay) & 1) == 0;
+    const int hax = ax >> 1, ncol = even ? hax * ay : ax * ay;
+    for (int n = slot; n < ncol; n += RR_SLOTS) {
+      int ii, jj;
+      if (even) {
+        jj = n / hax;
+        ii = 2 * (n - jj * hax) + ((colour + jj) & 1);
+      } else {
+        jj = n / ax;
+        ii = n - jj * ax;
+      }
+      const int loc = jj * ax + ii;
       const int i = bi * ax + ii, j = bj * ay + jj;
-      if (((i + j) & 1) != colour) continue;          // the residual is zero there
+      if (((i + j) & 1) != colour) continue;            // the residual is zero there
       const int s = j * nx + i;
       int nb[5];
       nb[0] = s;
@@ -348,12 +371,24 @@ __global__ void __launch_bounds__(128) k_residual_restrict(const T *__restrict__
         }
       }
     }
+  }
 #pragma unroll
-    for (int q = 0; q < DC; ++q) {
-      V o;
+  for (int q = 0; q < DC; ++q)
 #pragma unroll
-      for (int u = 0; u < VEC; ++u) o.v[u] = acc[q][u];
-      RC[((size_t)I * DC + q) * kv + c] = o;
+    for (int u = 0; u < VEC; ++u) red[slot][q][cc].v[u] = acc[q][u];
+  __syncthreads();
+  // DC x KC output packs, one per thread, the slots added in order
+  const int tid = slot * KC + cc;
+  if (tid < DC * KC) {
+    const int q = tid / KC, c2 = tid - (tid / KC) * KC;
+    const int co = blockIdx.y * KC + c2;
+    if (co < kv) {
+      V o = red[0][q][c2];
+#pragma unroll
+      for (int sl = 1; sl < RR_SLOTS; ++sl)
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) o.v[u] = o.v[u] + red[sl][q][c2].v[u];
+      ((V *)rc)[((size_t)I * DC + q) * kv + co] = o;
     }
   }
 }
@@ -444,17 +479,22 @@ static void residual_restrict_go(const StencilView &A, const ProlongView &P, con
   constexpr int VW = tr_vec<T>::v;
   const int vec = (VW > 1 && k % VW == 0) ? VW : 1;
   const int kv = k / vec;
-  const size_t items = (size_t)(P.nx / P.ax) * (P.ny / P.ay) * kv;
-  const size_t blocks = (items + 127) / 128;
-  static const int occ_v = blocks_per_sm(k_residual_restrict<T, D, DC, VW>, 128, 0);
-  static const int occ_1 = blocks_per_sm(k_residual_restrict<T, D, DC, 1>, 128, 0);
-  const unsigned g = resident_grid(blocks, vec == VW && VW > 1 ? occ_v : occ_1);
-  if (vec == VW && VW > 1)
-    k_residual_restrict<T, D, DC, VW><<<g, 128, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b,
-                                                        (const T *)P.P, (T *)rc, A.nx, A.ny, P.ax, P.ay, kv, colour);
-  else
-    k_residual_restrict<T, D, DC, 1><<<g, 128, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b,
-                                                       (const T *)P.P, (T *)rc, A.nx, A.ny, P.ax, P.ay, kv, colour);
+  const unsigned aggs = (unsigned)(P.nx / P.ax) * (P.ny / P.ay);
+  // column packs per block: 32, or fewer for narrow blocks
+  auto go = [&](auto vtag, auto ktag) {
+    constexpr int V = decltype(vtag)::value, KC = decltype(ktag)::value;
+    k_residual_restrict<T, D, DC, V, KC><<<dim3(aggs, (kv + KC - 1) / KC), dim3(KC, RR_SLOTS), 0, s>>>(
+        (const T *)A.coef, (const T *)x, (const T *)b, (const T *)P.P, (T *)rc, A.nx, A.ny, P.ax, P.ay, kv, colour);
+  };
+  if (vec == VW && VW > 1) {
+    if (kv >= 32) go(std::integral_constant<int, VW>(), std::integral_constant<int, 32>());
+    else if (kv >= 16) go(std::integral_constant<int, VW>(), std::integral_constant<int, 16>());
+    else go(std::integral_constant<int, VW>(), std::integral_constant<int, 8>());
+  } else {
+    if (kv >= 32) go(std::integral_constant<int, 1>(), std::integral_constant<int, 32>());
+    else if (kv >= 16) go(std::integral_constant<int, 1>(), std::integral_constant<int, 16>());
+    else go(std::integral_constant<int, 1>(), std::integral_constant<int, 8>());
+  }
 }
 
 template <class T, int DC>
