@@ -462,16 +462,6 @@ bool residual_restrict_ok(const StencilView &A, const ProlongView &P) {
   return A.d <= 4 && P.dc <= 4 && A.d == P.d;
 }
 
-// One thread per (aggregate, column group) walks its aggregate's sites in turn, so the
-// fused kernel needs many aggregates to fill the GPU: measured on the 1024^2 hierarchy it
-// beats residual + restriction from 32 K items up (level 1, k = 64: 96 vs ~210 us; level 2,
-// k = 128: 78 vs ~130 us; level 3, k = 512: 31 vs 47 us) and loses below (level 3, k = 128,
-// 8 K items: 29 vs 18 us).
-bool residual_restrict_pays(const ProlongView &P, int k) {
-  const int vw = P.t == F32 ? 4 : P.t == F64 ? 2 : P.t == C32 ? 2 : 1;
-  const int vec = k % vw == 0 ? vw : 1;
-  return (size_t)(P.nx / P.ax) * (P.ny / P.ay) * (k / vec) >= 32768;
-}
 
 template <class T, int D, int DC>
 static void residual_restrict_go(const StencilView &A, const ProlongView &P, const void *x, const void *b, void *rc,

@@ -472,7 +472,7 @@ void cycle(H_t &h, int lo, int l, const void *b, void *x, int k) {
     h.cost += nnz_of(h, l) * k;
   }
   const ProlongView Pv = pview(h, l, lo);
-  if (npre >= 1 && residual_restrict_ok(A, Pv) && residual_restrict_pays(Pv, k)) {
+  if (npre >= 1 && residual_restrict_ok(A, Pv)) {
     // the pre-smoothing sweeps end on colour 1, so the residual lives on colour 0 only:
     // residual and restriction in one pass, r never stored
     launch_residual_restrict(A, Pv, x, b, cn.b.p, k, 0, s);

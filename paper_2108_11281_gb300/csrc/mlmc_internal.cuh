@@ -205,7 +205,6 @@ void launch_prolong_add_colour(const ProlongView &P, const void *ec, void *x, in
 // other colour after a red-black Gauss-Seidel sweep that updated it last); aggregation
 // levels with d, dc <= 4 and the Example 5.1 fine level
 bool residual_restrict_ok(const StencilView &A, const ProlongView &P);
-bool residual_restrict_pays(const ProlongView &P, int k);   // enough aggregates x columns to fill the GPU
 void launch_residual_restrict(const StencilView &A, const ProlongView &P, const void *x, const void *b, void *rc,
                               int k, int colour, cudaStream_t s);
 // out = base + omega * D^{-1} (rhs - y), D = diagonal entries of the self blocks; base/rhs may be null
