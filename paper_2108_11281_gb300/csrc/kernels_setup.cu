@@ -2,6 +2,9 @@
 // modified Gram-Schmidt (P blocks), Galerkin coarse stencils P^* A P, dense
 // Gauss-Jordan inverse and trace of the coarsest operator, and the dense
 // coarsest-level apply used inside every multigrid cycle.
+#include <algorithm>
+
+#include "mlmc.h"
 #include "mlmc_internal.cuh"
 
 namespace mlmc {
@@ -202,9 +205,26 @@ void launch_galerkin(const StencilView &fine, const ProlongView &P, void *coarse
 }
 
 // ------------------------------------------------------------------ dense Gauss-Jordan inverse
-// work = [A | I] (n x 2n, row-major).  Per pivot column p: pick the largest
-// |entry| in rows >= p, swap it to row p, scale row p, save column p, then
-// eliminate column p from every other row.
+// Both kernels run the elimination in one cooperative launch (every block resident);
+// block b owns rows [b R, (b + 1) R).  Rows are never swapped: at step q the pivot is the
+// unused row with the largest |M[r][q]| (ties: the smaller r); after each step every
+// block publishes its best candidate for the next column and a grid barrier (an atomic
+// counter) separates the steps.  Every barrier wait is bounded (about a second): on
+// timeout the block records MLMC_ERR_TIMEOUT and returns, and the others time out at their
+// next wait.  Data written by other blocks is read through L2 (__ldcg).
+//
+// k_gj_inplace (the coarsest operators of the hierarchies: own rows fit in shared memory):
+// in-place Gauss-Jordan on M = A (n x n).  Step q with pivot row p, a = M[p][q]: every
+// other row i takes g = M[i][q] / a, M[i][c] -= g M[p][c] (c != q), M[i][q] = -g; row p is
+// scaled (M[p][c] /= a, M[p][q] = 1 / a) by its owner at the start of the next step, so
+// during a step all blocks read the unchanged pivot row while each writes only its own
+// rows (kept in shared memory, written through to M).  At the end M[piv_q][pos(c)] =
+// A^-1[q][c] with pos(piv_q) = q (k_gj_extract_inplace).
+//
+// k_gj_coop (larger n): the same pivoting on work = [A | I] (n x 2n) in global memory,
+// rows never scaled: every other row takes work[r][c] -= (work[r][q] / work[piv][q])
+// work[piv][c] for c > q; row piv_q ends as work[piv_q][q] x [e_q | row q of A^-1]
+// (k_gj_extract).
 template <class T>
 __global__ void k_gj_init(const T *A, T *work, int n) {
   size_t total = (size_t)n * 2 * n;
@@ -214,75 +234,322 @@ __global__ void k_gj_init(const T *A, T *work, int n) {
   }
 }
 
-template <class T>
-__global__ void k_gj_pivot(T *work, int n, int p, int *err, T *col) {
-  __shared__ double best[256];
-  __shared__ int where[256];
-  double b = -1.0;
-  int w = p;
-  for (int r = p + threadIdx.x; r < n; r += blockDim.x) {
-    double m = mag(work[(size_t)r * 2 * n + p]);
-    if (m > b) { b = m; w = r; }
-  }
-  best[threadIdx.x] = b;
-  where[threadIdx.x] = w;
+constexpr int GJ_THREADS = 256;
+constexpr int GJ_MAX_ROWS = 64;                 // rows per block (n <= 64 x blocks)
+constexpr long long GJ_WAIT_CYCLES = 2000000000LL;
+
+__device__ inline double ldcg_d(const double *p) { return __ldcg(p); }
+__device__ inline cdouble ldcg_d(const cdouble *p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+  return {v.x, v.y};
+}
+__device__ inline float ldcg_d(const float *p) { return __ldcg(p); }
+__device__ inline cfloat ldcg_d(const cfloat *p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+  return {v.x, v.y};
+}
+
+// largest (mag, smaller row on ties) over the block; returns it in every thread
+__device__ inline void gj_block_best(double &m, int &r, double *sm, int *sr) {
+  sm[threadIdx.x] = m;
+  sr[threadIdx.x] = r;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+  for (int o = GJ_THREADS / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
-      if (best[threadIdx.x + o] > best[threadIdx.x] ||
-          (best[threadIdx.x + o] == best[threadIdx.x] && where[threadIdx.x + o] < where[threadIdx.x])) {
-        best[threadIdx.x] = best[threadIdx.x + o];
-        where[threadIdx.x] = where[threadIdx.x + o];
+      const double m2 = sm[threadIdx.x + o];
+      const int r2 = sr[threadIdx.x + o];
+      if (m2 > sm[threadIdx.x] || (m2 == sm[threadIdx.x] && r2 < sr[threadIdx.x])) {
+        sm[threadIdx.x] = m2;
+        sr[threadIdx.x] = r2;
       }
     }
     __syncthreads();
   }
-  int piv = where[0];
-  if (best[0] <= 0.0) { if (threadIdx.x == 0) atomicExch(err, 3); return; }
-  // swap rows p and piv, then scale row p by 1 / pivot
-  T pv = work[(size_t)piv * 2 * n + p];
+  m = sm[0];
+  r = sr[0];
   __syncthreads();
-  for (int c = threadIdx.x; c < 2 * n; c += blockDim.x) {
-    T a = work[(size_t)p * 2 * n + c], bb = work[(size_t)piv * 2 * n + c];
-    work[(size_t)piv * 2 * n + c] = a;
-    work[(size_t)p * 2 * n + c] = divide(bb, pv);
+}
+
+// bounded grid barrier number `round` (1, 2, ...): false when the wait gave up
+__device__ inline bool gj_grid_barrier(unsigned *bar, unsigned round, long long wait_cycles, int *err, int *fail_sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    const unsigned target = round * gridDim.x;
+    const long long t0 = clock64();
+    unsigned seen = 0;
+    int failed = 0;
+    for (unsigned it = 0;; ++it) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(bar) : "memory");
+      if (seen >= target) break;
+      if (clock64() - t0 > wait_cycles) {
+        failed = 1;
+        atomicExch(err, (int)MLMC_ERR_TIMEOUT);
+        break;
+      }
+      if (it > 32) __nanosleep(32);
+    }
+    *fail_sh = failed;
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < n; r += blockDim.x) col[r] = work[(size_t)r * 2 * n + p];
+  return *fail_sh == 0;
 }
 
 template <class T>
-__global__ void k_gj_eliminate(T *work, int n, int p, const T *col) {
-  size_t width = (size_t)2 * n - p;
-  size_t total = (size_t)n * width;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    int r = (int)(t / width);
-    int c = p + (int)(t % width);
-    if (r == p) continue;
-    T f = col[r];
-    work[(size_t)r * 2 * n + c] = work[(size_t)r * 2 * n + c] - f * work[(size_t)p * 2 * n + c];
+__global__ void __launch_bounds__(GJ_THREADS) k_gj_coop(T *work, int n, int rows, int *pivrow, int *used,
+                                                      double *cand_mag, int *cand_row, unsigned *bar, int *err,
+                                                      long long wait_cycles) {
+  __shared__ double sm[GJ_THREADS];
+  __shared__ int sr[GJ_THREADS];
+  __shared__ T fr[GJ_MAX_ROWS];
+  __shared__ int fail_sh;
+  const int tid = threadIdx.x, G = gridDim.x;
+  const int r0 = blockIdx.x * rows, r1 = min(n, r0 + rows);
+  const size_t ld = (size_t)2 * n;
+  unsigned round = 0;
+  // candidates for column 0
+  {
+    double m = -1.0;
+    int r = n;
+    for (int rr = r0 + tid; rr < r1; rr += GJ_THREADS) {
+      const double v = mag(ldcg_d(work + (size_t)rr * ld));
+      if (v > m || (v == m && rr < r)) { m = v; r = rr; }
+    }
+    gj_block_best(m, r, sm, sr);
+    if (tid == 0) { cand_mag[blockIdx.x] = m; cand_row[blockIdx.x] = r; }
+    if (!gj_grid_barrier(bar, ++round, wait_cycles, err, &fail_sh)) return;
+  }
+  for (int q = 0; q < n; ++q) {
+    const int par = q & 1;
+    // the pivot: best of the blocks' candidates
+    double m = -1.0;
+    int piv = n;
+    for (int b = tid; b < G; b += GJ_THREADS) {
+      const double v = __ldcg(cand_mag + par * G + b);
+      const int r = __ldcg(cand_row + par * G + b);
+      if (v > m || (v == m && r < piv)) { m = v; piv = r; }
+    }
+    gj_block_best(m, piv, sm, sr);
+    if (!(m > 0.0) || piv >= n) {
+      if (blockIdx.x == 0 && tid == 0) atomicExch(err, 3);
+      return;
+    }
+    if (blockIdx.x == 0 && tid == 0) pivrow[q] = piv;
+    if (piv >= r0 && piv < r1 && tid == 0) used[piv] = 1;
+    const T pv = ldcg_d(work + (size_t)piv * ld + q);
+    // factors of the own rows (zero for the pivot row)
+    for (int rr = r0 + tid; rr < r1; rr += GJ_THREADS)
+      fr[rr - r0] = rr == piv ? zero<T>() : divide(ldcg_d(work + (size_t)rr * ld + q), pv);
+    __syncthreads();
+    for (int c = q + 1 + tid; c < 2 * n; c += GJ_THREADS) {
+      const T pc = ldcg_d(work + (size_t)piv * ld + c);
+      for (int rr = r0; rr < r1; ++rr) {
+        if (rr == piv) continue;
+        T *w = work + (size_t)rr * ld + c;
+        *w = *w - fr[rr - r0] * pc;
+      }
+    }
+    if (q + 1 == n) break;
+    __syncthreads();
+    // own candidate for column q + 1 (unused rows)
+    m = -1.0;
+    int cr = n;
+    for (int rr = r0 + tid; rr < r1; rr += GJ_THREADS) {
+      if (rr == piv || used[rr]) continue;
+      const double v = mag(ldcg_d(work + (size_t)rr * ld + q + 1));
+      if (v > m || (v == m && rr < cr)) { m = v; cr = rr; }
+    }
+    gj_block_best(m, cr, sm, sr);
+    if (tid == 0) { cand_mag[(1 - par) * G + blockIdx.x] = m; cand_row[(1 - par) * G + blockIdx.x] = cr; }
+    if (!gj_grid_barrier(bar, ++round, wait_cycles, err, &fail_sh)) return;
   }
 }
 
 template <class T>
-__global__ void k_gj_extract(const T *work, T *Ainv, int n) {
+__global__ void __launch_bounds__(GJ_THREADS) k_gj_inplace(const T *A, T *M, int n, int rows, int *pivrow,
+                                                         double *cand_mag, int *cand_row, unsigned *bar, int *err,
+                                                         long long wait_cycles) {
+  extern __shared__ __align__(16) unsigned char gj_smem[];
+  T *Ms = reinterpret_cast<T *>(gj_smem);          // own rows, rows x n
+  __shared__ double sm[GJ_THREADS];
+  __shared__ int sr[GJ_THREADS];
+  __shared__ T fr[GJ_MAX_ROWS];
+  __shared__ unsigned char used[GJ_MAX_ROWS];
+  __shared__ int fail_sh;
+  const int tid = threadIdx.x, G = gridDim.x;
+  const int r0 = blockIdx.x * rows, nr = max(0, min(n, r0 + rows) - r0);
+  for (int e = tid; e < nr * n; e += GJ_THREADS) {
+    const T v = A[(size_t)r0 * n + e];
+    Ms[e] = v;
+    M[(size_t)r0 * n + e] = v;
+  }
+  for (int i = tid; i < GJ_MAX_ROWS; i += GJ_THREADS) used[i] = 0;
+  __syncthreads();
+  unsigned round = 0;
+  {
+    double m = -1.0;
+    int r = n;
+    for (int i = tid; i < nr; i += GJ_THREADS) {
+      const double v = mag(Ms[(size_t)i * n]);
+      if (v > m || (v == m && r0 + i < r)) { m = v; r = r0 + i; }
+    }
+    gj_block_best(m, r, sm, sr);
+    if (tid == 0) { cand_mag[blockIdx.x] = m; cand_row[blockIdx.x] = r; }
+    if (!gj_grid_barrier(bar, ++round, wait_cycles, err, &fail_sh)) return;
+  }
+  int prev = -1;
+  for (int q = 0; q < n; ++q) {
+    const int par = q & 1;
+    double m = -1.0;
+    int p = n;
+    for (int b = tid; b < G; b += GJ_THREADS) {
+      const double v = __ldcg(cand_mag + par * G + b);
+      const int r = __ldcg(cand_row + par * G + b);
+      if (v > m || (v == m && r < p)) { m = v; p = r; }
+    }
+    gj_block_best(m, p, sm, sr);
+    if (!(m > 0.0) || p >= n) {
+      if (blockIdx.x == 0 && tid == 0) atomicExch(err, 3);
+      return;
+    }
+    if (blockIdx.x == 0 && tid == 0) pivrow[q] = p;
+    // the previous pivot row, if it is ours: its deferred scaling
+    if (prev >= r0 && prev < r0 + nr) {
+      T *row = Ms + (size_t)(prev - r0) * n;
+      const T a = row[q - 1];
+      __syncthreads();
+      for (int c = tid; c < n; c += GJ_THREADS) row[c] = c == q - 1 ? divide(make<T>(1.0, 0.0), a) : divide(row[c], a);
+      __syncthreads();
+    }
+    if (p >= r0 && p < r0 + nr && tid == 0) used[p - r0] = 1;
+    const T a = ldcg_d(M + (size_t)p * n + q);
+    for (int i = tid; i < nr; i += GJ_THREADS)
+      fr[i] = r0 + i == p ? zero<T>() : divide(Ms[(size_t)i * n + q], a);
+    __syncthreads();
+    for (int c = tid; c < n; c += GJ_THREADS) {
+      const T pc = ldcg_d(M + (size_t)p * n + c);
+      for (int i = 0; i < nr; ++i) {
+        if (r0 + i == p) continue;
+        const T v = c == q ? zero<T>() - fr[i] : Ms[(size_t)i * n + c] - fr[i] * pc;
+        Ms[(size_t)i * n + c] = v;
+        M[(size_t)(r0 + i) * n + c] = v;
+      }
+    }
+    prev = p;
+    if (q + 1 == n) break;
+    __syncthreads();
+    m = -1.0;
+    int cr = n;
+    for (int i = tid; i < nr; i += GJ_THREADS) {
+      if (used[i]) continue;
+      const double v = mag(Ms[(size_t)i * n + q + 1]);
+      if (v > m || (v == m && r0 + i < cr)) { m = v; cr = r0 + i; }
+    }
+    gj_block_best(m, cr, sm, sr);
+    if (tid == 0) { cand_mag[(1 - par) * G + blockIdx.x] = m; cand_row[(1 - par) * G + blockIdx.x] = cr; }
+    if (!gj_grid_barrier(bar, ++round, wait_cycles, err, &fail_sh)) return;
+  }
+  // the last pivot row's scaling, once every block has read that row in the last step
+  if (!gj_grid_barrier(bar, ++round, wait_cycles, err, &fail_sh)) return;
+  if (prev >= r0 && prev < r0 + nr) {
+    T *row = Ms + (size_t)(prev - r0) * n;
+    const T a = row[n - 1];
+    __syncthreads();
+    for (int c = tid; c < n; c += GJ_THREADS) {
+      const T v = c == n - 1 ? divide(make<T>(1.0, 0.0), a) : divide(row[c], a);
+      M[(size_t)prev * n + c] = v;
+    }
+  }
+}
+
+// A^-1[q][c] = M[piv_q][pos(c)], pos(piv_j) = j
+template <class T>
+__global__ void k_gj_extract_inplace(const T *M, const int *pivrow, T *Ainv, int n) {
   size_t total = (size_t)n * n;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    int r = (int)(t / n), c = (int)(t % n);
-    Ainv[t] = work[(size_t)r * 2 * n + n + c];
+    const int q = (int)(t / n), j = (int)(t % n);
+    Ainv[(size_t)q * n + pivrow[j]] = M[(size_t)pivrow[q] * n + j];
   }
 }
 
-void launch_gauss_jordan(DType t, const void *A, void *Ainv, void *work, int n, int *err, void *colbuf,
-                         cudaStream_t s) {
+template <class T>
+__global__ void k_gj_extract(const T *work, const int *pivrow, T *Ainv, int n) {
+  size_t total = (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t / n), c = (int)(t % n);
+    const int pr = pivrow[q];
+    Ainv[t] = divide(work[(size_t)pr * 2 * n + n + c], work[(size_t)pr * 2 * n + q]);
+  }
+}
+
+namespace {
+struct GjScratch {
+  size_t pivrow, used, cmag, crow, bar, total;
+};
+GjScratch gj_layout(int n, int G) {
+  GjScratch L{};
+  size_t o = 0;
+  auto take = [&o](size_t bytes) { size_t at = o; o = (o + bytes + 255) / 256 * 256; return at; };
+  L.pivrow = take((size_t)n * 4);
+  L.used = take((size_t)n * 4);
+  L.cmag = take((size_t)2 * G * 8);
+  L.crow = take((size_t)2 * G * 4);
+  L.bar = take(16);
+  L.total = o;
+  return L;
+}
+int gj_blocks(int n) {
+  int dev = 0, sms = 0;
+  MLMC_CUDA(cudaGetDevice(&dev));
+  MLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int G = std::min(sms, n);
+  while ((n + G - 1) / G > GJ_MAX_ROWS) G *= 2;     // more blocks than SMs only for n > 64 x SMs
+  return std::max(G, 1);
+}
+}  // namespace
+
+size_t gauss_jordan_scratch_bytes(int n) { return gj_layout(n, gj_blocks(n)).total; }
+
+constexpr size_t GJ_SMEM_MAX = 200 * 1024;      // own rows of k_gj_inplace in shared memory
+
+void launch_gauss_jordan(DType t, const void *A, void *Ainv, void *work, int n, int *err, void *scratch,
+                         size_t scratch_bytes, cudaStream_t s) {
+  const int G = gj_blocks(n);
+  const GjScratch L = gj_layout(n, G);
+  if (scratch_bytes < L.total) throw cuda_error{cudaErrorInvalidValue, "gauss_jordan: scratch too small"};
+  int dev = 0, sms = 0;
+  MLMC_CUDA(cudaGetDevice(&dev));
+  MLMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  char *sc = (char *)scratch;
+  MLMC_CUDA(cudaMemsetAsync(sc, 0, L.total, s));
+  int *pivrow = (int *)(sc + L.pivrow), *used = (int *)(sc + L.used), *crow = (int *)(sc + L.crow);
+  double *cmag = (double *)(sc + L.cmag);
+  unsigned *bar = (unsigned *)(sc + L.bar);
+  long long wait = GJ_WAIT_CYCLES;
+  int rows = (n + G - 1) / G;
   MLMC_DISPATCH(t, T, {
-    unsigned g = grid_for((size_t)n * 2 * n, 256);
-    k_gj_init<T><<<g, 256, 0, s>>>((const T *)A, (T *)work, n);
-    for (int p = 0; p < n; ++p) {
-      k_gj_pivot<T><<<1, 256, 0, s>>>((T *)work, n, p, err, (T *)colbuf);
-      k_gj_eliminate<T><<<g, 256, 0, s>>>((T *)work, n, p, (const T *)colbuf);
+    const unsigned g = grid_for((size_t)n * n, 256);
+    T *wk = (T *)work;
+    const size_t smem = (size_t)rows * n * sizeof(T);
+    int per_sm = 0;
+    if (smem <= GJ_SMEM_MAX) {
+      MLMC_CUDA(cudaFuncSetAttribute(k_gj_inplace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MLMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_inplace<T>, GJ_THREADS, smem));
+      if ((long long)per_sm * sms < G) throw cuda_error{cudaErrorInvalidValue, "gauss_jordan: blocks cannot be resident"};
+      const T *a = (const T *)A;
+      void *args[] = {&a, &wk, &n, &rows, &pivrow, &cmag, &crow, &bar, &err, &wait};
+      MLMC_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_inplace<T>, dim3(G), dim3(GJ_THREADS), args, smem, s));
+      k_gj_extract_inplace<T><<<g, 256, 0, s>>>((const T *)work, pivrow, (T *)Ainv, n);
+    } else {
+      MLMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_coop<T>, GJ_THREADS, 0));
+      if ((long long)per_sm * sms < G) throw cuda_error{cudaErrorInvalidValue, "gauss_jordan: blocks cannot be resident"};
+      const unsigned g2 = grid_for((size_t)n * 2 * n, 256);
+      k_gj_init<T><<<g2, 256, 0, s>>>((const T *)A, wk, n);
+      void *args[] = {&wk, &n, &rows, &pivrow, &used, &cmag, &crow, &bar, &err, &wait};
+      MLMC_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_coop<T>, dim3(G), dim3(GJ_THREADS), args, 0, s));
+      k_gj_extract<T><<<g, 256, 0, s>>>((const T *)work, pivrow, (T *)Ainv, n);
     }
-    k_gj_extract<T><<<g, 256, 0, s>>>((const T *)work, (T *)Ainv, n);
   });
   MLMC_LAUNCH_CHECK("gauss_jordan");
 }

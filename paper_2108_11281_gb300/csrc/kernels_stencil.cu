@@ -337,6 +337,56 @@ static int laplace_vec(int k) {
   return k % v == 0 ? v : 1;
 }
 
+// One damped-Jacobi sweep of the setup filter for Example 5.1 in one pass:
+// out = x - omega D^-1 (A x) with A x = diag x - (sum of the in-grid neighbours), the
+// same arithmetic as the apply followed by the update (out must not alias x).
+template <class T, int VEC>
+__global__ void __launch_bounds__(256) k_laplace_jacobi(const T *__restrict__ x, T *__restrict__ out, int nx, int ny,
+                                                        int kv, T diag, T scale, int periodic) {
+  typedef Pack<T, VEC> V;
+  const int j = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nx * kv) return;
+  const int i = t / kv, c = t - (t / kv) * kv;
+  const V *X = (const V *)x;
+  const int s = j * nx + i;
+  const Nbrs n = laplace_nbrs(i, j, nx, ny, periodic);
+  const V xc = X[(size_t)s * kv + c];
+  T sum[VEC];
+  laplace_nbr_sum<T, VEC>(X, n, kv, c, sum);
+  V o;
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) {
+    const T y = diag * xc.v[u] - sum[u];
+    const T q = scale * (diag * (-y));
+    o.v[u] = xc.v[u] + q;
+  }
+  ((V *)out)[(size_t)s * kv + c] = o;
+}
+
+void launch_laplace_jacobi(const StencilView &A, const void *x, void *out, int k, double omega, cudaStream_t s) {
+  if (!A.const_laplace) throw cuda_error{cudaErrorInvalidValue, "laplace_jacobi: constant-coefficient Laplacian only"};
+  auto go = [&](auto tag, auto vtag) {
+    typedef decltype(tag) T;
+    constexpr int VEC = decltype(vtag)::value;
+    const int kv = k / VEC;
+    const T diag = (T)A.diag;
+    const T scale = (T)(omega / ((double)diag * (double)diag));
+    dim3 g((A.nx * kv + 255) / 256, A.ny);
+    k_laplace_jacobi<T, VEC><<<g, 256, 0, s>>>((const T *)x, (T *)out, A.nx, A.ny, kv, diag, scale, A.periodic);
+  };
+  if (A.t == F64) {
+    if (laplace_vec<double>(k) == 2) go(double(), std::integral_constant<int, 2>());
+    else go(double(), std::integral_constant<int, 1>());
+  } else if (A.t == F32) {
+    if (laplace_vec<float>(k) == 4) go(float(), std::integral_constant<int, 4>());
+    else go(float(), std::integral_constant<int, 1>());
+  } else {
+    throw cuda_error{cudaErrorInvalidValue, "constant-coefficient Laplacian is real"};
+  }
+  MLMC_LAUNCH_CHECK("k_laplace_jacobi");
+}
+
 static void launch_laplace(const StencilView &A, const void *x, const void *b, void *y, int k, int mode,
                            cudaStream_t s) {
   auto go = [&](auto tag, auto vtag) {

@@ -842,6 +842,19 @@ void fine_hooks(H_t &h, void *x, const void *b, int k) {
 // ----------------------------------------------------------------- setup
 void filter(H_t &h, int l, void *V, void *tmp, void *tmp2, int ntv, int kind, int sweeps, double omega) {
   StencilView A = view(h, l, 0);
+  if (kind == MLMC_SETUP_SMOOTH && A.const_laplace) {
+    // Example 5.1: apply and update in one pass, alternating between V and tmp
+    void *src = V, *dst = tmp;
+    for (int it = 0; it < sweeps; ++it) {
+      launch_laplace_jacobi(A, src, dst, ntv, omega, h.stream);
+      h.launches++;
+      std::swap(src, dst);
+    }
+    if (src != V)
+      check_cuda(cudaMemcpyAsync(V, src, h.lv[l].n * (size_t)ntv * dtype_size(h.t64), cudaMemcpyDeviceToDevice,
+                                 h.stream), "copy filtered V");
+    return;
+  }
   for (int it = 0; it < sweeps; ++it) {
     if (kind == MLMC_SETUP_SMOOTH) {
       apply_op(h, l, 0, V, tmp, ntv);
@@ -860,7 +873,7 @@ void check_err(H_t &h, const char *what) {
   int e = 0;
   check_cuda(cudaMemcpyAsync(&e, h.err.p, sizeof(int), cudaMemcpyDeviceToHost, h.stream), "D2H err");
   check_cuda(cudaStreamSynchronize(h.stream), "sync");
-  if (e == MLMC_ERR_TIMEOUT) fail(MLMC_ERR_TIMEOUT, std::string(what) + ": a bounded tensor-core wait gave up");
+  if (e == MLMC_ERR_TIMEOUT) fail(MLMC_ERR_TIMEOUT, std::string(what) + ": a bounded wait gave up");
   if (e) fail(MLMC_ERR_SINGULAR, std::string(what) + ": singular block or dependent test vectors (code " +
                                       std::to_string(e) + ")");
 }
@@ -920,10 +933,11 @@ void build_levels(H_t &h, const void *V1, const void *const *user_P) {
     DevBuf dense, work, col;
     dense.alloc(C.n * C.n * es);
     work.alloc(C.n * 2 * C.n * es);
-    col.alloc(C.n * es);
+    const size_t gjb = gauss_jordan_scratch_bytes((int)C.n);
+    col.alloc(gjb);
     launch_stencil_to_dense(view(h, h.L - 1, 0), dense.p, h.stream);
-    launch_gauss_jordan(h.t64, dense.p, C.Ainv64.p, work.p, (int)C.n, h.err.as<int>(), col.p, h.stream);
-    h.launches += 5 + 2 * C.n + 2;
+    launch_gauss_jordan(h.t64, dense.p, C.Ainv64.p, work.p, (int)C.n, h.err.as<int>(), col.p, gjb, h.stream);
+    h.launches += 5 + 3;
     check_err(h, "coarsest inverse");
   }
   if (h.prm.precision == MLMC_PREC_MIXED_FP32) {
@@ -1042,10 +1056,11 @@ void build_bilinear(H_t &h, const mlmc_operator_desc *op) {
     DevBuf dd, work, col;
     dd.alloc(dense.size() * es);
     work.alloc((size_t)n * 2 * n * es);
-    col.alloc((size_t)n * es);
+    const size_t gjb = gauss_jordan_scratch_bytes(n);
+    col.alloc(gjb);
     check_cuda(cudaMemcpyAsync(dd.p, dense.data(), dense.size() * es, cudaMemcpyHostToDevice, h.stream), "H2D dense");
-    launch_gauss_jordan(h.t64, dd.p, C.Ainv64.p, work.p, n, h.err.as<int>(), col.p, h.stream);
-    h.launches += 5 + 2 * n + 2;
+    launch_gauss_jordan(h.t64, dd.p, C.Ainv64.p, work.p, n, h.err.as<int>(), col.p, gjb, h.stream);
+    h.launches += 3;
     check_err(h, "coarsest inverse");
     std::vector<double> Ainv((size_t)n * n);
     check_cuda(cudaMemcpyAsync(Ainv.data(), C.Ainv64.p, Ainv.size() * es, cudaMemcpyDeviceToHost, h.stream), "D2H Ainv");

@@ -208,6 +208,8 @@ bool residual_restrict_ok(const StencilView &A, const ProlongView &P);
 void launch_residual_restrict(const StencilView &A, const ProlongView &P, const void *x, const void *b, void *rc,
                               int k, int colour, cudaStream_t s);
 // out = base + omega * D^{-1} (rhs - y), D = diagonal entries of the self blocks; base/rhs may be null
+// one damped-Jacobi sweep out = x - omega D^-1 A x of the constant-coefficient Laplacian
+void launch_laplace_jacobi(const StencilView &A, const void *x, void *out, int k, double omega, cudaStream_t s);
 void launch_jacobi_update(const StencilView &A, void *out, const void *base, const void *rhs,
                           const void *y, double omega, int k, cudaStream_t s);
 // bilinear hierarchy of Example 5.1 (kernels_bilinear.cu), real data, d = 1
@@ -224,9 +226,12 @@ void launch_block_inverse(DType t, const void *coef, void *dinv, int nsite, int 
 void launch_mgs(DType t, const void *V, void *P, int nx, int ny, int d, int ax, int ay, int ntv,
                 int spin_split, int *err, cudaStream_t s);
 void launch_galerkin(const StencilView &fine, const ProlongView &P, void *coarse_coef, cudaStream_t s);
-// dense inverse of an n x n matrix (row-major), work = n x 2n
-void launch_gauss_jordan(DType t, const void *A, void *Ainv, void *work, int n, int *err,
-                         void *colbuf, cudaStream_t s);
+// dense inverse of an n x n matrix (row-major), work = n x 2n elements, scratch of
+// gauss_jordan_scratch_bytes(n) bytes; *err = 3 for a singular matrix, MLMC_ERR_TIMEOUT
+// when a bounded grid-barrier wait gave up
+size_t gauss_jordan_scratch_bytes(int n);
+void launch_gauss_jordan(DType t, const void *A, void *Ainv, void *work, int n, int *err, void *scratch,
+                         size_t scratch_bytes, cudaStream_t s);
 void launch_trace(DType t, const void *A, int n, void *out /* FP64 (complex) */, cudaStream_t s);
 // Y = Ainv * B  (n x n times n x k, row-major / [row][k])
 // part: scratch of dense_apply_splits(n, k) * n * k elements (or null: no split of j)

@@ -105,6 +105,41 @@ def test_wilson_apply(mlmc):
     h.close()
 
 
+@pytest.mark.parametrize("case", ["laplace-n64", "laplace-n1024", "laplace-n4096", "wilson-n64"])
+def test_coarsest_inverse(mlmc, case):
+    """The dense Gauss-Jordan inverse of the coarsest operator (Remark 4.2's exact term and
+    the coarsest solves): its trace against numpy's inverse of the GPU's own coarsest
+    stencil, and FP64 coarsest-level solves A_L x = b against the residual.  n_L = 64 and
+    1024 run the in-place kernel with the rows in shared memory (1 and 7 rows per block),
+    n_L = 4096 (27 rows per block, 884 KB) the kernel on [A | I] in global memory."""
+    if case.startswith("laplace"):
+        N = {"laplace-n64": 16, "laplace-n1024": 64, "laplace-n4096": 128}[case]
+        h = laplace_h(mlmc, N, 2, n_tv=4, setup_sweeps=4, bootstrap=0)
+    else:
+        N = 16
+        U = gauge_links(N, N, 0.3, 5)
+        prm = mlmc.default_params(levels=2, n_tv=2, spin_split=1, setup_kind=mlmc.SETUP_INVERSE, setup_sweeps=4,
+                                  setup_omega=1.0, block=8, bootstrap=0)
+        h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.1, links=U)
+    nx, ny, d = h.level_info(2)
+    A2 = block_from_stencil(h.operator(2), nx, ny).toarray()
+    n = A2.shape[0]
+    assert n == int(case.split("-n")[1])
+    inv = np.linalg.inv(A2)
+    tr = h.coarse_trace_exact()
+    assert abs(tr - np.trace(inv)) <= 1e-11 * abs(np.trace(inv))
+    k = 5
+    g = torch.Generator().manual_seed(11)
+    dt = torch.complex128 if h.complex else torch.float64
+    b = torch.randn(n, k, generator=g, dtype=torch.float64).to(dt).cuda()
+    x = torch.zeros_like(b)
+    h.solve(2, b.data_ptr(), x.data_ptr(), k, 1e-12)
+    xn, bn = x.cpu().numpy(), b.cpu().numpy()
+    assert np.abs(A2 @ xn - bn).max() <= 1e-10 * np.abs(bn).max() * np.abs(A2).max() * np.abs(inv).max()
+    assert np.abs(xn - inv @ bn).max() <= 1e-10 * np.abs(inv @ bn).max()
+    h.close()
+
+
 def projector_distance(Pa, Pb):
     """max over aggregates of || Pa Pa^* - Pb Pb^* ||: independent of the basis inside each aggregate."""
     return max(np.abs(a @ a.conj().T - b @ b.conj().T).max() for a, b in zip(Pa, Pb))
