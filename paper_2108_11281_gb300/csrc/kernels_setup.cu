@@ -236,6 +236,7 @@ __global__ void k_gj_init(const T *A, T *work, int n) {
 
 constexpr int GJ_THREADS = 256;
 constexpr int GJ_MAX_ROWS = 64;                 // rows per block (n <= 64 x blocks)
+constexpr int GJ_COLS = 16;                     // k_gj_inplace: columns per thread (n <= 4096)
 constexpr long long GJ_WAIT_CYCLES = 2000000000LL;
 
 __device__ inline double ldcg_d(const double *p) { return __ldcg(p); }
@@ -274,8 +275,9 @@ __device__ inline void gj_block_best(double &m, int &r, double *sm, int *sr) {
 __device__ inline bool gj_grid_barrier(unsigned *bar, unsigned round, long long wait_cycles, int *err, int *fail_sh) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1u);
+    // release: the block's writes (ordered before this thread by the barrier above) are
+    // visible to whoever acquires the count
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     const unsigned target = round * gridDim.x;
     const long long t0 = clock64();
     unsigned seen = 0;
@@ -417,21 +419,29 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_inplace(const T *A, T *M, int
     // the previous pivot row, if it is ours: its deferred scaling
     if (prev >= r0 && prev < r0 + nr) {
       T *row = Ms + (size_t)(prev - r0) * n;
-      const T a = row[q - 1];
+      const T ra = divide(make<T>(1.0, 0.0), row[q - 1]);     // one FP64 division per row
       __syncthreads();
-      for (int c = tid; c < n; c += GJ_THREADS) row[c] = c == q - 1 ? divide(make<T>(1.0, 0.0), a) : divide(row[c], a);
+      for (int c = tid; c < n; c += GJ_THREADS) row[c] = c == q - 1 ? ra : row[c] * ra;
       __syncthreads();
     }
     if (p >= r0 && p < r0 + nr && tid == 0) used[p - r0] = 1;
-    const T a = ldcg_d(M + (size_t)p * n + q);
-    for (int i = tid; i < nr; i += GJ_THREADS)
-      fr[i] = r0 + i == p ? zero<T>() : divide(Ms[(size_t)i * n + q], a);
+    // the pivot row: this thread's columns and the pivot, loaded together (one L2 latency)
+    T pcs[GJ_COLS];
+#pragma unroll
+    for (int u = 0; u < GJ_COLS; ++u) {
+      const int c = tid + u * GJ_THREADS;
+      pcs[u] = c < n ? ldcg_d(M + (size_t)p * n + c) : zero<T>();
+    }
+    const T ra = divide(make<T>(1.0, 0.0), ldcg_d(M + (size_t)p * n + q));
+    for (int i = tid; i < nr; i += GJ_THREADS) fr[i] = r0 + i == p ? zero<T>() : Ms[(size_t)i * n + q] * ra;
     __syncthreads();
-    for (int c = tid; c < n; c += GJ_THREADS) {
-      const T pc = ldcg_d(M + (size_t)p * n + c);
+#pragma unroll
+    for (int u = 0; u < GJ_COLS; ++u) {
+      const int c = tid + u * GJ_THREADS;
+      if (c >= n) break;
       for (int i = 0; i < nr; ++i) {
         if (r0 + i == p) continue;
-        const T v = c == q ? zero<T>() - fr[i] : Ms[(size_t)i * n + c] - fr[i] * pc;
+        const T v = c == q ? zero<T>() - fr[i] : Ms[(size_t)i * n + c] - fr[i] * pcs[u];
         Ms[(size_t)i * n + c] = v;
         M[(size_t)(r0 + i) * n + c] = v;
       }
@@ -454,12 +464,9 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_inplace(const T *A, T *M, int
   if (!gj_grid_barrier(bar, ++round, wait_cycles, err, &fail_sh)) return;
   if (prev >= r0 && prev < r0 + nr) {
     T *row = Ms + (size_t)(prev - r0) * n;
-    const T a = row[n - 1];
+    const T ra = divide(make<T>(1.0, 0.0), row[n - 1]);
     __syncthreads();
-    for (int c = tid; c < n; c += GJ_THREADS) {
-      const T v = c == n - 1 ? divide(make<T>(1.0, 0.0), a) : divide(row[c], a);
-      M[(size_t)prev * n + c] = v;
-    }
+    for (int c = tid; c < n; c += GJ_THREADS) M[(size_t)prev * n + c] = c == n - 1 ? ra : row[c] * ra;
   }
 }
 
@@ -533,7 +540,7 @@ void launch_gauss_jordan(DType t, const void *A, void *Ainv, void *work, int n, 
     T *wk = (T *)work;
     const size_t smem = (size_t)rows * n * sizeof(T);
     int per_sm = 0;
-    if (smem <= GJ_SMEM_MAX) {
+    if (smem <= GJ_SMEM_MAX && n <= GJ_COLS * GJ_THREADS) {
       MLMC_CUDA(cudaFuncSetAttribute(k_gj_inplace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       MLMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_inplace<T>, GJ_THREADS, smem));
       if ((long long)per_sm * sms < G) throw cuda_error{cudaErrorInvalidValue, "gauss_jordan: blocks cannot be resident"};
@@ -625,6 +632,52 @@ __global__ void __launch_bounds__(128) k_dense_apply(const T *__restrict__ A, co
     }
 }
 
+// Narrow blocks (k <= 8, e.g. the test vectors of the setup's bootstrap cycles): one warp
+// per row of Ainv, the lanes take j = lane, lane + 32, ... for all k columns, then a
+// fixed shuffle tree per column (deterministic).  Reads Ainv once; no padded columns.
+template <class T>
+__device__ inline T shfl_xor_t(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+template <>
+__device__ inline cdouble shfl_xor_t(cdouble v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.re, o), __shfl_xor_sync(0xffffffffu, v.im, o)};
+}
+template <>
+__device__ inline cfloat shfl_xor_t(cfloat v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.re, o), __shfl_xor_sync(0xffffffffu, v.im, o)};
+}
+
+template <class T, int KN>
+__global__ void __launch_bounds__(256) k_dense_apply_narrow(const T *__restrict__ A, const T *__restrict__ B,
+                                                            T *__restrict__ Y, int n, int k) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+    T acc[KN];
+#pragma unroll
+    for (int c = 0; c < KN; ++c) acc[c] = zero<T>();
+    const T *Ai = A + (size_t)i * n;
+    for (int j = lane; j < n; j += 32) {
+      const T a = Ai[j];
+      const T *Bj = B + (size_t)j * k;
+#pragma unroll
+      for (int c = 0; c < KN; ++c)
+        if (c < k) acc[c] = acc[c] + a * Bj[c];
+    }
+#pragma unroll
+    for (int c = 0; c < KN; ++c) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[c] = acc[c] + shfl_xor_t(acc[c], o);
+    }
+    if (lane < k) {
+      T out = acc[0];
+#pragma unroll
+      for (int c = 1; c < KN; ++c)
+        if (c == lane) out = acc[c];
+      Y[(size_t)i * k + lane] = out;
+    }
+  }
+}
+
 template <class T>
 __global__ void k_dense_sum(const T *part, int splits, size_t count, T *Y) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
@@ -644,6 +697,17 @@ int dense_apply_splits(int n, int k) {
 }
 
 void launch_dense_apply(DType t, const void *Ainv, const void *B, void *Y, int n, int k, void *part, cudaStream_t s) {
+  if (k <= 8) {
+    const unsigned g = resident_grid(((size_t)n * 32 + 255) / 256, 8);
+    MLMC_DISPATCH(t, T, {
+      if (k <= 4)
+        k_dense_apply_narrow<T, 4><<<g, 256, 0, s>>>((const T *)Ainv, (const T *)B, (T *)Y, n, k);
+      else
+        k_dense_apply_narrow<T, 8><<<g, 256, 0, s>>>((const T *)Ainv, (const T *)B, (T *)Y, n, k);
+    });
+    MLMC_LAUNCH_CHECK("k_dense_apply_narrow");
+    return;
+  }
   int splits = part ? dense_apply_splits(n, k) : 1;
   int jchunk = (n + splits - 1) / splits;
   jchunk = (jchunk + DA_BK - 1) / DA_BK * DA_BK;
