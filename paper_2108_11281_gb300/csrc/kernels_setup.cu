@@ -218,7 +218,8 @@ void launch_galerkin(const StencilView &fine, const ProlongView &P, void *coarse
 // other row i takes g = M[i][q] / a, M[i][c] -= g M[p][c] (c != q), M[i][q] = -g; row p is
 // scaled (M[p][c] /= a, M[p][q] = 1 / a) by its owner at the start of the next step, so
 // during a step all blocks read the unchanged pivot row while each writes only its own
-// rows (kept in shared memory, written through to M).  At the end M[piv_q][pos(c)] =
+// rows (kept in shared memory; a block publishes to M only its candidate for the next
+// pivot, and all its rows at the end).  At the end M[piv_q][pos(c)] =
 // A^-1[q][c] with pos(piv_q) = q (k_gj_extract_inplace).
 //
 // k_gj_coop (larger n): the same pivoting on work = [A | I] (n x 2n) in global memory,
@@ -237,6 +238,7 @@ __global__ void k_gj_init(const T *A, T *work, int n) {
 constexpr int GJ_THREADS = 256;
 constexpr int GJ_MAX_ROWS = 64;                 // rows per block (n <= 64 x blocks)
 constexpr int GJ_COLS = 16;                     // k_gj_inplace: columns per thread (n <= 4096)
+constexpr int GJ_ROWB = 8;                      // k_gj_inplace: rows updated together
 constexpr long long GJ_WAIT_CYCLES = 2000000000LL;
 
 __device__ inline double ldcg_d(const double *p) { return __ldcg(p); }
@@ -269,6 +271,38 @@ __device__ inline void gj_block_best(double &m, int &r, double *sm, int *sr) {
   m = sm[0];
   r = sr[0];
   __syncthreads();
+}
+
+// The same on an integer key: a magnitude m >= 0 orders like its bit pattern, so
+// (key, row) = (bits(m), r) compares on the integer units (0 = none or zero); warp shuffles,
+// then the warps' winners through shared memory.  Returns the winner in every thread.
+__device__ inline unsigned long long gj_key(double m) {
+  return m > 0.0 ? (unsigned long long)__double_as_longlong(m) : 0ull;
+}
+__device__ inline bool gj_better(unsigned long long k2, int r2, unsigned long long k1, int r1) {
+  return k2 > k1 || (k2 == k1 && r2 < r1);
+}
+__device__ inline void gj_block_best_key(unsigned long long &key, int &row, unsigned long long *wk, int *wr) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+    const int r2 = __shfl_xor_sync(0xffffffffu, row, o);
+    if (gj_better(k2, r2, key, row)) { key = k2; row = r2; }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { wk[warp] = key; wr[warp] = row; }
+  __syncthreads();
+  key = lane < (GJ_THREADS >> 5) ? wk[lane] : 0ull;
+  row = lane < (GJ_THREADS >> 5) ? wr[lane] : 0x7fffffff;
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+    const int r2 = __shfl_xor_sync(0xffffffffu, row, o);
+    if (gj_better(k2, r2, key, row)) { key = k2; row = r2; }
+  }
+  key = __shfl_sync(0xffffffffu, key, 0);
+  row = __shfl_sync(0xffffffffu, row, 0);
+  __syncthreads();                 // wk / wr free for the next call
 }
 
 // bounded grid barrier number `round` (1, 2, ...): false when the wait gave up
@@ -374,44 +408,47 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_inplace(const T *A, T *M, int
                                                          long long wait_cycles) {
   extern __shared__ __align__(16) unsigned char gj_smem[];
   T *Ms = reinterpret_cast<T *>(gj_smem);          // own rows, rows x n
-  __shared__ double sm[GJ_THREADS];
-  __shared__ int sr[GJ_THREADS];
+  __shared__ unsigned long long wk[GJ_THREADS / 32];
+  __shared__ int wr[GJ_THREADS / 32];
   __shared__ T fr[GJ_MAX_ROWS];
   __shared__ unsigned char used[GJ_MAX_ROWS];
   __shared__ int fail_sh;
   const int tid = threadIdx.x, G = gridDim.x;
   const int r0 = blockIdx.x * rows, nr = max(0, min(n, r0 + rows) - r0);
-  for (int e = tid; e < nr * n; e += GJ_THREADS) {
-    const T v = A[(size_t)r0 * n + e];
-    Ms[e] = v;
-    M[(size_t)r0 * n + e] = v;
-  }
+  unsigned long long *ckey = reinterpret_cast<unsigned long long *>(cand_mag);
+  for (int e = tid; e < nr * n; e += GJ_THREADS) Ms[e] = A[(size_t)r0 * n + e];
   for (int i = tid; i < GJ_MAX_ROWS; i += GJ_THREADS) used[i] = 0;
   __syncthreads();
-  unsigned round = 0;
-  {
-    double m = -1.0;
-    int r = n;
+  // this block's candidate for column q (unused own rows), published with its row, which
+  // is the only row of the block that can become the next pivot
+  auto candidate = [&](int col, int slot) {
+    unsigned long long key = 0ull;
+    int r = 0x7fffffff;
     for (int i = tid; i < nr; i += GJ_THREADS) {
-      const double v = mag(Ms[(size_t)i * n]);
-      if (v > m || (v == m && r0 + i < r)) { m = v; r = r0 + i; }
+      if (used[i]) continue;
+      const unsigned long long k2 = gj_key(mag(Ms[(size_t)i * n + col]));
+      if (gj_better(k2, r0 + i, key, r)) { key = k2; r = r0 + i; }
     }
-    gj_block_best(m, r, sm, sr);
-    if (tid == 0) { cand_mag[blockIdx.x] = m; cand_row[blockIdx.x] = r; }
-    if (!gj_grid_barrier(bar, ++round, wait_cycles, err, &fail_sh)) return;
-  }
+    gj_block_best_key(key, r, wk, wr);
+    if (tid == 0) { ckey[slot * G + blockIdx.x] = key; cand_row[slot * G + blockIdx.x] = r; }
+    if (r < n)
+      for (int c = tid; c < n; c += GJ_THREADS) M[(size_t)r * n + c] = Ms[(size_t)(r - r0) * n + c];
+  };
+  unsigned round = 0;
+  candidate(0, 0);
+  if (!gj_grid_barrier(bar, ++round, wait_cycles, err, &fail_sh)) return;
   int prev = -1;
   for (int q = 0; q < n; ++q) {
     const int par = q & 1;
-    double m = -1.0;
-    int p = n;
+    unsigned long long key = 0ull;
+    int p = 0x7fffffff;
     for (int b = tid; b < G; b += GJ_THREADS) {
-      const double v = __ldcg(cand_mag + par * G + b);
-      const int r = __ldcg(cand_row + par * G + b);
-      if (v > m || (v == m && r < p)) { m = v; p = r; }
+      const unsigned long long k2 = __ldcg(ckey + par * G + b);
+      const int r2 = __ldcg(cand_row + par * G + b);
+      if (gj_better(k2, r2, key, p)) { key = k2; p = r2; }
     }
-    gj_block_best(m, p, sm, sr);
-    if (!(m > 0.0) || p >= n) {
+    gj_block_best_key(key, p, wk, wr);
+    if (key == 0ull || p >= n) {
       if (blockIdx.x == 0 && tid == 0) atomicExch(err, 3);
       return;
     }
@@ -435,39 +472,42 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_inplace(const T *A, T *M, int
     const T ra = divide(make<T>(1.0, 0.0), ldcg_d(M + (size_t)p * n + q));
     for (int i = tid; i < nr; i += GJ_THREADS) fr[i] = r0 + i == p ? zero<T>() : Ms[(size_t)i * n + q] * ra;
     __syncthreads();
+    // own rows, up to GJ_ROWB at a time: all loads, then the FMAs, then the stores
 #pragma unroll
     for (int u = 0; u < GJ_COLS; ++u) {
       const int c = tid + u * GJ_THREADS;
       if (c >= n) break;
-      for (int i = 0; i < nr; ++i) {
-        if (r0 + i == p) continue;
-        const T v = c == q ? zero<T>() - fr[i] : Ms[(size_t)i * n + c] - fr[i] * pcs[u];
-        Ms[(size_t)i * n + c] = v;
-        M[(size_t)(r0 + i) * n + c] = v;
+      for (int i0 = 0; i0 < nr; i0 += GJ_ROWB) {
+        T v[GJ_ROWB];
+#pragma unroll
+        for (int w = 0; w < GJ_ROWB; ++w)
+          if (i0 + w < nr) v[w] = Ms[(size_t)(i0 + w) * n + c];
+#pragma unroll
+        for (int w = 0; w < GJ_ROWB; ++w) {
+          const int i = i0 + w;
+          if (i < nr && r0 + i != p) {
+            v[w] = c == q ? zero<T>() - fr[i] : v[w] - fr[i] * pcs[u];
+            Ms[(size_t)i * n + c] = v[w];
+          }
+        }
       }
     }
     prev = p;
-    if (q + 1 == n) break;
     __syncthreads();
-    m = -1.0;
-    int cr = n;
-    for (int i = tid; i < nr; i += GJ_THREADS) {
-      if (used[i]) continue;
-      const double v = mag(Ms[(size_t)i * n + q + 1]);
-      if (v > m || (v == m && r0 + i < cr)) { m = v; cr = r0 + i; }
-    }
-    gj_block_best(m, cr, sm, sr);
-    if (tid == 0) { cand_mag[(1 - par) * G + blockIdx.x] = m; cand_row[(1 - par) * G + blockIdx.x] = cr; }
+    if (q + 1 == n) break;
+    candidate(q + 1, 1 - par);
     if (!gj_grid_barrier(bar, ++round, wait_cycles, err, &fail_sh)) return;
   }
-  // the last pivot row's scaling, once every block has read that row in the last step
+  // every block has read the last pivot row: scale it, then publish all own rows
   if (!gj_grid_barrier(bar, ++round, wait_cycles, err, &fail_sh)) return;
   if (prev >= r0 && prev < r0 + nr) {
     T *row = Ms + (size_t)(prev - r0) * n;
     const T ra = divide(make<T>(1.0, 0.0), row[n - 1]);
     __syncthreads();
-    for (int c = tid; c < n; c += GJ_THREADS) M[(size_t)prev * n + c] = c == n - 1 ? ra : row[c] * ra;
+    for (int c = tid; c < n; c += GJ_THREADS) row[c] = c == n - 1 ? ra : row[c] * ra;
+    __syncthreads();
   }
+  for (int e = tid; e < nr * n; e += GJ_THREADS) M[(size_t)r0 * n + e] = Ms[e];
 }
 
 // A^-1[q][c] = M[piv_q][pos(c)], pos(piv_j) = j
