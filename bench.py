@@ -84,9 +84,11 @@ WORKLOAD = WORKLOADS["laplace1024"]
 # ncu DRAM traffic (read + write bytes) per launch unit of the roofline kernel, keyed by
 # (workload, kernel row); only for the kernel version the capture was taken on
 TRAFFIC = {
-    # k_rbgs_half_p<float,4,4>, level 2 (256^2 x 4, k = 128), both halves of one sweep:
-    # dram__bytes_read 149.44 + 149.43 MB, dram__bytes_write 39.54 + 36.90 MB (1 pass each)
-    ("laplace2d-1024x1024-L4-4tv-k64", "rbgs_sweep_fp32_level2"): 375.32e6,
+    # k_rbgs_half_p<float,4,4> (resident grid, colour 1 from the last row), level 2
+    # (256^2 x 4, k = 128), both halves of one sweep after six warm launches, caches kept
+    # between launches (ncu --cache-control none, 1 pass each): dram__bytes_read
+    # 127.47 + 127.13 MB, dram__bytes_write 69.69 + 67.33 MB
+    ("laplace2d-1024x1024-L4-4tv-k64", "rbgs_sweep_fp32_level2"): 391.62e6,
 }
 METRIC = "Seconds to tr(A^-1) at 1e-3 rel. error, mixed+learned vs plain FP64; HBM %"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
