@@ -188,7 +188,10 @@ typedef struct {
 
 /* Build the hierarchy on the GPU (Sec. 4.1; Example 5.3): fine operator,
  * test vectors, per-aggregate orthonormalisation, Galerkin coarse operators,
- * smoother blocks, dense inverse of A_L.  `stream` is a cudaStream_t or NULL
+ * smoother blocks, dense inverse of A_L (Gauss-Jordan with partial pivoting in
+ * one cooperative launch whose grid-barrier waits are bounded: a wait that
+ * gives up returns MLMC_ERR_TIMEOUT; a zero pivot MLMC_ERR_SINGULAR).
+ * `stream` is a cudaStream_t or NULL
  * (NULL: the handle creates and owns a private stream).  On success *out owns
  * the device memory until mlmc_destroy_hierarchy.  Device buffers are
  * stream-ordered on that stream (no device-wide synchronisation when a handle
