@@ -252,7 +252,8 @@ int mlmc_sample_block(mlmc_hierarchy *h, int level, int form, int noise, uint64_
  * Gauss-Seidel sweep the residual vanishes on the colour updated last, so the cycle
  * passes the other one.  Device blocks x, b [n_l][k], rc [n_{l+1}][k] in FP64
  * (precision MLMC_PREC_FP64) or FP32 (MLMC_PREC_MIXED_FP32, mixed form only);
- * aggregation levels with at most 4 dofs per site and coarse site.  Synchronous. */
+ * aggregation levels with at most 4 dofs per site and coarse site; 1 <= k <= 65536
+ * (the caller's blocks, independent of the hierarchy's block widths).  Synchronous. */
 int mlmc_residual_restrict(mlmc_hierarchy *h, int level, int precision, const void *x, const void *b, void *rc,
                            int k, int colour);
 /* Samples per block on level difference `level` (1 <= level < L): the widths the

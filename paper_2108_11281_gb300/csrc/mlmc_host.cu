@@ -1579,7 +1579,7 @@ int mlmc_residual_restrict(mlmc_hierarchy *h, int level, int precision, const vo
     need_level(h, level, 1, h ? h->L - 1 : 0);
     const int lo = precision == MLMC_PREC_MIXED_FP32 ? 1 : 0;
     if (lo && h->prm.precision != MLMC_PREC_MIXED_FP32) fail(MLMC_ERR_INVALID_ARG, "FP32 data needs the mixed form");
-    if (!x || !b || !rc || k < 1 || k > h->wl[level] || (colour != 0 && colour != 1))
+    if (!x || !b || !rc || k < 1 || k > 65536 || (colour != 0 && colour != 1))
       fail(MLMC_ERR_INVALID_ARG, "bad arguments");
     const StencilView A = view(*h, level - 1, lo);
     const ProlongView P = pview(*h, level - 1, lo);

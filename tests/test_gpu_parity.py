@@ -260,6 +260,26 @@ def test_samples_three_levels(mlmc, precision, rtol):
     h.close()
 
 
+@pytest.mark.parametrize("precision,rtol", [(0, 1e-9), (1, 1e-8)])
+def test_samples_odd_aggregates(mlmc, precision, rtol):
+    """3 x 3 aggregates (odd sides) on a 36^2 Laplacian, 3 levels, the oracle's P imported:
+    the cycle's fused residual-restriction walks every site of an aggregate and skips the
+    other colour; level-1 and level-2 samples against the oracle, in both forms."""
+    N = 36
+    A = laplace2d(N, N)
+    sp_ = SetupParams(levels=3, agg_x=3, agg_y=3, n_tv=2, sweeps=10, coarse_sweeps=5, bootstrap=0)
+    lv = build_hierarchy(A, N, N, 1, sp_)
+    prm = mlmc.default_params(levels=3, agg_x=3, agg_y=3, n_tv=2, block=8, bootstrap=0, precision=precision)
+    h = mlmc.Hierarchy(mlmc.OP_LAPLACE2D, N, N, prm, user_P=[lv[0].P_blocks, lv[1].P_blocks])
+    solv = E.LevelSolvers(lv)
+    tol = 1e-12 if precision == 0 else 1e-10
+    for level in (1, 2):
+        got, _ = h.sample_level(level, mlmc.NOISE_RADEMACHER, 5, 0, 6, tol)
+        ref = E.level_samples(lv, solv, level, "rademacher", 5, 0, 6)
+        compare_samples(got, ref, rtol)
+    h.close()
+
+
 def test_wilson_samples_imported_P(mlmc):
     N = 16
     U = gauge_links(N, N, 0.3, 11)
@@ -521,19 +541,29 @@ def test_block_width_growth_keeps_samples(mlmc):
     h1.close()
 
 
-@pytest.mark.parametrize("case", ["laplace", "wilson"])
-def test_fused_residual_restriction(mlmc, case):
+@pytest.mark.parametrize("case, k", [("laplace", 8), ("laplace", 6), ("laplace", 40), ("laplace", 136),
+                                     ("wilson", 8), ("wilson", 6), ("laplace-agg3", 8), ("laplace-agg3", 6)])
+def test_fused_residual_restriction(mlmc, case, k):
     """The cycle's fused residual-and-restriction kernel against P^* m (b - A x) formed
     with the level's own operator and prolongation (m = the sites of one colour), on
     random blocks: the Example 5.1 fine level and a d = 4 aggregation level (Laplace),
-    and the complex d = 2 fine level of a Wilson operator with spin-split P; FP64 data
-    (1e-12 of scale) and, for the Laplacian, FP32 data in the mixed form (1e-5)."""
+    the complex d = 2 fine level of a Wilson operator with spin-split P, and 3 x 3
+    aggregates (odd sides: the kernel walks every site and skips the other colour) on the
+    fine level and a d = 2 level; FP64 data (1e-12 of scale) and, for the Laplacian, FP32
+    data in the mixed form (1e-5).  k covers 16-byte and scalar column packs and blocks of
+    8, 16 and 32 packs with a ragged last chunk."""
     if case == "laplace":
         N = 32
         h = laplace_h(mlmc, N, 3, block=8, n_tv=4, setup_sweeps=10, coarse_sweeps=5, bootstrap=0,
                       precision=mlmc.PREC_MIXED_FP32)
         A1 = laplace2d(N, N)
         levels = [(1, A1), (2, block_from_stencil(h.operator(2), *h.level_info(2)[:2]))]
+        cplx = False
+    elif case == "laplace-agg3":
+        N = 36
+        h = laplace_h(mlmc, N, 3, block=8, n_tv=2, setup_sweeps=10, coarse_sweeps=5, bootstrap=0, agg_x=3,
+                      agg_y=3, precision=mlmc.PREC_MIXED_FP32)
+        levels = [(1, laplace2d(N, N)), (2, block_from_stencil(h.operator(2), *h.level_info(2)[:2]))]
         cplx = False
     else:
         N = 16
@@ -543,7 +573,6 @@ def test_fused_residual_restriction(mlmc, case):
         h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.1, links=U)
         levels = [(1, wilson2d(N, N, 0.1, U))]
         cplx = True
-    k = 8
     g = torch.Generator().manual_seed(3)
     for level, A in levels:
         nx, ny, d = h.level_info(level)
@@ -560,7 +589,7 @@ def test_fused_residual_restriction(mlmc, case):
             b = torch.randn(n, k, generator=g, dtype=dt)
         r = b.numpy() - A @ x.numpy()
         j, i = np.divmod(np.arange(nx * ny), nx)
-        ax = ay = 4
+        ax, ay = h.params.agg_x, h.params.agg_y
         ncx = nx // ax
         for colour in (0, 1):
             mask = np.repeat(((i + j) % 2 == colour).astype(float), d)
