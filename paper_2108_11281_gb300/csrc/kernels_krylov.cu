@@ -22,7 +22,7 @@ template <> __device__ inline cdouble hdiv<cdouble>(cdouble a, cdouble b) {
 template <class H> __device__ inline H hreal(double v) { return make<H>(v, 0.0); }
 
 // sc (optional): norms s_i of the unnormalised basis vectors of the fixed-length
-// variant (see k_lazy_coef); s_0 = |b|.
+// variant (see k_multidot_reduce); s_0 = |b|.
 template <class H>
 __global__ void k_arnoldi_init(H *g, double *bnorm, double *invnrm, int *active, int *jdone, int k,
                                double tol, int first, int *nactive, double *sc) {
@@ -40,21 +40,6 @@ __global__ void k_arnoldi_init(H *g, double *bnorm, double *invnrm, int *active,
   if (sc) sc[c] = beta > 0.0 ? beta : 1.0;
   if (a) atomicAdd(nactive, 1);
   else if (!finite) atomicAdd(nactive, NONFINITE_COLUMN);    // a residual that is NaN or infinite
-}
-
-// Fixed-length FGMRES with unnormalised basis vectors u_i = s_i v_i (the scaling pass
-// over each new basis vector is skipped; the cycle and the operator are linear, so
-// z_j and w scale along).  With d_i = u_i^* w for w = A z_j (z_j from u_j):
-//   Gram-Schmidt coefficient of u_i:  d_i / s_i^2,   Hessenberg entry:  d_i / (s_i s_j).
-template <class H>
-__global__ void k_lazy_coef(H *hcol, const double *sc, H *coef, int j, int k) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (j + 1) * k) return;
-  const int i = t / k, c = t - (t / k) * k;
-  const double si = sc[(size_t)i * k + c], sj = sc[(size_t)j * k + c];
-  const H d = hcol[t];
-  coef[t] = d * hreal<H>(1.0 / (si * si));
-  hcol[t] = d * hreal<H>(1.0 / (si * sj));
 }
 
 // y_i /= s_i for the computed rows: x = sum_i z_i y_i with z_i built from u_i.
@@ -156,12 +141,6 @@ void launch_arnoldi_init(int hc, void *g, double *bnorm, double *invnrm, int *ac
   MLMC_LAUNCH_CHECK("k_arnoldi_init");
 }
 
-void launch_lazy_coef(int hc, void *hcol, const double *sc, void *coef, int j, int k, cudaStream_t s) {
-  unsigned gr = ((j + 1) * k + 127) / 128;
-  if (hc) k_lazy_coef<cdouble><<<gr, 128, 0, s>>>((cdouble *)hcol, sc, (cdouble *)coef, j, k);
-  else k_lazy_coef<double><<<gr, 128, 0, s>>>((double *)hcol, sc, (double *)coef, j, k);
-  MLMC_LAUNCH_CHECK("k_lazy_coef");
-}
 
 void launch_lazy_y(int hc, void *y, const double *sc, const int *jdone, int m, int k, cudaStream_t s) {
   unsigned gr = (m * k + 127) / 128;

@@ -255,8 +255,14 @@ __device__ inline cdouble shfl_add(cdouble a, int o) {
   return {a.re + __shfl_xor_sync(0xffffffffu, a.re, o), a.im + __shfl_xor_sync(0xffffffffu, a.im, o)};
 }
 
+// Optional epilogue for the fixed-length FGMRES with unnormalised basis vectors
+// u_i = s_i v_i (the scaling pass over each new basis vector is skipped; the cycle and the
+// operator are linear, so z_j and w scale along).  With d_i = u_i^* w for w = A z_j and
+// sc = s per (i, c), column j the new one: the Gram-Schmidt coefficient of u_i is
+// coef = d_i / s_i^2 and the Hessenberg entry out = d_i / (s_i s_j), element by element.
 template <class A>
-__global__ void k_multidot_reduce(const A *partial, int nparts, int nvec, int k, A *out) {
+__global__ void k_multidot_reduce(const A *partial, int nparts, int nvec, int k, A *out, const double *sc, A *coef,
+                                  int j) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= nvec * k) return;
@@ -267,11 +273,21 @@ __global__ void k_multidot_reduce(const A *partial, int nparts, int nvec, int k,
   for (int p = lane; p < nparts; p += 32) s = addd(s, partial[(size_t)p * stride + warp]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s = shfl_add(s, o);
-  if (lane == 0) out[warp] = s;
+  if (lane == 0) {
+    if (sc) {
+      const int c = warp % k;
+      const double si = sc[warp], sj = sc[(size_t)j * k + c];
+      coef[warp] = s * make<A>(1.0 / (si * si), 0.0);
+      out[warp] = s * make<A>(1.0 / (si * sj), 0.0);
+    } else {
+      out[warp] = s;
+    }
+  }
 }
 
 void launch_multidot(DType t, const void *V, size_t vstride, int nvec, const void *w, size_t rows,
-                     int k, void *partials, int nparts, void *out, DType out_t, cudaStream_t s) {
+                     int k, void *partials, int nparts, void *out, DType out_t, cudaStream_t s,
+                     const double *lazy_sc, void *lazy_coef, int lazy_j) {
   (void)out_t;
   MLMC_DISPATCH(t, T, {
     typedef typename acc_of<T>::type A;
@@ -288,7 +304,8 @@ void launch_multidot(DType t, const void *V, size_t vstride, int nvec, const voi
                                                               (A *)partials);
     MLMC_LAUNCH_CHECK("k_multidot_partial");
     int tot = nvec * k;
-    k_multidot_reduce<A><<<(tot * 32 + 255) / 256, 256, 0, s>>>((const A *)partials, nparts, nvec, k, (A *)out);
+    k_multidot_reduce<A><<<(tot * 32 + 255) / 256, 256, 0, s>>>((const A *)partials, nparts, nvec, k, (A *)out,
+                                                                lazy_sc, (A *)lazy_coef, lazy_j);
     MLMC_LAUNCH_CHECK("k_multidot_reduce");
   });
 }
@@ -435,10 +452,10 @@ void launch_column_reduce(DType out_t, const void *partial, int nparts, int k, v
   const int tot = k;
   if (out_t == C64)
     k_multidot_reduce<cdouble><<<(tot * 32 + 255) / 256, 256, 0, s>>>((const cdouble *)partial, nparts, 1, k,
-                                                                        (cdouble *)out);
+                                                                        (cdouble *)out, nullptr, nullptr, 0);
   else
     k_multidot_reduce<double><<<(tot * 32 + 255) / 256, 256, 0, s>>>((const double *)partial, nparts, 1, k,
-                                                                       (double *)out);
+                                                                       (double *)out, nullptr, nullptr, 0);
   MLMC_LAUNCH_CHECK("k_multidot_reduce");
 }
 

@@ -321,9 +321,10 @@ void dense_apply(H_t &h, int lo, const void *b, void *x, int k) {
   h.cost += (double)C.n * C.n * k;
 }
 
-void multidot(H_t &h, Krylov &K, const void *V, int nvec, const void *w, int k, void *out) {
+void multidot(H_t &h, Krylov &K, const void *V, int nvec, const void *w, int k, void *out,
+              const double *lazy_sc = nullptr, void *lazy_coef = nullptr, int lazy_j = 0) {
   launch_multidot(K.t, V, K.n * (size_t)k, nvec, w, K.n, k, K.partials.p, multidot_parts(K.n, k), out,
-                  K.hc ? C64 : F64, h.stream);
+                  K.hc ? C64 : F64, h.stream, lazy_sc, lazy_coef, lazy_j);
   h.launches += 2;
 }
 
@@ -344,7 +345,7 @@ int fgmres(H_t &h, Krylov &K, int l, int lo, const void *b, void *x, int k, doub
   auto Hcol = [&](int j) { return (char *)K.H.p + (size_t)j * (m + 1) * k * as; };
   const bool fixed = fixed_its > 0;
   // fixed length (inner solves, K-cycle): the basis vectors stay unnormalised (no
-  // scaling pass over each new vector; see k_lazy_coef)
+  // scaling pass over each new vector; see k_multidot_reduce)
   const bool lazy = fixed && !reorth;
   double *sc = lazy ? K.sc.as<double>() : nullptr;
   cudaStream_t s = h.stream;
@@ -375,11 +376,9 @@ int fgmres(H_t &h, Krylov &K, int l, int lo, const void *b, void *x, int k, doub
     for (int j = 0; j < m; ++j) {
       M(Vj(j), Zj(j));
       apply_op(h, l, lo, Zj(j), Vj(j + 1), k);
-      multidot(h, K, K.V.p, j + 1, Vj(j + 1), k, Hcol(j));
-      if (lazy) {
-        launch_lazy_coef(K.hc, Hcol(j), sc, K.hco.p, j, k, s);
-        h.launches++;
-      }
+      // unnormalised basis: the reduction also forms the Hessenberg entries and the
+      // multi-AXPY's coefficients (see k_multidot_reduce)
+      multidot(h, K, K.V.p, j + 1, Vj(j + 1), k, Hcol(j), lazy ? sc : nullptr, lazy ? K.hco.p : nullptr, j);
       // fixed length: the multi-AXPY also sums |u_{j+1}|^2 per column (no separate norm pass)
       const int nparts = launch_multiaxpy(K.t, Vj(j + 1), K.V.p, blk, j + 1, lazy ? K.hco.p : Hcol(j),
                                           K.hc ? C64 : F64, k, -1.0, K.n, k, s, lazy ? K.partials.p : nullptr);

@@ -168,8 +168,11 @@ void launch_sub(DType t, void *out, const void *a, const void *b, size_t count, 
 void launch_scale_cols(DType t, void *y, const void *x, const void *alpha, int alpha_is_inverse_norm,
                        size_t rows, int k, cudaStream_t s);
 // partial[b][v][c] of sum_i conj(V_v[i][c]) * w[i][c], v < nvec; then out[v][c] (fixed order)
+// lazy_sc (optional): the unnormalised-basis epilogue of k_multidot_reduce (out = d / (s_i s_j),
+// lazy_coef = d / s_i^2 with s from lazy_sc, column lazy_j the new one)
 void launch_multidot(DType t, const void *V, size_t vstride, int nvec, const void *w, size_t rows,
-                     int k, void *partials, int nparts, void *out, DType out_t, cudaStream_t s);
+                     int k, void *partials, int nparts, void *out, DType out_t, cudaStream_t s,
+                     const double *lazy_sc = nullptr, void *lazy_coef = nullptr, int lazy_j = 0);
 // w[i][c] -= sum_v V_v[i][c] * h[v][c]  (h in out precision), optional column mask
 // norm_part (optional): per-block column sums of |w_new|^2 in the FP64 accumulation
 // type (multiaxpy_norm_parts(rows, k) x k entries at most); returns the block count
@@ -260,7 +263,6 @@ void launch_arnoldi_init(int hc, void *g, double *bnorm, double *invnrm, int *ac
                          int k, double tol, int first, int *nactive, cudaStream_t s, double *sc = nullptr);
 // unnormalised basis: Gram-Schmidt coefficients d_i / s_i^2 into coef, Hessenberg
 // entries d_i / (s_i s_j) in place; and y_i /= s_i before the solution update
-void launch_lazy_coef(int hc, void *hcol, const double *sc, void *coef, int j, int k, cudaStream_t s);
 void launch_lazy_y(int hc, void *y, const double *sc, const int *jdone, int m, int k, cudaStream_t s);
 void launch_arnoldi_step(int hc, void *H, void *cs, void *sn, void *g, int j, int m, int k, int *active,
                          int *jdone, const double *bnorm, double tol, double *invnrm, double *resid,
