@@ -3,6 +3,7 @@
 // Gauss-Jordan inverse and trace of the coarsest operator, and the dense
 // coarsest-level apply used inside every multigrid cycle.
 #include <algorithm>
+#include <mutex>
 
 #include "mlmc.h"
 #include "mlmc_internal.cuh"
@@ -560,6 +561,19 @@ size_t gauss_jordan_scratch_bytes(int n) { return gj_layout(n, gj_blocks(n)).tot
 
 constexpr size_t GJ_SMEM_MAX = 200 * 1024;      // own rows of k_gj_inplace in shared memory
 
+// The dynamic shared-memory limit of k_gj_inplace, raised once per device to GJ_SMEM_MAX
+// (a per-call value would race between host threads building hierarchies concurrently).
+template <class T>
+void gj_inplace_attrs() {
+  static std::once_flag once[64];
+  int dev = 0;
+  MLMC_CUDA(cudaGetDevice(&dev));
+  std::call_once(once[dev & 63], [] {
+    check_cuda(cudaFuncSetAttribute(k_gj_inplace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJ_SMEM_MAX),
+               "cudaFuncSetAttribute(k_gj_inplace)");
+  });
+}
+
 void launch_gauss_jordan(DType t, const void *A, void *Ainv, void *work, int n, int *err, void *scratch,
                          size_t scratch_bytes, cudaStream_t s) {
   const int G = gj_blocks(n);
@@ -581,7 +595,7 @@ void launch_gauss_jordan(DType t, const void *A, void *Ainv, void *work, int n, 
     const size_t smem = (size_t)rows * n * sizeof(T);
     int per_sm = 0;
     if (smem <= GJ_SMEM_MAX && n <= GJ_COLS * GJ_THREADS) {
-      MLMC_CUDA(cudaFuncSetAttribute(k_gj_inplace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      gj_inplace_attrs<T>();
       MLMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_inplace<T>, GJ_THREADS, smem));
       if ((long long)per_sm * sms < G) throw cuda_error{cudaErrorInvalidValue, "gauss_jordan: blocks cannot be resident"};
       const T *a = (const T *)A;
