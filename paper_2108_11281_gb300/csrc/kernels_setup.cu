@@ -214,7 +214,7 @@ void launch_galerkin(const StencilView &fine, const ProlongView &P, void *coarse
 // timeout the block records MLMC_ERR_TIMEOUT and returns, and the others time out at their
 // next wait.  Data written by other blocks is read through L2 (__ldcg).
 //
-// k_gj_inplace (the coarsest operators of the hierarchies: own rows fit in shared memory):
+// k_gj_inplace (n <= 4096; own rows in shared memory where they fit, else in place in M):
 // in-place Gauss-Jordan on M = A (n x n).  Step q with pivot row p, a = M[p][q]: every
 // other row i takes g = M[i][q] / a, M[i][c] -= g M[p][c] (c != q), M[i][q] = -g; row p is
 // scaled (M[p][c] /= a, M[p][q] = 1 / a) by its owner at the start of the next step, so
@@ -223,7 +223,7 @@ void launch_galerkin(const StencilView &fine, const ProlongView &P, void *coarse
 // pivot, and all its rows at the end).  At the end M[piv_q][pos(c)] =
 // A^-1[q][c] with pos(piv_q) = q (k_gj_extract_inplace).
 //
-// k_gj_coop (larger n): the same pivoting on work = [A | I] (n x 2n) in global memory,
+// k_gj_coop (n > 4096): the same pivoting on work = [A | I] (n x 2n) in global memory,
 // rows never scaled: every other row takes work[r][c] -= (work[r][q] / work[piv][q])
 // work[piv][c] for c > q; row piv_q ends as work[piv_q][q] x [e_q | row q of A^-1]
 // (k_gj_extract).
@@ -403,12 +403,15 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_coop(T *work, int n, int rows
   }
 }
 
-template <class T>
+// SMEM = false: the own rows are updated in place in M (initialised from A by the caller);
+// nothing to publish or write back.
+template <class T, bool SMEM>
 __global__ void __launch_bounds__(GJ_THREADS) k_gj_inplace(const T *A, T *M, int n, int rows, int *pivrow,
                                                          double *cand_mag, int *cand_row, unsigned *bar, int *err,
                                                          long long wait_cycles) {
   extern __shared__ __align__(16) unsigned char gj_smem[];
-  T *Ms = reinterpret_cast<T *>(gj_smem);          // own rows, rows x n
+  const int r0_ = blockIdx.x * rows;
+  T *Ms = SMEM ? reinterpret_cast<T *>(gj_smem) : M + (size_t)r0_ * n;   // own rows, rows x n
   __shared__ unsigned long long wk[GJ_THREADS / 32];
   __shared__ int wr[GJ_THREADS / 32];
   __shared__ T fr[GJ_MAX_ROWS];
@@ -417,7 +420,8 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_inplace(const T *A, T *M, int
   const int tid = threadIdx.x, G = gridDim.x;
   const int r0 = blockIdx.x * rows, nr = max(0, min(n, r0 + rows) - r0);
   unsigned long long *ckey = reinterpret_cast<unsigned long long *>(cand_mag);
-  for (int e = tid; e < nr * n; e += GJ_THREADS) Ms[e] = A[(size_t)r0 * n + e];
+  if (SMEM)
+    for (int e = tid; e < nr * n; e += GJ_THREADS) Ms[e] = A[(size_t)r0 * n + e];
   for (int i = tid; i < GJ_MAX_ROWS; i += GJ_THREADS) used[i] = 0;
   __syncthreads();
   // this block's candidate for column q (unused own rows), published with its row, which
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_inplace(const T *A, T *M, int
     }
     gj_block_best_key(key, r, wk, wr);
     if (tid == 0) { ckey[slot * G + blockIdx.x] = key; cand_row[slot * G + blockIdx.x] = r; }
-    if (r < n)
+    if (SMEM && r < n)
       for (int c = tid; c < n; c += GJ_THREADS) M[(size_t)r * n + c] = Ms[(size_t)(r - r0) * n + c];
   };
   unsigned round = 0;
@@ -508,7 +512,8 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_inplace(const T *A, T *M, int
     for (int c = tid; c < n; c += GJ_THREADS) row[c] = c == n - 1 ? ra : row[c] * ra;
     __syncthreads();
   }
-  for (int e = tid; e < nr * n; e += GJ_THREADS) M[(size_t)r0 * n + e] = Ms[e];
+  if (SMEM)
+    for (int e = tid; e < nr * n; e += GJ_THREADS) M[(size_t)r0 * n + e] = Ms[e];
 }
 
 // A^-1[q][c] = M[piv_q][pos(c)], pos(piv_j) = j
@@ -569,7 +574,8 @@ void gj_inplace_attrs() {
   int dev = 0;
   MLMC_CUDA(cudaGetDevice(&dev));
   std::call_once(once[dev & 63], [] {
-    check_cuda(cudaFuncSetAttribute(k_gj_inplace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJ_SMEM_MAX),
+    check_cuda(cudaFuncSetAttribute(k_gj_inplace<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)GJ_SMEM_MAX),
                "cudaFuncSetAttribute(k_gj_inplace)");
   });
 }
@@ -594,13 +600,24 @@ void launch_gauss_jordan(DType t, const void *A, void *Ainv, void *work, int n, 
     T *wk = (T *)work;
     const size_t smem = (size_t)rows * n * sizeof(T);
     int per_sm = 0;
+    const T *a = (const T *)A;
     if (smem <= GJ_SMEM_MAX && n <= GJ_COLS * GJ_THREADS) {
       gj_inplace_attrs<T>();
-      MLMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_inplace<T>, GJ_THREADS, smem));
+      MLMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_inplace<T, true>, GJ_THREADS, smem));
       if ((long long)per_sm * sms < G) throw cuda_error{cudaErrorInvalidValue, "gauss_jordan: blocks cannot be resident"};
-      const T *a = (const T *)A;
       void *args[] = {&a, &wk, &n, &rows, &pivrow, &cmag, &crow, &bar, &err, &wait};
-      MLMC_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_inplace<T>, dim3(G), dim3(GJ_THREADS), args, smem, s));
+      MLMC_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_inplace<T, true>, dim3(G), dim3(GJ_THREADS), args,
+                                            smem, s));
+      k_gj_extract_inplace<T><<<g, 256, 0, s>>>((const T *)work, pivrow, (T *)Ainv, n);
+    } else if (n <= GJ_COLS * GJ_THREADS) {
+      // the same elimination on the rows in place in global memory (n x n, L2-resident for
+      // the coarsest sizes of the hierarchies)
+      MLMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_inplace<T, false>, GJ_THREADS, 0));
+      if ((long long)per_sm * sms < G) throw cuda_error{cudaErrorInvalidValue, "gauss_jordan: blocks cannot be resident"};
+      MLMC_CUDA(cudaMemcpyAsync(wk, a, (size_t)n * n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      void *args[] = {&a, &wk, &n, &rows, &pivrow, &cmag, &crow, &bar, &err, &wait};
+      MLMC_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_inplace<T, false>, dim3(G), dim3(GJ_THREADS), args,
+                                            0, s));
       k_gj_extract_inplace<T><<<g, 256, 0, s>>>((const T *)work, pivrow, (T *)Ainv, n);
     } else {
       MLMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_coop<T>, GJ_THREADS, 0));

@@ -105,20 +105,23 @@ def test_wilson_apply(mlmc):
     h.close()
 
 
-@pytest.mark.parametrize("case", ["laplace-n64", "laplace-n1024", "laplace-n4096", "wilson-n64"])
+@pytest.mark.parametrize("case", ["laplace-n64", "laplace-n1024", "laplace-n4096", "laplace-n4608", "wilson-n64",
+                                  "wilson-n2048"])
 def test_coarsest_inverse(mlmc, case):
     """The dense Gauss-Jordan inverse of the coarsest operator (Remark 4.2's exact term and
     the coarsest solves): its trace against numpy's inverse of the GPU's own coarsest
     stencil, and FP64 coarsest-level solves A_L x = b against the residual.  n_L = 64 and
-    1024 run the in-place kernel with the rows in shared memory (1 and 7 rows per block),
-    n_L = 4096 (27 rows per block, 884 KB) the kernel on [A | I] in global memory."""
+    1024 run the in-place kernel with the rows in shared memory (1 and 7 rows per block);
+    n_L = 4096 (27 rows per block, 884 KB) and the complex 2048 (14 rows, 458 KB) the same
+    kernel with the rows in place in global memory; n_L = 4608 the kernel on [A | I]."""
     if case.startswith("laplace"):
-        N = {"laplace-n64": 16, "laplace-n1024": 64, "laplace-n4096": 128}[case]
-        h = laplace_h(mlmc, N, 2, n_tv=4, setup_sweeps=4, bootstrap=0)
+        N, ntv = {"laplace-n64": (16, 4), "laplace-n1024": (64, 4), "laplace-n4096": (128, 4),
+                  "laplace-n4608": (96, 8)}[case]
+        h = laplace_h(mlmc, N, 2, n_tv=ntv, setup_sweeps=4, bootstrap=0)
     else:
-        N = 16
+        N, ntv = (16, 2) if case == "wilson-n64" else (64, 4)
         U = gauge_links(N, N, 0.3, 5)
-        prm = mlmc.default_params(levels=2, n_tv=2, spin_split=1, setup_kind=mlmc.SETUP_INVERSE, setup_sweeps=4,
+        prm = mlmc.default_params(levels=2, n_tv=ntv, spin_split=1, setup_kind=mlmc.SETUP_INVERSE, setup_sweeps=4,
                                   setup_omega=1.0, block=8, bootstrap=0)
         h = mlmc.Hierarchy(mlmc.OP_WILSON2D, N, N, prm, mass=0.1, links=U)
     nx, ny, d = h.level_info(2)
