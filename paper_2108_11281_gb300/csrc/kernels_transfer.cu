@@ -470,7 +470,8 @@ static void residual_restrict_go(const StencilView &A, const ProlongView &P, con
   const int vec = (VW > 1 && k % VW == 0) ? VW : 1;
   const int kv = k / vec;
   const unsigned aggs = (unsigned)(P.nx / P.ax) * (P.ny / P.ay);
-  // column packs per block: 32, or fewer for narrow blocks
+  // column packs per block: 32, or fewer for narrow blocks (16 on the 256^2 x 4 level at
+  // k = 128: 62.2 against 59.5 us)
   auto go = [&](auto vtag, auto ktag) {
     constexpr int V = decltype(vtag)::value, KC = decltype(ktag)::value;
     k_residual_restrict<T, D, DC, V, KC><<<dim3(aggs, (kv + KC - 1) / KC), dim3(KC, RR_SLOTS), 0, s>>>(
