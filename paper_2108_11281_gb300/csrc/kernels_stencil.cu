@@ -91,11 +91,18 @@ __device__ __forceinline__ void stencil_body(const T *__restrict__ coef, const T
   }
 }
 
+// Resident grid striding over the units (row j, chunk of 256 threads of the row): the FP64
+// block applies are bound by the FP64 pipe, which one block per unit leaves idle between
+// blocks.
 template <class T, int D, int VEC>
 __global__ void __launch_bounds__(256) k_stencil(const T *__restrict__ coef, const T *__restrict__ x,
                                                  const T *__restrict__ b, T *__restrict__ y, int nx, int ny, int kv,
-                                                 int mode) {
-  stencil_body<T, D, VEC>(coef, x, b, y, nx, ny, kv, mode, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x);
+                                                 int mode, int bpr) {
+  const int units = bpr * ny;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int j = u / bpr;
+    stencil_body<T, D, VEC>(coef, x, b, y, nx, ny, kv, mode, j, (u - j * bpr) * 256 + threadIdx.x);
+  }
 }
 
 // The same in blocks of 128 threads pinned at 8 per SM (<= 64 registers), for FP32
@@ -213,19 +220,23 @@ static void stencil_go(const StencilView &A, const void *x, const void *b, void 
   constexpr int VW = gen_vec<T, D>::v;
   if (VW > 1 && k % VW == 0) {
     int kv = k / VW;
-    dim3 g((A.nx * kv + 255) / 256, A.ny);
     if constexpr (std::is_same<T, float>::value && D == 4)
     {
       const int bpr = (A.nx * kv + 127) / 128;
       k_stencil_p<T, D, VW><<<resident_grid(bpr * A.ny, 8), 128, 0, s>>>(
           (const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, mode, bpr, 0);
     }
-    else
-      k_stencil<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv,
-                                            mode);
+    else {
+      const int bpr = (A.nx * kv + 255) / 256;
+      static const int occ = blocks_per_sm(k_stencil<T, D, VW>, 256, 0);
+      k_stencil<T, D, VW><<<resident_grid((size_t)bpr * A.ny, occ), 256, 0, s>>>(
+          (const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, mode, bpr);
+    }
   } else {
-    dim3 g((A.nx * k + 255) / 256, A.ny);
-    k_stencil<T, D, 1><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, k, mode);
+    const int bpr = (A.nx * k + 255) / 256;
+    static const int occ = blocks_per_sm(k_stencil<T, D, 1>, 256, 0);
+    k_stencil<T, D, 1><<<resident_grid((size_t)bpr * A.ny, occ), 256, 0, s>>>(
+        (const T *)A.coef, (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, k, mode, bpr);
   }
 }
 
@@ -276,11 +287,9 @@ __device__ __forceinline__ void laplace_nbr_sum(const Pack<T, VEC> *__restrict__
 // hits).  Per element: three additions and one fused multiply-add (FP64 lanes
 // are the limit of the FP64 form on GB300).
 template <class T, int VEC>
-__global__ void __launch_bounds__(256) k_laplace(const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ y,
-                                                 int nx, int ny, int kv, T diag, int periodic, int mode) {
+__device__ __forceinline__ void laplace_body(const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ y,
+                                             int nx, int ny, int kv, T diag, int periodic, int mode, int j, int t) {
   typedef Pack<T, VEC> V;
-  const int j = blockIdx.y;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nx * kv) return;
   const int i = t / kv, c = t - (t / kv) * kv;
   const V *X = (const V *)x;
@@ -301,18 +310,30 @@ __global__ void __launch_bounds__(256) k_laplace(const T *__restrict__ x, const 
   ((V *)y)[(size_t)s * kv + c] = out;
 }
 
+// Resident grid striding over the units (row j, chunk of 256 threads of the row) in row
+// order: the FP64 apply is bound by the FP64 pipe, which a grid of one block per unit
+// leaves idle between blocks.
+template <class T, int VEC>
+__global__ void __launch_bounds__(256) k_laplace(const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ y,
+                                                 int nx, int ny, int kv, T diag, int periodic, int mode, int bpr) {
+  const int units = bpr * ny;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int j = u / bpr;
+    laplace_body<T, VEC>(x, b, y, nx, ny, kv, diag, periodic, mode, j, (u - j * bpr) * 256 + threadIdx.x);
+  }
+}
+
 // Red-black Gauss-Seidel half-sweep for Example 5.1: x_s = (b_s + sum of neighbours) / diag
 // on the sites of `colour`.  other_zero = 1: the other colour holds zeros (not read).
-// Colour 1 takes the rows from the last (grid.y reversed): consecutive half-sweeps
-// alternate direction, so each starts on the rows the previous one wrote last.
+// Colour 1 takes the rows from the last: consecutive half-sweeps alternate direction, so
+// each starts on the rows the previous one wrote last.
+// The grid strides over the units (row, chunk of 256 threads of the row).
 template <class T, int VEC>
-__global__ void __launch_bounds__(256) k_laplace_rbgs(T *__restrict__ x, const T *__restrict__ b, int nx, int ny,
-                                                      int kv, T dinv, int periodic, int colour, int other_zero) {
+__device__ __forceinline__ void laplace_rbgs_body(T *__restrict__ x, const T *__restrict__ b, int nx, int ny, int kv,
+                                                  T dinv, int periodic, int colour, int other_zero, int j, int t) {
   typedef Pack<T, VEC> V;
-  const int j = colour ? ny - 1 - (int)blockIdx.y : (int)blockIdx.y;
   const int i0 = (j + colour) & 1;
   const int hx = (nx - i0 + 1) >> 1;      // sites of this colour in row j (odd nx too)
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= hx * kv) return;
   const int m = t / kv, c = t - (t / kv) * kv;
   const int i = 2 * m + i0;
@@ -331,6 +352,18 @@ __global__ void __launch_bounds__(256) k_laplace_rbgs(T *__restrict__ x, const T
   X[(size_t)s * kv + c] = acc;
 }
 
+template <class T, int VEC>
+__global__ void __launch_bounds__(256) k_laplace_rbgs(T *__restrict__ x, const T *__restrict__ b, int nx, int ny,
+                                                      int kv, T dinv, int periodic, int colour, int other_zero,
+                                                      int bpr) {
+  const int units = bpr * ny;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int jr = u / bpr;
+    laplace_rbgs_body<T, VEC>(x, b, nx, ny, kv, dinv, periodic, colour, other_zero, colour ? ny - 1 - jr : jr,
+                              (u - jr * bpr) * 256 + threadIdx.x);
+  }
+}
+
 template <class T>
 static int laplace_vec(int k) {
   const int v = 16 / (int)sizeof(T);
@@ -342,11 +375,9 @@ static int laplace_vec(int k) {
 // as (1 - omega) x + (omega / diag) (sum of the neighbours): one multiply, one FMA and
 // the three additions of the sum per element (out must not alias x).
 template <class T, int VEC>
-__global__ void __launch_bounds__(256) k_laplace_jacobi(const T *__restrict__ x, T *__restrict__ out, int nx, int ny,
-                                                        int kv, T keep, T scale, int periodic) {
+__device__ __forceinline__ void laplace_jacobi_body(const T *__restrict__ x, T *__restrict__ out, int nx, int ny,
+                                                    int kv, T keep, T scale, int periodic, int j, int t) {
   typedef Pack<T, VEC> V;
-  const int j = blockIdx.y;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nx * kv) return;
   const int i = t / kv, c = t - (t / kv) * kv;
   const V *X = (const V *)x;
@@ -361,6 +392,16 @@ __global__ void __launch_bounds__(256) k_laplace_jacobi(const T *__restrict__ x,
   ((V *)out)[(size_t)s * kv + c] = o;
 }
 
+template <class T, int VEC>
+__global__ void __launch_bounds__(256) k_laplace_jacobi(const T *__restrict__ x, T *__restrict__ out, int nx, int ny,
+                                                        int kv, T keep, T scale, int periodic, int bpr) {
+  const int units = bpr * ny;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int j = u / bpr;
+    laplace_jacobi_body<T, VEC>(x, out, nx, ny, kv, keep, scale, periodic, j, (u - j * bpr) * 256 + threadIdx.x);
+  }
+}
+
 void launch_laplace_jacobi(const StencilView &A, const void *x, void *out, int k, double omega, cudaStream_t s) {
   if (!A.const_laplace) throw cuda_error{cudaErrorInvalidValue, "laplace_jacobi: constant-coefficient Laplacian only"};
   auto go = [&](auto tag, auto vtag) {
@@ -368,8 +409,10 @@ void launch_laplace_jacobi(const StencilView &A, const void *x, void *out, int k
     constexpr int VEC = decltype(vtag)::value;
     const int kv = k / VEC;
     const T keep = (T)(1.0 - omega), scale = (T)(omega / A.diag);
-    dim3 g((A.nx * kv + 255) / 256, A.ny);
-    k_laplace_jacobi<T, VEC><<<g, 256, 0, s>>>((const T *)x, (T *)out, A.nx, A.ny, kv, keep, scale, A.periodic);
+    const int bpr = (A.nx * kv + 255) / 256;
+    static const int occ = blocks_per_sm(k_laplace_jacobi<T, VEC>, 256, 0);
+    k_laplace_jacobi<T, VEC><<<resident_grid((size_t)bpr * A.ny, occ), 256, 0, s>>>(
+        (const T *)x, (T *)out, A.nx, A.ny, kv, keep, scale, A.periodic, bpr);
   };
   if (A.t == F64) {
     if (laplace_vec<double>(k) == 2) go(double(), std::integral_constant<int, 2>());
@@ -389,8 +432,10 @@ static void launch_laplace(const StencilView &A, const void *x, const void *b, v
     typedef decltype(tag) T;
     constexpr int VEC = decltype(vtag)::value;
     int kv = k / VEC;
-    dim3 g((A.nx * kv + 255) / 256, A.ny);
-    k_laplace<T, VEC><<<g, 256, 0, s>>>((const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, (T)A.diag, A.periodic, mode);
+    const int bpr = (A.nx * kv + 255) / 256;
+    static const int occ = blocks_per_sm(k_laplace<T, VEC>, 256, 0);
+    k_laplace<T, VEC><<<resident_grid((size_t)bpr * A.ny, occ), 256, 0, s>>>(
+        (const T *)x, (const T *)b, (T *)y, A.nx, A.ny, kv, (T)A.diag, A.periodic, mode, bpr);
   };
   if (A.t == F64) {
     if (laplace_vec<double>(k) == 2) go(double(), std::integral_constant<int, 2>());
@@ -410,9 +455,14 @@ static void launch_laplace_rbgs(const StencilView &A, void *x, const void *b, in
     typedef decltype(tag) T;
     constexpr int VEC = decltype(vtag)::value;
     int kv = k / VEC;
-    dim3 g((((A.nx + 1) / 2) * kv + 255) / 256, A.ny);
-    k_laplace_rbgs<T, VEC><<<g, 256, 0, s>>>((T *)x, (const T *)b, A.nx, A.ny, kv, (T)(1.0 / A.diag), A.periodic,
-                                             colour, other_zero);
+    const int bpr = (((A.nx + 1) / 2) * kv + 255) / 256;
+    static const int occ = blocks_per_sm(k_laplace_rbgs<T, VEC>, 256, 0);
+    // FP64: a resident grid (FP64-pipe bound); FP32: one block per unit, measured faster
+    // there (119 against 124 us per sweep on 1024^2 x 64)
+    const unsigned grid = std::is_same<T, double>::value ? resident_grid((size_t)bpr * A.ny, occ)
+                                                         : (unsigned)(bpr * A.ny);
+    k_laplace_rbgs<T, VEC><<<grid, 256, 0, s>>>(
+        (T *)x, (const T *)b, A.nx, A.ny, kv, (T)(1.0 / A.diag), A.periodic, colour, other_zero, bpr);
   };
   if (A.t == F64) {
     if (laplace_vec<double>(k) == 2) go(double(), std::integral_constant<int, 2>());
@@ -521,9 +571,13 @@ __device__ __forceinline__ void rbgs_half_body(const T *__restrict__ coef, const
 template <class T, int D, int VEC>
 __global__ void __launch_bounds__(256) k_rbgs_half(const T *__restrict__ coef, const T *__restrict__ dinv,
                                                    T *__restrict__ x, const T *__restrict__ b, int nx, int ny, int kv,
-                                                   int colour, int other_zero) {
-  rbgs_half_body<T, D, VEC>(coef, dinv, x, b, nx, ny, kv, colour, other_zero, blockIdx.y,
-                            blockIdx.x * blockDim.x + threadIdx.x);
+                                                   int colour, int other_zero, int bpr) {
+  // resident grid striding over the units (row j, chunk of 256 threads of the row)
+  const int units = bpr * ny;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int j = u / bpr;
+    rbgs_half_body<T, D, VEC>(coef, dinv, x, b, nx, ny, kv, colour, other_zero, j, (u - j * bpr) * 256 + threadIdx.x);
+  }
 }
 
 // The same half-sweep in blocks of 128 threads with residency pinned at 8 blocks
@@ -631,20 +685,23 @@ static void rbgs_go(const StencilView &A, void *x, const void *b, int k, int col
   constexpr int VW = rbgs_vec<T, D>::v;
   if (VW > 1 && k % VW == 0) {
     int kv = k / VW;
-    dim3 g(((A.nx / 2) * kv + 255) / 256, A.ny);
     if constexpr (std::is_same<T, float>::value && D == 4)
     {
       const int bpr = ((A.nx / 2) * kv + 127) / 128;
       k_rbgs_half_p<T, D, VW><<<resident_grid(bpr * A.ny, 8), 128, 0, s>>>(
           (const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny, kv, colour, other_zero, bpr);
     }
-    else
-      k_rbgs_half<T, D, VW><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny,
-                                              kv, colour, other_zero);
+    else {
+      const int bpr = ((A.nx / 2) * kv + 255) / 256;
+      static const int occ = blocks_per_sm(k_rbgs_half<T, D, VW>, 256, 0);
+      k_rbgs_half<T, D, VW><<<resident_grid((size_t)bpr * A.ny, occ), 256, 0, s>>>(
+          (const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny, kv, colour, other_zero, bpr);
+    }
   } else {
-    dim3 g(((A.nx / 2) * k + 255) / 256, A.ny);
-    k_rbgs_half<T, D, 1><<<g, 256, 0, s>>>((const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny,
-                                           k, colour, other_zero);
+    const int bpr = ((A.nx / 2) * k + 255) / 256;
+    static const int occ = blocks_per_sm(k_rbgs_half<T, D, 1>, 256, 0);
+    k_rbgs_half<T, D, 1><<<resident_grid((size_t)bpr * A.ny, occ), 256, 0, s>>>(
+        (const T *)A.coef, (const T *)A.dinv, (T *)x, (const T *)b, A.nx, A.ny, k, colour, other_zero, bpr);
   }
 }
 
