@@ -4,8 +4,9 @@ Oracle (test infrastructure only): imported by tests, ``__graft_entry__.smoke``
 and the CPU-baseline leg of ``bench.py``; never by the product path.
 
 The paper has no learned component; this is the project's definition of the
-learned correction used inside the multigrid cycle (parity unpinned by the
-paper: its pins are finite differences and the exact linear special case).
+learned correction used inside the multigrid cycle.  With nothing in the paper
+to pin it to, it is pinned by mathematics alone: its gradients against central
+differences of its loss, and the exact linear special case.
 
 Network: channels c0 -> 16 -> 16 -> c0 with ReLU after the first two layers,
 3x3 taps on the lattice (periodic wrap, or zero padding for Dirichlet
